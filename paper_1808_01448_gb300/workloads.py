@@ -1,0 +1,151 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds input generation only -- particle outlines, parameter sets
+and random smooth fields -- and none of the method's arithmetic.  Both the
+CUDA path and the CPU oracle take what it returns.
+
+Workloads (Sec. "Modeling the adhesion dynamics", Table 1): a channel of
+height H (lattice rows) with a fixed bottom wall and a moving top wall
+(linear shear, Re = u_max H / nu), particles of equal area -- circles and
+ellipses of aspect ratio 2 and 3 with the major axis normal to the wall --
+released at rest a gap y_0 = 3e-3 H above the bottom wall, ligand densities
+0.3..0.9 and spring constants 1 and 2 (lattice units).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+NU_PAPER = 1.0 / 6.0          # Table 1: nu_ref in lattice units (tau = 1)
+Y0_OVER_H = 3.0e-3            # initial gap
+YCR_OVER_H = 6.8e-3           # critical bond length
+KF_OVER_KR0 = 8.5e3           # biochemical affinity k_f / k_r0
+
+
+def ramanujan_perimeter(a: float, b: float) -> float:
+    h = ((a - b) / (a + b)) ** 2
+    return math.pi * (a + b) * (1.0 + 3.0 * h / (10.0 + math.sqrt(4.0 - 3.0 * h)))
+
+
+def n_markers(a: float, b: float) -> int:
+    """One element per lattice spacing of perimeter."""
+    return max(8, int(round(ramanujan_perimeter(a, b))))
+
+
+def circle_polygon(r: float, n: int):
+    t = 2.0 * np.pi * np.arange(n) / n
+    return r * np.cos(t), r * np.sin(t)
+
+
+def ellipse_polygon(ax: float, by: float, n: int, samples: int = 200_000):
+    """Counter-clockwise polygon on the ellipse (x/ax)^2 + (y/by)^2 = 1 with
+    vertices at equal arc length, starting at (ax, 0)."""
+    t = np.linspace(0.0, 2.0 * np.pi, samples + 1)
+    x, y = ax * np.cos(t), by * np.sin(t)
+    seg = np.hypot(np.diff(x), np.diff(y))
+    s = np.concatenate([[0.0], np.cumsum(seg)])
+    targets = s[-1] * np.arange(n) / n
+    tv = np.interp(targets, s, t)
+    return ax * np.cos(tv), by * np.sin(tv)
+
+
+def particle_outline(shape: str, radius_eq: float, n: int | None = None):
+    """Outline of equal area pi * radius_eq^2.  shape: 'circle', 'ar2', 'ar3'
+    (or 'arK' for any aspect ratio K); ellipses have the major axis along the
+    body y axis, so theta = 0 puts it normal to the wall."""
+    if shape == "circle":
+        n = n or n_markers(radius_eq, radius_eq)
+        return circle_polygon(radius_eq, n)
+    k = float(shape[2:])
+    a = radius_eq * math.sqrt(k)          # semi-major (body y)
+    b = radius_eq / math.sqrt(k)          # semi-minor (body x)
+    n = n or n_markers(a, b)
+    return ellipse_polygon(b, a, n)
+
+
+def half_height(shape: str, radius_eq: float) -> float:
+    """Extent of the outline below its centroid at theta = 0."""
+    if shape == "circle":
+        return radius_eq
+    return radius_eq * math.sqrt(float(shape[2:]))
+
+
+def shear_channel(nx: int, ny: int, Re: float, tau: float = 1.0, **extra) -> dict:
+    """Linear-shear channel of the paper: Zou-He walls on rows 0 and ny-1
+    (H = ny - 1), bottom fixed, top moving at u_max = Re nu / H."""
+    nu = (tau - 0.5) / 3.0
+    H = ny - 1
+    cfg = dict(nx=nx, ny=ny, wall_bottom="zou_he", wall_top="zou_he", tau=tau,
+               u_bottom=0.0, u_top=Re * nu / H, y_cr=YCR_OVER_H * H)
+    cfg.update(extra)
+    return cfg
+
+
+def adhesion_particle(cfg: dict, shape: str, radius_eq: float, x: float,
+                      ligand_density: float, sigma: float, gap_over_h: float = Y0_OVER_H,
+                      n: int | None = None) -> dict:
+    """Particle at rest with its lowest point gap_over_h * H above the bottom
+    wall line, major axis normal to the wall."""
+    vx, vy = particle_outline(shape, radius_eq, n)
+    H = cfg["ny"] - 1 if cfg.get("wall_bottom", "zou_he") == "zou_he" else cfg["ny"]
+    y_wall = 0.0 if cfg.get("wall_bottom", "zou_he") == "zou_he" else -0.5
+    yc = y_wall + half_height(shape, radius_eq) + gap_over_h * H
+    return dict(vx=vx, vy=vy, xc=x, yc=yc, theta=0.0, rho_p=1.0,
+                ligand_density=ligand_density, sigma=sigma)
+
+
+def single_ellipse_sweep(nx: int = 1024, ny: int = 256, radius_eq: float = 20.0,
+                         shapes=("ar2", "ar3"), reynolds=(0.01, 0.1, 1.0),
+                         ligand_density: float = 0.7, sigma: float = 2.0,
+                         seed: int = 2):
+    """Single elliptical particle, aspect ratio 2 and 3, equal area to a circle
+    of radius 20, in a 1024 x 256 channel at Re 0.01, 0.1 and 1: one sim per
+    (shape, Re).  Returns a list of (config, [particle]) pairs."""
+    out = []
+    sim_id = 0
+    for shape in shapes:
+        for Re in reynolds:
+            cfg = shear_channel(nx, ny, Re, seed=seed, sim_id=sim_id)
+            p = adhesion_particle(cfg, shape, radius_eq, x=nx / 4.0,
+                                  ligand_density=ligand_density, sigma=sigma)
+            out.append((cfg, [p]))
+            sim_id += 1
+    return out
+
+
+def poiseuille_circle(nx: int = 200, ny: int = 50, radius: float = 10.0, tau: float = 0.8,
+                      Re: float = 0.1, n: int = 63, ligand_density: float = 0.5,
+                      sigma: float = 1.0, seed: int = 1):
+    """Single circle of radius 10 in a 200 x 50 body-force Poiseuille channel
+    with half-way bounce-back walls (H = ny), centre 1.5 radii above the
+    wall, 63 markers.  Re = u_c H / nu with the centre-line speed u_c."""
+    nu = (tau - 0.5) / 3.0
+    H = ny
+    u_c = Re * nu / H
+    g = 8.0 * nu * u_c / (H * H)
+    cfg = dict(nx=nx, ny=ny, wall_bottom="bounce_back", wall_top="bounce_back", tau=tau,
+               gx=g, y_cr=YCR_OVER_H * H, seed=seed, sim_id=0)
+    vx, vy = circle_polygon(radius, n)
+    p = dict(vx=vx, vy=vy, xc=nx / 4.0, yc=-0.5 + 1.5 * radius, theta=0.0, rho_p=1.0,
+             ligand_density=ligand_density, sigma=sigma)
+    return cfg, [p]
+
+
+def smooth_field(rng: np.random.Generator, nx: int, ny: int, amplitude: float,
+                 modes: int = 3) -> np.ndarray:
+    """Random smooth periodic-in-x field: a few low Fourier modes."""
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    out = np.zeros((ny, nx))
+    for _ in range(modes):
+        kx = rng.integers(1, 4)
+        ky = rng.uniform(0.5, 3.0)
+        ph = rng.uniform(0, 2 * np.pi, size=2)
+        out += rng.uniform(-1, 1) * np.cos(2 * np.pi * kx * x / nx + ph[0]) * \
+            np.cos(np.pi * ky * y / ny + ph[1])
+    return amplitude * out / modes
+
+
+def random_noise(rng: np.random.Generator, shape, amplitude: float) -> np.ndarray:
+    return amplitude * rng.uniform(-1.0, 1.0, size=shape)
