@@ -1,0 +1,338 @@
+"""Throughput of the LB-IB-MLS adhesion step on GB300 (one JSON line).
+
+Workload (default): single elliptical particle, aspect ratio 2 and 3
+(equal area to a circle of radius 20), channel 1024 x 256 D2Q9, Re in
+{0.01, 0.1, 1.0}, ligand density 0.7, bond strength 2, FP32 populations
+with FP64 MLS solves and rigid-body update: six independent simulations
+stepped together (one lattice kernel and one particle kernel per step).
+A "step" is one time step of all six.  The working set (6 x 2 x 9.4 MB of
+populations) is larger than L2, so no flush is needed between steps.
+
+Metric: aggregate MLUPS = sum(nx * ny) * steps / time, with the fraction of
+the HBM roofline at 72 B per FP32 lattice update.  Under torchrun every rank
+runs the same six simulations on its own GPU (independent replicas, no
+collective on the data path); value is the total over ranks.
+
+--impl reference times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_UPDATE = {"f32": 72, "f64": 144, "f16": 36, "bf16": 36}
+WORKLOAD = ("single ellipse AR2/AR3 x Re{0.01,0.1,1}, 1024x256 D2Q9, ligand 0.7, sigma 2, "
+            "6 sims batched")
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def lattice_kernel_sha():
+    h = hashlib.sha256()
+    for rel in ("paper_1808_01448_gb300/csrc/lbib_lattice.cu",
+                "paper_1808_01448_gb300/csrc/lbib_internal.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(storage):
+    """DRAM bytes per lattice-kernel launch from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "lattice_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(storage)
+    if not e or e.get("kernel_sha") != lattice_kernel_sha():
+        return None
+    return e.get("bytes_per_launch_full_workload")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lbib_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def build_workload(L, W, storage, stream, allocator):
+    sims = []
+    for cfg, parts in W.single_ellipse_sweep():
+        s = L.Sim(storage=storage, stream=stream, allocator=allocator, **cfg)
+        for p in parts:
+            s.add_particle(**p)
+        sims.append(s)
+    return sims
+
+
+# ---- CPU oracle baseline -----------------------------------------------------
+
+def _oracle_worker(args):
+    idx, steps = args
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    from paper_1808_01448_gb300 import workloads as W
+    cfg, parts = W.single_ellipse_sweep()[idx]
+    s = O.OracleSim(**cfg)
+    for p in parts:
+        s.add_particle(**p)
+    s.step(1)                       # setup and first step outside the clock
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return cfg["nx"] * cfg["ny"] * steps, dt
+
+
+def cpu_baseline(steps_per_sim, nsims=6):
+    """The oracle as it stands (single-threaded C, FP64), one process per
+    simulation of the workload, started with spawn."""
+    from oracle import oracle as O
+    O.build()
+    cores = min(nsims, os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(i, steps_per_sim) for i in range(nsims)])
+    wall = time.perf_counter() - t0
+    updates = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"value": updates / busy / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{nsims} sims x {steps_per_sim} steps of the 1024x256 workload, "
+                      f"{cores} processes (wall {wall:.1f} s incl. setup)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the workload, K timed steps of
+    the six simulations (one worker process each)."""
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    # bounded sample: cap the oracle work so that K steps end within minutes
+    per_step_s = 0.06
+    cap = max(1, int(150.0 / per_step_s))
+    k_run = min(args.steps, cap)
+    base = cpu_baseline(k_run + args.warmup * 0)
+    line = {
+        "metric": "aggregate MLUPS + % HBM roofline (FP32 vs FP16-storage), p50/p99 sim latency",
+        "impl": "reference", "value": base["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 6 * 1024 * 256 / (base["value"] * 1e6) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "storage": "f64 (oracle)"},
+        "cpu_baseline": base,
+        "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    if k_run < args.steps:
+        line["cpu_baseline"]["sample"] += f"; {k_run} of {args.steps} steps timed"
+    print(json.dumps(line))
+    return 0
+
+
+# ---- GPU arm -------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1808_01448_gb300 import lbib
+    from paper_1808_01448_gb300 import workloads as W
+
+    rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
+    local = env_int("LOCAL_RANK", 0)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    # the oracle pool is spawned before any GPU work
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(args.cpu_steps)
+    lbib.lib()
+    stream = torch.cuda.Stream()
+    alloc = lbib.torch_allocator()
+    sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc)
+    nodes = sum(s.nx * s.ny for s in sims)
+    batch = lbib.Batch(sims)
+    batch.set_timing(16)
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+    batch.kernel_times()            # drop samples taken during warm-up
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    batch.step(args.steps)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    kt = batch.kernel_times()
+    for s in sims:
+        s.synchronize()             # raises on a device-side error
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: fresh simulations, the
+    # initial populations uploaded from pinned host memory, K steps in chunks
+    # of 100 with the particle states read back to the host after each chunk
+    e2e = None
+    if rank == 0 or world > 1:
+        e2e_sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc)
+        f0 = torch.empty((9, 256, 1024), dtype=torch.float64).pin_memory()
+        f0.copy_(torch.tensor([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4,
+                              dtype=torch.float64)[:, None, None].expand(9, 256, 1024))
+        f0_np = f0.numpy()
+        eb = lbib.Batch(e2e_sims)
+        barrier()
+        t0 = time.perf_counter()
+        for s in e2e_sims:
+            s.set_populations(f0_np)
+        chunk, done, d2h = 100, 0, 0
+        while done < args.steps:
+            n = min(chunk, args.steps - done)
+            eb.step(n)
+            for s in e2e_sims:
+                s.particles()
+                d2h += 160
+            done += n
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": nodes * args.steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 9 * nodes * 8 / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps}
+        eb.close()
+        for s in e2e_sims:
+            s.close()
+
+    if rank == 0:
+        peak, peak_kind = read_peaks()
+        bpu = BYTES_PER_UPDATE[args.storage]
+        lat_ms = kt["lattice_ms"]
+        achieved = nodes * bpu / (lat_ms * 1e-3) / 1e9 if lat_ms > 0 else None
+        launches = 2 * args.steps + (1 if args.steps % 2 else 0)
+        line = {
+            "metric": "aggregate MLUPS + % HBM roofline (FP32 vs FP16-storage), p50/p99 sim latency",
+            "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": 1024, "ny": 256, "sims": len(sims),
+                       "storage": args.storage, "l2": "working set 226 MB > L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "hbm_roofline_frac_of_step": value * 1e6 * bpu / (peak * 1e9) / world,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None,
+                         "traffic": ncu_traffic(args.storage), "peak_source": peak_kind,
+                         "kernel": "lattice_kernel", "bytes_per_update": bpu,
+                         "lattice_kernel_ms": lat_ms, "particle_kernel_ms": kt["particle_ms"],
+                         "samples": kt["lattice_n"]},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "cpu_baseline": base,
+        }
+        print(json.dumps(line))
+    batch.close()
+    for s in sims:
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=64)
+    ap.add_argument("--impl", default="lbib", choices=["lbib", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--cpu-steps", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

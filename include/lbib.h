@@ -1,0 +1,234 @@
+/*
+ * lbib.h -- C ABI of the GB300 (sm_103a) LB-IB-MLS adhesion solver.
+ *
+ * The library advances 2D lattice Boltzmann channels (D2Q9 BGK, Eq. 1-6 of
+ * Coclite et al., arXiv:1808.01448) coupled to rigid particles through an
+ * immersed boundary with moving-least-squares interpolation and spreading
+ * (Sec. "The combined LB-IB method"), hydrodynamic loads from probes
+ * (Eq. 7-8), stochastic ligand-receptor bonds (Eq. 9-11), a wall force
+ * (Eq. 12) and a second-order rigid-body update (Eq. 13-16).  Every step of
+ * that path runs in the library's CUDA kernels.
+ *
+ * Conventions shared by all calls:
+ *  - Every call returns an lbib_status and never aborts; on failure
+ *    lbib_last_error() gives a message (thread-local, valid until the next
+ *    failing call on the same thread).
+ *  - Structs are copied at the call; the caller keeps every pointer it
+ *    passes.  Array arguments named *_host are host memory.
+ *  - The library owns all device memory of a simulation (allocated in
+ *    lbib_create / lbib_add_particle / first step, freed in lbib_destroy),
+ *    through the caller's allocator hook when one is given.
+ *  - Stepping is asynchronous on the configured CUDA stream; read calls
+ *    synchronise that stream.  A device-side error (a non-finite state, a
+ *    bounded wait that ran out) is reported by the next call.
+ *  - A handle is not thread-safe; different handles are independent.
+ *  - Lattice units: dx = dt = 1, c_s^2 = 1/3, nu = (tau - 1/2) / 3.
+ *  - Node arrays are row-major [ny][nx]; populations [9][ny][nx] with the
+ *    D2Q9 order e_0 = (0,0), e_1..4 = (1,0), (0,1), (-1,0), (0,-1),
+ *    e_5..8 = (1,1), (-1,1), (-1,-1), (1,-1) (Eq. 3).
+ */
+#ifndef LBIB_H
+#define LBIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbib_status {
+    LBIB_OK = 0,
+    LBIB_E_ARG = 1,          /* invalid argument; nothing was changed */
+    LBIB_E_OOM = 2,          /* device or host allocation failed */
+    LBIB_E_CUDA = 3,         /* a CUDA runtime call failed */
+    LBIB_E_STATE = 4,        /* call not allowed in the handle's state */
+    LBIB_E_UNSTABLE = 5,     /* the state became non-finite */
+    LBIB_E_TIMEOUT = 6,      /* a bounded device wait ran out */
+    LBIB_E_UNSUPPORTED = 7   /* feature not built / not supported by device */
+} lbib_status;
+
+/* Wall kinds for the bottom (y = 0) and top (y = ny - 1) rows.
+ * ZOU_HE: known-velocity wall nodes on rows 0 and ny-1 (the paper's walls,
+ *         Sec. "The combined LB-IB method", ref. [40]).
+ * BOUNCE_BACK: half-way bounce-back, wall lines at y = -1/2 and ny - 1/2,
+ *         with the moving-wall correction 6 w_i (e_i . u_w).
+ * PERIODIC: both walls periodic (set on both or neither). */
+typedef enum lbib_wall { LBIB_WALL_ZOU_HE = 0, LBIB_WALL_BOUNCE_BACK = 1,
+                         LBIB_WALL_PERIODIC = 2 } lbib_wall;
+
+/* Storage of the populations in device memory.  Collision arithmetic is
+ * FP32 for F32/F16/BF16 and FP64 for F64.  Populations are stored as
+ * deviations f_i - w_i; F16 stores them times a power-of-two scale. */
+typedef enum lbib_storage { LBIB_STORE_F32 = 0, LBIB_STORE_F64 = 1,
+                            LBIB_STORE_F16 = 2, LBIB_STORE_BF16 = 3 } lbib_storage;
+
+/* Optional device allocator hook (e.g. a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` bytes usable on `stream`,
+ * or NULL; free releases it.  When NULL the library uses cudaMalloc. */
+typedef void *(*lbib_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*lbib_free_fn)(void *ptr, void *stream, void *ctx);
+
+/* Channel and model parameters (Sec. "Modeling the adhesion dynamics",
+ * Table 1).  The physical part mirrors the problem statement:
+ *  nx, ny            lattice size (nx >= 8, ny >= 4; nx * ny < 2^31)
+ *  wall_bottom/top   lbib_wall
+ *  tau               BGK relaxation time (> 1/2), Eq. 1
+ *  u_bottom, u_top   tangential wall velocities (x), e.g. u_top = u_max
+ *  gx, gy            uniform body-force density (Poiseuille drive, Eq. 4)
+ *  k_f, k_r0, kBT    forward / reverse rates per step and thermal energy,
+ *                    Eq. 10-11
+ *  sigma_star_ratio  sigma* / sigma (0.5: slip bonds), Eq. 11
+ *  y_cr, y_eq_ratio  critical bond length and y_cr,eq / y_cr, Eq. 9
+ *  hamaker, eps_min  Eq. 12 constant H_k and the lower clamp of the gap
+ *  receptor_bottom/top receptor density on each wall (1 = fully covered)
+ *  seed, sim_id      key of the counter-based bond draws
+ * Device-side settings:
+ *  storage           lbib_storage
+ *  f16_scale         F16 only: power-of-two scale of f - w (0 = automatic)
+ *  cuda_stream       cudaStream_t to run on (NULL = the legacy default)
+ *  alloc, free, alloc_ctx   optional allocator hook */
+typedef struct lbib_config {
+    int32_t nx, ny;
+    int32_t wall_bottom, wall_top;
+    double tau;
+    double u_bottom, u_top;
+    double gx, gy;
+    double k_f, k_r0, kBT;
+    double sigma_star_ratio, y_cr, y_eq_ratio;
+    double hamaker, eps_min;
+    double receptor_bottom, receptor_top;
+    uint64_t seed, sim_id;
+    int32_t storage;
+    int32_t reserved0;
+    double f16_scale;
+    void *cuda_stream;
+    lbib_alloc_fn alloc;
+    lbib_free_fn free;
+    void *alloc_ctx;
+} lbib_config;
+
+/* A rigid particle (Sec. "Pressure and viscous stresses"): a closed polygon
+ * of nl linear elements in its body frame (counter-clockwise, centroid at
+ * the origin).  When vx/vy are NULL the outline is generated: shape 0 is a
+ * circle of radius a, shape 1 an ellipse with semi-axes a (body x) and b
+ * (body y), with n_vertices vertices (0 = one per unit of perimeter) at
+ * equal arc length.  Pose (xc, yc, theta); density rho_p (mass = rho_p *
+ * area); ligand_density is the fraction of elements carrying a ligand,
+ * spread evenly; sigma is the spring constant of Eq. 9.  fixed != 0 holds
+ * the pose (loads and bonds are still computed).  The outline must fit the
+ * on-chip force tile: max radius <= LBIB_MAX_PARTICLE_RADIUS and
+ * 3 <= nl <= LBIB_MAX_MARKERS. */
+#define LBIB_MAX_MARKERS 1024
+#define LBIB_MAX_PARTICLE_RADIUS 60.0
+#define LBIB_MAX_PARTICLES_PER_SIM 16
+
+typedef struct lbib_particle {
+    int32_t n_vertices;
+    int32_t fixed;
+    const double *vx, *vy;
+    int32_t shape;
+    int32_t reserved0;
+    double a, b;
+    double xc, yc, theta;
+    double rho_p;
+    double ligand_density;
+    double sigma;
+} lbib_particle;
+
+/* Particle state after the last completed step: pose and velocities, the
+ * loads of that step (hydrodynamic Eq. 7-8, bond Eq. 9, wall Eq. 12), mass
+ * properties, and counts of elements, ligands, probing and bonded ligands. */
+typedef struct lbib_particle_state {
+    double xc, yc, theta, u, v, omega;
+    double Fh[2], Mh;
+    double Fb[2], Mb;
+    double Fw[2];
+    double area, mass, inertia, r_eq;
+    int32_t nl, n_ligands, n_probing, n_bonded;
+} lbib_particle_state;
+
+typedef struct lbib_state {
+    int64_t step;          /* completed steps */
+    int32_t n_particles;
+    int32_t storage;
+    int32_t nx, ny;
+} lbib_state;
+
+typedef struct lbib_sim lbib_sim;
+typedef struct lbib_batch lbib_batch;
+
+/* Create a simulation; populations start at f = f^eq(rho = 1, u = 0).
+ * Errors: E_ARG (invalid config), E_OOM, E_CUDA. */
+lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out);
+
+/* Free all memory of the handle (synchronises its stream).  NULL is a no-op. */
+lbib_status lbib_destroy(lbib_sim *sim);
+
+/* Add a particle before the first step; *pid receives its index.
+ * Errors: E_ARG (bad outline, too large, too many), E_STATE (already
+ * stepped), E_OOM. */
+lbib_status lbib_add_particle(lbib_sim *sim, const lbib_particle *p, int32_t *pid);
+
+/* Receptor density on a wall (0 bottom, 1 top), before the first step.
+ * Bonds form only to walls with density > 0; the forward rate of Eq. 10 is
+ * scaled by the density.  Errors: E_ARG, E_STATE. */
+lbib_status lbib_set_receptors(lbib_sim *sim, int32_t wall, double density);
+
+/* Set the post-collision populations f*_i of "step -1" ([9][ny][nx], host,
+ * full f, not deviations) before the first step.  Errors: E_STATE, E_CUDA. */
+lbib_status lbib_set_populations(lbib_sim *sim, const double *f_post_host);
+
+/* Enqueue nsteps time steps (weak coupling, Sec. "Fluid-structure
+ * interaction strategy"): collide + stream, loads, bonds, wall force, rigid
+ * update, IB forcing.  Asynchronous; nsteps == 0 is a no-op.
+ * Errors: E_ARG (nsteps < 0), E_CUDA, E_UNSTABLE (reported late). */
+lbib_status lbib_step(lbib_sim *sim, int64_t nsteps);
+
+/* Batched stepping: all simulations of a batch advance together, one
+ * lattice kernel and one particle kernel per step over all of them, on the
+ * first simulation's stream.  All members must share storage and device.
+ * A simulation may be stepped alone or in a batch, not both concurrently. */
+lbib_status lbib_batch_create(lbib_sim *const *sims, int32_t n, lbib_batch **out);
+lbib_status lbib_batch_step(lbib_batch *b, int64_t nsteps);
+lbib_status lbib_batch_destroy(lbib_batch *b);
+/* Kernel timing with CUDA events: when nsamples > 0, later batch steps
+ * record the duration of sampled lattice and particle kernels on the batch
+ * stream.  lbib_batch_kernel_times returns the mean duration (ms) of the
+ * samples taken since the last call, [0] lattice, [1] particle, and their
+ * counts (it synchronises the stream). */
+lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples);
+lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count);
+
+/* Wait for all enqueued work of the handle; reports deferred device errors. */
+lbib_status lbib_synchronize(lbib_sim *sim);
+
+/* Read the state (synchronises).  Any output may be NULL.  Fields are the
+ * density and the velocity u = (sum_i f_i e_i + (g + f_ib)/2) / rho of the
+ * current step (Eq. 5-6), each [ny][nx] host doubles; n_nodes must be
+ * nx * ny when a field pointer is given.  parts receives up to n_parts
+ * particle states. */
+lbib_status lbib_read_state(lbib_sim *sim, lbib_state *st, lbib_particle_state *parts,
+                            int32_t n_parts, double *rho_host, double *ux_host,
+                            double *uy_host, size_t n_nodes);
+
+/* Post-collision populations of the last step (full f, [9][ny][nx]). */
+lbib_status lbib_read_populations(lbib_sim *sim, double *f_post_host);
+
+/* Bond state of a particle: bond[l] in {0, 1} and the anchor x of each
+ * element's bond (n must equal the particle's element count). */
+lbib_status lbib_read_bonds(lbib_sim *sim, int32_t pid, uint8_t *bond_host,
+                            double *anchor_x_host, int32_t n);
+
+/* IB force density of the current step on the lattice ([ny][nx] each). */
+lbib_status lbib_read_ib_force(lbib_sim *sim, double *fx_host, double *fy_host);
+
+const char *lbib_last_error(void);
+
+/* Library build information ("lbib <version> sm_103a ..."). */
+const char *lbib_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -462,7 +462,9 @@ void or_loads(const or_config *c, const double *rho, const double *ux, const dou
     for (int l = 0; l < nv; ++l) {
         double qx = mx[l] + 1.2 * nxo[l], qy = my[l] + 1.2 * nyo[l];
         double r, drx, dry, a, dudx, dudy, b, dvdx, dvdy;
-        or_mls_fit(c, rho, qx, qy, &r, &drx, &dry);
+        /* a probe whose support cannot carry a linear fit (inside a wall)
+         * contributes no traction */
+        if (or_mls_fit(c, rho, qx, qy, &r, &drx, &dry) == 0) continue;
         or_mls_fit(c, ux, qx, qy, &a, &dudx, &dudy);
         or_mls_fit(c, uy, qx, qy, &b, &dvdx, &dvdy);
         double p = (r - 1.0) / 3.0;

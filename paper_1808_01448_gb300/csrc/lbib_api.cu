@@ -1,0 +1,788 @@
+// lbib_api.cu -- host implementation of the C ABI declared in include/lbib.h.
+//
+// Owns device memory (through the caller's allocator hook or cudaMalloc),
+// builds particle geometry, marker colouring and force tiles, and drives the
+// two kernels of a time step (lattice, then particles) for a batch of
+// simulations, replaying CUDA graphs of GRAPH_STEPS steps.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbib_internal.cuh"
+
+using namespace lbib;
+
+namespace {
+
+constexpr int GRAPH_STEPS = 32;   // steps per captured graph (even: parity-neutral)
+constexpr int SMEM_LIMIT = 227 * 1024;
+
+thread_local std::string g_err;
+
+lbib_status fail(lbib_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+lbib_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(LBIB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);             \
+    } while (0)
+
+size_t compute_size(int kind) { return kind == ST_F64 ? 8 : 4; }
+size_t storage_size(int kind) {
+    switch (kind) {
+        case ST_F32: return 4;
+        case ST_F64: return 8;
+        default: return 2;
+    }
+}
+
+struct HostParticle {
+    std::vector<double> vx, vy;
+    int fixed = 0;
+    double xc = 0, yc = 0, th = 0, rho_p = 1, lig = 0, sigma = 0;
+    int nl = 0, n_ligands = 0, T = 0, ncolors = 0;
+    double area = 0, mass = 0, inertia = 0, r_eq = 0, rmax = 0;
+    std::vector<double> mbx, mby, nbx, nby, S;
+    std::vector<uint8_t> ligand;
+    std::vector<int> color_order, color_off;
+    ParticleDev *d_part = nullptr;   // device struct
+    void *d_block = nullptr;         // geometry, bonds, tile
+};
+
+}  // namespace
+
+struct lbib_sim {
+    lbib_config cfg{};
+    int kind = ST_F32;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    size_t N = 0;
+    void *pop[2] = {nullptr, nullptr};
+    int cur = 0;                  // host mirror of *d_cur
+    int64_t step = 0;             // host count of enqueued steps
+    int *d_cur = nullptr;         // small device block: cur, err, step
+    int *d_err = nullptr;
+    long long *d_step = nullptr;
+    void *d_small = nullptr;
+    double *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    float scale = 1.f;
+    bool primed = false;
+    std::vector<HostParticle> parts;
+    lbib_batch *self = nullptr;
+};
+
+struct lbib_batch {
+    std::vector<lbib_sim *> sims;
+    int kind = ST_F32;
+    cudaStream_t stream = nullptr;
+    void *d_block = nullptr;
+    int **d_curs = nullptr;             // device table of the members' parity words
+    BatchDev bd{};
+    int smem = 0;
+    cudaGraphExec_t graph = nullptr;
+    // timing: one graph exec per sample slot, each with events around the
+    // first step's kernels
+    int nsamples = 0;
+    std::vector<cudaGraphExec_t> tgraphs;
+    std::vector<cudaEvent_t> ev;        // 4 per slot: lb0, lb1, p0, p1
+    std::vector<int> replayed;          // slot replayed since the last read
+    int next_slot = 0;
+};
+
+namespace {
+
+void *dalloc(const lbib_config &c, cudaStream_t st, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (c.alloc) return c.alloc(bytes, (void *)st, c.alloc_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dfree(const lbib_config &c, cudaStream_t st, void *p) {
+    if (!p) return;
+    if (c.free) c.free(p, (void *)st, c.alloc_ctx);
+    else cudaFree(p);
+}
+
+SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
+    SimDev d{};
+    const lbib_config &c = s->cfg;
+    d.nx = c.nx; d.ny = c.ny; d.wall_b = c.wall_bottom; d.wall_t = c.wall_top;
+    d.p0 = p0; d.np = (int)s->parts.size();
+    d.tile0 = tile0;
+    d.ntiles = (int)((s->N + 255) / 256);
+    d.tau = c.tau; d.u_b = c.u_bottom; d.u_t = c.u_top; d.gx = c.gx; d.gy = c.gy;
+    d.k_f = c.k_f; d.k_r0 = c.k_r0; d.kBT = c.kBT; d.sigma_star_ratio = c.sigma_star_ratio;
+    d.y_cr = c.y_cr; d.y_eq_ratio = c.y_eq_ratio; d.hamaker = c.hamaker; d.eps_min = c.eps_min;
+    d.rec_b = c.receptor_bottom; d.rec_t = c.receptor_top;
+    d.seed = c.seed; d.sim_id = c.sim_id;
+    d.scale = s->scale; d.inv_scale = 1.f / s->scale;
+    d.pop[0] = s->pop[0]; d.pop[1] = s->pop[1];
+    d.cur = s->d_cur; d.step = s->d_step; d.err = s->d_err;
+    return d;
+}
+
+// Polygon elements, mass properties, ligands and marker colouring.  Two
+// markers of one colour are at least 4 sqrt 2 apart, so their 4 x 4 supports
+// are disjoint in some axis for every rotation of the body.
+void build_geometry(HostParticle &p) {
+    const int n = (int)p.vx.size();
+    p.nl = n;
+    p.mbx.resize(n); p.mby.resize(n); p.nbx.resize(n); p.nby.resize(n); p.S.resize(n);
+    p.ligand.assign(n, 0);
+    double A = 0, J = 0, rmax = 0;
+    for (int l = 0; l < n; ++l) {
+        const int m = (l + 1) % n;
+        const double ax = p.vx[l], ay = p.vy[l], bx = p.vx[m], by = p.vy[m];
+        const double dx = bx - ax, dy = by - ay, len = sqrt(dx * dx + dy * dy);
+        p.mbx[l] = 0.5 * (ax + bx);
+        p.mby[l] = 0.5 * (ay + by);
+        p.S[l] = len;
+        p.nbx[l] = dy / len;
+        p.nby[l] = -dx / len;
+        const double cr = ax * by - bx * ay;
+        A += 0.5 * cr;
+        J += cr * (ax * ax + ax * bx + bx * bx + ay * ay + ay * by + by * by) / 12.0;
+        rmax = std::max(rmax, sqrt(ax * ax + ay * ay));
+    }
+    p.area = A;
+    p.mass = p.rho_p * A;
+    p.inertia = p.rho_p * J;
+    p.r_eq = sqrt(A / M_PI);
+    p.rmax = rmax;
+    p.T = 2 * (int)ceil(rmax) + 8;
+    p.n_ligands = 0;
+    for (int l = 0; l < n; ++l) {
+        p.ligand[l] = floor((double)(l + 1) * p.lig) > floor((double)l * p.lig);
+        p.n_ligands += p.ligand[l];
+    }
+    const double D2 = 32.0 * (1.0 + 1e-9);
+    std::vector<int> color(n, -1);
+    int nc = 0;
+    for (int l = 0; l < n; ++l) {
+        std::vector<char> used(nc + 1, 0);
+        for (int q = 0; q < l; ++q) {
+            const double dx = p.mbx[l] - p.mbx[q], dy = p.mby[l] - p.mby[q];
+            if (dx * dx + dy * dy < D2) used[color[q]] = 1;
+        }
+        int c = 0;
+        while (c < nc && used[c]) ++c;
+        color[l] = c;
+        if (c == nc) ++nc;
+    }
+    p.ncolors = nc;
+    p.color_off.assign(nc + 1, 0);
+    for (int l = 0; l < n; ++l) p.color_off[color[l] + 1]++;
+    for (int c = 0; c < nc; ++c) p.color_off[c + 1] += p.color_off[c];
+    p.color_order.resize(n);
+    std::vector<int> fill(p.color_off.begin(), p.color_off.end() - 1);
+    for (int l = 0; l < n; ++l) p.color_order[fill[color[l]]++] = l;
+}
+
+void ellipse_outline(double ax, double by, int n, std::vector<double> &vx,
+                     std::vector<double> &vy) {
+    const int M = 20000;
+    std::vector<double> s(M + 1, 0.0);
+    for (int i = 1; i <= M; ++i) {
+        const double t0 = 2 * M_PI * (i - 1) / M, t1 = 2 * M_PI * i / M;
+        const double dx = ax * (cos(t1) - cos(t0)), dy = by * (sin(t1) - sin(t0));
+        s[i] = s[i - 1] + sqrt(dx * dx + dy * dy);
+    }
+    vx.resize(n);
+    vy.resize(n);
+    int i = 0;
+    for (int k = 0; k < n; ++k) {
+        const double target = s[M] * k / n;
+        while (i < M && s[i + 1] < target) ++i;
+        const double f = (s[i + 1] > s[i]) ? (target - s[i]) / (s[i + 1] - s[i]) : 0.0;
+        const double t = 2 * M_PI * (i + f) / M;
+        vx[k] = ax * cos(t);
+        vy[k] = by * sin(t);
+    }
+}
+
+lbib_status check_err_word(lbib_sim *s) {
+    int err = 0;
+    CK(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & ERR_UNSTABLE)
+        return fail(LBIB_E_UNSTABLE, "simulation %llu became unstable (non-finite or |u| >= 0.5)",
+                    (unsigned long long)s->cfg.sim_id);
+    return LBIB_OK;
+}
+
+lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
+    const int n = p.nl;
+    const size_t rsz = compute_size(s->kind);
+    const size_t bytes = sizeof(ParticleDev) + 5 * n * 8 + n + 4 * n + 4 * (p.ncolors + 1) + n +
+                         8 * n + n + 2 * rsz * p.T * p.T + 16 * 16;
+    unsigned char *blk = (unsigned char *)dalloc(s->cfg, s->stream, bytes);
+    if (!blk) return fail(LBIB_E_OOM, "device allocation of %zu bytes for a particle failed", bytes);
+    p.d_block = blk;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        unsigned char *q = blk + off;
+        off += (b + 15) & ~size_t(15);
+        return q;
+    };
+    ParticleDev h{};
+    unsigned char *pd = take(sizeof(ParticleDev));
+    double *mbx = (double *)take(8 * n), *mby = (double *)take(8 * n);
+    double *nbx = (double *)take(8 * n), *nby = (double *)take(8 * n), *S = (double *)take(8 * n);
+    uint8_t *lig = take(n);
+    int *co = (int *)take(4 * n), *coff = (int *)take(4 * (p.ncolors + 1));
+    uint8_t *bond = take(n);
+    double *ax = (double *)take(8 * n);
+    int8_t *aw = (int8_t *)take(n);
+    void *tile = take(2 * rsz * p.T * p.T);
+    h.xc = h.xc1 = p.xc; h.yc = h.yc1 = p.yc; h.th = h.th1 = p.th;
+    h.mass = p.mass; h.inertia = p.inertia; h.r_eq = p.r_eq; h.sigma = p.sigma;
+    h.nl = n; h.n_ligands = p.n_ligands; h.fixed = p.fixed; h.T = p.T; h.ncolors = p.ncolors;
+    h.tile_ox = 0; h.tile_oy = -(1 << 28);   // no tile until the first IB pass
+    h.mbx = mbx; h.mby = mby; h.nbx = nbx; h.nby = nby; h.S = S;
+    h.ligand = lig; h.color_order = co; h.color_off = coff;
+    h.bond = bond; h.anchor_x = ax; h.anchor_wall = aw; h.tile = tile;
+    p.d_part = (ParticleDev *)pd;
+    cudaStream_t st = s->stream;
+    CK(cudaMemcpyAsync(pd, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mbx, p.mbx.data(), 8 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mby, p.mby.data(), 8 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(nbx, p.nbx.data(), 8 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(nby, p.nby.data(), 8 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S, p.S.data(), 8 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lig, p.ligand.data(), n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(co, p.color_order.data(), 4 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(coff, p.color_off.data(), 4 * (p.ncolors + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(bond, 0, n, st));
+    CK(cudaMemsetAsync(ax, 0, 8 * n, st));
+    CK(cudaMemsetAsync(aw, 0, n, st));
+    CK(cudaMemsetAsync(tile, 0, 2 * rsz * p.T * p.T, st));
+    CK(cudaStreamSynchronize(st));   // host vectors may be released afterwards
+    return LBIB_OK;
+}
+
+void free_batch(lbib_batch *b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto g : b->tgraphs)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto e : b->ev) cudaEventDestroy(e);
+    if (b->d_block && !b->sims.empty())
+        dfree(b->sims[0]->cfg, b->stream, b->d_block);
+    delete b;
+}
+
+lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
+    if (!sims || n <= 0 || !out) return fail(LBIB_E_ARG, "batch needs at least one simulation");
+    lbib_batch *b = new (std::nothrow) lbib_batch();
+    if (!b) return fail(LBIB_E_OOM, "host allocation failed");
+    b->kind = sims[0]->kind;
+    b->stream = sims[0]->stream;
+    int nparts = 0, tiles = 0, smem = 0;
+    for (int i = 0; i < n; ++i) {
+        lbib_sim *s = sims[i];
+        if (!s) { delete b; return fail(LBIB_E_ARG, "null simulation in batch"); }
+        if (s->kind != b->kind) { delete b; return fail(LBIB_E_ARG, "batch members must share storage"); }
+        if (s->device != sims[0]->device) { delete b; return fail(LBIB_E_ARG, "batch members must share the device"); }
+        for (int j = 0; j < i; ++j)
+            if (sims[j] == s) { delete b; return fail(LBIB_E_ARG, "simulation listed twice in batch"); }
+        b->sims.push_back(s);
+        nparts += (int)s->parts.size();
+        tiles += (int)((s->N + 255) / 256);
+        for (auto &p : s->parts) smem = std::max(smem, particle_smem_bytes(b->kind, p.T, p.nl));
+    }
+    const size_t bytes = sizeof(SimDev) * n + sizeof(ParticleDev *) * (nparts + 1) +
+                         sizeof(int) * (nparts + 1) + sizeof(int *) * n + 64;
+    unsigned char *blk = (unsigned char *)dalloc(sims[0]->cfg, b->stream, bytes);
+    if (!blk) { delete b; return fail(LBIB_E_OOM, "device allocation for the batch failed"); }
+    b->d_block = blk;
+    size_t off = 0;
+    auto take = [&](size_t sz) {
+        unsigned char *q = blk + off;
+        off += (sz + 15) & ~size_t(15);
+        return q;
+    };
+    SimDev *dsims = (SimDev *)take(sizeof(SimDev) * n);
+    ParticleDev **dparts = (ParticleDev **)take(sizeof(ParticleDev *) * (nparts + 1));
+    int *dpsim = (int *)take(sizeof(int) * (nparts + 1));
+    int **dcurs = (int **)take(sizeof(int *) * n);
+    std::vector<SimDev> hs;
+    std::vector<ParticleDev *> hp;
+    std::vector<int> hps;
+    std::vector<int *> hc;
+    int tile0 = 0;
+    for (int i = 0; i < n; ++i) {
+        lbib_sim *s = sims[i];
+        hs.push_back(make_simdev(s, (int)hp.size(), tile0));
+        tile0 += hs.back().ntiles;
+        for (auto &p : s->parts) {
+            hp.push_back(p.d_part);
+            hps.push_back(i);
+        }
+        hc.push_back(s->d_cur);
+    }
+    hp.push_back(nullptr);
+    hps.push_back(0);
+    cudaStream_t st = b->stream;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dsims, hs.data(), sizeof(SimDev) * n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(dparts, hp.data(), sizeof(ParticleDev *) * hp.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(dpsim, hps.data(), sizeof(int) * hps.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(dcurs, hc.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaStreamSynchronize(st))) {
+        free_batch(b);
+        return cuda_fail(e, "batch upload");
+    }
+    if (smem > SMEM_LIMIT) {
+        free_batch(b);
+        return fail(LBIB_E_ARG, "particle kernel needs %d bytes of shared memory", smem);
+    }
+    if (nparts > 0) {
+        // allow the largest tile any batch may use (the attribute is per kernel)
+        if ((e = particle_kernel_setup(b->kind, SMEM_LIMIT)) != cudaSuccess) {
+            free_batch(b);
+            return cuda_fail(e, "particle kernel setup");
+        }
+    }
+    b->smem = smem;
+    b->bd.sims = dsims;
+    b->bd.parts = dparts;
+    b->bd.part_sim = dpsim;
+    b->bd.nsims = n;
+    b->bd.nparts = nparts;
+    b->bd.total_tiles = tile0;
+    b->d_curs = dcurs;
+    *out = b;
+    return LBIB_OK;
+}
+
+lbib_status ensure_self(lbib_sim *s) {
+    if (s->self) return LBIB_OK;
+    lbib_sim *one[1] = {s};
+    return make_batch(one, 1, &s->self);
+}
+
+// IB forcing of step 0 at the initial pose (the particle kernel in init mode).
+lbib_status prime(lbib_sim *s, cudaStream_t st) {
+    if (s->primed) return LBIB_OK;
+    lbib_status r = ensure_self(s);
+    if (r != LBIB_OK) return r;
+    if (!s->parts.empty()) {
+        cudaError_t e = launch_particles(s->kind, s->self->bd, 0, 1, s->self->smem, st);
+        if (e != cudaSuccess) return cuda_fail(e, "particle kernel (init)");
+    }
+    s->primed = true;
+    return LBIB_OK;
+}
+
+cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nsteps; ++k) {
+        const int f = k & 1;
+        if (ev && k == 0 && (e = cudaEventRecord(ev[0], b->stream))) return e;
+        if ((e = launch_lattice(b->kind, b->bd, f, b->stream))) return e;
+        if (ev && k == 0 && (e = cudaEventRecord(ev[1], b->stream))) return e;
+        if (ev && k == 0 && (e = cudaEventRecord(ev[2], b->stream))) return e;
+        if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->stream))) return e;
+        if (ev && k == 0 && (e = cudaEventRecord(ev[3], b->stream))) return e;
+    }
+    return e;
+}
+
+lbib_status capture(lbib_batch *b, cudaEvent_t *ev, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_steps(b, GRAPH_STEPS, ev);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e, "graph capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return LBIB_OK;
+}
+
+lbib_status batch_step_impl(lbib_batch *b, int64_t n) {
+    if (n < 0) return fail(LBIB_E_ARG, "nsteps must be >= 0");
+    if (n == 0) return LBIB_OK;
+    for (lbib_sim *s : b->sims) {
+        lbib_status r = prime(s, b->stream);
+        if (r != LBIB_OK) return r;
+    }
+    const int64_t full = n / GRAPH_STEPS;
+    const int rem = (int)(n % GRAPH_STEPS);
+    if (full > 0 && !b->graph) {
+        lbib_status r = capture(b, nullptr, &b->graph);
+        if (r != LBIB_OK) return r;
+    }
+    for (int64_t i = 0; i < full; ++i) {
+        cudaGraphExec_t g = b->graph;
+        if (b->nsamples > 0) {
+            // sampled replays carry event records around their first step
+            const int slot = b->next_slot;
+            b->next_slot = (slot + 1) % b->nsamples;
+            g = b->tgraphs[slot];
+            b->replayed[slot] = 1;
+        }
+        CK(cudaGraphLaunch(g, b->stream));
+    }
+    if (rem > 0) {
+        cudaError_t e = enqueue_steps(b, rem, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if (rem & 1) {
+            e = launch_flip(b->d_curs, (int)b->sims.size(), b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "parity flip");
+        }
+    }
+    for (lbib_sim *s : b->sims) {
+        s->step += n;
+        s->cur ^= (int)(n & 1);
+    }
+    return LBIB_OK;
+}
+
+lbib_status ensure_scratch(lbib_sim *s, size_t bytes) {
+    if (s->scratch_bytes >= bytes) return LBIB_OK;
+    dfree(s->cfg, s->stream, s->d_scratch);
+    s->d_scratch = (double *)dalloc(s->cfg, s->stream, bytes);
+    s->scratch_bytes = s->d_scratch ? bytes : 0;
+    if (!s->d_scratch) return fail(LBIB_E_OOM, "device scratch of %zu bytes", bytes);
+    return LBIB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbib_last_error(void) { return g_err.c_str(); }
+
+const char *lbib_version(void) { return "lbib 0.1 sm_103a (D2Q9 LB-IB-MLS, Philox4x64-10)"; }
+
+lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out) {
+    if (!cfg || !out) return fail(LBIB_E_ARG, "null argument");
+    *out = nullptr;
+    const lbib_config &c = *cfg;
+    if (c.nx < 8 || c.ny < 4 || (int64_t)c.nx * c.ny >= (1ll << 31) / 9)
+        return fail(LBIB_E_ARG, "lattice %d x %d outside 8 x 4 .. 2^31/9 nodes", c.nx, c.ny);
+    if (!(c.tau > 0.5) || !isfinite(c.tau)) return fail(LBIB_E_ARG, "tau must be > 1/2");
+    for (int w : {c.wall_bottom, c.wall_top})
+        if (w < 0 || w > 2) return fail(LBIB_E_ARG, "unknown wall kind %d", w);
+    if ((c.wall_bottom == LBIB_WALL_PERIODIC) != (c.wall_top == LBIB_WALL_PERIODIC))
+        return fail(LBIB_E_ARG, "periodic walls must be set on both sides");
+    if (c.storage < 0 || c.storage > 3) return fail(LBIB_E_ARG, "unknown storage %d", c.storage);
+    if (!(c.kBT > 0) || c.k_f < 0 || c.k_r0 < 0 || c.y_cr < 0 || c.eps_min <= 0 ||
+        c.receptor_bottom < 0 || c.receptor_top < 0)
+        return fail(LBIB_E_ARG, "bond / wall-force parameters out of range");
+    lbib_sim *s = new (std::nothrow) lbib_sim();
+    if (!s) return fail(LBIB_E_OOM, "host allocation failed");
+    s->cfg = c;
+    s->kind = c.storage;
+    s->N = (size_t)c.nx * c.ny;
+    cudaGetDevice(&s->device);
+    if (c.cuda_stream) {
+        s->stream = (cudaStream_t)c.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return cuda_fail(cudaGetLastError(), "cudaStreamCreate");
+        }
+        s->own_stream = true;
+    }
+    if (s->kind == ST_F16) {
+        double sc = c.f16_scale;
+        if (sc <= 0) {
+            // keep |f - w| of a flow with speeds up to u_ref well inside the
+            // normal range: scale ~ 2^floor(log2(64 / u_ref))
+            const double uref = std::max({fabs(c.u_top), fabs(c.u_bottom),
+                                          1e3 * std::max(fabs(c.gx), fabs(c.gy)), 1e-6});
+            sc = exp2(floor(log2(64.0 / uref)));
+            sc = std::min(sc, 1.0 * (1 << 24));
+        }
+        s->scale = (float)sc;
+    }
+    const size_t pb = 9 * s->N * storage_size(s->kind);
+    s->pop[0] = dalloc(c, s->stream, pb);
+    s->pop[1] = dalloc(c, s->stream, pb);
+    s->d_small = dalloc(c, s->stream, 64);
+    if (!s->pop[0] || !s->pop[1] || !s->d_small) {
+        lbib_destroy(s);
+        return fail(LBIB_E_OOM, "device allocation of 2 x %zu bytes failed", pb);
+    }
+    s->d_step = (long long *)s->d_small;
+    s->d_cur = (int *)((char *)s->d_small + 8);
+    s->d_err = (int *)((char *)s->d_small + 12);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(s->d_small, 0, 64, s->stream)) ||
+        (e = cudaMemsetAsync(s->pop[0], 0, pb, s->stream)) ||
+        (e = cudaMemsetAsync(s->pop[1], 0, pb, s->stream)) ||
+        (e = cudaStreamSynchronize(s->stream))) {
+        lbib_destroy(s);
+        return cuda_fail(e, "initialisation");
+    }
+    *out = s;
+    return LBIB_OK;
+}
+
+lbib_status lbib_destroy(lbib_sim *s) {
+    if (!s) return LBIB_OK;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    free_batch(s->self);
+    for (auto &p : s->parts) dfree(s->cfg, s->stream, p.d_block);
+    dfree(s->cfg, s->stream, s->pop[0]);
+    dfree(s->cfg, s->stream, s->pop[1]);
+    dfree(s->cfg, s->stream, s->d_small);
+    dfree(s->cfg, s->stream, s->d_scratch);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return LBIB_OK;
+}
+
+lbib_status lbib_add_particle(lbib_sim *s, const lbib_particle *in, int32_t *pid) {
+    if (!s || !in) return fail(LBIB_E_ARG, "null argument");
+    if (s->primed || s->step > 0) return fail(LBIB_E_STATE, "particles must be added before the first step");
+    if ((int)s->parts.size() >= LBIB_MAX_PARTICLES_PER_SIM)
+        return fail(LBIB_E_ARG, "at most %d particles per simulation", LBIB_MAX_PARTICLES_PER_SIM);
+    HostParticle p;
+    if (in->vx && in->vy) {
+        if (in->n_vertices < 3 || in->n_vertices > LBIB_MAX_MARKERS)
+            return fail(LBIB_E_ARG, "n_vertices %d outside 3..%d", in->n_vertices, LBIB_MAX_MARKERS);
+        p.vx.assign(in->vx, in->vx + in->n_vertices);
+        p.vy.assign(in->vy, in->vy + in->n_vertices);
+    } else {
+        if (!(in->a > 0) || (in->shape == 1 && !(in->b > 0)) || in->shape < 0 || in->shape > 1)
+            return fail(LBIB_E_ARG, "shape needs positive semi-axes");
+        const double a = in->a, b = in->shape == 1 ? in->b : in->a;
+        const double h = ((a - b) / (a + b)) * ((a - b) / (a + b));
+        const double per = M_PI * (a + b) * (1 + 3 * h / (10 + sqrt(4 - 3 * h)));
+        const int n = in->n_vertices > 0 ? in->n_vertices : std::max(8, (int)lround(per));
+        if (n < 3 || n > LBIB_MAX_MARKERS) return fail(LBIB_E_ARG, "marker count %d", n);
+        ellipse_outline(a, b, n, p.vx, p.vy);
+    }
+    for (size_t i = 0; i < p.vx.size(); ++i)
+        if (!isfinite(p.vx[i]) || !isfinite(p.vy[i])) return fail(LBIB_E_ARG, "non-finite vertex");
+    if (!(in->rho_p > 0) || in->ligand_density < 0 || in->ligand_density > 1 || in->sigma < 0 ||
+        !isfinite(in->xc) || !isfinite(in->yc) || !isfinite(in->theta))
+        return fail(LBIB_E_ARG, "particle parameters out of range");
+    p.fixed = in->fixed != 0;
+    p.xc = in->xc; p.yc = in->yc; p.th = in->theta;
+    p.rho_p = in->rho_p; p.lig = in->ligand_density; p.sigma = in->sigma;
+    build_geometry(p);
+    if (!(p.area > 0)) return fail(LBIB_E_ARG, "outline must be counter-clockwise with positive area");
+    if (p.rmax > LBIB_MAX_PARTICLE_RADIUS)
+        return fail(LBIB_E_ARG, "particle radius %.2f above %.1f", p.rmax, LBIB_MAX_PARTICLE_RADIUS);
+    if (p.T >= s->cfg.nx) return fail(LBIB_E_ARG, "force tile %d not narrower than the lattice", p.T);
+    if (s->cfg.wall_bottom == LBIB_WALL_PERIODIC && p.T >= s->cfg.ny)
+        return fail(LBIB_E_ARG, "force tile %d not lower than the periodic lattice", p.T);
+    for (size_t l = 0; l < p.S.size(); ++l)
+        if (!(p.S[l] > 0)) return fail(LBIB_E_ARG, "degenerate element %zu", l);
+    if (particle_smem_bytes(s->kind, p.T, p.nl) > SMEM_LIMIT)
+        return fail(LBIB_E_ARG, "particle needs more on-chip memory than one SM has");
+    lbib_status r = upload_particle(s, p);
+    if (r != LBIB_OK) return r;
+    s->parts.push_back(std::move(p));
+    if (pid) *pid = (int32_t)s->parts.size() - 1;
+    return LBIB_OK;
+}
+
+lbib_status lbib_set_receptors(lbib_sim *s, int32_t wall, double density) {
+    if (!s) return fail(LBIB_E_ARG, "null simulation");
+    if (wall < 0 || wall > 1 || !(density >= 0) || !isfinite(density))
+        return fail(LBIB_E_ARG, "wall must be 0 or 1 and density >= 0");
+    if (s->primed || s->step > 0) return fail(LBIB_E_STATE, "receptors must be set before the first step");
+    (wall == 0 ? s->cfg.receptor_bottom : s->cfg.receptor_top) = density;
+    return LBIB_OK;
+}
+
+lbib_status lbib_set_populations(lbib_sim *s, const double *f) {
+    if (!s || !f) return fail(LBIB_E_ARG, "null argument");
+    if (s->primed || s->step > 0) return fail(LBIB_E_STATE, "populations can only be set before the first step");
+    lbib_status r = ensure_scratch(s, 9 * s->N * sizeof(double));
+    if (r != LBIB_OK) return r;
+    CK(cudaMemcpyAsync(s->d_scratch, f, 9 * s->N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    SimDev d = make_simdev(s, 0, 0);
+    CK(launch_set_populations(s->kind, d, s->d_scratch, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBIB_OK;
+}
+
+lbib_status lbib_step(lbib_sim *s, int64_t n) {
+    if (!s) return fail(LBIB_E_ARG, "null simulation");
+    lbib_status r = ensure_self(s);
+    if (r != LBIB_OK) return r;
+    return batch_step_impl(s->self, n);
+}
+
+lbib_status lbib_batch_create(lbib_sim *const *sims, int32_t n, lbib_batch **out) {
+    return make_batch(sims, n, out);
+}
+
+lbib_status lbib_batch_step(lbib_batch *b, int64_t n) {
+    if (!b) return fail(LBIB_E_ARG, "null batch");
+    return batch_step_impl(b, n);
+}
+
+lbib_status lbib_batch_destroy(lbib_batch *b) {
+    if (b) cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return LBIB_OK;
+}
+
+lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples) {
+    if (!b || nsamples < 0 || nsamples > 64) return fail(LBIB_E_ARG, "nsamples must be 0..64");
+    CK(cudaStreamSynchronize(b->stream));
+    for (auto g : b->tgraphs)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto e : b->ev) cudaEventDestroy(e);
+    b->tgraphs.assign(nsamples, nullptr);
+    b->ev.assign(4 * nsamples, nullptr);
+    b->replayed.assign(nsamples, 0);
+    b->next_slot = 0;
+    b->nsamples = nsamples;
+    for (auto &e : b->ev) CK(cudaEventCreate(&e));
+    // capture every sampled graph now, so that timed stepping does no capture
+    for (int s = 0; s < nsamples; ++s) {
+        lbib_status r = capture(b, &b->ev[4 * s], &b->tgraphs[s]);
+        if (r != LBIB_OK) return r;
+    }
+    return LBIB_OK;
+}
+
+lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count) {
+    if (!b || !mean_ms || !count) return fail(LBIB_E_ARG, "null argument");
+    CK(cudaStreamSynchronize(b->stream));
+    double sum[2] = {0, 0};
+    int64_t cnt[2] = {0, 0};
+    for (int s = 0; s < b->nsamples; ++s) {
+        if (!b->replayed[s]) continue;
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, b->ev[4 * s], b->ev[4 * s + 1]));
+        sum[0] += ms; cnt[0]++;
+        CK(cudaEventElapsedTime(&ms, b->ev[4 * s + 2], b->ev[4 * s + 3]));
+        sum[1] += ms; cnt[1]++;
+        b->replayed[s] = 0;
+    }
+    for (int k = 0; k < 2; ++k) {
+        mean_ms[k] = cnt[k] ? sum[k] / cnt[k] : 0.0;
+        count[k] = cnt[k];
+    }
+    return LBIB_OK;
+}
+
+lbib_status lbib_synchronize(lbib_sim *s) {
+    if (!s) return fail(LBIB_E_ARG, "null simulation");
+    CK(cudaStreamSynchronize(s->stream));
+    return check_err_word(s);
+}
+
+lbib_status lbib_read_state(lbib_sim *s, lbib_state *st, lbib_particle_state *parts,
+                            int32_t n_parts, double *rho, double *ux, double *uy, size_t n_nodes) {
+    if (!s) return fail(LBIB_E_ARG, "null simulation");
+    if ((rho || ux || uy) && n_nodes != s->N)
+        return fail(LBIB_E_ARG, "field buffers hold %zu nodes, lattice has %zu", n_nodes, s->N);
+    lbib_status r = prime(s, s->stream);
+    if (r != LBIB_OK) return r;
+    CK(cudaStreamSynchronize(s->stream));
+    r = check_err_word(s);
+    if (r != LBIB_OK) return r;
+    if (st) {
+        st->step = s->step;
+        st->n_particles = (int32_t)s->parts.size();
+        st->storage = s->kind;
+        st->nx = s->cfg.nx;
+        st->ny = s->cfg.ny;
+    }
+    if (parts) {
+        const int m = std::min<int>(n_parts, (int)s->parts.size());
+        for (int k = 0; k < m; ++k) {
+            ParticleDev h;
+            CK(cudaMemcpy(&h, s->parts[k].d_part, sizeof h, cudaMemcpyDeviceToHost));
+            lbib_particle_state &o = parts[k];
+            const HostParticle &p = s->parts[k];
+            o.xc = h.xc; o.yc = h.yc; o.theta = h.th; o.u = h.u; o.v = h.v; o.omega = h.om;
+            o.Fh[0] = h.Fh[0]; o.Fh[1] = h.Fh[1]; o.Mh = h.Mh;
+            o.Fb[0] = h.Fb[0]; o.Fb[1] = h.Fb[1]; o.Mb = h.Mb;
+            o.Fw[0] = h.Fw[0]; o.Fw[1] = h.Fw[1];
+            o.area = p.area; o.mass = p.mass; o.inertia = p.inertia; o.r_eq = p.r_eq;
+            o.nl = p.nl; o.n_ligands = p.n_ligands; o.n_probing = h.n_probing;
+            o.n_bonded = h.n_bonded;
+        }
+    }
+    if (rho || ux || uy) {
+        r = ensure_scratch(s, 3 * s->N * sizeof(double));
+        if (r != LBIB_OK) return r;
+        SimDev d = make_simdev(s, 0, 0);
+        double *dr = s->d_scratch, *du = dr + s->N, *dv = du + s->N;
+        CK(launch_fields(s->kind, d, s->self->bd.parts, dr, du, dv, s->stream));
+        if (rho) CK(cudaMemcpyAsync(rho, dr, s->N * 8, cudaMemcpyDeviceToHost, s->stream));
+        if (ux) CK(cudaMemcpyAsync(ux, du, s->N * 8, cudaMemcpyDeviceToHost, s->stream));
+        if (uy) CK(cudaMemcpyAsync(uy, dv, s->N * 8, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    return LBIB_OK;
+}
+
+lbib_status lbib_read_populations(lbib_sim *s, double *f) {
+    if (!s || !f) return fail(LBIB_E_ARG, "null argument");
+    CK(cudaStreamSynchronize(s->stream));
+    lbib_status r = ensure_scratch(s, 9 * s->N * sizeof(double));
+    if (r != LBIB_OK) return r;
+    SimDev d = make_simdev(s, 0, 0);
+    CK(launch_populations(s->kind, d, s->d_scratch, s->stream));
+    CK(cudaMemcpyAsync(f, s->d_scratch, 9 * s->N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return check_err_word(s);
+}
+
+lbib_status lbib_read_bonds(lbib_sim *s, int32_t pid, uint8_t *bond, double *ax, int32_t n) {
+    if (!s) return fail(LBIB_E_ARG, "null simulation");
+    if (pid < 0 || pid >= (int)s->parts.size()) return fail(LBIB_E_ARG, "no particle %d", pid);
+    if (n != s->parts[pid].nl) return fail(LBIB_E_ARG, "particle %d has %d elements", pid, s->parts[pid].nl);
+    CK(cudaStreamSynchronize(s->stream));
+    ParticleDev h;
+    CK(cudaMemcpy(&h, s->parts[pid].d_part, sizeof h, cudaMemcpyDeviceToHost));
+    if (bond) CK(cudaMemcpy(bond, h.bond, n, cudaMemcpyDeviceToHost));
+    if (ax) CK(cudaMemcpy(ax, h.anchor_x, 8 * (size_t)n, cudaMemcpyDeviceToHost));
+    return LBIB_OK;
+}
+
+lbib_status lbib_read_ib_force(lbib_sim *s, double *fx, double *fy) {
+    if (!s || !fx || !fy) return fail(LBIB_E_ARG, "null argument");
+    lbib_status r = prime(s, s->stream);
+    if (r != LBIB_OK) return r;
+    r = ensure_scratch(s, 2 * s->N * sizeof(double));
+    if (r != LBIB_OK) return r;
+    SimDev d = make_simdev(s, 0, 0);
+    CK(launch_ib_export(s->kind, d, s->self->bd.parts, s->d_scratch, s->d_scratch + s->N, s->stream));
+    CK(cudaMemcpyAsync(fx, s->d_scratch, s->N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(fy, s->d_scratch + s->N, s->N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBIB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// lbib_internal.cuh -- device data structures and the lattice helpers shared
+// by the lattice and particle kernels of the sm_103a library.
+//
+// Populations are stored as deviations d_i = f_i - w_i in structure-of-arrays
+// planes [9][ny][nx] (one buffer per parity, A/B pull scheme).  The stored
+// state is post-collision f*; a node's pre-collision populations of the next
+// step are gathered by pulling from its neighbours (Eq. 1 left-hand side) with
+// the wall conditions applied on the fly.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbib.h"
+
+namespace lbib {
+
+enum StorageKind { ST_F32 = 0, ST_F64 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+// Error bits of the per-simulation device error word.
+enum { ERR_UNSTABLE = 1 };
+
+// Per-simulation descriptor as seen by the kernels of one batch.
+struct SimDev {
+    int nx, ny, wall_b, wall_t;
+    int p0, np;          // particle range in the batch's particle table
+    int tile0, ntiles;   // lattice work tiles of this simulation
+    double tau, u_b, u_t, gx, gy;
+    double k_f, k_r0, kBT, sigma_star_ratio, y_cr, y_eq_ratio;
+    double hamaker, eps_min, rec_b, rec_t;
+    unsigned long long seed, sim_id;
+    float scale, inv_scale;   // storage scale of f - w (1 except F16)
+    void *pop[2];             // A/B population buffers
+    int *cur;                 // device: which buffer holds the latest f*
+    long long *step;          // device: completed steps
+    int *err;                 // device: error bits
+};
+
+// Rigid particle, resident in device memory (FP64 state and loads).
+struct ParticleDev {
+    double xc, yc, th, u, v, om;        // pose and velocities at step n
+    double xc1, yc1, th1, u1, v1, om1;  // one step earlier
+    double mass, inertia, r_eq, sigma;
+    double Fh[2], Mh, Fb[2], Mb, Fw[2];
+    int nl, n_ligands, n_probing, n_bonded;
+    int fixed, T, ncolors, tile_ox;     // T: force-tile edge; tile origin x in [0, nx)
+    int tile_oy, pad0, pad1, pad2;
+    // body-frame element centroids, outward normals and lengths
+    const double *mbx, *mby, *nbx, *nby, *S;
+    const uint8_t *ligand;
+    const int *color_order;  // markers grouped by colour
+    const int *color_off;    // [ncolors + 1]
+    uint8_t *bond;
+    double *anchor_x;
+    int8_t *anchor_wall;
+    void *tile;              // IB force density, [2][T][T] of the compute type
+};
+
+struct BatchDev {
+    SimDev *sims;
+    ParticleDev **parts;
+    int *part_sim;
+    int nsims, nparts, total_tiles;
+};
+
+// Storage traits: load a deviation into the compute type, store one back.
+template <typename S> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p, size_t i, float) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(float *p, size_t i, float v, float) { p[i] = v; }
+};
+template <> struct Store<double> {
+    static __device__ __forceinline__ double ld(const double *p, size_t i, float) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(double *p, size_t i, double v, float) { p[i] = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p, size_t i, float inv) {
+        return __half2float(p[i]) * inv;
+    }
+    static __device__ __forceinline__ void st(__half *p, size_t i, float v, float scale) {
+        p[i] = __float2half_rn(v * scale);
+    }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, size_t i, float inv) {
+        return __bfloat162float(p[i]) * inv;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, size_t i, float v, float scale) {
+        p[i] = __float2bfloat16_rn(v * scale);
+    }
+};
+
+// Pre-collision deviations of node (x, y) for the coming step, pulled from
+// the post-collision buffer `src` (Eq. 1 LHS): population i comes from
+// (x - e_i).  x is periodic; rows beyond the walls follow the wall kind:
+//  - periodic: wrap in y;
+//  - half-way bounce-back: the node's own opposite population plus the
+//    moving-wall term 6 w_i (e_i . u_w) (rho_w = 1);
+//  - Zou-He: the three unknowns are rebuilt from the known ones and the wall
+//    velocity (u_w, 0), in deviation form (all weights cancel, rho = 1 + ...).
+// Directions (Eq. 3): 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1)
+// 7 (-1,-1) 8 (1,-1).
+template <typename S, typename R>
+__device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__ src, int x,
+                                          int y, R d[9]) {
+    const int nx = s.nx, ny = s.ny;
+    const size_t N = (size_t)nx * (size_t)ny;
+    const float inv = s.inv_scale;
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x == nx - 1) ? 0 : x + 1;
+    int ym = y - 1, yp = y + 1;
+    bool bot = ym < 0, top = yp >= ny;
+    if (s.wall_b == LBIB_WALL_PERIODIC) {
+        if (bot) ym = ny - 1;
+        if (top) yp = 0;
+        bot = top = false;
+    }
+    const size_t r0 = (size_t)y * nx;
+    d[0] = Store<S>::ld(src, 0 * N + r0 + x, inv);
+    d[1] = Store<S>::ld(src, 1 * N + r0 + xm, inv);
+    d[3] = Store<S>::ld(src, 3 * N + r0 + xp, inv);
+    if (!bot) {
+        const size_t rm = (size_t)ym * nx;
+        d[2] = Store<S>::ld(src, 2 * N + rm + x, inv);
+        d[5] = Store<S>::ld(src, 5 * N + rm + xm, inv);
+        d[6] = Store<S>::ld(src, 6 * N + rm + xp, inv);
+    } else if (s.wall_b == LBIB_WALL_BOUNCE_BACK) {
+        const R uw6 = (R)(s.u_b * (1.0 / 6.0));
+        d[2] = Store<S>::ld(src, 4 * N + r0 + x, inv);
+        d[5] = Store<S>::ld(src, 7 * N + r0 + x, inv) + uw6;
+        d[6] = Store<S>::ld(src, 8 * N + r0 + x, inv) - uw6;
+    }
+    if (!top) {
+        const size_t rp = (size_t)yp * nx;
+        d[4] = Store<S>::ld(src, 4 * N + rp + x, inv);
+        d[7] = Store<S>::ld(src, 7 * N + rp + xp, inv);
+        d[8] = Store<S>::ld(src, 8 * N + rp + xm, inv);
+    } else if (s.wall_t == LBIB_WALL_BOUNCE_BACK) {
+        const R uw6 = (R)(s.u_t * (1.0 / 6.0));
+        d[4] = Store<S>::ld(src, 2 * N + r0 + x, inv);
+        d[7] = Store<S>::ld(src, 5 * N + r0 + x, inv) - uw6;
+        d[8] = Store<S>::ld(src, 6 * N + r0 + x, inv) + uw6;
+    }
+    if (bot && s.wall_b == LBIB_WALL_ZOU_HE) {
+        const R uw = (R)s.u_b;
+        const R rho = (R)1 + d[0] + d[1] + d[3] + (R)2 * (d[4] + d[7] + d[8]);
+        const R h = (R)0.5 * (d[1] - d[3]);
+        d[2] = d[4];
+        d[5] = d[7] - h + (R)0.5 * rho * uw;
+        d[6] = d[8] + h - (R)0.5 * rho * uw;
+    }
+    if (top && s.wall_t == LBIB_WALL_ZOU_HE) {
+        const R uw = (R)s.u_t;
+        const R rho = (R)1 + d[0] + d[1] + d[3] + (R)2 * (d[2] + d[5] + d[6]);
+        const R h = (R)0.5 * (d[1] - d[3]);
+        d[4] = d[2];
+        d[7] = d[5] + h - (R)0.5 * rho * uw;
+        d[8] = d[6] - h + (R)0.5 * rho * uw;
+    }
+}
+
+// Density deviation and momentum of a set of deviations (sum_i w_i e_i = 0).
+template <typename R>
+__device__ __forceinline__ void node_moments(const R d[9], R &drho, R &jx, R &jy) {
+    drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+}
+
+// Force-tile lookup: IB force density at (x, y) summed over the simulation's
+// particles whose tile covers the node.
+template <typename R>
+__device__ __forceinline__ void tile_force(const SimDev &s, ParticleDev *const *parts, int x,
+                                           int y, R &fx, R &fy) {
+    for (int k = 0; k < s.np; ++k) {
+        const ParticleDev *p = parts[s.p0 + k];
+        const int T = p->T;
+        int dx = x - p->tile_ox;
+        if (dx < 0) dx += s.nx;
+        int dy = y - p->tile_oy;
+        if (dy < 0 && s.wall_b == LBIB_WALL_PERIODIC) dy += s.ny;
+        if (dx < T && (unsigned)dy < (unsigned)T) {
+            const R *t = (const R *)p->tile;
+            fx += t[dy * T + dx];
+            fy += t[T * T + dy * T + dx];
+        }
+    }
+}
+
+// Launchers (defined in the .cu files), one instantiation per storage kind.
+cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, cudaStream_t st);
+cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int init, int smem,
+                             cudaStream_t st);
+cudaError_t launch_fields(int kind, const SimDev &s, ParticleDev *const *parts, double *rho,
+                          double *ux, double *uy, cudaStream_t st);
+cudaError_t launch_populations(int kind, const SimDev &s, double *out, cudaStream_t st);
+cudaError_t launch_set_populations(int kind, const SimDev &s, const double *in, cudaStream_t st);
+cudaError_t launch_flip(int *const *curs, int n, cudaStream_t st);
+cudaError_t launch_ib_export(int kind, const SimDev &s, ParticleDev *const *parts, double *fx,
+                             double *fy, cudaStream_t st);
+int particle_smem_bytes(int kind, int T, int nl);
+cudaError_t particle_kernel_setup(int kind, int smem);
+
+}  // namespace lbib

@@ -1,0 +1,195 @@
+// lbib_lattice.cu -- fused stream-collide kernel over a batch of lattices,
+// plus the small export/import kernels used by the read/write calls.
+//
+// One thread per node.  A node pulls its nine pre-collision populations from
+// the post-collision buffer (Eq. 1 LHS, walls in pull_node), takes the
+// moments of Eq. 5-6 with the half-force of the uniform body force g plus the
+// IB force density f_ib of any particle tile covering it, relaxes to the
+// equilibrium of Eq. 2 and adds the Guo source of Eq. 4, and writes its nine
+// post-collision deviations to the other buffer.  Algorithmic traffic: 9
+// reads + 9 writes of the storage type per node (72 B in FP32).
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+namespace {
+
+constexpr int LB_THREADS = 256;
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int flip) {
+    const int tile = blockIdx.x;
+    int lo = 0, hi = b.nsims - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.sims[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    const SimDev &s = b.sims[lo];
+    const int nx = s.nx, ny = s.ny;
+    const int k = (tile - s.tile0) * LB_THREADS + (int)threadIdx.x;
+    if (tile == s.tile0 && threadIdx.x == 0) *s.step += 1;
+    if (k >= nx * ny) return;
+    const int y = k / nx, x = k - y * nx;
+    const int cur = *s.cur ^ flip;
+    const S *__restrict__ src = (const S *)s.pop[cur];
+    S *__restrict__ dst = (S *)s.pop[cur ^ 1];
+
+    R d[9];
+    pull_node<S, R>(s, src, x, y, d);
+    R drho, jx, jy;
+    node_moments(d, drho, jx, jy);
+    R Fx = (R)s.gx, Fy = (R)s.gy;
+    if (s.np) tile_force<R>(s, b.parts, x, y, Fx, Fy);
+
+    const R rho = (R)1 + drho;
+    const R irho = (R)1 / rho;
+    const R ux = (jx + (R)0.5 * Fx) * irho;
+    const R uy = (jy + (R)0.5 * Fy) * irho;
+    const R om = (R)(1.0 / s.tau);
+    const R pref = (R)1 - (R)0.5 * om;
+    const R uu15 = (R)1.5 * (ux * ux + uy * uy);
+    const R uF = ux * Fx + uy * Fy;
+    const size_t N = (size_t)nx * ny;
+    const size_t node = (size_t)k;
+    constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R w = i == 0 ? (R)(4.0 / 9.0) : (i < 5 ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0));
+        const R eu = (R)EX[i] * ux + (R)EY[i] * uy;
+        const R eF = (R)EX[i] * Fx + (R)EY[i] * Fy;
+        // f^eq - w_i = w_i (rho - 1) + w_i rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)
+        const R deq = w * (drho + rho * ((R)3 * eu + (R)4.5 * eu * eu - uu15));
+        // Guo: (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
+        const R src_i = pref * w * ((R)3 * (eF - uF) + (R)9 * eu * eF);
+        const R out = d[i] - om * (d[i] - deq) + src_i;
+        Store<S>::st(dst, (size_t)i * N + node, out, s.scale);
+    }
+    if (!(fabs((double)drho) < 0.5) || !(fabs((double)ux) < 0.5)) atomicOr(s.err, ERR_UNSTABLE);
+}
+
+template <typename S, typename R>
+__global__ void fields_kernel(SimDev s, ParticleDev *const *parts, double *rho_o, double *ux_o,
+                              double *uy_o) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.nx * s.ny) return;
+    const int y = k / s.nx, x = k - y * s.nx;
+    const S *src = (const S *)s.pop[*s.cur];
+    R d[9];
+    pull_node<S, R>(s, src, x, y, d);
+    R drho, jx, jy;
+    node_moments(d, drho, jx, jy);
+    R Fx = (R)s.gx, Fy = (R)s.gy;
+    if (s.np) tile_force<R>(s, parts, x, y, Fx, Fy);
+    const double rho = 1.0 + (double)drho;
+    if (rho_o) rho_o[k] = rho;
+    if (ux_o) ux_o[k] = ((double)jx + 0.5 * (double)Fx) / rho;
+    if (uy_o) uy_o[k] = ((double)jy + 0.5 * (double)Fy) / rho;
+}
+
+template <typename S>
+__global__ void export_pops_kernel(SimDev s, double *out) {
+    const size_t N = (size_t)s.nx * s.ny;
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 9 * N) return;
+    const int i = (int)(k / N);
+    const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    const S *src = (const S *)s.pop[*s.cur];
+    out[k] = w + (double)Store<S>::ld(src, k, s.inv_scale);
+}
+
+template <typename S, typename R>
+__global__ void import_pops_kernel(SimDev s, const double *in) {
+    const size_t N = (size_t)s.nx * s.ny;
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 9 * N) return;
+    const int i = (int)(k / N);
+    const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    S *dst = (S *)s.pop[*s.cur];
+    Store<S>::st(dst, k, (R)(in[k] - w), s.scale);
+}
+
+template <typename R>
+__global__ void ib_export_kernel(SimDev s, ParticleDev *const *parts, double *fx, double *fy) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.nx * s.ny) return;
+    const int y = k / s.nx, x = k - y * s.nx;
+    R a = 0, c = 0;
+    tile_force<R>(s, parts, x, y, a, c);
+    fx[k] = (double)a;
+    fy[k] = (double)c;
+}
+
+__global__ void flip_kernel(int *const *curs, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) *curs[i] ^= 1;
+}
+
+template <typename F>
+cudaError_t by_kind(int kind, F &&f) {
+    switch (kind) {
+        case ST_F32: return f(float{}, float{});
+        case ST_F64: return f(double{}, double{});
+        case ST_F16: return f(__half{}, float{});
+        case ST_BF16: return f(__nv_bfloat16{}, float{});
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, cudaStream_t st) {
+    return by_kind(kind, [&](auto sv, auto rv) {
+        using S = decltype(sv);
+        using R = decltype(rv);
+        lattice_kernel<S, R><<<b.total_tiles, LB_THREADS, 0, st>>>(b, flip);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_fields(int kind, const SimDev &s, ParticleDev *const *parts, double *rho,
+                          double *ux, double *uy, cudaStream_t st) {
+    const int n = s.nx * s.ny;
+    return by_kind(kind, [&](auto sv, auto rv) {
+        using S = decltype(sv);
+        using R = decltype(rv);
+        fields_kernel<S, R><<<(n + 255) / 256, 256, 0, st>>>(s, parts, rho, ux, uy);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_populations(int kind, const SimDev &s, double *out, cudaStream_t st) {
+    const size_t n = 9 * (size_t)s.nx * s.ny;
+    return by_kind(kind, [&](auto sv, auto) {
+        using S = decltype(sv);
+        export_pops_kernel<S><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, out);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_set_populations(int kind, const SimDev &s, const double *in, cudaStream_t st) {
+    const size_t n = 9 * (size_t)s.nx * s.ny;
+    return by_kind(kind, [&](auto sv, auto rv) {
+        using S = decltype(sv);
+        using R = decltype(rv);
+        import_pops_kernel<S, R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, in);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_ib_export(int kind, const SimDev &s, ParticleDev *const *parts, double *fx,
+                             double *fy, cudaStream_t st) {
+    const int n = s.nx * s.ny;
+    return by_kind(kind, [&](auto, auto rv) {
+        using R = decltype(rv);
+        ib_export_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(s, parts, fx, fy);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_flip(int *const *curs, int n, cudaStream_t st) {
+    flip_kernel<<<(n + 127) / 128, 128, 0, st>>>(curs, n);
+    return cudaGetLastError();
+}
+
+}  // namespace lbib
