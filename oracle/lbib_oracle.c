@@ -286,9 +286,11 @@ static void collide(or_sim *s) {
 /* Reading: linear basis p = (1, x - X, y - Y); tensor-product cubic B-spline
  * weight with radius 2 per axis; support = the 4 x 4 nodes floor(X)-1 ..
  * floor(X)+2 in each direction (periodic in x, and in y for periodic walls),
- * limited in y to fluid rows (rows 0..ny-1 for bounce-back walls, 1..ny-2
- * for Zou-He wall rows).  A support with fewer than two rows or two columns
- * of non-zero weight cannot carry a linear fit and yields no nodes. */
+ * limited in y to the lattice rows 0..ny-1 (Zou-He wall nodes are nodes of
+ * the fluid domain and stay in the support, so a marker between the wall
+ * row and row 1 is interpolated, not extrapolated).  A support with fewer
+ * than two rows or two columns of non-zero weight cannot carry a linear fit
+ * and yields no nodes. */
 double or_weight(double r) {
     double a = fabs(r);
     if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
@@ -300,8 +302,8 @@ double or_weight(double r) {
 }
 
 static void row_limits(const or_config *c, int *lo, int *hi) {
-    *lo = (c->wall_bottom == OR_WALL_ZOU_HE) ? 1 : 0;
-    *hi = (c->wall_top == OR_WALL_ZOU_HE) ? c->ny - 2 : c->ny - 1;
+    *lo = 0;
+    *hi = c->ny - 1;
 }
 
 /* Gaussian elimination with partial pivoting on a 3x3 system. */

@@ -88,7 +88,8 @@ struct lbib_sim {
     float scale = 1.f;
     bool primed = false;
     std::vector<HostParticle> parts;
-    lbib_batch *self = nullptr;
+    lbib_batch *self = nullptr;           // private batch of one (lbib_step)
+    std::vector<lbib_batch *> batches;    // user batches that contain this simulation
 };
 
 struct lbib_batch {
@@ -107,6 +108,9 @@ struct lbib_batch {
     std::vector<cudaEvent_t> ev;        // 4 per slot: lb0, lb1, p0, p1
     std::vector<int> replayed;          // slot replayed since the last read
     int next_slot = 0;
+    lbib_config acfg{};                 // allocator hook used for d_block
+    bool is_self = false;
+    bool orphan = false;                // a member was destroyed: the batch is unusable
 };
 
 namespace {
@@ -284,15 +288,37 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     return LBIB_OK;
 }
 
+void unregister(lbib_batch *b) {
+    if (b->is_self || b->orphan) return;
+    for (lbib_sim *s : b->sims) {
+        auto &v = s->batches;
+        v.erase(std::remove(v.begin(), v.end(), b), v.end());
+    }
+}
+
 void free_batch(lbib_batch *b) {
     if (!b) return;
+    unregister(b);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (auto g : b->tgraphs)
         if (g) cudaGraphExecDestroy(g);
     for (auto e : b->ev) cudaEventDestroy(e);
-    if (b->d_block && !b->sims.empty())
-        dfree(b->sims[0]->cfg, b->stream, b->d_block);
+    if (b->d_block) dfree(b->acfg, b->orphan ? nullptr : b->stream, b->d_block);
     delete b;
+}
+
+// Setup calls are allowed until the first step, while no user batch holds
+// the simulation; they drop the private batch and the initial IB forcing.
+lbib_status reopen_setup(lbib_sim *s, const char *what) {
+    if (s->step > 0) return fail(LBIB_E_STATE, "%s: only before the first step", what);
+    if (!s->batches.empty()) return fail(LBIB_E_STATE, "%s: the simulation is in a batch", what);
+    if (s->self) {
+        cudaStreamSynchronize(s->stream);
+        free_batch(s->self);
+        s->self = nullptr;
+    }
+    s->primed = false;
+    return LBIB_OK;
 }
 
 lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
@@ -301,6 +327,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     if (!b) return fail(LBIB_E_OOM, "host allocation failed");
     b->kind = sims[0]->kind;
     b->stream = sims[0]->stream;
+    b->acfg = sims[0]->cfg;
     int nparts = 0, tiles = 0, smem = 0;
     for (int i = 0; i < n; ++i) {
         lbib_sim *s = sims[i];
@@ -382,7 +409,9 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
 lbib_status ensure_self(lbib_sim *s) {
     if (s->self) return LBIB_OK;
     lbib_sim *one[1] = {s};
-    return make_batch(one, 1, &s->self);
+    lbib_status r = make_batch(one, 1, &s->self);
+    if (r == LBIB_OK) s->self->is_self = true;
+    return r;
 }
 
 // IB forcing of step 0 at the initial pose (the particle kernel in init mode).
@@ -402,12 +431,14 @@ cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < nsteps; ++k) {
         const int f = k & 1;
-        if (ev && k == 0 && (e = cudaEventRecord(ev[0], b->stream))) return e;
+        // inside a capture, external records become event-record nodes
+        const unsigned fl = cudaEventRecordExternal;
+        if (ev && k == 0 && (e = cudaEventRecordWithFlags(ev[0], b->stream, fl))) return e;
         if ((e = launch_lattice(b->kind, b->bd, f, b->stream))) return e;
-        if (ev && k == 0 && (e = cudaEventRecord(ev[1], b->stream))) return e;
-        if (ev && k == 0 && (e = cudaEventRecord(ev[2], b->stream))) return e;
+        if (ev && k == 0 && (e = cudaEventRecordWithFlags(ev[1], b->stream, fl))) return e;
+        if (ev && k == 0 && (e = cudaEventRecordWithFlags(ev[2], b->stream, fl))) return e;
         if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->stream))) return e;
-        if (ev && k == 0 && (e = cudaEventRecord(ev[3], b->stream))) return e;
+        if (ev && k == 0 && (e = cudaEventRecordWithFlags(ev[3], b->stream, fl))) return e;
     }
     return e;
 }
@@ -429,6 +460,7 @@ lbib_status capture(lbib_batch *b, cudaEvent_t *ev, cudaGraphExec_t *out) {
 }
 
 lbib_status batch_step_impl(lbib_batch *b, int64_t n) {
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
     if (n < 0) return fail(LBIB_E_ARG, "nsteps must be >= 0");
     if (n == 0) return LBIB_OK;
     for (lbib_sim *s : b->sims) {
@@ -552,6 +584,14 @@ lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out) {
 lbib_status lbib_destroy(lbib_sim *s) {
     if (!s) return LBIB_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
+    // batches holding this simulation become orphans: they keep their own
+    // memory (freed by lbib_batch_destroy) and refuse to step
+    std::vector<lbib_batch *> held = s->batches;
+    for (lbib_batch *b : held) {
+        cudaStreamSynchronize(b->stream);
+        unregister(b);
+        b->orphan = true;
+    }
     free_batch(s->self);
     for (auto &p : s->parts) dfree(s->cfg, s->stream, p.d_block);
     dfree(s->cfg, s->stream, s->pop[0]);
@@ -565,7 +605,10 @@ lbib_status lbib_destroy(lbib_sim *s) {
 
 lbib_status lbib_add_particle(lbib_sim *s, const lbib_particle *in, int32_t *pid) {
     if (!s || !in) return fail(LBIB_E_ARG, "null argument");
-    if (s->primed || s->step > 0) return fail(LBIB_E_STATE, "particles must be added before the first step");
+    {
+        lbib_status r0 = reopen_setup(s, "lbib_add_particle");
+        if (r0 != LBIB_OK) return r0;
+    }
     if ((int)s->parts.size() >= LBIB_MAX_PARTICLES_PER_SIM)
         return fail(LBIB_E_ARG, "at most %d particles per simulation", LBIB_MAX_PARTICLES_PER_SIM);
     HostParticle p;
@@ -614,15 +657,19 @@ lbib_status lbib_set_receptors(lbib_sim *s, int32_t wall, double density) {
     if (!s) return fail(LBIB_E_ARG, "null simulation");
     if (wall < 0 || wall > 1 || !(density >= 0) || !isfinite(density))
         return fail(LBIB_E_ARG, "wall must be 0 or 1 and density >= 0");
-    if (s->primed || s->step > 0) return fail(LBIB_E_STATE, "receptors must be set before the first step");
+    {
+        lbib_status r0 = reopen_setup(s, "lbib_set_receptors");
+        if (r0 != LBIB_OK) return r0;
+    }
     (wall == 0 ? s->cfg.receptor_bottom : s->cfg.receptor_top) = density;
     return LBIB_OK;
 }
 
 lbib_status lbib_set_populations(lbib_sim *s, const double *f) {
     if (!s || !f) return fail(LBIB_E_ARG, "null argument");
-    if (s->primed || s->step > 0) return fail(LBIB_E_STATE, "populations can only be set before the first step");
-    lbib_status r = ensure_scratch(s, 9 * s->N * sizeof(double));
+    lbib_status r = reopen_setup(s, "lbib_set_populations");
+    if (r != LBIB_OK) return r;
+    r = ensure_scratch(s, 9 * s->N * sizeof(double));
     if (r != LBIB_OK) return r;
     CK(cudaMemcpyAsync(s->d_scratch, f, 9 * s->N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     SimDev d = make_simdev(s, 0, 0);
@@ -639,7 +686,10 @@ lbib_status lbib_step(lbib_sim *s, int64_t n) {
 }
 
 lbib_status lbib_batch_create(lbib_sim *const *sims, int32_t n, lbib_batch **out) {
-    return make_batch(sims, n, out);
+    lbib_status r = make_batch(sims, n, out);
+    if (r != LBIB_OK) return r;
+    for (lbib_sim *s : (*out)->sims) s->batches.push_back(*out);
+    return LBIB_OK;
 }
 
 lbib_status lbib_batch_step(lbib_batch *b, int64_t n) {
@@ -648,13 +698,14 @@ lbib_status lbib_batch_step(lbib_batch *b, int64_t n) {
 }
 
 lbib_status lbib_batch_destroy(lbib_batch *b) {
-    if (b) cudaStreamSynchronize(b->stream);
+    if (b && !b->orphan) cudaStreamSynchronize(b->stream);
     free_batch(b);
     return LBIB_OK;
 }
 
 lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples) {
     if (!b || nsamples < 0 || nsamples > 64) return fail(LBIB_E_ARG, "nsamples must be 0..64");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
     CK(cudaStreamSynchronize(b->stream));
     for (auto g : b->tgraphs)
         if (g) cudaGraphExecDestroy(g);
@@ -675,6 +726,7 @@ lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples) {
 
 lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count) {
     if (!b || !mean_ms || !count) return fail(LBIB_E_ARG, "null argument");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
     CK(cudaStreamSynchronize(b->stream));
     double sum[2] = {0, 0};
     int64_t cnt[2] = {0, 0};
@@ -705,8 +757,11 @@ lbib_status lbib_read_state(lbib_sim *s, lbib_state *st, lbib_particle_state *pa
     if (!s) return fail(LBIB_E_ARG, "null simulation");
     if ((rho || ux || uy) && n_nodes != s->N)
         return fail(LBIB_E_ARG, "field buffers hold %zu nodes, lattice has %zu", n_nodes, s->N);
-    lbib_status r = prime(s, s->stream);
-    if (r != LBIB_OK) return r;
+    lbib_status r = LBIB_OK;
+    if (rho || ux || uy) {
+        r = prime(s, s->stream);   // the fields include the IB force of this step
+        if (r != LBIB_OK) return r;
+    }
     CK(cudaStreamSynchronize(s->stream));
     r = check_err_word(s);
     if (r != LBIB_OK) return r;

@@ -91,9 +91,10 @@ struct Support {
     bool ok;
 };
 
+// Support rows: every lattice row (wall nodes included) unless periodic.
 __device__ __forceinline__ void row_limits(const SimDev &s, int &lo, int &hi) {
-    lo = s.wall_b == LBIB_WALL_ZOU_HE ? 1 : 0;
-    hi = s.wall_t == LBIB_WALL_ZOU_HE ? s.ny - 2 : s.ny - 1;
+    lo = 0;
+    hi = s.ny - 1;
 }
 
 template <typename R>

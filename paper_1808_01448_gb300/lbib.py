@@ -295,6 +295,8 @@ class Batch:
 
     def __init__(self, sims):
         self.sims = list(sims)
+        # keep the members' allocator callbacks alive as long as the batch
+        self._allocs = [s._alloc_ref for s in self.sims]
         arr = (C.c_void_p * len(self.sims))(*[s.handle for s in self.sims])
         h = C.c_void_p()
         _check(lib().lbib_batch_create(arr, len(self.sims), C.byref(h)))

@@ -104,11 +104,15 @@ def test_ib_force_parity(O, L, walls, shape):
     assert abs(fg[0].sum() - fo[0].sum()) < 1e-12 * scale * nx
 
 
-def adhesion_case(shape="ar2", Re=1.0, nx=96, ny=40, rl=0.7, sigma=2.0, seed=5, r=6.0):
-    cfg = W.shear_channel(nx, ny, Re, tau=0.9, k_f=0.85, k_r0=1e-3, kBT=0.1, seed=seed,
-                          sim_id=2, hamaker=1e-9)
-    cfg["y_cr"] = 1.6
-    p = W.adhesion_particle(cfg, shape, r, x=nx / 3, ligand_density=rl, sigma=sigma)
+def adhesion_case(shape="ar2", Re=1.0, nx=96, ny=40, rl=0.7, sigma=0.02, seed=5, r=6.0):
+    """Particle released 0.3 lu above the bottom Zou-He wall of a shear
+    channel, with soft bonds (y_cr = 1, sigma = 0.02) so that bonds form and
+    the weakly coupled step stays stable for a small, light particle."""
+    cfg = W.shear_channel(nx, ny, Re, tau=0.9, k_f=0.85, k_r0=1e-3, kBT=0.02, seed=seed,
+                          sim_id=2, hamaker=1e-6)
+    cfg["y_cr"] = 1.0
+    p = W.adhesion_particle(cfg, shape, r, x=nx / 3, ligand_density=rl, sigma=sigma,
+                            gap_over_h=0.3 / (ny - 1))
     return cfg, p
 
 

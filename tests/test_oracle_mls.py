@@ -54,19 +54,19 @@ def test_partition_of_unity_and_linear_reproduction(O, walls):
 
 
 def test_support_respects_walls(O):
-    """Zou-He wall rows never enter the support; bounce-back rows do; a
+    """Only lattice rows enter the support (wall nodes included, so a point
+    between the wall row and row 1 is inside its support's row span); a
     support with a single usable row has no linear fit."""
-    zh = cfg(O, wall_bottom="zou_he", wall_top="zou_he")
-    bb = cfg(O)
-    _, iy, _ = O.mls_shape(zh, 10.3, 0.6)
-    assert iy.min() >= 1
-    _, iy, _ = O.mls_shape(bb, 10.3, 0.6)
-    assert iy.min() == 0
-    _, iy, _ = O.mls_shape(zh, 10.3, zh.ny - 1.4)
-    assert iy.max() <= zh.ny - 2
-    assert len(O.mls_shape(zh, 10.3, -0.9)[2]) == 0     # only row 1 is usable
-    assert len(O.mls_shape(zh, 10.3, 0.0)[2]) == 0      # row 2 sits at |dy| = 2
-    assert len(O.mls_shape(zh, 10.3, 0.2)[2]) > 0        # rows 1 and 2 remain
+    for walls in ("zou_he", "bounce_back"):
+        c = cfg(O, wall_bottom=walls, wall_top=walls)
+        ix, iy, phi = O.mls_shape(c, 10.3, 0.4)
+        assert iy.min() == 0 and iy.max() == 2
+        assert np.all(phi > -1e-12)                       # no extrapolation weights
+        _, iy, _ = O.mls_shape(c, 10.3, c.ny - 1.4)
+        assert iy.max() == c.ny - 1
+        assert len(O.mls_shape(c, 10.3, -1.9)[2]) == 0    # only row 0 is usable
+        assert len(O.mls_shape(c, 10.3, -1.0)[2]) == 0    # row 1 sits at |dy| = 2
+        assert len(O.mls_shape(c, 10.3, -0.8)[2]) > 0     # rows 0 and 1 remain
 
 
 def test_fit_is_exact_on_linear_fields(O):
