@@ -65,7 +65,9 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int fli
         const R out = d[i] - om * (d[i] - deq) + src_i;
         Store<S>::st(dst, (size_t)i * N + node, out, s.scale);
     }
-    if (!(fabs((double)drho) < 0.5) || !(fabs((double)ux) < 0.5)) atomicOr(s.err, ERR_UNSTABLE);
+    // non-finite state or a density outside (0, 2): the run has broken down
+    if (!(fabs((double)drho) < 1.0) || !(fabs((double)ux) + fabs((double)uy) < 10.0))
+        atomicOr(s.err, ERR_UNSTABLE);
 }
 
 template <typename S, typename R>

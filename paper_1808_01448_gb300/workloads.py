@@ -21,6 +21,26 @@ NU_PAPER = 1.0 / 6.0          # Table 1: nu_ref in lattice units (tau = 1)
 Y0_OVER_H = 3.0e-3            # initial gap
 YCR_OVER_H = 6.8e-3           # critical bond length
 KF_OVER_KR0 = 8.5e3           # biochemical affinity k_f / k_r0
+# Table 1's dimensionless groups, which agree with its SI column:
+SIGMA_HAT = {1: 27.8, 2: 55.5}   # sigma / (rho_ref nu_ref^2 / H) for bond strength 1 and 2
+HAMAKER_HAT = 1.74e-8            # H_k / (rho_ref nu_ref^2 H)
+K_R0 = 1.0e-4                    # reverse rate per step (absolute value not given)
+
+
+def bond_sigma(strength: int, H: float, nu: float) -> float:
+    """Spring constant in lattice units for bond strength 1 or 2 (rho = 1)."""
+    return SIGMA_HAT[strength] * nu * nu / H
+
+
+def hamaker_lu(H: float, nu: float) -> float:
+    return HAMAKER_HAT * nu * nu * H
+
+
+def thermal_energy(sigma: float, y_cr: float, y_eq_ratio: float = 0.5,
+                   sigma_star_ratio: float = 0.5) -> float:
+    """k_B T such that the exponent of Eq. 11 is 1 at the critical length."""
+    d = (1.0 - y_eq_ratio) * y_cr
+    return (1.0 - sigma_star_ratio) * sigma * d * d / 2.0
 
 
 def ramanujan_perimeter(a: float, b: float) -> float:
@@ -95,18 +115,32 @@ def adhesion_particle(cfg: dict, shape: str, radius_eq: float, x: float,
                 ligand_density=ligand_density, sigma=sigma)
 
 
+def adhesion_params(H: float, nu: float, strength: int) -> dict:
+    """Bond and wall-force constants in lattice units for bond strength 1 or
+    2: Table 1's dimensionless groups scaled by rho nu^2 / H (spring) and
+    rho nu^2 H (Hamaker), k_f / k_r0 = 8.5e3, k_B T from thermal_energy."""
+    sigma = bond_sigma(strength, H, nu)
+    y_cr = YCR_OVER_H * H
+    return dict(sigma=sigma, y_cr=y_cr, k_r0=K_R0, k_f=KF_OVER_KR0 * K_R0,
+                kBT=thermal_energy(sigma, y_cr), hamaker=hamaker_lu(H, nu))
+
+
 def single_ellipse_sweep(nx: int = 1024, ny: int = 256, radius_eq: float = 20.0,
                          shapes=("ar2", "ar3"), reynolds=(0.01, 0.1, 1.0),
-                         ligand_density: float = 0.7, sigma: float = 2.0,
+                         ligand_density: float = 0.7, strength: int = 2,
                          seed: int = 2):
     """Single elliptical particle, aspect ratio 2 and 3, equal area to a circle
-    of radius 20, in a 1024 x 256 channel at Re 0.01, 0.1 and 1: one sim per
-    (shape, Re).  Returns a list of (config, [particle]) pairs."""
+    of radius 20, in a 1024 x 256 channel at Re 0.01, 0.1 and 1, ligand
+    density 0.7, bond strength 2: one sim per (shape, Re).  Returns a list of
+    (config, [particle]) pairs."""
     out = []
     sim_id = 0
     for shape in shapes:
         for Re in reynolds:
             cfg = shear_channel(nx, ny, Re, seed=seed, sim_id=sim_id)
+            ap = adhesion_params(ny - 1, (cfg["tau"] - 0.5) / 3.0, strength)
+            sigma = ap.pop("sigma")
+            cfg.update(ap)
             p = adhesion_particle(cfg, shape, radius_eq, x=nx / 4.0,
                                   ligand_density=ligand_density, sigma=sigma)
             out.append((cfg, [p]))
@@ -116,7 +150,7 @@ def single_ellipse_sweep(nx: int = 1024, ny: int = 256, radius_eq: float = 20.0,
 
 def poiseuille_circle(nx: int = 200, ny: int = 50, radius: float = 10.0, tau: float = 0.8,
                       Re: float = 0.1, n: int = 63, ligand_density: float = 0.5,
-                      sigma: float = 1.0, seed: int = 1):
+                      strength: int = 1, seed: int = 1):
     """Single circle of radius 10 in a 200 x 50 body-force Poiseuille channel
     with half-way bounce-back walls (H = ny), centre 1.5 radii above the
     wall, 63 markers.  Re = u_c H / nu with the centre-line speed u_c."""
@@ -125,7 +159,10 @@ def poiseuille_circle(nx: int = 200, ny: int = 50, radius: float = 10.0, tau: fl
     u_c = Re * nu / H
     g = 8.0 * nu * u_c / (H * H)
     cfg = dict(nx=nx, ny=ny, wall_bottom="bounce_back", wall_top="bounce_back", tau=tau,
-               gx=g, y_cr=YCR_OVER_H * H, seed=seed, sim_id=0)
+               gx=g, seed=seed, sim_id=0)
+    ap = adhesion_params(H, nu, strength)
+    sigma = ap.pop("sigma")
+    cfg.update(ap)
     vx, vy = circle_polygon(radius, n)
     p = dict(vx=vx, vy=vy, xc=nx / 4.0, yc=-0.5 + 1.5 * radius, theta=0.0, rho_p=1.0,
              ligand_density=ligand_density, sigma=sigma)
