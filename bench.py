@@ -262,11 +262,11 @@ def run_gpu(args):
         f0.copy_(torch.tensor([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4,
                               dtype=torch.float64)[:, None, None].expand(9, 256, 1024))
         f0_np = f0.numpy()
-        eb = lbib.Batch(e2e_sims)
         barrier()
         t0 = time.perf_counter()
         for s in e2e_sims:
             s.set_populations(f0_np)
+        eb = lbib.Batch(e2e_sims)
         chunk, done, d2h = 100, 0, 0
         while done < args.steps:
             n = min(chunk, args.steps - done)

@@ -119,8 +119,8 @@ typedef struct lbib_config {
  * the pose (loads and bonds are still computed).  The outline must fit the
  * on-chip force tile: max radius <= LBIB_MAX_PARTICLE_RADIUS and
  * 3 <= nl <= LBIB_MAX_MARKERS. */
-#define LBIB_MAX_MARKERS 1024
-#define LBIB_MAX_PARTICLE_RADIUS 60.0
+#define LBIB_MAX_MARKERS 512
+#define LBIB_MAX_PARTICLE_RADIUS 44.0
 #define LBIB_MAX_PARTICLES_PER_SIM 16
 
 typedef struct lbib_particle {

@@ -138,13 +138,21 @@ SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
     d.nx = c.nx; d.ny = c.ny; d.wall_b = c.wall_bottom; d.wall_t = c.wall_top;
     d.p0 = p0; d.np = (int)s->parts.size();
     d.tile0 = tile0;
-    d.ntiles = (int)((s->N + 255) / 256);
+    d.ntiles = (int)((s->N + LB_TILE_NODES - 1) / LB_TILE_NODES);
     d.tau = c.tau; d.u_b = c.u_bottom; d.u_t = c.u_top; d.gx = c.gx; d.gy = c.gy;
     d.k_f = c.k_f; d.k_r0 = c.k_r0; d.kBT = c.kBT; d.sigma_star_ratio = c.sigma_star_ratio;
     d.y_cr = c.y_cr; d.y_eq_ratio = c.y_eq_ratio; d.hamaker = c.hamaker; d.eps_min = c.eps_min;
     d.rec_b = c.receptor_bottom; d.rec_t = c.receptor_top;
     d.seed = c.seed; d.sim_id = c.sim_id;
     d.scale = s->scale; d.inv_scale = 1.f / s->scale;
+    const double om = 1.0 / c.tau;
+    d.d_om = om; d.d_pref = 1.0 - 0.5 * om;
+    d.d_ub6 = c.u_bottom / 6.0; d.d_ut6 = c.u_top / 6.0;
+    d.f_om = (float)om; d.f_pref = (float)d.d_pref;
+    d.f_gx = (float)c.gx; d.f_gy = (float)c.gy;
+    d.f_ub = (float)c.u_bottom; d.f_ut = (float)c.u_top;
+    d.f_ub6 = (float)d.d_ub6; d.f_ut6 = (float)d.d_ut6;
+    d.d_nu = (c.tau - 0.5) / 3.0; d.f_nu = (float)d.d_nu;
     d.pop[0] = s->pop[0]; d.pop[1] = s->pop[1];
     d.cur = s->d_cur; d.step = s->d_step; d.err = s->d_err;
     return d;
@@ -242,6 +250,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     const int n = p.nl;
     const size_t rsz = compute_size(s->kind);
     const size_t bytes = sizeof(ParticleDev) + 5 * n * 8 + n + 4 * n + 4 * (p.ncolors + 1) + n +
+                         16 * (size_t)(n + 1) +
                          8 * n + n + 2 * rsz * p.T * p.T + 16 * 16;
     unsigned char *blk = (unsigned char *)dalloc(s->cfg, s->stream, bytes);
     if (!blk) return fail(LBIB_E_OOM, "device allocation of %zu bytes for a particle failed", bytes);
@@ -262,13 +271,15 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     double *ax = (double *)take(8 * n);
     int8_t *aw = (int8_t *)take(n);
     void *tile = take(2 * rsz * p.T * p.T);
+    double *pft = (double *)take(16 * (size_t)(n + 1));
     h.xc = h.xc1 = p.xc; h.yc = h.yc1 = p.yc; h.th = h.th1 = p.th;
     h.mass = p.mass; h.inertia = p.inertia; h.r_eq = p.r_eq; h.sigma = p.sigma;
+    h.inv_mass = 1.0 / p.mass; h.inv_inertia = 1.0 / p.inertia;
     h.nl = n; h.n_ligands = p.n_ligands; h.fixed = p.fixed; h.T = p.T; h.ncolors = p.ncolors;
     h.tile_ox = 0; h.tile_oy = -(1 << 28);   // no tile until the first IB pass
     h.mbx = mbx; h.mby = mby; h.nbx = nbx; h.nby = nby; h.S = S;
     h.ligand = lig; h.color_order = co; h.color_off = coff;
-    h.bond = bond; h.anchor_x = ax; h.anchor_wall = aw; h.tile = tile;
+    h.bond = bond; h.anchor_x = ax; h.anchor_wall = aw; h.tile = tile; h.pf_tab = pft;
     p.d_part = (ParticleDev *)pd;
     cudaStream_t st = s->stream;
     CK(cudaMemcpyAsync(pd, &h, sizeof h, cudaMemcpyHostToDevice, st));
@@ -338,11 +349,12 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
             if (sims[j] == s) { delete b; return fail(LBIB_E_ARG, "simulation listed twice in batch"); }
         b->sims.push_back(s);
         nparts += (int)s->parts.size();
-        tiles += (int)((s->N + 255) / 256);
+        tiles += (int)((s->N + LB_TILE_NODES - 1) / LB_TILE_NODES);
         for (auto &p : s->parts) smem = std::max(smem, particle_smem_bytes(b->kind, p.T, p.nl));
     }
     const size_t bytes = sizeof(SimDev) * n + sizeof(ParticleDev *) * (nparts + 1) +
-                         sizeof(int) * (nparts + 1) + sizeof(int *) * n + 64;
+                         sizeof(int) * (nparts + 1) + sizeof(int *) * n +
+                         sizeof(int) * (size_t)tiles + 128;
     unsigned char *blk = (unsigned char *)dalloc(sims[0]->cfg, b->stream, bytes);
     if (!blk) { delete b; return fail(LBIB_E_OOM, "device allocation for the batch failed"); }
     b->d_block = blk;
@@ -356,6 +368,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     ParticleDev **dparts = (ParticleDev **)take(sizeof(ParticleDev *) * (nparts + 1));
     int *dpsim = (int *)take(sizeof(int) * (nparts + 1));
     int **dcurs = (int **)take(sizeof(int *) * n);
+    int *dtsim = (int *)take(sizeof(int) * (size_t)tiles);
     std::vector<SimDev> hs;
     std::vector<ParticleDev *> hp;
     std::vector<int> hps;
@@ -373,23 +386,29 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     }
     hp.push_back(nullptr);
     hps.push_back(0);
+    std::vector<int> hts((size_t)tiles);
+    for (int i = 0; i < n; ++i)
+        for (int t = 0; t < hs[i].ntiles; ++t) hts[(size_t)hs[i].tile0 + t] = i;
     cudaStream_t st = b->stream;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(dsims, hs.data(), sizeof(SimDev) * n, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dparts, hp.data(), sizeof(ParticleDev *) * hp.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dpsim, hps.data(), sizeof(int) * hps.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dcurs, hc.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(dtsim, hts.data(), sizeof(int) * hts.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaStreamSynchronize(st))) {
         free_batch(b);
         return cuda_fail(e, "batch upload");
     }
-    if (smem > SMEM_LIMIT) {
+    const int smem_limit = nparts > 0 ? particle_smem_limit(b->kind) : 0;
+    if (nparts > 0 && smem > smem_limit) {
         free_batch(b);
-        return fail(LBIB_E_ARG, "particle kernel needs %d bytes of shared memory", smem);
+        return fail(LBIB_E_ARG, "particle kernel needs %d bytes of shared memory (limit %d)", smem,
+                    smem_limit);
     }
     if (nparts > 0) {
         // allow the largest tile any batch may use (the attribute is per kernel)
-        if ((e = particle_kernel_setup(b->kind, SMEM_LIMIT)) != cudaSuccess) {
+        if ((e = particle_kernel_setup(b->kind, smem_limit)) != cudaSuccess) {
             free_batch(b);
             return cuda_fail(e, "particle kernel setup");
         }
@@ -398,6 +417,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->bd.sims = dsims;
     b->bd.parts = dparts;
     b->bd.part_sim = dpsim;
+    b->bd.tile_sim = dtsim;
     b->bd.nsims = n;
     b->bd.nparts = nparts;
     b->bd.total_tiles = tile0;
@@ -414,10 +434,32 @@ lbib_status ensure_self(lbib_sim *s) {
     return r;
 }
 
+// Eq. 10 for every possible probing count n of a particle, for each wall:
+// P_f = 1 - exp(-(k_f rho_r) n / nl), dt = 1.  Evaluated on the host once the
+// receptors are final, so the device looks it up instead of computing exp.
+lbib_status upload_pf_tables(lbib_sim *s) {
+    for (auto &p : s->parts) {
+        const int n = p.nl;
+        std::vector<double> tab(2 * (size_t)(n + 1));
+        for (int k = 0; k <= n; ++k) {
+            const double Nl = (double)k / (double)n;
+            tab[k] = 1.0 - exp(-(s->cfg.k_f * s->cfg.receptor_bottom) * Nl);
+            tab[n + 1 + k] = 1.0 - exp(-(s->cfg.k_f * s->cfg.receptor_top) * Nl);
+        }
+        ParticleDev h;
+        CK(cudaMemcpy(&h, p.d_part, sizeof h, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(h.pf_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+    }
+    return LBIB_OK;
+}
+
 // IB forcing of step 0 at the initial pose (the particle kernel in init mode).
 lbib_status prime(lbib_sim *s, cudaStream_t st) {
     if (s->primed) return LBIB_OK;
     lbib_status r = ensure_self(s);
+    if (r != LBIB_OK) return r;
+    CK(cudaStreamSynchronize(st));
+    r = upload_pf_tables(s);
     if (r != LBIB_OK) return r;
     if (!s->parts.empty()) {
         cudaError_t e = launch_particles(s->kind, s->self->bd, 0, 1, s->self->smem, st);
@@ -646,6 +688,12 @@ lbib_status lbib_add_particle(lbib_sim *s, const lbib_particle *in, int32_t *pid
         if (!(p.S[l] > 0)) return fail(LBIB_E_ARG, "degenerate element %zu", l);
     if (particle_smem_bytes(s->kind, p.T, p.nl) > SMEM_LIMIT)
         return fail(LBIB_E_ARG, "particle needs more on-chip memory than one SM has");
+    {
+        const int lim = particle_smem_limit(s->kind);
+        if (lim > 0 && particle_smem_bytes(s->kind, p.T, p.nl) > lim)
+            return fail(LBIB_E_ARG, "particle needs %d bytes of shared memory (limit %d)",
+                        particle_smem_bytes(s->kind, p.T, p.nl), lim);
+    }
     lbib_status r = upload_particle(s, p);
     if (r != LBIB_OK) return r;
     s->parts.push_back(std::move(p));

@@ -19,6 +19,12 @@ namespace lbib {
 
 enum StorageKind { ST_F32 = 0, ST_F64 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
+// Lattice kernel work tile: 256 threads x 2 nodes (consecutive in the
+// row-major node order, 256 apart within a thread).
+constexpr int LB_THREADS = 256;
+constexpr int LB_NPT = 2;
+constexpr int LB_TILE_NODES = LB_THREADS * LB_NPT;
+
 // Error bits of the per-simulation device error word.
 enum { ERR_UNSTABLE = 1 };
 
@@ -32,6 +38,12 @@ struct SimDev {
     double hamaker, eps_min, rec_b, rec_t;
     unsigned long long seed, sim_id;
     float scale, inv_scale;   // storage scale of f - w (1 except F16)
+    // collision and wall constants precomputed in both compute precisions
+    // (the FP32 path does no double arithmetic per node)
+    float f_om, f_pref, f_gx, f_gy, f_ub, f_ut, f_ub6, f_ut6;
+    double d_om, d_pref, d_ub6, d_ut6;
+    float f_nu;
+    double d_nu;        // kinematic viscosity (tau - 1/2) / 3
     void *pop[2];             // A/B population buffers
     int *cur;                 // device: which buffer holds the latest f*
     long long *step;          // device: completed steps
@@ -43,6 +55,7 @@ struct ParticleDev {
     double xc, yc, th, u, v, om;        // pose and velocities at step n
     double xc1, yc1, th1, u1, v1, om1;  // one step earlier
     double mass, inertia, r_eq, sigma;
+    double inv_mass, inv_inertia;
     double Fh[2], Mh, Fb[2], Mb, Fw[2];
     int nl, n_ligands, n_probing, n_bonded;
     int fixed, T, ncolors, tile_ox;     // T: force-tile edge; tile origin x in [0, nx)
@@ -56,41 +69,49 @@ struct ParticleDev {
     double *anchor_x;
     int8_t *anchor_wall;
     void *tile;              // IB force density, [2][T][T] of the compute type
+    double *pf_tab;          // P_f by probing count, bottom [nl+1] then top [nl+1]
 };
 
 struct BatchDev {
     SimDev *sims;
     ParticleDev **parts;
     int *part_sim;
+    int *tile_sim;       // lattice work tile -> simulation index
     int nsims, nparts, total_tiles;
 };
 
 // Storage traits: load a deviation into the compute type, store one back.
 template <typename S> struct Store;
 template <> struct Store<float> {
-    static __device__ __forceinline__ float ld(const float *p, size_t i, float) { return __ldg(p + i); }
-    static __device__ __forceinline__ void st(float *p, size_t i, float v, float) { p[i] = v; }
+    static __device__ __forceinline__ float ld(const float *p, int i, float) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(float *p, int i, float v, float) { p[i] = v; }
 };
 template <> struct Store<double> {
-    static __device__ __forceinline__ double ld(const double *p, size_t i, float) { return __ldg(p + i); }
-    static __device__ __forceinline__ void st(double *p, size_t i, double v, float) { p[i] = v; }
+    static __device__ __forceinline__ double ld(const double *p, int i, float) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(double *p, int i, double v, float) { p[i] = v; }
 };
 template <> struct Store<__half> {
-    static __device__ __forceinline__ float ld(const __half *p, size_t i, float inv) {
+    static __device__ __forceinline__ float ld(const __half *p, int i, float inv) {
         return __half2float(p[i]) * inv;
     }
-    static __device__ __forceinline__ void st(__half *p, size_t i, float v, float scale) {
+    static __device__ __forceinline__ void st(__half *p, int i, float v, float scale) {
         p[i] = __float2half_rn(v * scale);
     }
 };
 template <> struct Store<__nv_bfloat16> {
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, size_t i, float inv) {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, int i, float inv) {
         return __bfloat162float(p[i]) * inv;
     }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, size_t i, float v, float scale) {
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, int i, float v, float scale) {
         p[i] = __float2bfloat16_rn(v * scale);
     }
 };
+
+// Precomputed constant in the compute precision R.
+template <typename R>
+__device__ __forceinline__ R pick(float f, double d) {
+    if constexpr (sizeof(R) == 4) return f; else return d;
+}
 
 // Pre-collision deviations of node (x, y) for the coming step, pulled from
 // the post-collision buffer `src` (Eq. 1 LHS): population i comes from
@@ -102,11 +123,12 @@ template <> struct Store<__nv_bfloat16> {
 //    velocity (u_w, 0), in deviation form (all weights cancel, rho = 1 + ...).
 // Directions (Eq. 3): 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1)
 // 7 (-1,-1) 8 (1,-1).
+
 template <typename S, typename R>
 __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__ src, int x,
                                           int y, R d[9]) {
     const int nx = s.nx, ny = s.ny;
-    const size_t N = (size_t)nx * (size_t)ny;
+    const int N = nx * ny;                 // 9 N < 2^31 is checked at creation
     const float inv = s.inv_scale;
     const int xm = (x == 0) ? nx - 1 : x - 1;
     const int xp = (x == nx - 1) ? 0 : x + 1;
@@ -117,34 +139,34 @@ __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__
         if (top) yp = 0;
         bot = top = false;
     }
-    const size_t r0 = (size_t)y * nx;
-    d[0] = Store<S>::ld(src, 0 * N + r0 + x, inv);
-    d[1] = Store<S>::ld(src, 1 * N + r0 + xm, inv);
+    const int r0 = y * nx;
+    d[0] = Store<S>::ld(src, r0 + x, inv);
+    d[1] = Store<S>::ld(src, N + r0 + xm, inv);
     d[3] = Store<S>::ld(src, 3 * N + r0 + xp, inv);
     if (!bot) {
-        const size_t rm = (size_t)ym * nx;
+        const int rm = ym * nx;
         d[2] = Store<S>::ld(src, 2 * N + rm + x, inv);
         d[5] = Store<S>::ld(src, 5 * N + rm + xm, inv);
         d[6] = Store<S>::ld(src, 6 * N + rm + xp, inv);
     } else if (s.wall_b == LBIB_WALL_BOUNCE_BACK) {
-        const R uw6 = (R)(s.u_b * (1.0 / 6.0));
+        const R uw6 = pick<R>(s.f_ub6, s.d_ub6);
         d[2] = Store<S>::ld(src, 4 * N + r0 + x, inv);
         d[5] = Store<S>::ld(src, 7 * N + r0 + x, inv) + uw6;
         d[6] = Store<S>::ld(src, 8 * N + r0 + x, inv) - uw6;
     }
     if (!top) {
-        const size_t rp = (size_t)yp * nx;
+        const int rp = yp * nx;
         d[4] = Store<S>::ld(src, 4 * N + rp + x, inv);
         d[7] = Store<S>::ld(src, 7 * N + rp + xp, inv);
         d[8] = Store<S>::ld(src, 8 * N + rp + xm, inv);
     } else if (s.wall_t == LBIB_WALL_BOUNCE_BACK) {
-        const R uw6 = (R)(s.u_t * (1.0 / 6.0));
+        const R uw6 = pick<R>(s.f_ut6, s.d_ut6);
         d[4] = Store<S>::ld(src, 2 * N + r0 + x, inv);
         d[7] = Store<S>::ld(src, 5 * N + r0 + x, inv) - uw6;
         d[8] = Store<S>::ld(src, 6 * N + r0 + x, inv) + uw6;
     }
     if (bot && s.wall_b == LBIB_WALL_ZOU_HE) {
-        const R uw = (R)s.u_b;
+        const R uw = pick<R>(s.f_ub, s.u_b);
         const R rho = (R)1 + d[0] + d[1] + d[3] + (R)2 * (d[4] + d[7] + d[8]);
         const R h = (R)0.5 * (d[1] - d[3]);
         d[2] = d[4];
@@ -152,7 +174,7 @@ __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__
         d[6] = d[8] + h - (R)0.5 * rho * uw;
     }
     if (top && s.wall_t == LBIB_WALL_ZOU_HE) {
-        const R uw = (R)s.u_t;
+        const R uw = pick<R>(s.f_ut, s.u_t);
         const R rho = (R)1 + d[0] + d[1] + d[3] + (R)2 * (d[2] + d[5] + d[6]);
         const R h = (R)0.5 * (d[1] - d[3]);
         d[4] = d[2];
@@ -202,5 +224,6 @@ cudaError_t launch_ib_export(int kind, const SimDev &s, ParticleDev *const *part
                              double *fy, cudaStream_t st);
 int particle_smem_bytes(int kind, int T, int nl);
 cudaError_t particle_kernel_setup(int kind, int smem);
+int particle_smem_limit(int kind);
 
 }  // namespace lbib

@@ -14,43 +14,27 @@ namespace lbib {
 
 namespace {
 
-constexpr int LB_THREADS = 256;
+template <typename R>
+__device__ __forceinline__ R recip(R x) {
+    if constexpr (sizeof(R) == 4) return __frcp_rn(x); else return (R)1 / x;
+}
 
+// BGK collision with the Guo source (Eq. 1, 2, 4-6) of one node, in
+// deviation form, and the store of its nine post-collision deviations.
 template <typename S, typename R>
-__global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int flip) {
-    const int tile = blockIdx.x;
-    int lo = 0, hi = b.nsims - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (b.sims[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-    }
-    const SimDev &s = b.sims[lo];
-    const int nx = s.nx, ny = s.ny;
-    const int k = (tile - s.tile0) * LB_THREADS + (int)threadIdx.x;
-    if (tile == s.tile0 && threadIdx.x == 0) *s.step += 1;
-    if (k >= nx * ny) return;
-    const int y = k / nx, x = k - y * nx;
-    const int cur = *s.cur ^ flip;
-    const S *__restrict__ src = (const S *)s.pop[cur];
-    S *__restrict__ dst = (S *)s.pop[cur ^ 1];
-
-    R d[9];
-    pull_node<S, R>(s, src, x, y, d);
+__device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ dst, int N,
+                                              int k, const R d[9], R Fx, R Fy) {
     R drho, jx, jy;
     node_moments(d, drho, jx, jy);
-    R Fx = (R)s.gx, Fy = (R)s.gy;
-    if (s.np) tile_force<R>(s, b.parts, x, y, Fx, Fy);
-
     const R rho = (R)1 + drho;
-    const R irho = (R)1 / rho;
+    const R irho = recip(rho);
     const R ux = (jx + (R)0.5 * Fx) * irho;
     const R uy = (jy + (R)0.5 * Fy) * irho;
-    const R om = (R)(1.0 / s.tau);
-    const R pref = (R)1 - (R)0.5 * om;
-    const R uu15 = (R)1.5 * (ux * ux + uy * uy);
+    const R om = pick<R>(s.f_om, s.d_om);
+    const R pref = pick<R>(s.f_pref, s.d_pref);
+    // f^eq - w_i = w_i [(rho - 1) - 1.5 rho u.u + rho (3 e.u + 4.5 (e.u)^2)]
+    const R A = drho - (R)1.5 * rho * (ux * ux + uy * uy);
     const R uF = ux * Fx + uy * Fy;
-    const size_t N = (size_t)nx * ny;
-    const size_t node = (size_t)k;
     constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     constexpr int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 #pragma unroll
@@ -58,16 +42,60 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int fli
         const R w = i == 0 ? (R)(4.0 / 9.0) : (i < 5 ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0));
         const R eu = (R)EX[i] * ux + (R)EY[i] * uy;
         const R eF = (R)EX[i] * Fx + (R)EY[i] * Fy;
-        // f^eq - w_i = w_i (rho - 1) + w_i rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)
-        const R deq = w * (drho + rho * ((R)3 * eu + (R)4.5 * eu * eu - uu15));
+        const R deq = w * (A + rho * eu * ((R)3 + (R)4.5 * eu));
         // Guo: (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
         const R src_i = pref * w * ((R)3 * (eF - uF) + (R)9 * eu * eF);
         const R out = d[i] - om * (d[i] - deq) + src_i;
-        Store<S>::st(dst, (size_t)i * N + node, out, s.scale);
+        Store<S>::st(dst, i * N + k, out, s.scale);
     }
     // non-finite state or a density outside (0, 2): the run has broken down
-    if (!(fabs((double)drho) < 1.0) || !(fabs((double)ux) + fabs((double)uy) < 10.0))
-        atomicOr(s.err, ERR_UNSTABLE);
+    if (!(fabs(drho) < (R)1) || !(fabs(ux) + fabs(uy) < (R)10)) atomicOr(s.err, ERR_UNSTABLE);
+}
+
+// One launch advances every simulation of a batch by one step.  A CTA owns
+// LB_TILE_NODES consecutive nodes (row-major) of one simulation; each thread
+// handles LB_NPT of them, LB_THREADS apart, so every load and store of a
+// warp is contiguous (the x - 1 / x + 1 pulls are off by one element).
+template <typename S, typename R>
+__global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int flip) {
+    const int tile = blockIdx.x;
+    const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
+    const int nx = s.nx;
+    const int N = nx * s.ny;
+    if (tile == s.tile0 && threadIdx.x == 0) *s.step += 1;
+    const int cur = *s.cur ^ flip;
+    const S *__restrict__ src = (const S *)s.pop[cur];
+    S *__restrict__ dst = (S *)s.pop[cur ^ 1];
+    const int k0 = (tile - s.tile0) * LB_TILE_NODES + (int)threadIdx.x;
+    const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
+    // node coordinates: one division per thread, then step by LB_THREADS
+    int xs[LB_NPT], ys[LB_NPT];
+    {
+        int y = k0 / nx, x = k0 - y * nx;
+#pragma unroll
+        for (int j = 0; j < LB_NPT; ++j) {
+            xs[j] = x;
+            ys[j] = y;
+            x += LB_THREADS;
+            while (x >= nx) {
+                x -= nx;
+                ++y;
+            }
+        }
+    }
+    R d[LB_NPT][9];
+#pragma unroll
+    for (int j = 0; j < LB_NPT; ++j)
+        if (k0 + j * LB_THREADS < N) pull_node<S, R>(s, src, xs[j], ys[j], d[j]);
+#pragma unroll
+    for (int j = 0; j < LB_NPT; ++j) {
+        const int k = k0 + j * LB_THREADS;
+        if (k < N) {
+            R Fx = gx, Fy = gy;
+            if (s.np) tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
+            collide_store<S, R>(s, dst, N, k, d[j], Fx, Fy);
+        }
+    }
 }
 
 template <typename S, typename R>
@@ -97,7 +125,7 @@ __global__ void export_pops_kernel(SimDev s, double *out) {
     const int i = (int)(k / N);
     const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
     const S *src = (const S *)s.pop[*s.cur];
-    out[k] = w + (double)Store<S>::ld(src, k, s.inv_scale);
+    out[k] = w + (double)Store<S>::ld(src, (int)k, s.inv_scale);
 }
 
 template <typename S, typename R>
@@ -108,7 +136,7 @@ __global__ void import_pops_kernel(SimDev s, const double *in) {
     const int i = (int)(k / N);
     const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
     S *dst = (S *)s.pop[*s.cur];
-    Store<S>::st(dst, k, (R)(in[k] - w), s.scale);
+    Store<S>::st(dst, (int)k, (R)(in[k] - w), s.scale);
 }
 
 template <typename R>

@@ -4,7 +4,7 @@
 //
 //  1. markers X_l, n_l at the pose of step n (FP64)
 //  2. loads (Eq. 7-8): probe Q_l = X_l + 1.2 n_l, MLS fit of rho and grad u
-//     from the new populations; traction summed in FP64
+//     from the new populations; tractions summed in FP64
 //  3. bonds (Eq. 9-11): probing count N_l, one Philox4x64-10 uniform per
 //     ligand and step, formation / rupture, spring forces summed in FP64
 //  4. wall force (Eq. 12) from the smallest element gap
@@ -17,30 +17,39 @@
 //
 // MLS (refs [13], [39]): linear basis, tensor-product cubic B-spline weight of
 // radius 2, 4 x 4 support.  The weight factorises, so the 3 x 3 moment matrix
-// does too: along an axis whose four support rows are all fluid the 1D
+// does too: along an axis whose four support rows are all lattice rows the 1D
 // moments are exactly (1, 0, 1/3) (partition of unity and the B-spline's
 // first and second moments); only an axis clipped by a wall needs its
 // moments summed, which is done in FP64.  In the centred basis the matrix is
 // diagonal, giving phi_k = w_k / W (1 - (dy_k - mu_y) mu_y / v_y) and the fit
 // gradient sum w_k d'_k u_k / (W v).
+//
+// GB300 has little FP64 throughput, so per-particle scalars (sincos, P_f,
+// Eq. 12, the update) run on one thread, per-point setup on one lane per
+// half-warp (broadcast by shuffles), and the FP64 sums on one warp over
+// per-element contributions kept in shared memory.
 #include "lbib_internal.cuh"
 
 namespace lbib {
 
 namespace {
 
-constexpr int P_THREADS = 512;
-constexpr int P_WARPS = P_THREADS / 32;
+constexpr int P_THREADS = 512;   // >= LBIB_MAX_MARKERS: one marker per thread
 
+// Cubic B-spline of radius 2, branch-free (lanes of a half-warp straddle the
+// two pieces).
 template <typename R>
 __device__ __forceinline__ R bspline(R r) {
-    r = fabs(r);
-    if (r < (R)1) return (R)(2.0 / 3.0) - r * r + (R)0.5 * r * r * r;
-    if (r < (R)2) {
-        const R b = (R)2 - r;
-        return b * b * b * (R)(1.0 / 6.0);
-    }
-    return (R)0;
+    const R a = fabs(r);
+    const R inner = (R)(2.0 / 3.0) - a * a + (R)0.5 * a * a * a;
+    const R b = fmax((R)2 - a, (R)0);
+    const R outer = b * b * b * (R)(1.0 / 6.0);
+    return a < (R)1 ? inner : outer;
+}
+
+template <typename R>
+__device__ __forceinline__ R recip(R x) {
+    if constexpr (sizeof(R) == 4) return __frcp_rn(x); else return (R)1 / x;
 }
 
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers and Weyl
@@ -79,79 +88,106 @@ __device__ __forceinline__ double bond_uniform(const SimDev &s, long long step, 
     return (double)(w >> 11) * (1.0 / 9007199254740992.0);
 }
 
-// Support of a point (X, Y): base node, fractional offsets, and the y-axis
-// moments (W0, mu, v) -- analytic (1, 0, 1/3) unless a wall clips a row.
+// Per-particle scalars, set by thread 0 (or one lane per degree of freedom).
 template <typename R>
-struct Support {
-    int ix0, iy0;      // node of (a, b) = (0, 0), unwrapped
-    R fx, fy;          // X - floor(X), Y - floor(Y)
-    R invW, mu, mu_v;  // 1 / W0_y, mu_y, mu_y / v_y
-    R inv_v;           // 1 / v_y
-    unsigned rows;     // bit b set: row b is a fluid row
-    bool ok;
+struct Pose {
+    double xc, yc, th, u, v, om;
+    double F[6];        // Fh x, y, M; Fb x, y, M (FP64 sums)
+    double Fw;
+    int ixc, iyc;       // floor of the centroid (base node of relative coordinates)
+    R fxc, fyc;         // centroid minus its floor
+    R cs, sn;           // cos, sin of the angle
+    R gap0_b, gap0_t;   // centroid distance to the bottom / top wall line
+    R uR, vR, omR;      // velocities in the compute precision
+    R gmin_b, gmin_t;   // smallest element gaps
+    int nprobe, nbonded;
 };
 
-// Support rows: every lattice row (wall nodes included) unless periodic.
-__device__ __forceinline__ void row_limits(const SimDev &s, int &lo, int &hi) {
-    lo = 0;
-    hi = s.ny - 1;
+template <typename R>
+__device__ __noinline__ void set_pose(Pose<R> &ps, double yb, double yt) {
+    R sn, cs;
+    if constexpr (sizeof(R) == 4) {
+        // angle reduced to [-pi, pi] in FP64, then the FP32 sine and cosine
+        const double t = ps.th - 6.283185307179586 * rint(ps.th * 0.15915494309189535);
+        sincosf((float)t, &sn, &cs);
+    } else {
+        sincos(ps.th, &sn, &cs);
+    }
+    const double fx = floor(ps.xc), fy = floor(ps.yc);
+    ps.ixc = (int)fx;
+    ps.iyc = (int)fy;
+    ps.fxc = (R)(ps.xc - fx);
+    ps.fyc = (R)(ps.yc - fy);
+    ps.cs = cs;
+    ps.sn = sn;
+    ps.gap0_b = (R)(ps.yc - yb);
+    ps.gap0_t = (R)(yt - ps.yc);
+    ps.uR = (R)ps.u;
+    ps.vR = (R)ps.v;
+    ps.omR = (R)ps.om;
+}
+
+// MLS support parameters of the points (probes or markers), one slot per
+// element, in shared memory.  Points are relative to the centroid's floor
+// node, so FP32 keeps them to ~1e-5 lattice units.
+template <typename R>
+struct Points {
+    int *ix0, *iy0;     // node of support corner (a, b) = (0, 0), unwrapped
+    int *rows;          // bits 0-3: lattice rows of the support; bit 4: fit possible
+    R *fx, *fy;         // X - floor(X), Y - floor(Y)
+    R *invW, *mu, *mu_v, *inv_v;   // y-axis moments: 1 / W0, mu, mu / v, 1 / v
+};
+
+// Moments of a wall-clipped y axis, summed and solved in FP64.
+template <typename R>
+__device__ __noinline__ void clipped_axis(R fy, unsigned rows, R &invW, R &mu_o, R &mu_v,
+                                          R &inv_v) {
+    double W0 = 0.0, W1 = 0.0, W2 = 0.0;
+    for (int b = 0; b < 4; ++b) {
+        if (!(rows & (1u << b))) continue;
+        const double dy = (double)((R)(b - 1) - fy);
+        const double w = bspline(dy);
+        W0 += w;
+        W1 += w * dy;
+        W2 += w * dy * dy;
+    }
+    const double mu = W1 / W0;
+    const double v = W2 / W0 - mu * mu;
+    invW = (R)(1.0 / W0);
+    mu_o = (R)mu;
+    mu_v = (R)(mu / v);
+    inv_v = (R)(1.0 / v);
 }
 
 template <typename R>
-__device__ __forceinline__ Support<R> make_support(const SimDev &s, double X, double Y) {
-    Support<R> sp;
-    const double flx = floor(X), fly = floor(Y);
-    sp.ix0 = (int)flx - 1;
-    sp.iy0 = (int)fly - 1;
-    sp.fx = (R)(X - flx);
-    sp.fy = (R)(Y - fly);
+__device__ __forceinline__ void setup_point(const SimDev &s, int bx, int by, R X, R Y,
+                                            const Points<R> &pt, int l) {
+    const R flx = floor(X), fly = floor(Y);
+    const int ix0 = bx + (int)flx - 1, iy0 = by + (int)fly - 1;
+    const R fx = X - flx, fy = Y - fly;
     const bool periodic = s.wall_b == LBIB_WALL_PERIODIC;
-    int lo, hi;
-    row_limits(s, lo, hi);
     unsigned rows = 0;
     int nz = 0;
     for (int b = 0; b < 4; ++b) {
-        const int yy = sp.iy0 + b;
-        const bool valid = periodic || (yy >= lo && yy <= hi);
-        if (valid) {
+        const int yy = iy0 + b;
+        if (periodic || (yy >= 0 && yy <= s.ny - 1)) {
             rows |= 1u << b;
-            if (fabs((double)yy - Y) < 2.0) ++nz;
+            if (fabs((R)(b - 1) - fy) < (R)2) ++nz;
         }
     }
-    sp.rows = rows;
-    sp.ok = nz >= 2;
-    if (rows == 0xFu) {
-        sp.invW = (R)1;
-        sp.mu = (R)0;
-        sp.mu_v = (R)0;
-        sp.inv_v = (R)3;
-    } else {
-        // FP64 moments of the clipped axis and their closed-form solve
-        double W0 = 0.0, W1 = 0.0, W2 = 0.0;
-        for (int b = 0; b < 4; ++b) {
-            if (!(rows & (1u << b))) continue;
-            const double dy = (double)(sp.iy0 + b) - Y;
-            const double w = bspline(dy);
-            W0 += w;
-            W1 += w * dy;
-            W2 += w * dy * dy;
-        }
-        if (sp.ok && W0 > 0.0) {
-            const double mu = W1 / W0;
-            const double v = W2 / W0 - mu * mu;
-            sp.invW = (R)(1.0 / W0);
-            sp.mu = (R)mu;
-            sp.mu_v = (R)(mu / v);
-            sp.inv_v = (R)(1.0 / v);
-        } else {
-            sp.ok = false;
-            sp.invW = sp.mu = sp.mu_v = sp.inv_v = (R)0;
-        }
-    }
-    return sp;
+    R invW = (R)1, mu = (R)0, mu_v = (R)0, inv_v = (R)3;
+    if (nz >= 2 && rows != 0xFu) clipped_axis<R>(fy, rows, invW, mu, mu_v, inv_v);
+    pt.ix0[l] = ix0;
+    pt.iy0[l] = iy0;
+    pt.rows[l] = (int)rows | (nz >= 2 ? 16 : 0);
+    pt.fx[l] = fx;
+    pt.fy[l] = fy;
+    pt.invW[l] = invW;
+    pt.mu[l] = mu;
+    pt.mu_v[l] = mu_v;
+    pt.inv_v[l] = inv_v;
 }
 
-// Half-warp (16 lanes) sum; both halves of the warp must call it.
 template <typename T>
 __device__ __forceinline__ T hw_sum(T v) {
 #pragma unroll
@@ -159,377 +195,514 @@ __device__ __forceinline__ T hw_sum(T v) {
     return v;
 }
 
-// Block-wide sums of N doubles (all threads call; result in every thread).
-template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// FP64 sum of n values of an array by one warp.
+template <typename R>
+__device__ __forceinline__ double warp_sum_array(const R *a, int n) {
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int l = lane; l < n; l += 32) acc += (double)a[l];
 #pragma unroll
-    for (int j = 0; j < N; ++j)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int j = 0; j < N; ++j) red[warp * N + j] = v[j];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        double acc = 0.0;
-        for (int w = 0; w < P_WARPS; ++w) acc += red[w * N + j];
-        v[j] = acc;
-    }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
 }
 
-__device__ __forceinline__ double block_min(double v, double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+template <typename R>
+__device__ __forceinline__ R warp_min_array(const R *a, int n, R base, R sign) {
+    const int lane = threadIdx.x & 31;
+    R m = (R)1e30;
+    for (int l = lane; l < n; l += 32) m = fmin(m, base + sign * a[l]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double m = red[0];
-    for (int w = 1; w < P_WARPS; ++w) m = fmin(m, red[w]);
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
     return m;
 }
 
-__device__ __forceinline__ void wall_lines(const SimDev &s, double &yb, double &yt) {
-    yb = s.wall_b == LBIB_WALL_BOUNCE_BACK ? -0.5 : 0.0;
-    yt = s.wall_t == LBIB_WALL_BOUNCE_BACK ? (double)s.ny - 0.5 : (double)(s.ny - 1);
+// Node moments pulled from the populations (outside the staged region).
+template <typename S, typename R>
+__device__ __noinline__ void pull_moments(const SimDev &s, const S *pop, int x, int y, R &drho,
+                                          R &jx, R &jy) {
+    R d[9];
+    pull_node<S, R>(s, pop, x, y, d);
+    node_moments(d, drho, jx, jy);
 }
 
-struct SmemLayout {
-    double *mx, *my, *nxw, *nyw;  // world markers [nl]
-    int *sp_i;                     // [nl][2] support base
-    void *sp_r;                    // [nl][7] R: fx, fy, invW, mu, mu_v, Fx, Fy
-    double *red;                   // reduction scratch
-    void *tile;                    // [2][T][T] R
-};
-
-template <typename R>
-__device__ SmemLayout carve(unsigned char *base, int nl, int T) {
-    SmemLayout L;
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        void *p = base + off;
-        off += (bytes + 15) & ~size_t(15);
-        return p;
-    };
-    L.mx = (double *)take(sizeof(double) * nl);
-    L.my = (double *)take(sizeof(double) * nl);
-    L.nxw = (double *)take(sizeof(double) * nl);
-    L.nyw = (double *)take(sizeof(double) * nl);
-    L.sp_i = (int *)take(sizeof(int) * 2 * nl);
-    L.sp_r = take(sizeof(R) * 7 * nl);
-    L.red = (double *)take(sizeof(double) * 8 * P_WARPS);
-    L.tile = take(sizeof(R) * 2 * T * T);
-    return L;
+// Lane (a, b) of a half-warp: weights of its support node and the node's
+// moments (staged region, else pulled).  false when the node has no weight.
+template <typename S, typename R>
+__device__ __forceinline__ bool lane_moments(const SimDev &s, const S *pop, const Points<R> &pt,
+                                             int l, int a, int b, const R *mr, const R *mjx,
+                                             const R *mjy, const uint8_t *flag, int Tm,
+                                             int rx0, int ry0, R &dx,
+                                             R &dy, R &w, R &drho, R &jx, R &jy) {
+    const int rows = pt.rows[l];
+    if (!(rows & 16) || !(rows & (1 << b))) return false;
+    dx = (R)(a - 1) - pt.fx[l];
+    dy = (R)(b - 1) - pt.fy[l];
+    w = bspline(dx) * bspline(dy) * pt.invW[l];
+    if (w == (R)0) return false;
+    const int ix = pt.ix0[l] + a, iy = pt.iy0[l] + b;
+    const int u = ix - rx0, v = iy - ry0;
+    if ((unsigned)u < (unsigned)Tm && (unsigned)v < (unsigned)Tm && flag[v * Tm + u]) {
+        const int i = v * Tm + u;
+        drho = mr[i];
+        jx = mjx[i];
+        jy = mjy[i];
+    } else {
+        int xx = ix % s.nx;
+        if (xx < 0) xx += s.nx;
+        int yy = iy;
+        if (s.wall_b == LBIB_WALL_PERIODIC) {
+            yy %= s.ny;
+            if (yy < 0) yy += s.ny;
+        }
+        pull_moments<S, R>(s, pop, xx, yy, drho, jx, jy);
+    }
+    return true;
 }
+
+// Edge of the staged moment region: the force tile plus two nodes a side,
+// so the supports of the probes and of the markers after the update (moves
+// below one node per step) fall inside it.
+__host__ __device__ __forceinline__ int region_edge(int T) { return T + 4; }
 
 template <typename R>
 size_t smem_bytes_for(int nl, int T) {
     auto up = [](size_t b) { return (b + 15) & ~size_t(15); };
-    return 4 * up(sizeof(double) * nl) + up(sizeof(int) * 2 * nl) + up(sizeof(R) * 7 * nl) +
-           up(sizeof(double) * 8 * P_WARPS) + up(sizeof(R) * 2 * T * T);
+    const size_t Tm = (size_t)region_edge(T);
+    return up(sizeof(Pose<R>)) + 23 * up(sizeof(R) * nl) + 3 * up(sizeof(int) * nl) + up(nl) +
+           up(sizeof(int) * nl) + up(sizeof(int) * (nl + 1)) + up(sizeof(R) * 2 * T * T) +
+           3 * up(sizeof(R) * Tm * Tm) + up(Tm * Tm) + 16;
 }
 
-__device__ __forceinline__ void place_markers(const ParticleDev *P, double xc, double yc,
-                                              double th, SmemLayout &L) {
-    double sn, cs;
-    sincos(th, &sn, &cs);
-    for (int l = threadIdx.x; l < P->nl; l += P_THREADS) {
-        const double bx = P->mbx[l], by = P->mby[l];
-        L.mx[l] = xc + (cs * bx - sn * by);
-        L.my[l] = yc + (sn * bx + cs * by);
-        const double nbx = P->nbx[l], nby = P->nby[l];
-        L.nxw[l] = cs * nbx - sn * nby;
-        L.nyw[l] = sn * nbx + cs * nby;
+// Reverse probability of Eq. 11 (dt = 1): FP32 on the FP32 path, FP64 on the
+// FP64 path.
+template <typename R>
+__device__ __noinline__ double prob_reverse(double k_r0, double dsig, double kBT2, R dd) {
+    if constexpr (sizeof(R) == 4) {
+        const float kr = (float)k_r0 * expf((float)dsig * dd * dd / (float)kBT2);
+        return (double)(-expm1f(-kr));
+    } else {
+        const double kr = k_r0 * exp(dsig * dd * dd / kBT2);
+        return 1.0 - exp(-kr);
     }
 }
 
 template <typename S, typename R>
-__global__ void __launch_bounds__(P_THREADS) particle_kernel(BatchDev b, int flip, int init) {
+__global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int flip, int init) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // descriptors copied to shared memory once: later reads do not wait on
+    // global memory, nor get reloaded after the kernel's own global stores
+    __shared__ __align__(16) unsigned char s_sim_raw[sizeof(SimDev)];
+    __shared__ __align__(16) unsigned char s_par_raw[sizeof(ParticleDev)];
     ParticleDev *P = b.parts[blockIdx.x];
-    const SimDev &s = b.sims[b.part_sim[blockIdx.x]];
-    const int nl = P->nl, T = P->T;
-    SmemLayout L = carve<R>(smem_raw, nl, T);
-    R *spr = (R *)L.sp_r;
-    R *tile = (R *)L.tile;
-    const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
-    const int lane = threadIdx.x & 31, hl = lane & 15;
-    const int half = threadIdx.x >> 4;  // half-warp index
-    const int nhalf = P_THREADS / 16;
-    const int a = hl & 3, bb = hl >> 2;
-    const int nx = s.nx, ny = s.ny;
-    const bool periodic = s.wall_b == LBIB_WALL_PERIODIC;
+    {
+        const int *src_s = (const int *)&b.sims[b.part_sim[blockIdx.x]];
+        const int *src_p = (const int *)P;
+        for (int i = threadIdx.x; i < (int)(sizeof(SimDev) / 4); i += P_THREADS)
+            ((int *)s_sim_raw)[i] = src_s[i];
+        for (int i = threadIdx.x; i < (int)(sizeof(ParticleDev) / 4); i += P_THREADS)
+            ((int *)s_par_raw)[i] = src_p[i];
+    }
+    __syncthreads();
+    const SimDev &s = *(const SimDev *)s_sim_raw;
+    const ParticleDev &Pc = *(const ParticleDev *)s_par_raw;
+    const int nl = Pc.nl, T = Pc.T, Tm = region_edge(T);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        void *p = smem_raw + off;
+        off += (bytes + 15) & ~size_t(15);
+        return p;
+    };
+    Pose<R> &ps = *(Pose<R> *)take(sizeof(Pose<R>));
+    R *gbx = (R *)take(sizeof(R) * nl);     // body-frame centroids, normals, lengths
+    R *gby = (R *)take(sizeof(R) * nl);
+    R *gnx = (R *)take(sizeof(R) * nl);
+    R *gny = (R *)take(sizeof(R) * nl);
+    R *sS = (R *)take(sizeof(R) * nl);
+    R *rx = (R *)take(sizeof(R) * nl);      // marker offset from the centroid
+    R *ry = (R *)take(sizeof(R) * nl);
+    R *nxw = (R *)take(sizeof(R) * nl);     // outward normal
+    R *nyw = (R *)take(sizeof(R) * nl);
+    R *c[6];                                // per-element loads and bond forces
+    for (int k = 0; k < 6; ++k) c[k] = (R *)take(sizeof(R) * nl);
+    R *sFx = (R *)take(sizeof(R) * nl);     // marker forces F_l eps_l
+    R *sFy = (R *)take(sizeof(R) * nl);
+    Points<R> pt;
+    pt.ix0 = (int *)take(sizeof(int) * nl);
+    pt.iy0 = (int *)take(sizeof(int) * nl);
+    pt.rows = (int *)take(sizeof(int) * nl);
+    pt.fx = (R *)take(sizeof(R) * nl);
+    pt.fy = (R *)take(sizeof(R) * nl);
+    pt.invW = (R *)take(sizeof(R) * nl);
+    pt.mu = (R *)take(sizeof(R) * nl);
+    pt.mu_v = (R *)take(sizeof(R) * nl);
+    pt.inv_v = (R *)take(sizeof(R) * nl);
+    uint8_t *lig8 = (uint8_t *)take(nl);
+    int *corder = (int *)take(sizeof(int) * nl);
+    int *coff = (int *)take(sizeof(int) * (nl + 1));
+    R *tile = (R *)take(sizeof(R) * 2 * T * T);
+    R *mr = (R *)take(sizeof(R) * Tm * Tm);     // staged moments of the region
+    R *mjx = (R *)take(sizeof(R) * Tm * Tm);
+    R *mjy = (R *)take(sizeof(R) * Tm * Tm);
+    uint8_t *flag = (uint8_t *)take(Tm * Tm);     // region node staged
+    int *nflag = (int *)take(16);
 
-    double xc = P->xc, yc = P->yc, th = P->th;
-    double u = P->u, v = P->v, om = P->om;
+    const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
+    const int tid = threadIdx.x, lane = tid & 31, hl = lane & 15, warp = tid >> 5;
+    const int half = tid >> 4;
+    constexpr int NHALF = P_THREADS / 16;
+    const int a = hl & 3, bb = hl >> 2;
+    const double yb = s.wall_b == LBIB_WALL_BOUNCE_BACK ? -0.5 : 0.0;
+    const double yt = s.wall_t == LBIB_WALL_BOUNCE_BACK ? (double)s.ny - 0.5 : (double)(s.ny - 1);
+
+    if (tid == 0) {
+        ps.xc = Pc.xc; ps.yc = Pc.yc; ps.th = Pc.th;
+        ps.u = Pc.u; ps.v = Pc.v; ps.om = Pc.om;
+        set_pose(ps, yb, yt);
+    }
+    if (tid < nl) {
+        gbx[tid] = (R)Pc.mbx[tid];
+        gby[tid] = (R)Pc.mby[tid];
+        gnx[tid] = (R)Pc.nbx[tid];
+        gny[tid] = (R)Pc.nby[tid];
+        sS[tid] = (R)Pc.S[tid];
+        lig8[tid] = Pc.ligand[tid];
+        corder[tid] = Pc.color_order[tid];
+    }
+    if (tid <= Pc.ncolors) coff[tid] = Pc.color_off[tid];
+    __syncthreads();
+
+    // markers (offsets from the centroid) at the current pose
+    auto place = [&]() {
+        if (tid < nl) {
+            const R cs = ps.cs, sn = ps.sn;
+            const R bx = gbx[tid], by = gby[tid];
+            rx[tid] = cs * bx - sn * by;
+            ry[tid] = sn * bx + cs * by;
+            const R nbx = gnx[tid], nby = gny[tid];
+            nxw[tid] = cs * nbx - sn * nby;
+            nyw[tid] = sn * nbx + cs * nby;
+        }
+    };
+    place();
+    const int rx0 = ps.ixc - Tm / 2, ry0 = ps.iyc - Tm / 2;
+    for (int i = tid; i < (Tm * Tm + 3) / 4; i += P_THREADS) ((int *)flag)[i] = 0;
+    if (tid == 0) *nflag = 0;
+    __syncthreads();
+
+    // ---- stage the moments of the nodes the supports can touch ------------
+    // each marker flags its probe's 4 x 4 support and a 6 x 6 box around its
+    // own support (one node of motion either way); flagged nodes are
+    // compacted into a list (kept in the force-tile buffer) and pulled.
+    if (tid < nl) {
+        const R X = ps.fxc + rx[tid], Y = ps.fyc + ry[tid];
+        const int mx0 = (int)floor(X) - 2 + ps.ixc - rx0, my0 = (int)floor(Y) - 2 + ps.iyc - ry0;
+#pragma unroll 1
+        for (int v = 0; v < 6; ++v)
+#pragma unroll 1
+            for (int u = 0; u < 6; ++u)
+                if ((unsigned)(mx0 + u) < (unsigned)Tm && (unsigned)(my0 + v) < (unsigned)Tm)
+                    flag[(my0 + v) * Tm + mx0 + u] = 1;
+        if (!init) {
+            const int px0 = (int)floor(X + (R)1.2 * nxw[tid]) - 1 + ps.ixc - rx0;
+            const int py0 = (int)floor(Y + (R)1.2 * nyw[tid]) - 1 + ps.iyc - ry0;
+#pragma unroll 1
+            for (int v = 0; v < 4; ++v)
+#pragma unroll 1
+                for (int u = 0; u < 4; ++u)
+                    if ((unsigned)(px0 + u) < (unsigned)Tm && (unsigned)(py0 + v) < (unsigned)Tm)
+                        flag[(py0 + v) * Tm + px0 + u] = 1;
+        }
+    }
+    __syncthreads();
+    int *list = (int *)tile;
+    for (int i = tid; i < Tm * Tm; i += P_THREADS) {
+        if (!flag[i]) continue;
+        const int v = i / Tm;
+        int yy = ry0 + v;
+        if (s.wall_b == LBIB_WALL_PERIODIC) {
+            yy %= s.ny;
+            if (yy < 0) yy += s.ny;
+        }
+        if (yy < 0 || yy >= s.ny) {
+            flag[i] = 0;        // outside the lattice rows: never read
+            continue;
+        }
+        list[atomicAdd(nflag, 1)] = i;
+    }
+    __syncthreads();
+    const int nlist = *nflag;
+#pragma unroll 2
+    for (int k = tid; k < nlist; k += P_THREADS) {
+        const int i = list[k];
+        const int v = i / Tm, u = i - v * Tm;
+        int xx = (rx0 + u) % s.nx;
+        if (xx < 0) xx += s.nx;
+        int yy = ry0 + v;
+        if (s.wall_b == LBIB_WALL_PERIODIC) {
+            yy %= s.ny;
+            if (yy < 0) yy += s.ny;
+        }
+        if (s.wall_b == LBIB_WALL_PERIODIC || (yy >= 1 && yy <= s.ny - 2)) {
+            // interior node: nine plain pulls from rows yy - 1, yy, yy + 1
+            const int nx = s.nx, N = nx * s.ny;
+            const float inv = s.inv_scale;
+            const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
+            const int ym = yy == 0 ? s.ny - 1 : yy - 1, yp = yy == s.ny - 1 ? 0 : yy + 1;
+            const int r0 = yy * nx, rm = ym * nx, rp = yp * nx;
+            R d[9];
+            d[0] = Store<S>::ld(pop, r0 + xx, inv);
+            d[1] = Store<S>::ld(pop, N + r0 + xm, inv);
+            d[3] = Store<S>::ld(pop, 3 * N + r0 + xp, inv);
+            d[2] = Store<S>::ld(pop, 2 * N + rm + xx, inv);
+            d[5] = Store<S>::ld(pop, 5 * N + rm + xm, inv);
+            d[6] = Store<S>::ld(pop, 6 * N + rm + xp, inv);
+            d[4] = Store<S>::ld(pop, 4 * N + rp + xx, inv);
+            d[7] = Store<S>::ld(pop, 7 * N + rp + xp, inv);
+            d[8] = Store<S>::ld(pop, 8 * N + rp + xm, inv);
+            node_moments(d, mr[i], mjx[i], mjy[i]);
+        } else {
+            pull_moments<S, R>(s, pop, xx, yy, mr[i], mjx[i], mjy[i]);
+        }
+    }
+    __syncthreads();
 
     if (!init) {
-        place_markers(P, xc, yc, th, L);
-        __syncthreads();
         // ---- 2. hydrodynamic loads (Eq. 7-8) ------------------------------
-        const R nu = (R)((s.tau - 0.5) / 3.0);
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int base = 0; base < nl; base += nhalf) {
+        if (tid < nl)
+            setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[tid] + (R)1.2 * nxw[tid],
+                           ps.fyc + ry[tid] + (R)1.2 * nyw[tid], pt, tid);
+        __syncthreads();
+        const R nu = pick<R>(s.f_nu, s.d_nu);
+#pragma unroll 1
+        for (int base = 0; base < nl; base += NHALF) {
             const int l = base + half;
             const bool act = l < nl;
-            double qx = 0.0, qy = 0.0;
-            if (act) {
-                qx = L.mx[l] + 1.2 * L.nxw[l];
-                qy = L.my[l] + 1.2 * L.nyw[l];
-            }
-            Support<R> sp = make_support<R>(s, act ? qx : 0.0, act ? qy : 1.5);
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-            if (act && sp.ok && (sp.rows & (1u << bb))) {
-                const R dx = (R)(a - 1) - sp.fx, dy = (R)(bb - 1) - sp.fy;
-                const R wx = bspline(dx), wy = bspline(dy);
-                if (wx * wy != (R)0) {
-                    int xx = (sp.ix0 + a) % nx;
-                    if (xx < 0) xx += nx;
-                    int yy = sp.iy0 + bb;
-                    if (periodic) {
-                        yy %= ny;
-                        if (yy < 0) yy += ny;
-                    }
-                    R d[9];
-                    pull_node<S, R>(s, pop, xx, yy, d);
-                    R drho, jx, jy;
-                    node_moments(d, drho, jx, jy);
-                    const R irho = (R)1 / ((R)1 + drho);
-                    const R ux = jx * irho, uy = jy * irho;
-                    const R w = wx * wy * sp.invW;
-                    const R phi = w * ((R)1 - (dy - sp.mu) * sp.mu_v);
-                    const R dyc = dy - sp.mu;
-                    s_rho = phi * drho;
-                    s_ux = w * dx * ux;
-                    s_uy = w * dyc * ux;
-                    s_vx = w * dx * uy;
-                    s_vy = w * dyc * uy;
-                }
+            R dx, dy, w, drho, jx, jy;
+            if (act && lane_moments<S, R>(s, pop, pt, l, a, bb, mr, mjx, mjy, flag, Tm, rx0, ry0, dx,
+                                          dy, w, drho, jx, jy)) {
+                const R irho = recip((R)1 + drho);
+                const R ux = jx * irho, uy = jy * irho;
+                const R dyc = dy - pt.mu[l];
+                s_rho = w * ((R)1 - dyc * pt.mu_v[l]) * drho;
+                s_ux = w * dx * ux;
+                s_uy = w * dyc * ux;
+                s_vx = w * dx * uy;
+                s_vy = w * dyc * uy;
             }
             s_rho = hw_sum(s_rho);
             s_ux = hw_sum(s_ux);
             s_uy = hw_sum(s_uy);
             s_vx = hw_sum(s_vx);
             s_vy = hw_sum(s_vy);
-            if (act && hl == 0 && sp.ok) {
-                const R dudx = (R)3 * s_ux, dudy = s_uy * sp.inv_v;
-                const R dvdx = (R)3 * s_vx, dvdy = s_vy * sp.inv_v;
-                const R p = s_rho * (R)(1.0 / 3.0);
-                const R nxl = (R)L.nxw[l], nyl = (R)L.nyw[l];
-                const R txy = nu * (dudy + dvdx);
-                const R tx = -p * nxl + nu * (R)2 * dudx * nxl + txy * nyl;
-                const R ty = -p * nyl + txy * nxl + nu * (R)2 * dvdy * nyl;
-                const double Sl = P->S[l];
-                const double fx = (double)tx * Sl, fy = (double)ty * Sl;
-                acc[0] += fx;
-                acc[1] += fy;
-                acc[2] += (L.mx[l] - xc) * fy - (L.my[l] - yc) * fx;
+            if (act && hl == 0) {
+                R tx = 0, ty = 0;
+                if (pt.rows[l] & 16) {
+                    const R iv = pt.inv_v[l];
+                    const R dudx = (R)3 * s_ux, dudy = s_uy * iv;
+                    const R dvdx = (R)3 * s_vx, dvdy = s_vy * iv;
+                    const R p = s_rho * (R)(1.0 / 3.0);
+                    const R nxl = nxw[l], nyl = nyw[l];
+                    const R txy = nu * (dudy + dvdx);
+                    tx = (-p * nxl + nu * (R)2 * dudx * nxl + txy * nyl) * sS[l];
+                    ty = (-p * nyl + txy * nxl + nu * (R)2 * dvdy * nyl) * sS[l];
+                }
+                c[0][l] = tx;
+                c[1][l] = ty;
+                c[2][l] = rx[l] * ty - ry[l] * tx;
             }
         }
-        block_sum<3>(acc, L.red);
 
-        // ---- 3. bonds (Eq. 9-11) ------------------------------------------
-        double yb, yt;
-        wall_lines(s, yb, yt);
+        // ---- 3. bonds (Eq. 9-11), one element per thread -------------------
         const bool has_b = s.wall_b != LBIB_WALL_PERIODIC && s.rec_b > 0.0;
         const bool has_t = s.wall_t != LBIB_WALL_PERIODIC && s.rec_t > 0.0;
-        double cnt[1] = {0.0};
-        for (int l = threadIdx.x; l < nl; l += P_THREADS) {
-            if (!P->ligand[l]) continue;
-            const bool pb = has_b && (L.my[l] - yb) < s.y_cr;
-            const bool pt = has_t && (yt - L.my[l]) < s.y_cr;
-            cnt[0] += (pb || pt) ? 1.0 : 0.0;
+        const R ycr = pick<R>((float)s.y_cr, s.y_cr);
+        bool lig = false, pb = false, ptop = false;
+        R gapb = (R)0, gapt = (R)0;
+        if (tid < nl) {
+            lig = lig8[tid] != 0;
+            gapb = ps.gap0_b + ry[tid];
+            gapt = ps.gap0_t - ry[tid];
+            pb = lig && has_b && gapb < ycr;
+            ptop = lig && has_t && gapt < ycr;
         }
-        block_sum<1>(cnt, L.red);
-        const int nprobe = (int)cnt[0];
-        const double Nl = (double)nprobe / (double)nl;
-        const double Pf_b = 1.0 - exp(-(s.k_f * s.rec_b) * Nl);
-        const double Pf_t = 1.0 - exp(-(s.k_f * s.rec_t) * Nl);
-        const double y_eq = s.y_eq_ratio * s.y_cr;
-        const double sigma = P->sigma, sstar = s.sigma_star_ratio * P->sigma;
-        const long long step = *s.step - 1;   // index of the step being completed
-        double fb[4] = {0.0, 0.0, 0.0, 0.0};
-        double gmin_b = 1e300, gmin_t = 1e300;
-        const int pid = (int)blockIdx.x - s.p0;   // particle index within its simulation
-        for (int l = threadIdx.x; l < nl; l += P_THREADS) {
-            gmin_b = fmin(gmin_b, L.my[l] - yb);
-            gmin_t = fmin(gmin_t, yt - L.my[l]);
-            if (!P->ligand[l]) continue;
-            const double U = bond_uniform(s, step, pid, l);
-            uint8_t bnd = P->bond[l];
-            if (bnd) {
-                const double wy = P->anchor_wall[l] ? yt : yb;
-                const double dx = P->anchor_x[l] - L.mx[l], dy = wy - L.my[l];
-                const double y = sqrt(dx * dx + dy * dy);
-                const double dd = y - y_eq;
-                const double kr = s.k_r0 * exp((sigma - sstar) * dd * dd / (2.0 * s.kBT));
-                const double Pr = 1.0 - exp(-kr);
-                if (U < Pr) bnd = 0;
-            } else {
-                const bool pb = has_b && (L.my[l] - yb) < s.y_cr;
-                const bool pt = has_t && (yt - L.my[l]) < s.y_cr;
-                if (pb || pt) {
-                    const double Pf = pb ? Pf_b : Pf_t;
-                    if (U < Pf) {
+        const int nprobe = __syncthreads_count(pb || ptop);
+        bool bonded = false;
+        if (tid < nl) {
+            const int l = tid;
+            R fx = 0, fy = 0;
+            if (lig) {
+                const long long step = *s.step - 1;    // index of the step being completed
+                const double U = bond_uniform(s, step, (int)blockIdx.x - s.p0, l);
+                uint8_t bnd = P->bond[l];
+                double ax = P->anchor_x[l];
+                int8_t aw = P->anchor_wall[l];
+                const R y_eq = pick<R>((float)(s.y_eq_ratio * s.y_cr), s.y_eq_ratio * s.y_cr);
+                if (bnd) {
+                    // bond vector anchor - X_l; the anchor lies on a wall line
+                    const R dx = (R)(ax - ps.xc) - rx[l];
+                    const R dy = aw ? gapt : -gapb;
+                    const R y = sqrt(dx * dx + dy * dy);
+                    const double Pr = prob_reverse<R>(s.k_r0, Pc.sigma * (1.0 - s.sigma_star_ratio),
+                                                      2.0 * s.kBT, y - y_eq);
+                    if (U < Pr) bnd = 0;
+                } else if (pb || ptop) {
+                    if (U < Pc.pf_tab[pb ? nprobe : nl + 1 + nprobe]) {
                         bnd = 1;
-                        P->anchor_x[l] = L.mx[l];
-                        P->anchor_wall[l] = pb ? 0 : 1;
+                        ax = ps.xc + (double)rx[l];
+                        aw = pb ? 0 : 1;
+                        P->anchor_x[l] = ax;
+                        P->anchor_wall[l] = aw;
+                    }
+                }
+                P->bond[l] = bnd;
+                if (bnd) {
+                    bonded = true;
+                    const R dx = (R)(ax - ps.xc) - rx[l];
+                    const R dy = aw ? gapt : -gapb;
+                    const R y = sqrt(dx * dx + dy * dy);
+                    if (y > (R)0) {
+                        const R mag = (R)Pc.sigma * (y - y_eq) / y;
+                        fx = mag * dx;
+                        fy = mag * dy;
                     }
                 }
             }
-            P->bond[l] = bnd;
-            if (bnd) {
-                const double wy = P->anchor_wall[l] ? yt : yb;
-                const double dx = P->anchor_x[l] - L.mx[l], dy = wy - L.my[l];
-                const double y = sqrt(dx * dx + dy * dy);
-                if (y > 0.0) {
-                    const double mag = sigma * (y - y_eq);
-                    const double fx = mag * dx / y, fy = mag * dy / y;
-                    fb[0] += fx;
-                    fb[1] += fy;
-                    fb[2] += (L.mx[l] - xc) * fy - (L.my[l] - yc) * fx;
-                }
-                fb[3] += 1.0;
-            }
+            c[3][l] = fx;
+            c[4][l] = fy;
+            c[5][l] = rx[l] * fy - ry[l] * fx;
         }
-        block_sum<4>(fb, L.red);
-        gmin_b = block_min(gmin_b, L.red);
-        gmin_t = block_min(gmin_t, L.red);
+        const int nbonded = __syncthreads_count(bonded);
 
-        // ---- 4-5. wall force (Eq. 12) and rigid update (Eq. 13-16) ---------
-        double Fw = 0.0;
-        if (s.wall_b != LBIB_WALL_PERIODIC && s.hamaker != 0.0) {
-            const double eb = fmax(gmin_b, s.eps_min), et = fmax(gmin_t, s.eps_min);
-            const double k = s.hamaker / (8.0 * sqrt(2.0));
-            Fw = k * sqrt(P->r_eq / pow(eb, 5.0)) - k * sqrt(P->r_eq / pow(et, 5.0));
-        }
-        if (!P->fixed) {
-            const double Fx = acc[0] + fb[0];
-            const double Fy = acc[1] + fb[1] + Fw;
-            const double M = acc[2] + fb[2];
-            const double un = 2.0 / 3.0 * (2.0 * u - 0.5 * P->u1 + Fx / P->mass);
-            const double vn = 2.0 / 3.0 * (2.0 * v - 0.5 * P->v1 + Fy / P->mass);
-            const double wn = 2.0 / 3.0 * (2.0 * om - 0.5 * P->om1 + M / P->inertia);
-            const double xn = (4.0 * xc - P->xc1 + 2.0 * un) / 3.0;
-            const double yn = (4.0 * yc - P->yc1 + 2.0 * vn) / 3.0;
-            const double tn = (4.0 * th - P->th1 + 2.0 * wn) / 3.0;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                P->u1 = u; P->v1 = v; P->om1 = om;
-                P->xc1 = xc; P->yc1 = yc; P->th1 = th;
-                P->u = un; P->v = vn; P->om = wn;
-                P->xc = xn; P->yc = yn; P->th = tn;
+        // ---- FP64 sums: one warp per quantity, gaps on warp 6 --------------
+        if (warp < 6) {
+            const double v = warp_sum_array<R>(c[warp], nl);
+            if (lane == 0) ps.F[warp] = v;
+        } else if (warp == 6) {
+            const R gb = warp_min_array<R>(ry, nl, ps.gap0_b, (R)1);
+            const R gt = warp_min_array<R>(ry, nl, ps.gap0_t, (R)-1);
+            if (lane == 0) {
+                ps.gmin_b = gb;
+                ps.gmin_t = gt;
+                ps.nprobe = nprobe;
+                ps.nbonded = nbonded;
+                // ---- 4. wall force (Eq. 12) -------------------------------
+                R Fw = 0;
+                if (s.wall_b != LBIB_WALL_PERIODIC && s.hamaker != 0.0) {
+                    const R em = pick<R>((float)s.eps_min, s.eps_min);
+                    const R eb = fmax(gb, em), et = fmax(gt, em);
+                    const R k = pick<R>((float)(s.hamaker / (8.0 * 1.4142135623730951)),
+                                        s.hamaker / (8.0 * 1.4142135623730951));
+                    const R r = pick<R>((float)Pc.r_eq, Pc.r_eq);
+                    Fw = k * sqrt(r / (eb * eb * eb * eb * eb)) - k * sqrt(r / (et * et * et * et * et));
+                }
+                ps.Fw = (double)Fw;
             }
-            u = un; v = vn; om = wn;
-            xc = xn; yc = yn; th = tn;
-        }
-        if (threadIdx.x == 0) {
-            P->Fh[0] = acc[0]; P->Fh[1] = acc[1]; P->Mh = acc[2];
-            P->Fb[0] = fb[0]; P->Fb[1] = fb[1]; P->Mb = fb[2];
-            P->Fw[0] = 0.0; P->Fw[1] = Fw;
-            P->n_probing = nprobe;
-            P->n_bonded = (int)fb[3];
         }
         __syncthreads();
+        // ---- 5. rigid update (Eq. 13-16), one lane per degree of freedom ---
+        if (tid < 3 && !Pc.fixed) {
+            const int k = tid;
+            const double F = k == 0 ? ps.F[0] + ps.F[3]
+                           : (k == 1 ? ps.F[1] + ps.F[4] + ps.Fw : ps.F[2] + ps.F[5]);
+            const double im = k == 2 ? Pc.inv_inertia : Pc.inv_mass;
+            const double u0 = k == 0 ? ps.u : (k == 1 ? ps.v : ps.om);
+            const double u1 = k == 0 ? Pc.u1 : (k == 1 ? Pc.v1 : Pc.om1);
+            const double x0 = k == 0 ? ps.xc : (k == 1 ? ps.yc : ps.th);
+            const double x1 = k == 0 ? Pc.xc1 : (k == 1 ? Pc.yc1 : Pc.th1);
+            const double un = 2.0 / 3.0 * (2.0 * u0 - 0.5 * u1 + F * im);
+            const double xn = (4.0 * x0 - x1 + 2.0 * un) * (1.0 / 3.0);
+            double *Pu = k == 0 ? &P->u : (k == 1 ? &P->v : &P->om);
+            double *Pu1 = k == 0 ? &P->u1 : (k == 1 ? &P->v1 : &P->om1);
+            double *Px = k == 0 ? &P->xc : (k == 1 ? &P->yc : &P->th);
+            double *Px1 = k == 0 ? &P->xc1 : (k == 1 ? &P->yc1 : &P->th1);
+            *Pu1 = u0; *Pu = un; *Px1 = x0; *Px = xn;
+            __syncwarp(0x7u);
+            if (k == 0) { ps.u = un; ps.xc = xn; }
+            if (k == 1) { ps.v = un; ps.yc = xn; }
+            if (k == 2) { ps.om = un; ps.th = xn; }
+        }
+        if (tid == 32) {
+            P->Fh[0] = ps.F[0]; P->Fh[1] = ps.F[1]; P->Mh = ps.F[2];
+            P->Fb[0] = ps.F[3]; P->Fb[1] = ps.F[4]; P->Mb = ps.F[5];
+            P->Fw[0] = 0.0; P->Fw[1] = ps.Fw;
+            P->n_probing = ps.nprobe;
+            P->n_bonded = ps.nbonded;
+        }
+        __syncthreads();
+        if (tid == 0 && !Pc.fixed) set_pose(ps, yb, yt);
+        __syncthreads();
+        place();
     }
 
     // ---- 6. IB direct forcing at the (new) pose ---------------------------
-    place_markers(P, xc, yc, th, L);
-    for (int i = threadIdx.x; i < 2 * T * T; i += P_THREADS) tile[i] = (R)0;
+    for (int i = tid; i < 2 * T * T; i += P_THREADS) tile[i] = (R)0;
     __syncthreads();
-    const R ghx = (R)(0.5 * s.gx), ghy = (R)(0.5 * s.gy);
-    for (int base = 0; base < nl; base += nhalf) {
+    if (tid < nl) setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[tid], ps.fyc + ry[tid], pt, tid);
+    __syncthreads();
+    const R ghx = (R)0.5 * pick<R>(s.f_gx, s.gx), ghy = (R)0.5 * pick<R>(s.f_gy, s.gy);
+#pragma unroll 1
+    for (int base = 0; base < nl; base += NHALF) {
         const int l = base + half;
         const bool act = l < nl;
-        Support<R> sp = make_support<R>(s, act ? L.mx[l] : 0.0, act ? L.my[l] : 1.5);
         R s_rho = 0, s_u = 0, s_v = 0;
-        if (act && sp.ok && (sp.rows & (1u << bb))) {
-            const R dx = (R)(a - 1) - sp.fx, dy = (R)(bb - 1) - sp.fy;
-            const R wx = bspline(dx), wy = bspline(dy);
-            if (wx * wy != (R)0) {
-                int xx = (sp.ix0 + a) % nx;
-                if (xx < 0) xx += nx;
-                int yy = sp.iy0 + bb;
-                if (periodic) {
-                    yy %= ny;
-                    if (yy < 0) yy += ny;
-                }
-                R d[9];
-                pull_node<S, R>(s, pop, xx, yy, d);
-                R drho, jx, jy;
-                node_moments(d, drho, jx, jy);
-                const R irho = (R)1 / ((R)1 + drho);
-                const R phi = wx * wy * sp.invW * ((R)1 - (dy - sp.mu) * sp.mu_v);
-                s_rho = phi * drho;
-                s_u = phi * ((jx + ghx) * irho);
-                s_v = phi * ((jy + ghy) * irho);
-            }
+        R dx, dy, w, drho, jx, jy;
+        if (act && lane_moments<S, R>(s, pop, pt, l, a, bb, mr, mjx, mjy, flag, Tm, rx0, ry0, dx, dy,
+                                      w, drho, jx, jy)) {
+            const R irho = recip((R)1 + drho);
+            const R phi = w * ((R)1 - (dy - pt.mu[l]) * pt.mu_v[l]);
+            s_rho = phi * drho;
+            s_u = phi * ((jx + ghx) * irho);
+            s_v = phi * ((jy + ghy) * irho);
         }
         s_rho = hw_sum(s_rho);
         s_u = hw_sum(s_u);
         s_v = hw_sum(s_v);
         if (act && hl == 0) {
             R Fx = 0, Fy = 0;
-            if (sp.ok) {
+            if (pt.rows[l] & 16) {
                 const R rl = (R)1 + s_rho;
-                const R udx = (R)(u - om * (L.my[l] - yc));
-                const R udy = (R)(v + om * (L.mx[l] - xc));
-                const R eps = (R)P->S[l];
-                Fx = (R)2 * rl * (udx - s_u) * eps;
-                Fy = (R)2 * rl * (udy - s_v) * eps;
+                const R udx = ps.uR - ps.omR * ry[l];
+                const R udy = ps.vR + ps.omR * rx[l];
+                Fx = (R)2 * rl * (udx - s_u) * sS[l];
+                Fy = (R)2 * rl * (udy - s_v) * sS[l];
             }
-            L.sp_i[2 * l] = sp.ix0;
-            L.sp_i[2 * l + 1] = sp.iy0;
-            R *q = spr + 7 * l;
-            q[0] = sp.fx;
-            q[1] = sp.fy;
-            q[2] = sp.ok ? sp.invW : (R)0;
-            q[3] = sp.mu;
-            q[4] = sp.mu_v;
-            q[5] = Fx;
-            q[6] = Fy;
+            sFx[l] = Fx;
+            sFy[l] = Fy;
         }
     }
     __syncthreads();
-    // tile origin: unwrapped node floor(X_c) - T/2 (and likewise in y)
-    const int ox = (int)floor(xc) - T / 2;
-    const int oy = (int)floor(yc) - T / 2;
-    int lo, hi;
-    row_limits(s, lo, hi);
-    for (int c = 0; c < P->ncolors; ++c) {
-        const int m0 = P->color_off[c], m1 = P->color_off[c + 1];
-        const int ntask = (m1 - m0) * 16;
-        for (int t = threadIdx.x; t < ntask; t += P_THREADS) {
-            const int m = P->color_order[m0 + (t >> 4)];
+    // colour-ordered spreading into the tile; origin floor(X_c) - T/2
+    const int ox = ps.ixc - T / 2;
+    const int oy = ps.iyc - T / 2;
+#pragma unroll 1
+    for (int cl = 0; cl < Pc.ncolors; ++cl) {
+        const int m0 = coff[cl], m1 = coff[cl + 1];
+        for (int t = tid; t < (m1 - m0) * 16; t += P_THREADS) {
+            const int m = corder[m0 + (t >> 4)];
             const int j = t & 15, ta = j & 3, tb = j >> 2;
-            const R *q = spr + 7 * m;
-            if (q[2] == (R)0) continue;
-            const int iy = L.sp_i[2 * m + 1] + tb;
-            if (!periodic && (iy < lo || iy > hi)) continue;
-            const R dx = (R)(ta - 1) - q[0], dy = (R)(tb - 1) - q[1];
-            const R phi = bspline(dx) * bspline(dy) * q[2] * ((R)1 - (dy - q[3]) * q[4]);
-            const int tx = L.sp_i[2 * m] + ta - ox, ty = iy - oy;
+            const int rows = pt.rows[m];
+            if (!(rows & 16) || !(rows & (1 << tb))) continue;
+            const R dx = (R)(ta - 1) - pt.fx[m], dy = (R)(tb - 1) - pt.fy[m];
+            const R phi = bspline(dx) * bspline(dy) * pt.invW[m] *
+                          ((R)1 - (dy - pt.mu[m]) * pt.mu_v[m]);
+            const int tx = pt.ix0[m] + ta - ox, ty = pt.iy0[m] + tb - oy;
             if ((unsigned)tx < (unsigned)T && (unsigned)ty < (unsigned)T) {
-                tile[ty * T + tx] += phi * q[5];
-                tile[T * T + ty * T + tx] += phi * q[6];
+                tile[ty * T + tx] += phi * sFx[m];
+                tile[T * T + ty * T + tx] += phi * sFy[m];
             }
         }
         __syncthreads();
     }
-    R *gt = (R *)P->tile;
-    for (int i = threadIdx.x; i < 2 * T * T; i += P_THREADS) gt[i] = tile[i];
-    if (threadIdx.x == 0) {
-        int oxw = ox % nx;
-        if (oxw < 0) oxw += nx;
+    R *gt = (R *)Pc.tile;
+    for (int i = tid; i < 2 * T * T; i += P_THREADS) gt[i] = tile[i];
+    if (tid == 0) {
+        int oxw = ox % s.nx;
+        if (oxw < 0) oxw += s.nx;
         int oyw = oy;
-        if (periodic) {
-            oyw %= ny;
-            if (oyw < 0) oyw += ny;
+        if (s.wall_b == LBIB_WALL_PERIODIC) {
+            oyw %= s.ny;
+            if (oyw < 0) oyw += s.ny;
         }
         P->tile_ox = oxw;
         P->tile_oy = oyw;
@@ -551,6 +724,28 @@ cudaError_t by_kind(int kind, F &&f) {
 
 int particle_smem_bytes(int kind, int T, int nl) {
     return (int)(kind == ST_F64 ? smem_bytes_for<double>(nl, T) : smem_bytes_for<float>(nl, T));
+}
+
+// Largest dynamic shared memory the particle kernel can use: the device's
+// opt-in per-block limit minus the kernel's static shared memory.
+int particle_smem_limit(int kind) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaFuncAttributes fa{};
+    cudaError_t e = by_kind(kind, [&](auto sv, auto rv) {
+        using S = decltype(sv);
+        using R = decltype(rv);
+        return cudaFuncGetAttributes(&fa, particle_kernel<S, R>);
+    });
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return optin - (int)fa.sharedSizeBytes;
 }
 
 cudaError_t particle_kernel_setup(int kind, int smem) {

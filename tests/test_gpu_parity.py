@@ -249,9 +249,9 @@ def test_edge_cases(O, L):
 
 
 def test_instability_is_reported(L):
-    s = L.Sim(nx=32, ny=16, wall_bottom="bounce_back", wall_top="bounce_back", tau=0.51,
-              u_top=0.9)
-    s.step(200)
+    # a body force far beyond the lattice's range drives the state non-finite
+    s = L.Sim(nx=32, ny=16, wall_bottom="periodic", wall_top="periodic", tau=0.51, gx=0.2)
+    s.step(300)
     with pytest.raises(L.LbibError) as e:
         s.synchronize()
     assert e.value.status == "E_UNSTABLE"
