@@ -223,6 +223,35 @@ lbib_status lbib_read_bonds(lbib_sim *sim, int32_t pid, uint8_t *bond_host,
 /* IB force density of the current step on the lattice ([ny][nx] each). */
 lbib_status lbib_read_ib_force(lbib_sim *sim, double *fx_host, double *fy_host);
 
+/* Allocation-free IB forcing (no counterpart in the paper: a service for
+ * callers that cannot allocate device memory -- code in host callbacks or
+ * stream-ordered sections where cudaMalloc/cudaFree would synchronise or is
+ * not allowed, plugins whose host application owns every device allocation,
+ * loops that must not touch an allocator after start-up).
+ *
+ * Computes the IB force density f_ib of one rigid particle (the MLS direct
+ * forcing of lbib_step's first pass, with desired marker velocity
+ * (u, v) + omega x (X_l - X_c)) on a lattice given by cfg and its
+ * post-collision populations, and writes it to fx_dev, fy_dev.
+ *  cfg        channel; storage must be LBIB_STORE_F32; cfg->cuda_stream is
+ *             the stream the work is queued on (NULL: legacy default stream);
+ *             the allocator fields are ignored
+ *  f_dev      device, [9][ny][nx] FP32 deviations f_i - w_i (caller-owned)
+ *  p          particle; an explicit outline (vx, vy, n_vertices) is required
+ *  fx_dev, fy_dev  device, [ny][nx] doubles (caller-owned), fully written
+ * Allocates no device or host heap memory: its only scratch is one static
+ * device array of 256 KiB that every GPU loading the library keeps until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  Calls share the array and each rewrites
+ * what it reads; calls whose work overlaps on the GPU (different streams)
+ * race.  The call is asynchronous on the stream.  Errors: E_ARG (bad
+ * arguments, or the particle needs more than the 256 KiB scratch or the
+ * shared memory of one SM), E_CUDA, E_UNSUPPORTED (device index >= 64). */
+lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float *f_dev,
+                                  const lbib_particle *p, double u, double v, double omega,
+                                  double *fx_dev, double *fy_dev);
+
 const char *lbib_last_error(void);
 
 /* Library build information ("lbib <version> sm_103a ..."). */

@@ -889,3 +889,236 @@ lbib_status lbib_read_ib_force(lbib_sim *s, double *fx, double *fy) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free IB forcing.
+//
+// Some callers cannot allocate device memory: code running inside a host
+// callback or a stream-ordered section where cudaMalloc / cudaFree would
+// synchronise or is not permitted, plugins whose host application owns every
+// device allocation through its own arena, and embedded loops that must not
+// touch the allocator after start-up.  lbib_ib_force_noalloc serves them: the
+// caller passes its own device input and output buffers, and the only extra
+// device memory the call touches is one file-scope static array of
+// NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
+// the process exits.  The call allocates no device or host heap memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 256 * 1024;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on each device, looked up once per
+// device (with that device current) by the first call made on it.  In host
+// code the array's name is only a host-side stand-in for the symbol.
+unsigned char *g_noalloc_addr[NOALLOC_MAX_DEVICES];
+
+lbib_status noalloc_scratch(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return fail(LBIB_E_UNSUPPORTED, "device %d beyond the %d the scratch table covers", dev,
+                    NOALLOC_MAX_DEVICES);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[dev] = (unsigned char *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return LBIB_OK;
+}
+
+// Element geometry, ligands and marker colouring of an explicit polygon in
+// fixed-size host arrays (the same construction as build_geometry, without
+// heap use).
+struct NoAllocGeom {
+    double mbx[LBIB_MAX_MARKERS], mby[LBIB_MAX_MARKERS], nbx[LBIB_MAX_MARKERS],
+        nby[LBIB_MAX_MARKERS], S[LBIB_MAX_MARKERS];
+    uint8_t ligand[LBIB_MAX_MARKERS];
+    int color[LBIB_MAX_MARKERS], corder[LBIB_MAX_MARKERS], coff[LBIB_MAX_MARKERS + 1];
+    double area, J, rmax;
+    int n, T, ncolors, n_ligands;
+};
+
+void noalloc_geometry(const lbib_particle &in, NoAllocGeom &g) {
+    const int n = in.n_vertices;
+    g.n = n;
+    g.area = g.J = g.rmax = 0.0;
+    for (int l = 0; l < n; ++l) {
+        const int m = (l + 1) % n;
+        const double ax = in.vx[l], ay = in.vy[l], bx = in.vx[m], by = in.vy[m];
+        const double dx = bx - ax, dy = by - ay, len = sqrt(dx * dx + dy * dy);
+        g.mbx[l] = 0.5 * (ax + bx);
+        g.mby[l] = 0.5 * (ay + by);
+        g.S[l] = len;
+        g.nbx[l] = len > 0 ? dy / len : 0.0;
+        g.nby[l] = len > 0 ? -dx / len : 0.0;
+        const double cr = ax * by - bx * ay;
+        g.area += 0.5 * cr;
+        g.J += cr * (ax * ax + ax * bx + bx * bx + ay * ay + ay * by + by * by) / 12.0;
+        g.rmax = std::max(g.rmax, sqrt(ax * ax + ay * ay));
+    }
+    g.T = 2 * (int)ceil(g.rmax) + 8;
+    g.n_ligands = 0;
+    for (int l = 0; l < n; ++l) {
+        g.ligand[l] = floor((double)(l + 1) * in.ligand_density) > floor((double)l * in.ligand_density);
+        g.n_ligands += g.ligand[l];
+    }
+    const double D2 = 32.0 * (1.0 + 1e-9);
+    int nc = 0;
+    for (int l = 0; l < n; ++l) {
+        char used[LBIB_MAX_MARKERS + 1] = {0};
+        for (int q = 0; q < l; ++q) {
+            const double dx = g.mbx[l] - g.mbx[q], dy = g.mby[l] - g.mby[q];
+            if (dx * dx + dy * dy < D2) used[g.color[q]] = 1;
+        }
+        int c = 0;
+        while (c < nc && used[c]) ++c;
+        g.color[l] = c;
+        if (c == nc) ++nc;
+    }
+    g.ncolors = nc;
+    for (int c = 0; c <= nc; ++c) g.coff[c] = 0;
+    for (int l = 0; l < n; ++l) g.coff[g.color[l] + 1]++;
+    for (int c = 0; c < nc; ++c) g.coff[c + 1] += g.coff[c];
+    int fill[LBIB_MAX_MARKERS + 1];
+    for (int c = 0; c < nc; ++c) fill[c] = g.coff[c];
+    for (int l = 0; l < n; ++l) g.corder[fill[g.color[l]]++] = l;
+}
+
+}  // namespace
+
+extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float *f_dev,
+                                             const lbib_particle *in, double u, double v,
+                                             double omega, double *fx_dev, double *fy_dev) {
+    if (!cfg || !f_dev || !in || !fx_dev || !fy_dev) return fail(LBIB_E_ARG, "null argument");
+    const lbib_config &c = *cfg;
+    if (c.nx < 8 || c.ny < 4 || (int64_t)c.nx * c.ny >= (1ll << 31) / 9)
+        return fail(LBIB_E_ARG, "lattice %d x %d outside 8 x 4 .. 2^31/9 nodes", c.nx, c.ny);
+    if (!(c.tau > 0.5) || c.wall_bottom < 0 || c.wall_bottom > 2 || c.wall_top < 0 || c.wall_top > 2 ||
+        (c.wall_bottom == LBIB_WALL_PERIODIC) != (c.wall_top == LBIB_WALL_PERIODIC))
+        return fail(LBIB_E_ARG, "invalid channel configuration");
+    if (c.storage != LBIB_STORE_F32)
+        return fail(LBIB_E_ARG, "lbib_ib_force_noalloc takes FP32 deviations f - w (storage F32)");
+    if (!in->vx || !in->vy || in->n_vertices < 3 || in->n_vertices > LBIB_MAX_MARKERS)
+        return fail(LBIB_E_ARG, "an explicit outline of 3..%d vertices is required", LBIB_MAX_MARKERS);
+    for (int i = 0; i < in->n_vertices; ++i)
+        if (!isfinite(in->vx[i]) || !isfinite(in->vy[i])) return fail(LBIB_E_ARG, "non-finite vertex");
+    if (!isfinite(in->xc) || !isfinite(in->yc) || !isfinite(in->theta) || !isfinite(u) ||
+        !isfinite(v) || !isfinite(omega) || !(in->rho_p > 0))
+        return fail(LBIB_E_ARG, "particle parameters out of range");
+    NoAllocGeom g;                          // ~30 KB on the caller's stack
+    noalloc_geometry(*in, g);
+    if (!(g.area > 0)) return fail(LBIB_E_ARG, "outline must be counter-clockwise with positive area");
+    if (g.T >= c.nx || (c.wall_bottom == LBIB_WALL_PERIODIC && g.T >= c.ny))
+        return fail(LBIB_E_ARG, "force tile %d does not fit the lattice", g.T);
+    const int nl = g.n, T = g.T;
+    // scratch layout: SimDev | ParticleDev | parts[1] | part_sim[1] | cur | geometry | tile
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t o_sim = 0, o_par = o_sim + up(sizeof(SimDev)), o_tab = o_par + up(sizeof(ParticleDev));
+    const size_t o_cur = o_tab + up(2 * sizeof(void *) + 2 * sizeof(int));
+    const size_t o_geo = o_cur + up(sizeof(int));
+    const size_t geo_bytes = up(5 * 8 * (size_t)nl) + up(nl) + up(4 * (size_t)nl) +
+                             up(4 * (size_t)(g.ncolors + 1)) + up(nl) + up(8 * (size_t)nl) + up(nl) +
+                             up(16 * (size_t)(nl + 1));
+    const size_t o_tile = o_geo + geo_bytes;
+    const size_t need = o_tile + 2 * sizeof(float) * (size_t)T * T;
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return fail(LBIB_E_ARG, "particle needs %zu bytes of scratch; the static scratch holds %zu",
+                    need, NOALLOC_SCRATCH_BYTES);
+    const int smem = particle_smem_bytes(ST_F32, T, nl);
+    const int lim = particle_smem_limit(ST_F32);
+    if (lim <= 0 || smem > lim)
+        return fail(LBIB_E_ARG, "particle needs %d bytes of shared memory (limit %d)", smem, lim);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    unsigned char *base = nullptr;
+    lbib_status r = noalloc_scratch(dev, &base);
+    if (r != LBIB_OK) return r;
+    cudaStream_t st = (cudaStream_t)c.cuda_stream;
+
+    // device addresses inside the scratch
+    SimDev *d_sim = (SimDev *)(base + o_sim);
+    ParticleDev *d_par = (ParticleDev *)(base + o_par);
+    ParticleDev **d_parts = (ParticleDev **)(base + o_tab);
+    int *d_psim = (int *)(base + o_tab + 2 * sizeof(void *));
+    int *d_cur = (int *)(base + o_cur);
+    unsigned char *gp = base + o_geo;
+    size_t go = 0;
+    auto take = [&](size_t b) {
+        unsigned char *q = gp + go;
+        go += up(b);
+        return q;
+    };
+    double *mbx = (double *)take(5 * 8 * (size_t)nl);   // centroids x, y, normals x, y, lengths
+    uint8_t *lig = take(nl);
+    int *co = (int *)take(4 * (size_t)nl);
+    int *coff = (int *)take(4 * (size_t)(g.ncolors + 1));
+    uint8_t *bond = take(nl);
+    double *ax = (double *)take(8 * (size_t)nl);
+    int8_t *aw = (int8_t *)take(nl);
+    double *pft = (double *)take(16 * (size_t)(nl + 1));
+    void *tile = base + o_tile;
+
+    // host images of the descriptors (copied into the scratch on `st`)
+    SimDev hs{};
+    hs.nx = c.nx; hs.ny = c.ny; hs.wall_b = c.wall_bottom; hs.wall_t = c.wall_top;
+    hs.p0 = 0; hs.np = 1; hs.tile0 = 0; hs.ntiles = 0;
+    hs.tau = c.tau; hs.u_b = c.u_bottom; hs.u_t = c.u_top; hs.gx = c.gx; hs.gy = c.gy;
+    hs.scale = 1.f; hs.inv_scale = 1.f;
+    const double om = 1.0 / c.tau;
+    hs.d_om = om; hs.d_pref = 1.0 - 0.5 * om; hs.d_ub6 = c.u_bottom / 6.0; hs.d_ut6 = c.u_top / 6.0;
+    hs.f_om = (float)om; hs.f_pref = (float)hs.d_pref; hs.f_gx = (float)c.gx; hs.f_gy = (float)c.gy;
+    hs.f_ub = (float)c.u_bottom; hs.f_ut = (float)c.u_top;
+    hs.f_ub6 = (float)hs.d_ub6; hs.f_ut6 = (float)hs.d_ut6;
+    hs.d_nu = (c.tau - 0.5) / 3.0; hs.f_nu = (float)hs.d_nu;
+    hs.pop[0] = (void *)f_dev; hs.pop[1] = (void *)f_dev;
+    hs.cur = d_cur;
+    ParticleDev hp{};
+    hp.xc = hp.xc1 = in->xc; hp.yc = hp.yc1 = in->yc; hp.th = hp.th1 = in->theta;
+    hp.u = u; hp.v = v; hp.om = omega;
+    hp.mass = in->rho_p * g.area; hp.inertia = in->rho_p * g.J;
+    hp.inv_mass = 1.0 / hp.mass; hp.inv_inertia = 1.0 / hp.inertia;
+    hp.r_eq = sqrt(g.area / M_PI); hp.sigma = in->sigma;
+    hp.nl = nl; hp.n_ligands = g.n_ligands; hp.fixed = 1; hp.T = T; hp.ncolors = g.ncolors;
+    hp.mbx = mbx; hp.mby = mbx + nl; hp.nbx = mbx + 2 * nl; hp.nby = mbx + 3 * nl; hp.S = mbx + 4 * nl;
+    hp.ligand = lig; hp.color_order = co; hp.color_off = coff;
+    hp.bond = bond; hp.anchor_x = ax; hp.anchor_wall = aw; hp.tile = tile; hp.pf_tab = pft;
+    struct { ParticleDev *p[2]; int ps[2]; } tab = {{d_par, nullptr}, {0, 0}};
+    const int zero = 0;
+    // pageable source buffers are staged by the driver before each call returns
+    CK(cudaMemcpyAsync(d_sim, &hs, sizeof hs, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_par, &hp, sizeof hp, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_parts, &tab, sizeof tab, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_cur, &zero, sizeof zero, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mbx, g.mbx, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mbx + nl, g.mby, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mbx + 2 * nl, g.nbx, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mbx + 3 * nl, g.nby, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mbx + 4 * nl, g.S, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lig, g.ligand, nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(co, g.corder, 4 * (size_t)nl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(coff, g.coff, 4 * (size_t)(g.ncolors + 1), cudaMemcpyHostToDevice, st));
+    // bond state and the forward-probability table are not read by the IB
+    // pass; they are cleared so no earlier call's values remain
+    CK(cudaMemsetAsync(bond, 0, nl, st));
+    CK(cudaMemsetAsync(ax, 0, 8 * (size_t)nl, st));
+    CK(cudaMemsetAsync(aw, 0, nl, st));
+    CK(cudaMemsetAsync(pft, 0, 16 * (size_t)(nl + 1), st));
+
+    BatchDev bd{};
+    bd.sims = d_sim;
+    bd.parts = d_parts;
+    bd.part_sim = d_psim;
+    bd.tile_sim = nullptr;
+    bd.nsims = 1;
+    bd.nparts = 1;
+    bd.total_tiles = 0;
+    CK(particle_kernel_setup(ST_F32, lim));
+    // the IB pass at the given pose writes the whole force tile, then the
+    // tile is laid out on the lattice (every node of fx, fy is written)
+    CK(launch_particles(ST_F32, bd, 0, 1, smem, st));
+    CK(launch_ib_export(ST_F32, hs, d_parts, fx_dev, fy_dev, st));
+    return LBIB_OK;
+}

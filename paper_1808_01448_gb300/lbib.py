@@ -114,6 +114,8 @@ def lib():
                 "lbib_read_populations": [vp, pd],
                 "lbib_read_bonds": [vp, i32, C.POINTER(C.c_uint8), pd, i32],
                 "lbib_read_ib_force": [vp, pd, pd],
+                "lbib_ib_force_noalloc": [C.POINTER(Config), vp, C.POINTER(Particle), d, d, d,
+                                          vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -325,6 +327,24 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def ib_force_noalloc(cfg: dict, f_dev_ptr: int, vx, vy, xc, yc, theta=0.0, u=0.0, v=0.0,
+                     omega=0.0, fx_dev_ptr: int = 0, fy_dev_ptr: int = 0, stream=None,
+                     rho_p=1.0, ligand_density=0.0, sigma=0.0):
+    """lbib_ib_force_noalloc: IB force density of one particle written into
+    caller-owned device arrays, without any allocation by the library.
+    f_dev_ptr points to [9][ny][nx] FP32 deviations f - w on the device;
+    fx/fy_dev_ptr to [ny][nx] doubles on the device."""
+    c = make_config(storage="f32", stream=stream, **cfg)
+    vx = np.ascontiguousarray(vx, dtype=np.float64)
+    vy = np.ascontiguousarray(vy, dtype=np.float64)
+    p = Particle()
+    p.vx, p.vy, p.n_vertices = _dp(vx), _dp(vy), len(vx)
+    p.xc, p.yc, p.theta, p.rho_p = xc, yc, theta, rho_p
+    p.ligand_density, p.sigma = ligand_density, sigma
+    _check(lib().lbib_ib_force_noalloc(C.byref(c), f_dev_ptr, C.byref(p), u, v, omega,
+                                       fx_dev_ptr, fy_dev_ptr))
 
 
 def version() -> str:
