@@ -185,18 +185,24 @@ lbib_status lbib_set_populations(lbib_sim *sim, const double *f_post_host);
  * Errors: E_ARG (nsteps < 0), E_CUDA, E_UNSTABLE (reported late). */
 lbib_status lbib_step(lbib_sim *sim, int64_t nsteps);
 
-/* Batched stepping: all simulations of a batch advance together, one
- * lattice kernel and one particle kernel per step over all of them, on the
- * first simulation's stream.  All members must share storage and device.
- * A simulation may be stepped alone or in a batch, not both concurrently. */
+/* Batched stepping: all simulations of a batch advance together, on the
+ * first simulation's stream.  Per step, one lattice launch covers the nodes
+ * away from the particles of all members (on a second, library-owned
+ * stream), one covers the boxes around the particles, and one particle
+ * launch runs the loads, bonds, update and IB forcing of every particle; the
+ * first overlaps the particle launch of the previous step.  All members must
+ * share storage and device.  A simulation may be stepped alone or in a
+ * batch, not both concurrently. */
 lbib_status lbib_batch_create(lbib_sim *const *sims, int32_t n, lbib_batch **out);
 lbib_status lbib_batch_step(lbib_batch *b, int64_t nsteps);
 lbib_status lbib_batch_destroy(lbib_batch *b);
 /* Kernel timing with CUDA events: when nsamples > 0, later batch steps
- * record the duration of sampled lattice and particle kernels on the batch
- * stream.  lbib_batch_kernel_times returns the mean duration (ms) of the
- * samples taken since the last call, [0] lattice, [1] particle, and their
- * counts (it synchronises the stream). */
+ * record the duration of sampled kernels (event records inside the replayed
+ * graphs).  lbib_batch_kernel_times fills mean_ms[3] and count[3] with the
+ * mean duration (ms) and number of samples taken since the last call:
+ * [0] the lattice pass (the bulk pass when particle work is overlapped),
+ * [1] the particle pass, [2] the near-box lattice pass (0 samples when not
+ * overlapped).  It synchronises the stream. */
 lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples);
 lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count);
 

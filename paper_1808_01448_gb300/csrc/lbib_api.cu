@@ -105,12 +105,20 @@ struct lbib_batch {
     // first step's kernels
     int nsamples = 0;
     std::vector<cudaGraphExec_t> tgraphs;
-    std::vector<cudaEvent_t> ev;        // 4 per slot: lb0, lb1, p0, p1
+    std::vector<cudaEvent_t> ev;        // 6 per slot: lattice, particle, near (start, end)
     std::vector<int> replayed;          // slot replayed since the last read
     int next_slot = 0;
     lbib_config acfg{};                 // allocator hook used for d_block
     bool is_self = false;
     bool orphan = false;                // a member was destroyed: the batch is unusable
+    // overlapped stepping: the bulk lattice pass runs on s2 while the particle
+    // pass of the previous step runs on `stream`
+    // (s1: near + particle passes, high priority; s2: bulk passes, low
+    // priority, so freed SMs go to the particle pass first)
+    bool overlap = false;
+    cudaStream_t s1 = nullptr, s2 = nullptr;
+    cudaEvent_t evb[2] = {nullptr, nullptr}, evn[2] = {nullptr, nullptr};
+    cudaEvent_t evfork = nullptr, evjoin = nullptr, evjoin1 = nullptr;
 };
 
 namespace {
@@ -277,6 +285,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     h.inv_mass = 1.0 / p.mass; h.inv_inertia = 1.0 / p.inertia;
     h.nl = n; h.n_ligands = p.n_ligands; h.fixed = p.fixed; h.T = p.T; h.ncolors = p.ncolors;
     h.tile_ox = 0; h.tile_oy = -(1 << 28);   // no tile until the first IB pass
+    h.NB = near_edge(p.T); h.step = 0;
     h.mbx = mbx; h.mby = mby; h.nbx = nbx; h.nby = nby; h.S = S;
     h.ligand = lig; h.color_order = co; h.color_off = coff;
     h.bond = bond; h.anchor_x = ax; h.anchor_wall = aw; h.tile = tile; h.pf_tab = pft;
@@ -310,6 +319,13 @@ void unregister(lbib_batch *b) {
 void free_batch(lbib_batch *b) {
     if (!b) return;
     unregister(b);
+    if (b->s2 && !b->orphan) cudaStreamSynchronize(b->s2);
+    if (b->s1 && !b->orphan) cudaStreamSynchronize(b->s1);
+    for (cudaEvent_t e : {b->evb[0], b->evb[1], b->evn[0], b->evn[1], b->evfork, b->evjoin,
+                          b->evjoin1})
+        if (e) cudaEventDestroy(e);
+    if (b->s2) cudaStreamDestroy(b->s2);
+    if (b->s1) cudaStreamDestroy(b->s1);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (auto g : b->tgraphs)
         if (g) cudaGraphExecDestroy(g);
@@ -339,7 +355,8 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->kind = sims[0]->kind;
     b->stream = sims[0]->stream;
     b->acfg = sims[0]->cfg;
-    int nparts = 0, tiles = 0, smem = 0;
+    int nparts = 0, tiles = 0, smem = 0, near_tiles = 0;
+    bool boxes_fit = true;
     for (int i = 0; i < n; ++i) {
         lbib_sim *s = sims[i];
         if (!s) { delete b; return fail(LBIB_E_ARG, "null simulation in batch"); }
@@ -350,11 +367,18 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         b->sims.push_back(s);
         nparts += (int)s->parts.size();
         tiles += (int)((s->N + LB_TILE_NODES - 1) / LB_TILE_NODES);
-        for (auto &p : s->parts) smem = std::max(smem, particle_smem_bytes(b->kind, p.T, p.nl));
+        for (auto &p : s->parts) {
+            smem = std::max(smem, particle_smem_bytes(b->kind, p.T, p.nl));
+            const int NB = near_edge(p.T);
+            near_tiles += (NB * NB + LB_TILE_NODES - 1) / LB_TILE_NODES;
+            if (NB > s->cfg.nx || (s->cfg.wall_bottom == LBIB_WALL_PERIODIC && NB > s->cfg.ny))
+                boxes_fit = false;
+        }
     }
     const size_t bytes = sizeof(SimDev) * n + sizeof(ParticleDev *) * (nparts + 1) +
                          sizeof(int) * (nparts + 1) + sizeof(int *) * n +
-                         sizeof(int) * (size_t)tiles + 128;
+                         sizeof(int) * (size_t)tiles + sizeof(int) * (size_t)(near_tiles + nparts) +
+                         256;
     unsigned char *blk = (unsigned char *)dalloc(sims[0]->cfg, b->stream, bytes);
     if (!blk) { delete b; return fail(LBIB_E_OOM, "device allocation for the batch failed"); }
     b->d_block = blk;
@@ -369,6 +393,8 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     int *dpsim = (int *)take(sizeof(int) * (nparts + 1));
     int **dcurs = (int **)take(sizeof(int *) * n);
     int *dtsim = (int *)take(sizeof(int) * (size_t)tiles);
+    int *dnpart = (int *)take(sizeof(int) * (size_t)(near_tiles + 1));
+    int *dntile0 = (int *)take(sizeof(int) * (size_t)(nparts + 1));
     std::vector<SimDev> hs;
     std::vector<ParticleDev *> hp;
     std::vector<int> hps;
@@ -389,6 +415,16 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     std::vector<int> hts((size_t)tiles);
     for (int i = 0; i < n; ++i)
         for (int t = 0; t < hs[i].ntiles; ++t) hts[(size_t)hs[i].tile0 + t] = i;
+    std::vector<int> hnp, hnt0;
+    for (int i = 0; i < n; ++i)
+        for (auto &p : sims[i]->parts) {
+            const int NB = near_edge(p.T);
+            hnt0.push_back((int)hnp.size());
+            for (int t = 0; t < (NB * NB + LB_TILE_NODES - 1) / LB_TILE_NODES; ++t)
+                hnp.push_back((int)hnt0.size() - 1);
+        }
+    hnp.push_back(0);
+    hnt0.push_back(0);
     cudaStream_t st = b->stream;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(dsims, hs.data(), sizeof(SimDev) * n, cudaMemcpyHostToDevice, st)) ||
@@ -396,6 +432,8 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         (e = cudaMemcpyAsync(dpsim, hps.data(), sizeof(int) * hps.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dcurs, hc.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dtsim, hts.data(), sizeof(int) * hts.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(dnpart, hnp.data(), sizeof(int) * hnp.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(dntile0, hnt0.data(), sizeof(int) * hnt0.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaStreamSynchronize(st))) {
         free_batch(b);
         return cuda_fail(e, "batch upload");
@@ -421,7 +459,27 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->bd.nsims = n;
     b->bd.nparts = nparts;
     b->bd.total_tiles = tile0;
+    b->bd.near_part = dnpart;
+    b->bd.near_tile0 = dntile0;
+    b->bd.total_near_tiles = near_tiles;
     b->d_curs = dcurs;
+    b->overlap = nparts > 0 && boxes_fit;
+    if (b->overlap) {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if ((e = cudaStreamCreateWithPriority(&b->s1, cudaStreamNonBlocking, greatest)) ||
+            (e = cudaStreamCreateWithPriority(&b->s2, cudaStreamNonBlocking, least)) ||
+            (e = cudaEventCreateWithFlags(&b->evjoin1, cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&b->evb[0], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&b->evb[1], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&b->evn[0], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&b->evn[1], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&b->evfork, cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&b->evjoin, cudaEventDisableTiming))) {
+            free_batch(b);
+            return cuda_fail(e, "batch streams");
+        }
+    }
     *out = b;
     return LBIB_OK;
 }
@@ -469,19 +527,60 @@ lbib_status prime(lbib_sim *s, cudaStream_t st) {
     return LBIB_OK;
 }
 
+// Enqueue nsteps steps.  ev (inside a capture only) receives event records
+// around the first step's kernels: lattice / bulk [0, 1], particle [2, 3],
+// near boxes [4, 5].
 cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
     cudaError_t e = cudaSuccess;
+    // inside a capture, external records become event-record nodes
+    const unsigned fl = cudaEventRecordExternal;
+    auto mark = [&](int i, cudaStream_t st) {
+        return (ev) ? cudaEventRecordWithFlags(ev[i], st, fl) : cudaSuccess;
+    };
+    if (!b->overlap) {
+        for (int k = 0; k < nsteps; ++k) {
+            const int f = k & 1;
+            if (k == 0 && (e = mark(0, b->stream))) return e;
+            if ((e = launch_lattice(b->kind, b->bd, f, 0, b->stream))) return e;
+            if (k == 0 && (e = mark(1, b->stream))) return e;
+            if (k == 0 && (e = mark(2, b->stream))) return e;
+            if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->stream))) return e;
+            if (k == 0 && (e = mark(3, b->stream))) return e;
+            if (ev && k == 0 && ((e = mark(4, b->stream)) || (e = mark(5, b->stream)))) return e;
+        }
+        return e;
+    }
+    // Overlapped form.  Step k: bulk(k) on s2 after near(k-1); near(k) on the
+    // main stream after bulk(k-1); then particle(k), which needs only near(k)
+    // (its staged nodes lie in the near boxes).  bulk(k+1) therefore runs while
+    // particle(k) runs.  The fork / join make the call ordered with all other
+    // work on the main stream.
+    if ((e = cudaEventRecord(b->evfork, b->stream)) ||
+        (e = cudaStreamWaitEvent(b->s1, b->evfork, 0)) ||
+        (e = cudaStreamWaitEvent(b->s2, b->evfork, 0)))
+        return e;
     for (int k = 0; k < nsteps; ++k) {
         const int f = k & 1;
-        // inside a capture, external records become event-record nodes
-        const unsigned fl = cudaEventRecordExternal;
-        if (ev && k == 0 && (e = cudaEventRecordWithFlags(ev[0], b->stream, fl))) return e;
-        if ((e = launch_lattice(b->kind, b->bd, f, b->stream))) return e;
-        if (ev && k == 0 && (e = cudaEventRecordWithFlags(ev[1], b->stream, fl))) return e;
-        if (ev && k == 0 && (e = cudaEventRecordWithFlags(ev[2], b->stream, fl))) return e;
-        if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->stream))) return e;
-        if (ev && k == 0 && (e = cudaEventRecordWithFlags(ev[3], b->stream, fl))) return e;
+        if (k > 0 && (e = cudaStreamWaitEvent(b->s2, b->evn[(k - 1) & 1], 0))) return e;
+        if (k == 0 && (e = mark(0, b->s2))) return e;
+        if ((e = launch_lattice(b->kind, b->bd, f, 1, b->s2))) return e;
+        if (k == 0 && (e = mark(1, b->s2))) return e;
+        if ((e = cudaEventRecord(b->evb[k & 1], b->s2))) return e;
+        if (k > 0 && (e = cudaStreamWaitEvent(b->s1, b->evb[(k - 1) & 1], 0))) return e;
+        if (k == 0 && (e = mark(4, b->s1))) return e;
+        if ((e = launch_lattice(b->kind, b->bd, f, 2, b->s1))) return e;
+        if (k == 0 && (e = mark(5, b->s1))) return e;
+        if ((e = cudaEventRecord(b->evn[k & 1], b->s1))) return e;
+        if (k == 0 && (e = mark(2, b->s1))) return e;
+        // programmatic dependent of the near pass (its prologue overlaps it),
+        // unless an event record sits between them
+        if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->s1, !(ev && k == 0)))) return e;
+        if (k == 0 && (e = mark(3, b->s1))) return e;
     }
+    if ((e = cudaEventRecord(b->evjoin, b->s2)) || (e = cudaEventRecord(b->evjoin1, b->s1)) ||
+        (e = cudaStreamWaitEvent(b->stream, b->evjoin, 0)) ||
+        (e = cudaStreamWaitEvent(b->stream, b->evjoin1, 0)))
+        return e;
     return e;
 }
 
@@ -495,7 +594,8 @@ lbib_status capture(lbib_batch *b, cudaEvent_t *ev, cudaGraphExec_t *out) {
         return cuda_fail(e, "graph capture");
     }
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(out, g, 0);
+    // per-node priorities keep the particle pass ahead of the bulk pass
+    e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     return LBIB_OK;
@@ -759,14 +859,14 @@ lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples) {
         if (g) cudaGraphExecDestroy(g);
     for (auto e : b->ev) cudaEventDestroy(e);
     b->tgraphs.assign(nsamples, nullptr);
-    b->ev.assign(4 * nsamples, nullptr);
+    b->ev.assign(6 * nsamples, nullptr);
     b->replayed.assign(nsamples, 0);
     b->next_slot = 0;
     b->nsamples = nsamples;
     for (auto &e : b->ev) CK(cudaEventCreate(&e));
     // capture every sampled graph now, so that timed stepping does no capture
     for (int s = 0; s < nsamples; ++s) {
-        lbib_status r = capture(b, &b->ev[4 * s], &b->tgraphs[s]);
+        lbib_status r = capture(b, &b->ev[6 * s], &b->tgraphs[s]);
         if (r != LBIB_OK) return r;
     }
     return LBIB_OK;
@@ -776,18 +876,20 @@ lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *cou
     if (!b || !mean_ms || !count) return fail(LBIB_E_ARG, "null argument");
     if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
     CK(cudaStreamSynchronize(b->stream));
-    double sum[2] = {0, 0};
-    int64_t cnt[2] = {0, 0};
+    double sum[3] = {0, 0, 0};
+    int64_t cnt[3] = {0, 0, 0};
     for (int s = 0; s < b->nsamples; ++s) {
         if (!b->replayed[s]) continue;
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, b->ev[4 * s], b->ev[4 * s + 1]));
-        sum[0] += ms; cnt[0]++;
-        CK(cudaEventElapsedTime(&ms, b->ev[4 * s + 2], b->ev[4 * s + 3]));
-        sum[1] += ms; cnt[1]++;
+        for (int k = 0; k < 3; ++k) {
+            if (k == 2 && !b->overlap) continue;
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, b->ev[6 * s + 2 * k], b->ev[6 * s + 2 * k + 1]));
+            sum[k] += ms;
+            cnt[k]++;
+        }
         b->replayed[s] = 0;
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
         mean_ms[k] = cnt[k] ? sum[k] / cnt[k] : 0.0;
         count[k] = cnt[k];
     }
@@ -1082,6 +1184,7 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
     hp.inv_mass = 1.0 / hp.mass; hp.inv_inertia = 1.0 / hp.inertia;
     hp.r_eq = sqrt(g.area / M_PI); hp.sigma = in->sigma;
     hp.nl = nl; hp.n_ligands = g.n_ligands; hp.fixed = 1; hp.T = T; hp.ncolors = g.ncolors;
+    hp.NB = near_edge(T);
     hp.mbx = mbx; hp.mby = mbx + nl; hp.nbx = mbx + 2 * nl; hp.nby = mbx + 3 * nl; hp.S = mbx + 4 * nl;
     hp.ligand = lig; hp.color_order = co; hp.color_off = coff;
     hp.bond = bond; hp.anchor_x = ax; hp.anchor_wall = aw; hp.tile = tile; hp.pf_tab = pft;

@@ -59,7 +59,14 @@ struct ParticleDev {
     double Fh[2], Mh, Fb[2], Mb, Fw[2];
     int nl, n_ligands, n_probing, n_bonded;
     int fixed, T, ncolors, tile_ox;     // T: force-tile edge; tile origin x in [0, nx)
-    int tile_oy, pad0, pad1, pad2;
+    int tile_oy, NB, pad1, pad2;        // NB: edge of the near box
+    long long step;                     // completed steps of this particle (bond draws)
+    // Near box of the lattice step that reads buffer parity p: nodes
+    // [box_ox[p], +NB) x [box_oy[p], +NB), x wrapped to [0, nx).  The particle
+    // kernel of step k leaves the box for step k + 2 in pend_ox / pend_oy; the
+    // near lattice kernel of step k + 1 publishes it into the slot of step k + 2.
+    int box_ox[2], box_oy[2];
+    int pend_ox, pend_oy;
     // body-frame element centroids, outward normals and lengths
     const double *mbx, *mby, *nbx, *nby, *S;
     const uint8_t *ligand;
@@ -77,6 +84,9 @@ struct BatchDev {
     ParticleDev **parts;
     int *part_sim;
     int *tile_sim;       // lattice work tile -> simulation index
+    int *near_part;      // near-box work tile -> batch particle index
+    int *near_tile0;     // first near-box tile of each batch particle
+    int total_near_tiles;
     int nsims, nparts, total_tiles;
 };
 
@@ -85,10 +95,16 @@ template <typename S> struct Store;
 template <> struct Store<float> {
     static __device__ __forceinline__ float ld(const float *p, int i, float) { return __ldg(p + i); }
     static __device__ __forceinline__ void st(float *p, int i, float v, float) { p[i] = v; }
+    // evict-first forms for the bulk pass, so that its stream does not push
+    // the particle data and code out of L2
+    static __device__ __forceinline__ float ld_cs(const float *p, int i, float) { return __ldcs(p + i); }
+    static __device__ __forceinline__ void st_cs(float *p, int i, float v, float) { __stcs(p + i, v); }
 };
 template <> struct Store<double> {
     static __device__ __forceinline__ double ld(const double *p, int i, float) { return __ldg(p + i); }
     static __device__ __forceinline__ void st(double *p, int i, double v, float) { p[i] = v; }
+    static __device__ __forceinline__ double ld_cs(const double *p, int i, float) { return __ldcs(p + i); }
+    static __device__ __forceinline__ void st_cs(double *p, int i, double v, float) { __stcs(p + i, v); }
 };
 template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half *p, int i, float inv) {
@@ -97,6 +113,12 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ void st(__half *p, int i, float v, float scale) {
         p[i] = __float2half_rn(v * scale);
     }
+    static __device__ __forceinline__ float ld_cs(const __half *p, int i, float inv) {
+        return __half2float(__ldcs(p + i)) * inv;
+    }
+    static __device__ __forceinline__ void st_cs(__half *p, int i, float v, float scale) {
+        __stcs(p + i, __float2half_rn(v * scale));
+    }
 };
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, int i, float inv) {
@@ -104,6 +126,12 @@ template <> struct Store<__nv_bfloat16> {
     }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, int i, float v, float scale) {
         p[i] = __float2bfloat16_rn(v * scale);
+    }
+    static __device__ __forceinline__ float ld_cs(const __nv_bfloat16 *p, int i, float inv) {
+        return __bfloat162float(__ldcs(p + i)) * inv;
+    }
+    static __device__ __forceinline__ void st_cs(__nv_bfloat16 *p, int i, float v, float scale) {
+        __stcs(p + i, __float2bfloat16_rn(v * scale));
     }
 };
 
@@ -124,9 +152,12 @@ __device__ __forceinline__ R pick(float f, double d) {
 // Directions (Eq. 3): 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1)
 // 7 (-1,-1) 8 (1,-1).
 
-template <typename S, typename R>
+template <typename S, typename R, bool STREAM = false>
 __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__ src, int x,
                                           int y, R d[9]) {
+    auto ld = [&](int i, float inv) -> R {
+        if constexpr (STREAM) return Store<S>::ld_cs(src, i, inv); else return Store<S>::ld(src, i, inv);
+    };
     const int nx = s.nx, ny = s.ny;
     const int N = nx * ny;                 // 9 N < 2^31 is checked at creation
     const float inv = s.inv_scale;
@@ -140,30 +171,30 @@ __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__
         bot = top = false;
     }
     const int r0 = y * nx;
-    d[0] = Store<S>::ld(src, r0 + x, inv);
-    d[1] = Store<S>::ld(src, N + r0 + xm, inv);
-    d[3] = Store<S>::ld(src, 3 * N + r0 + xp, inv);
+    d[0] = ld(r0 + x, inv);
+    d[1] = ld(N + r0 + xm, inv);
+    d[3] = ld(3 * N + r0 + xp, inv);
     if (!bot) {
         const int rm = ym * nx;
-        d[2] = Store<S>::ld(src, 2 * N + rm + x, inv);
-        d[5] = Store<S>::ld(src, 5 * N + rm + xm, inv);
-        d[6] = Store<S>::ld(src, 6 * N + rm + xp, inv);
+        d[2] = ld(2 * N + rm + x, inv);
+        d[5] = ld(5 * N + rm + xm, inv);
+        d[6] = ld(6 * N + rm + xp, inv);
     } else if (s.wall_b == LBIB_WALL_BOUNCE_BACK) {
         const R uw6 = pick<R>(s.f_ub6, s.d_ub6);
-        d[2] = Store<S>::ld(src, 4 * N + r0 + x, inv);
-        d[5] = Store<S>::ld(src, 7 * N + r0 + x, inv) + uw6;
-        d[6] = Store<S>::ld(src, 8 * N + r0 + x, inv) - uw6;
+        d[2] = ld(4 * N + r0 + x, inv);
+        d[5] = ld(7 * N + r0 + x, inv) + uw6;
+        d[6] = ld(8 * N + r0 + x, inv) - uw6;
     }
     if (!top) {
         const int rp = yp * nx;
-        d[4] = Store<S>::ld(src, 4 * N + rp + x, inv);
-        d[7] = Store<S>::ld(src, 7 * N + rp + xp, inv);
-        d[8] = Store<S>::ld(src, 8 * N + rp + xm, inv);
+        d[4] = ld(4 * N + rp + x, inv);
+        d[7] = ld(7 * N + rp + xp, inv);
+        d[8] = ld(8 * N + rp + xm, inv);
     } else if (s.wall_t == LBIB_WALL_BOUNCE_BACK) {
         const R uw6 = pick<R>(s.f_ut6, s.d_ut6);
-        d[4] = Store<S>::ld(src, 2 * N + r0 + x, inv);
-        d[7] = Store<S>::ld(src, 5 * N + r0 + x, inv) - uw6;
-        d[8] = Store<S>::ld(src, 6 * N + r0 + x, inv) + uw6;
+        d[4] = ld(2 * N + r0 + x, inv);
+        d[7] = ld(5 * N + r0 + x, inv) - uw6;
+        d[8] = ld(6 * N + r0 + x, inv) + uw6;
     }
     if (bot && s.wall_b == LBIB_WALL_ZOU_HE) {
         const R uw = pick<R>(s.f_ub, s.u_b);
@@ -191,6 +222,11 @@ __device__ __forceinline__ void node_moments(const R d[9], R &drho, R &jx, R &jy
     jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
 }
 
+// Edge of the near box: the force tile plus four nodes a side.  It contains
+// the force tile and the staged region (plus its pull halo) of the next
+// particle pass for any motion below one node per step.
+__host__ __device__ __forceinline__ int near_edge(int T) { return T + 8; }
+
 // Force-tile lookup: IB force density at (x, y) summed over the simulation's
 // particles whose tile covers the node.
 template <typename R>
@@ -212,9 +248,11 @@ __device__ __forceinline__ void tile_force(const SimDev &s, ParticleDev *const *
 }
 
 // Launchers (defined in the .cu files), one instantiation per storage kind.
-cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, cudaStream_t st);
+// mode: 0 every node; 1 bulk (nodes outside the near boxes); 2 near boxes only
+cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st);
+// pdl: launched as a programmatic dependent of the previous kernel on st
 cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int init, int smem,
-                             cudaStream_t st);
+                             cudaStream_t st, bool pdl = false);
 cudaError_t launch_fields(int kind, const SimDev &s, ParticleDev *const *parts, double *rho,
                           double *ux, double *uy, cudaStream_t st);
 cudaError_t launch_populations(int kind, const SimDev &s, double *out, cudaStream_t st);

@@ -21,7 +21,7 @@ __device__ __forceinline__ R recip(R x) {
 
 // BGK collision with the Guo source (Eq. 1, 2, 4-6) of one node, in
 // deviation form, and the store of its nine post-collision deviations.
-template <typename S, typename R>
+template <typename S, typename R, bool STREAM = false>
 __device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ dst, int N,
                                               int k, const R d[9], R Fx, R Fy) {
     R drho, jx, jy;
@@ -46,17 +46,36 @@ __device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ d
         // Guo: (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
         const R src_i = pref * w * ((R)3 * (eF - uF) + (R)9 * eu * eF);
         const R out = d[i] - om * (d[i] - deq) + src_i;
-        Store<S>::st(dst, i * N + k, out, s.scale);
+        if constexpr (STREAM) Store<S>::st_cs(dst, i * N + k, out, s.scale);
+        else Store<S>::st(dst, i * N + k, out, s.scale);
     }
     // non-finite state or a density outside (0, 2): the run has broken down
     if (!(fabs(drho) < (R)1) || !(fabs(ux) + fabs(uy) < (R)10)) atomicOr(s.err, ERR_UNSTABLE);
+}
+
+// Node (x, y) inside a near box of the simulation's particles (box slot =
+// the parity of the buffer this step reads).
+__device__ __forceinline__ bool in_near_box(const SimDev &s, ParticleDev *const *parts, int slot,
+                                            int x, int y) {
+    for (int k = 0; k < s.np; ++k) {
+        const ParticleDev *p = parts[s.p0 + k];
+        const int NB = p->NB;
+        int dx = x - p->box_ox[slot];
+        if (dx < 0) dx += s.nx;
+        int dy = y - p->box_oy[slot];
+        if (dy < 0 && s.wall_b == LBIB_WALL_PERIODIC) dy += s.ny;
+        if (dx < NB && (unsigned)dy < (unsigned)NB) return true;
+    }
+    return false;
 }
 
 // One launch advances every simulation of a batch by one step.  A CTA owns
 // LB_TILE_NODES consecutive nodes (row-major) of one simulation; each thread
 // handles LB_NPT of them, LB_THREADS apart, so every load and store of a
 // warp is contiguous (the x - 1 / x + 1 pulls are off by one element).
-template <typename S, typename R>
+// BULK: skip the nodes of the particles' near boxes (they carry no IB force
+// and are updated by lattice_near_kernel, after the particle pass).
+template <typename S, typename R, bool BULK>
 __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int flip) {
     const int tile = blockIdx.x;
     const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
@@ -67,6 +86,7 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int fli
     const S *__restrict__ src = (const S *)s.pop[cur];
     S *__restrict__ dst = (S *)s.pop[cur ^ 1];
     const int k0 = (tile - s.tile0) * LB_TILE_NODES + (int)threadIdx.x;
+    bool skip[LB_NPT];
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
     // node coordinates: one division per thread, then step by LB_THREADS
     int xs[LB_NPT], ys[LB_NPT];
@@ -83,17 +103,78 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int fli
             }
         }
     }
+#pragma unroll
+    for (int j = 0; j < LB_NPT; ++j) {
+        skip[j] = k0 + j * LB_THREADS >= N;
+        if (BULK && !skip[j] && s.np) skip[j] = in_near_box(s, b.parts, cur, xs[j], ys[j]);
+    }
     R d[LB_NPT][9];
 #pragma unroll
     for (int j = 0; j < LB_NPT; ++j)
-        if (k0 + j * LB_THREADS < N) pull_node<S, R>(s, src, xs[j], ys[j], d[j]);
+        if (!skip[j]) pull_node<S, R, BULK>(s, src, xs[j], ys[j], d[j]);
+#pragma unroll
+    for (int j = 0; j < LB_NPT; ++j) {
+        if (!skip[j]) {
+            R Fx = gx, Fy = gy;
+            if (!BULK && s.np) tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
+            collide_store<S, R, BULK>(s, dst, N, k0 + j * LB_THREADS, d[j], Fx, Fy);
+        }
+    }
+}
+
+// The nodes of the near boxes (one box per particle; NB x NB nodes, rows
+// outside the lattice skipped), with the IB force of every force tile of the
+// simulation.  Runs after the particle pass that wrote the tiles.  The first
+// CTA of each particle also publishes the box the last particle pass left for
+// the next step but one.
+template <typename S, typename R>
+__global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, int flip) {
+    // let the particle pass that follows start its prologue now; it waits
+    // for this grid to complete before reading the populations
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int tile = blockIdx.x;
+    const int pi = __ldg(b.near_part + tile);
+    ParticleDev *P = b.parts[pi];
+    const SimDev &s = b.sims[b.part_sim[pi]];
+    const int cur = *s.cur ^ flip;
+    const int NB = P->NB, ox = P->box_ox[cur], oy = P->box_oy[cur];
+    const int t0 = __ldg(b.near_tile0 + pi);
+    if (tile == t0 && threadIdx.x == 0) {
+        P->box_ox[cur ^ 1] = P->pend_ox;
+        P->box_oy[cur ^ 1] = P->pend_oy;
+    }
+    const int nx = s.nx, ny = s.ny, N = nx * ny;
+    const S *__restrict__ src = (const S *)s.pop[cur];
+    S *__restrict__ dst = (S *)s.pop[cur ^ 1];
+    const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
+    const int k0 = (tile - t0) * LB_TILE_NODES + (int)threadIdx.x;
+    int xs[LB_NPT], ys[LB_NPT];
+    bool skip[LB_NPT];
 #pragma unroll
     for (int j = 0; j < LB_NPT; ++j) {
         const int k = k0 + j * LB_THREADS;
-        if (k < N) {
+        const int by = k / NB, bx = k - by * NB;
+        int x = ox + bx;
+        if (x >= nx) x -= nx;
+        int y = oy + by;
+        if (s.wall_b == LBIB_WALL_PERIODIC) {
+            if (y < 0) y += ny;
+            if (y >= ny) y -= ny;
+        }
+        xs[j] = x;
+        ys[j] = y;
+        skip[j] = k >= NB * NB || y < 0 || y >= ny;
+    }
+    R d[LB_NPT][9];
+#pragma unroll
+    for (int j = 0; j < LB_NPT; ++j)
+        if (!skip[j]) pull_node<S, R>(s, src, xs[j], ys[j], d[j]);
+#pragma unroll
+    for (int j = 0; j < LB_NPT; ++j) {
+        if (!skip[j]) {
             R Fx = gx, Fy = gy;
-            if (s.np) tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
-            collide_store<S, R>(s, dst, N, k, d[j], Fx, Fy);
+            tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
+            collide_store<S, R>(s, dst, N, ys[j] * nx + xs[j], d[j], Fx, Fy);
         }
     }
 }
@@ -168,11 +249,17 @@ cudaError_t by_kind(int kind, F &&f) {
 
 }  // namespace
 
-cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, cudaStream_t st) {
+cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st) {
     return by_kind(kind, [&](auto sv, auto rv) {
         using S = decltype(sv);
         using R = decltype(rv);
-        lattice_kernel<S, R><<<b.total_tiles, LB_THREADS, 0, st>>>(b, flip);
+        if (mode == 0) {
+            lattice_kernel<S, R, false><<<b.total_tiles, LB_THREADS, 0, st>>>(b, flip);
+        } else if (mode == 1) {
+            lattice_kernel<S, R, true><<<b.total_tiles, LB_THREADS, 0, st>>>(b, flip);
+        } else if (b.total_near_tiles > 0) {
+            lattice_near_kernel<S, R><<<b.total_near_tiles, LB_THREADS, 0, st>>>(b, flip);
+        }
         return cudaGetLastError();
     });
 }

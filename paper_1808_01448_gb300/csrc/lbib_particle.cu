@@ -151,12 +151,21 @@ __device__ __noinline__ void clipped_axis(R fy, unsigned rows, R &invW, R &mu_o,
         W1 += w * dy;
         W2 += w * dy * dy;
     }
-    const double mu = W1 / W0;
-    const double v = W2 / W0 - mu * mu;
-    invW = (R)(1.0 / W0);
+    // reciprocals: FP32 seed, two Newton-Raphson steps r <- r (2 - a r) in
+    // FP64 (relative error ~1e-7 squares to below FP64 rounding)
+    auto rcp = [](double a) {
+        double r = (double)__frcp_rn((float)a);
+        r = r * (2.0 - a * r);
+        return r * (2.0 - a * r);
+    };
+    const double iW = rcp(W0);
+    const double mu = W1 * iW;
+    const double v = W2 * iW - mu * mu;
+    const double iv = rcp(v);
+    invW = (R)iW;
     mu_o = (R)mu;
-    mu_v = (R)(mu / v);
-    inv_v = (R)(1.0 / v);
+    mu_v = (R)(mu * iv);
+    inv_v = (R)iv;
 }
 
 template <typename R>
@@ -415,21 +424,46 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     }
     __syncthreads();
     int *list = (int *)tile;
-    for (int i = tid; i < Tm * Tm; i += P_THREADS) {
-        if (!flag[i]) continue;
-        const int v = i / Tm;
-        int yy = ry0 + v;
-        if (s.wall_b == LBIB_WALL_PERIODIC) {
-            yy %= s.ny;
-            if (yy < 0) yy += s.ny;
+    const int nwords = (Tm * Tm + 3) / 4;
+    for (int base = 0; base < nwords; base += P_THREADS) {
+        // four flags per thread; one shared atomic per warp
+        const int wi = base + tid;
+        int idx[4], cnt = 0;
+        if (wi < nwords) {
+            const unsigned fw = ((const unsigned *)flag)[wi];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = 4 * wi + q;
+                if (i >= Tm * Tm || !((fw >> (8 * q)) & 0xFFu)) continue;
+                int yy = ry0 + i / Tm;
+                if (s.wall_b == LBIB_WALL_PERIODIC) {
+                    yy %= s.ny;
+                    if (yy < 0) yy += s.ny;
+                }
+                if (yy < 0 || yy >= s.ny) {
+                    flag[i] = 0;        // outside the lattice rows: never read
+                    continue;
+                }
+                idx[cnt++] = i;
+            }
         }
-        if (yy < 0 || yy >= s.ny) {
-            flag[i] = 0;        // outside the lattice rows: never read
-            continue;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        list[atomicAdd(nflag, 1)] = i;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int wbase = 0;
+        if (lane == 31 && total) wbase = atomicAdd(nflag, total);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        const int at = wbase + incl - cnt;
+        for (int q = 0; q < cnt; ++q) list[at + q] = idx[q];
     }
     __syncthreads();
+    // populations of this step come from the lattice pass just before: wait
+    // for it here (everything above reads only particle and geometry data)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nlist = *nflag;
 #pragma unroll 2
     for (int k = tid; k < nlist; k += P_THREADS) {
@@ -532,8 +566,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             const int l = tid;
             R fx = 0, fy = 0;
             if (lig) {
-                const long long step = *s.step - 1;    // index of the step being completed
-                const double U = bond_uniform(s, step, (int)blockIdx.x - s.p0, l);
+                // one draw per (step, element); the step is this particle's count
+                const double U = bond_uniform(s, Pc.step, (int)blockIdx.x - s.p0, l);
                 uint8_t bnd = P->bond[l];
                 double ax = P->anchor_x[l];
                 int8_t aw = P->anchor_wall[l];
@@ -706,6 +740,23 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         }
         P->tile_ox = oxw;
         P->tile_oy = oyw;
+        // near box of the lattice step after next, around the new pose
+        int bx = (ps.ixc - Pc.NB / 2) % s.nx;
+        if (bx < 0) bx += s.nx;
+        int by = ps.iyc - Pc.NB / 2;
+        if (s.wall_b == LBIB_WALL_PERIODIC) {
+            by %= s.ny;
+            if (by < 0) by += s.ny;
+        }
+        P->pend_ox = bx;
+        P->pend_oy = by;
+        if (init) {
+            // before the first step both lattice steps use the initial pose
+            P->box_ox[0] = P->box_ox[1] = bx;
+            P->box_oy[0] = P->box_oy[1] = by;
+        } else {
+            P->step = Pc.step + 1;
+        }
     }
 }
 
@@ -758,13 +809,22 @@ cudaError_t particle_kernel_setup(int kind, int smem) {
 }
 
 cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int init, int smem,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool pdl) {
     if (b.nparts == 0) return cudaSuccess;
     return by_kind(kind, [&](auto sv, auto rv) {
         using S = decltype(sv);
         using R = decltype(rv);
-        particle_kernel<S, R><<<b.nparts, P_THREADS, smem, st>>>(b, flip, init);
-        return cudaGetLastError();
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(b.nparts);
+        cfg.blockDim = dim3(P_THREADS);
+        cfg.dynamicSmemBytes = (size_t)smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = pdl ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, particle_kernel<S, R>, b, flip, init);
     });
 }
 

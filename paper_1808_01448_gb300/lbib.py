@@ -311,10 +311,10 @@ class Batch:
         _check(lib().lbib_batch_set_timing(self._h, int(nsamples)))
 
     def kernel_times(self):
-        ms = (C.c_double * 2)(); cnt = (C.c_int64 * 2)()
+        ms = (C.c_double * 3)(); cnt = (C.c_int64 * 3)()
         _check(lib().lbib_batch_kernel_times(self._h, ms, cnt))
         return {"lattice_ms": ms[0], "lattice_n": cnt[0], "particle_ms": ms[1],
-                "particle_n": cnt[1]}
+                "particle_n": cnt[1], "near_ms": ms[2], "near_n": cnt[2]}
 
     def close(self):
         h = getattr(self, "_h", None)

@@ -159,6 +159,23 @@ def test_full_step_parity_f32(O, L, shape):
     assert np.array_equal(bo, bg)
 
 
+def test_step_without_overlap_when_near_box_exceeds_lattice(O, L):
+    """A particle whose near box (force tile + 8) is wider than the lattice
+    is stepped with the plain lattice pass instead of the overlapped
+    bulk/near split; results still follow the oracle."""
+    cfg, p = adhesion_case(nx=30, ny=40, r=8.0, shape="circle")
+    p["xc"] = 15.0
+    o, g = pair(O, L, cfg, [p])
+    o.step(40)
+    g.step(40)
+    po, pg = o.particle(0), g.particle(0)
+    for k in ("xc", "yc", "theta"):
+        assert pg[k] == pytest.approx(po[k], abs=1e-10), k
+    ro, uo, vo = o.fields()
+    rg, ug, vg = g.fields()
+    assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) < 1e-11
+
+
 def test_poiseuille_circle_workload_f32(O, L):
     """Single circle of radius 10 (63 markers) in the 200 x 50 body-force
     channel with bounce-back walls, tau 0.8, Re 0.1."""
@@ -279,8 +296,8 @@ def test_kernel_timing(L):
     b.set_timing(4)
     b.step(32 * 16)
     t = b.kernel_times()
-    assert t["lattice_n"] == 4 and t["particle_n"] == 4
-    assert 0 < t["lattice_ms"] < 5 and 0 < t["particle_ms"] < 5
+    assert t["lattice_n"] == 4 and t["particle_n"] == 4 and t["near_n"] == 4
+    assert 0 < t["lattice_ms"] < 5 and 0 < t["particle_ms"] < 5 and 0 < t["near_ms"] < 5
     b.close()
 
 
