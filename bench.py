@@ -244,6 +244,7 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     kt = batch.kernel_times()
+    pn = batch.pass_nodes()
     for s in sims:
         s.synchronize()             # raises on a device-side error
     if world > 1:
@@ -288,8 +289,10 @@ def run_gpu(args):
         peak, peak_kind = read_peaks()
         bpu = BYTES_PER_UPDATE[args.storage]
         lat_ms = kt["lattice_ms"]
-        achieved = nodes * bpu / (lat_ms * 1e-3) / 1e9 if lat_ms > 0 else None
-        launches = 2 * args.steps + (1 if args.steps % 2 else 0)
+        # algorithmic bytes of one bulk-pass launch: the nodes it updates
+        achieved = pn["bulk"] * bpu / (lat_ms * 1e-3) / 1e9 if lat_ms > 0 else None
+        per_step = 3 if kt["near_n"] else 2
+        launches = per_step * args.steps + (1 if args.steps % 2 else 0)
         line = {
             "metric": "aggregate MLUPS + % HBM roofline (FP32 vs FP16-storage), p50/p99 sim latency",
             "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -304,6 +307,7 @@ def run_gpu(args):
                          "traffic": ncu_traffic(args.storage), "peak_source": peak_kind,
                          "kernel": "lattice_kernel", "bytes_per_update": bpu,
                          "lattice_kernel_ms": lat_ms, "particle_kernel_ms": kt["particle_ms"],
+                         "near_kernel_ms": kt["near_ms"], "nodes_per_launch": pn["bulk"],
                          "samples": kt["lattice_n"]},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": base,

@@ -205,6 +205,13 @@ lbib_status lbib_batch_destroy(lbib_batch *b);
  * overlapped).  It synchronises the stream. */
 lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples);
 lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count);
+/* Nodes each lattice pass of the next step updates, at the particles'
+ * current near boxes: nodes[0] the lattice (bulk) pass, nodes[1] the
+ * near-box pass (NB x NB per particle, rows outside the lattice left out; 0
+ * when not overlapped), nodes[2] all nodes of the members.  For the
+ * algorithmic bytes of the timed passes.  Synchronises the stream and reads
+ * the particle structs back (a few hundred bytes per particle). */
+lbib_status lbib_batch_pass_nodes(lbib_batch *b, int64_t *nodes);
 
 /* Wait for all enqueued work of the handle; reports deferred device errors. */
 lbib_status lbib_synchronize(lbib_sim *sim);

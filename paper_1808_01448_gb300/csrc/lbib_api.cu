@@ -163,6 +163,8 @@ SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
     d.d_nu = (c.tau - 0.5) / 3.0; d.f_nu = (float)d.d_nu;
     d.pop[0] = s->pop[0]; d.pop[1] = s->pop[1];
     d.cur = s->d_cur; d.step = s->d_step; d.err = s->d_err;
+    // vector path: whole groups of four nodes per row, buffers 32-byte aligned
+    d.vec4 = c.nx % 4 == 0 && ((uintptr_t)s->pop[0] % 32) == 0 && ((uintptr_t)s->pop[1] % 32) == 0;
     return d;
 }
 
@@ -893,6 +895,44 @@ lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *cou
         mean_ms[k] = cnt[k] ? sum[k] / cnt[k] : 0.0;
         count[k] = cnt[k];
     }
+    return LBIB_OK;
+}
+
+lbib_status lbib_batch_pass_nodes(lbib_batch *b, int64_t *nodes) {
+    if (!b || !nodes) return fail(LBIB_E_ARG, "null argument");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
+    CK(cudaStreamSynchronize(b->stream));
+    int64_t bulk = 0, near = 0, total = 0;
+    for (lbib_sim *s : b->sims) {
+        const int nx = s->cfg.nx, ny = s->cfg.ny;
+        const bool periodic = s->cfg.wall_bottom == LBIB_WALL_PERIODIC;
+        total += (int64_t)nx * ny;
+        if (!b->overlap) {
+            bulk += (int64_t)nx * ny;
+            continue;
+        }
+        int cur = 0;
+        CK(cudaMemcpy(&cur, s->d_cur, sizeof(int), cudaMemcpyDeviceToHost));
+        std::vector<uint8_t> in_box((size_t)nx * ny, 0);
+        for (const HostParticle &hp : s->parts) {
+            ParticleDev P;
+            CK(cudaMemcpy(&P, hp.d_part, sizeof(P), cudaMemcpyDeviceToHost));
+            for (int by = 0; by < P.NB; ++by) {
+                int y = P.box_oy[cur] + by;
+                if (periodic) y = ((y % ny) + ny) % ny;
+                if (y < 0 || y >= ny) continue;
+                near += P.NB;   // one row of the box, as the near pass does it
+                for (int bx = 0; bx < P.NB; ++bx) {
+                    const int x = ((P.box_ox[cur] + bx) % nx + nx) % nx;
+                    in_box[(size_t)y * nx + x] = 1;
+                }
+            }
+        }
+        for (uint8_t v : in_box) bulk += !v;
+    }
+    nodes[0] = bulk;
+    nodes[1] = near;
+    nodes[2] = total;
     return LBIB_OK;
 }
 

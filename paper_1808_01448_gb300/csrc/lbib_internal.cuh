@@ -19,10 +19,12 @@ namespace lbib {
 
 enum StorageKind { ST_F32 = 0, ST_F64 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
-// Lattice kernel work tile: 256 threads x 2 nodes (consecutive in the
-// row-major node order, 256 apart within a thread).
+// Lattice kernel work tile: 256 threads x 4 nodes.  Where rows are whole
+// multiples of four nodes (and the buffers suitably aligned) a thread takes
+// four consecutive nodes of one row with vector loads and stores; otherwise
+// four nodes 256 apart in the row-major order.
 constexpr int LB_THREADS = 256;
-constexpr int LB_NPT = 2;
+constexpr int LB_NPT = 4;
 constexpr int LB_TILE_NODES = LB_THREADS * LB_NPT;
 
 // Error bits of the per-simulation device error word.
@@ -33,6 +35,7 @@ struct SimDev {
     int nx, ny, wall_b, wall_t;
     int p0, np;          // particle range in the batch's particle table
     int tile0, ntiles;   // lattice work tiles of this simulation
+    int vec4, pad0;      // rows in whole groups of four aligned nodes
     double tau, u_b, u_t, gx, gy;
     double k_f, k_r0, kBT, sigma_star_ratio, y_cr, y_eq_ratio;
     double hamaker, eps_min, rec_b, rec_t;
@@ -132,6 +135,73 @@ template <> struct Store<__nv_bfloat16> {
     }
     static __device__ __forceinline__ void st_cs(__nv_bfloat16 *p, int i, float v, float scale) {
         __stcs(p + i, __float2bfloat16_rn(v * scale));
+    }
+};
+
+// Four consecutive deviations (16-byte aligned for FP32, 8 for FP16/BF16,
+// 32 for FP64) into / out of the compute type.  STREAM: evict-first.
+template <bool STREAM, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+    if constexpr (STREAM) return __ldcs(p); else return __ldg(p);
+}
+template <bool STREAM, typename T>
+__device__ __forceinline__ void stv(T *p, T v) {
+    if constexpr (STREAM) __stcs(p, v); else *p = v;
+}
+template <typename S, bool STREAM> struct Vec4;
+template <bool STREAM> struct Vec4<float, STREAM> {
+    static __device__ __forceinline__ void ld(const float *p, float, float o[4]) {
+        const float4 v = ldv<STREAM>((const float4 *)p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float o[4], float) {
+        stv<STREAM>((float4 *)p, make_float4(o[0], o[1], o[2], o[3]));
+    }
+};
+template <bool STREAM> struct Vec4<double, STREAM> {
+    static __device__ __forceinline__ void ld(const double *p, float, double o[4]) {
+        const double2 a = ldv<STREAM>((const double2 *)p), b = ldv<STREAM>((const double2 *)p + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double o[4], float) {
+        stv<STREAM>((double2 *)p, make_double2(o[0], o[1]));
+        stv<STREAM>((double2 *)p + 1, make_double2(o[2], o[3]));
+    }
+};
+template <bool STREAM> struct Vec4<__half, STREAM> {
+    static __device__ __forceinline__ void ld(const __half *p, float inv, float o[4]) {
+        const uint2 u = ldv<STREAM>((const uint2 *)p);
+        __half2 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        o[0] = fa.x * inv; o[1] = fa.y * inv; o[2] = fb.x * inv; o[3] = fb.y * inv;
+    }
+    static __device__ __forceinline__ void st(__half *p, const float o[4], float sc) {
+        const __half2 a = __floats2half2_rn(o[0] * sc, o[1] * sc);
+        const __half2 b = __floats2half2_rn(o[2] * sc, o[3] * sc);
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        stv<STREAM>((uint2 *)p, u);
+    }
+};
+template <bool STREAM> struct Vec4<__nv_bfloat16, STREAM> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float inv, float o[4]) {
+        const uint2 u = ldv<STREAM>((const uint2 *)p);
+        __nv_bfloat162 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        o[0] = fa.x * inv; o[1] = fa.y * inv; o[2] = fb.x * inv; o[3] = fb.y * inv;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, const float o[4], float sc) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(o[0] * sc, o[1] * sc);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(o[2] * sc, o[3] * sc);
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        stv<STREAM>((uint2 *)p, u);
     }
 };
 

@@ -20,10 +20,10 @@ __device__ __forceinline__ R recip(R x) {
 }
 
 // BGK collision with the Guo source (Eq. 1, 2, 4-6) of one node, in
-// deviation form, and the store of its nine post-collision deviations.
-template <typename S, typename R, bool STREAM = false>
-__device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ dst, int N,
-                                              int k, const R d[9], R Fx, R Fy) {
+// deviation form: d holds the pre-collision deviations on entry and the
+// post-collision ones on return.
+template <typename R>
+__device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy) {
     R drho, jx, jy;
     node_moments(d, drho, jx, jy);
     const R rho = (R)1 + drho;
@@ -45,12 +45,72 @@ __device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ d
         const R deq = w * (A + rho * eu * ((R)3 + (R)4.5 * eu));
         // Guo: (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
         const R src_i = pref * w * ((R)3 * (eF - uF) + (R)9 * eu * eF);
-        const R out = d[i] - om * (d[i] - deq) + src_i;
-        if constexpr (STREAM) Store<S>::st_cs(dst, i * N + k, out, s.scale);
-        else Store<S>::st(dst, i * N + k, out, s.scale);
+        d[i] = d[i] - om * (d[i] - deq) + src_i;
     }
     // non-finite state or a density outside (0, 2): the run has broken down
     if (!(fabs(drho) < (R)1) || !(fabs(ux) + fabs(uy) < (R)10)) atomicOr(s.err, ERR_UNSTABLE);
+}
+
+template <typename S, typename R, bool STREAM = false>
+__device__ __forceinline__ void store_node(const SimDev &s, S *__restrict__ dst, int N, int k,
+                                           const R d[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if constexpr (STREAM) Store<S>::st_cs(dst, i * N + k, d[i], s.scale);
+        else Store<S>::st(dst, i * N + k, d[i], s.scale);
+    }
+}
+
+template <typename S, typename R, bool STREAM = false>
+__device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ dst, int N,
+                                              int k, R d[9], R Fx, R Fy) {
+    collide_node<R>(s, d, Fx, Fy);
+    store_node<S, R, STREAM>(s, dst, N, k, d);
+}
+
+// Pre-collision deviations of the four nodes (x0 .. x0 + 3, y) of a row away
+// from the walls (or of a lattice periodic in y): one vector load per
+// population plane, plus one scalar load for the node the x shift brings in
+// from the next group (x periodic).  Same values as pull_node per node.
+template <typename S, typename R, bool STREAM>
+__device__ __forceinline__ void pull_group(const SimDev &s, const S *__restrict__ src, int x0,
+                                           int y, R d[4][9]) {
+    const int nx = s.nx, ny = s.ny, N = nx * ny;
+    const float inv = s.inv_scale;
+    const int ym = y == 0 ? ny - 1 : y - 1;
+    const int yp = y == ny - 1 ? 0 : y + 1;
+    const int r0 = y * nx, rm = ym * nx, rp = yp * nx;
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;       // left of the group
+    const int xr = x0 + 4 == nx ? 0 : x0 + 4;        // right of the group
+    auto ld1 = [&](int i) -> R {
+        if constexpr (STREAM) return Store<S>::ld_cs(src, i, inv); else return Store<S>::ld(src, i, inv);
+    };
+    R v[4];
+    // (plane, row of the source, x shift of the pull: +1 pulls from x - 1)
+    auto plane = [&](int i, int row, int sh) {
+        Vec4<S, STREAM>::ld(src + i * N + row + x0, inv, v);
+        if (sh == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) d[j][i] = v[j];
+        } else if (sh > 0) {
+            d[0][i] = ld1(i * N + row + xl);
+#pragma unroll
+            for (int j = 1; j < 4; ++j) d[j][i] = v[j - 1];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) d[j][i] = v[j + 1];
+            d[3][i] = ld1(i * N + row + xr);
+        }
+    };
+    plane(0, r0, 0);
+    plane(1, r0, 1);
+    plane(2, rm, 0);
+    plane(3, r0, -1);
+    plane(4, rp, 0);
+    plane(5, rm, 1);
+    plane(6, rm, -1);
+    plane(7, rp, -1);
+    plane(8, rp, 1);
 }
 
 // Node (x, y) inside a near box of the simulation's particles (box slot =
@@ -69,10 +129,36 @@ __device__ __forceinline__ bool in_near_box(const SimDev &s, ParticleDev *const 
     return false;
 }
 
+// Bit j set: node (x0 + j, y) lies outside every near box (x0 + 3 < nx).
+__device__ __forceinline__ unsigned outside_near_boxes4(const SimDev &s,
+                                                        ParticleDev *const *parts, int slot,
+                                                        int x0, int y) {
+    unsigned keep = 0xFu;
+    for (int k = 0; k < s.np; ++k) {
+        const ParticleDev *p = parts[s.p0 + k];
+        const int NB = p->NB;
+        int dy = y - p->box_oy[slot];
+        if (dy < 0 && s.wall_b == LBIB_WALL_PERIODIC) dy += s.ny;
+        if ((unsigned)dy >= (unsigned)NB) continue;
+        int dx = x0 - p->box_ox[slot];
+        if (dx < 0) dx += s.nx;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int e = dx + j;
+            if (e >= s.nx) e -= s.nx;
+            if (e < NB) keep &= ~(1u << j);
+        }
+    }
+    return keep;
+}
+
 // One launch advances every simulation of a batch by one step.  A CTA owns
-// LB_TILE_NODES consecutive nodes (row-major) of one simulation; each thread
-// handles LB_NPT of them, LB_THREADS apart, so every load and store of a
-// warp is contiguous (the x - 1 / x + 1 pulls are off by one element).
+// LB_TILE_NODES consecutive nodes (row-major) of one simulation.  With rows
+// in whole aligned groups of four, thread t takes nodes 4t .. 4t + 3 of the
+// tile (one row) with vector loads and stores; rows next to a wall take the
+// per-node pull.  Otherwise thread t takes nodes t, t + 256, ... (every
+// scalar access of a warp still contiguous, the x - 1 / x + 1 pulls off by
+// one element).
 // BULK: skip the nodes of the particles' near boxes (they carry no IB force
 // and are updated by lattice_near_kernel, after the particle pass).
 template <typename S, typename R, bool BULK>
@@ -85,9 +171,45 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int fli
     const int cur = *s.cur ^ flip;
     const S *__restrict__ src = (const S *)s.pop[cur];
     S *__restrict__ dst = (S *)s.pop[cur ^ 1];
+    const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
+    R d[LB_NPT][9];
+    if (s.vec4) {
+        const int k = (tile - s.tile0) * LB_TILE_NODES + 4 * (int)threadIdx.x;
+        if (k >= N) return;
+        const int y = k / nx, x0 = k - y * nx;
+        unsigned keep = 0xFu;
+        if (BULK && s.np) {
+            keep = outside_near_boxes4(s, b.parts, cur, x0, y);
+            if (!keep) return;
+        }
+        const bool wall_row = s.wall_b != LBIB_WALL_PERIODIC && (y == 0 || y == s.ny - 1);
+        if (wall_row) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pull_node<S, R, BULK>(s, src, x0 + j, y, d[j]);
+        } else {
+            pull_group<S, R, BULK>(s, src, x0, y, d);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            R Fx = gx, Fy = gy;
+            if (!BULK && s.np) tile_force<R>(s, b.parts, x0 + j, y, Fx, Fy);
+            collide_node<R>(s, d[j], Fx, Fy);
+        }
+        if (keep == 0xFu) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
+                Vec4<S, BULK>::st(dst + i * N + k, o, s.scale);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (keep & (1u << j)) store_node<S, R, BULK>(s, dst, N, k + j, d[j]);
+        }
+        return;
+    }
     const int k0 = (tile - s.tile0) * LB_TILE_NODES + (int)threadIdx.x;
     bool skip[LB_NPT];
-    const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
     // node coordinates: one division per thread, then step by LB_THREADS
     int xs[LB_NPT], ys[LB_NPT];
     {
@@ -108,7 +230,6 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int fli
         skip[j] = k0 + j * LB_THREADS >= N;
         if (BULK && !skip[j] && s.np) skip[j] = in_near_box(s, b.parts, cur, xs[j], ys[j]);
     }
-    R d[LB_NPT][9];
 #pragma unroll
     for (int j = 0; j < LB_NPT; ++j)
         if (!skip[j]) pull_node<S, R, BULK>(s, src, xs[j], ys[j], d[j]);

@@ -108,6 +108,7 @@ def lib():
                 "lbib_batch_destroy": [vp],
                 "lbib_batch_set_timing": [vp, i32],
                 "lbib_batch_kernel_times": [vp, pd, C.POINTER(i64)],
+                "lbib_batch_pass_nodes": [vp, C.POINTER(i64)],
                 "lbib_synchronize": [vp],
                 "lbib_read_state": [vp, C.POINTER(State), C.POINTER(ParticleState), i32,
                                     pd, pd, pd, C.c_size_t],
@@ -315,6 +316,13 @@ class Batch:
         _check(lib().lbib_batch_kernel_times(self._h, ms, cnt))
         return {"lattice_ms": ms[0], "lattice_n": cnt[0], "particle_ms": ms[1],
                 "particle_n": cnt[1], "near_ms": ms[2], "near_n": cnt[2]}
+
+    def pass_nodes(self):
+        """Nodes updated per step by the bulk and near-box lattice passes at
+        the current particle positions, and all nodes of the members."""
+        n = (C.c_int64 * 3)()
+        _check(lib().lbib_batch_pass_nodes(self._h, n))
+        return {"bulk": n[0], "near": n[1], "total": n[2]}
 
     def close(self):
         h = getattr(self, "_h", None)

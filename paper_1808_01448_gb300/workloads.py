@@ -148,6 +148,77 @@ def single_ellipse_sweep(nx: int = 1024, ny: int = 256, radius_eq: float = 20.0,
     return out
 
 
+def design_sweep(seed: int = 3, shapes=("circle", "ar2", "ar3"),
+                 ligand_densities=(0.3, 0.5, 0.7, 0.9), strengths=(1, 2),
+                 reynolds=(0.01, 0.1, 1.0)):
+    """Batched design sweep: one simulation per (shape, ligand density, bond
+    strength, Re), sim_id in that order (72 by default).  Lattice sizes drawn
+    with PCG64(seed): nx uniform in {256, 288, ..., 1024}, ny uniform in
+    {64, 72, ..., 256}.  Shear channel as in the paper; a circle of diameter
+    0.18 ny or an ellipse of equal area, major axis normal to the wall, at
+    rest a gap 3e-3 H above the bottom wall, x = nx / 4.  Returns a list of
+    (config, [particle]) pairs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    combos = [(sh, rl, st, Re) for sh in shapes for rl in ligand_densities
+              for st in strengths for Re in reynolds]
+    nxs = rng.integers(0, (1024 - 256) // 32 + 1, size=len(combos)) * 32 + 256
+    nys = rng.integers(0, (256 - 64) // 8 + 1, size=len(combos)) * 8 + 64
+    out = []
+    for sim_id, ((shape, rl, strength, Re), nx, ny) in enumerate(zip(combos, nxs, nys)):
+        nx, ny = int(nx), int(ny)
+        cfg = shear_channel(nx, ny, Re, seed=seed, sim_id=sim_id)
+        ap = adhesion_params(ny - 1, (cfg["tau"] - 0.5) / 3.0, strength)
+        sigma = ap.pop("sigma")
+        cfg.update(ap)
+        p = adhesion_particle(cfg, shape, 0.09 * ny, x=nx / 4.0, ligand_density=rl,
+                              sigma=sigma)
+        out.append((cfg, [p]))
+    return out
+
+
+def particle_cluster(nx: int = 4096, ny: int = 1024, n_particles: int = 8, Re: float = 1.0,
+                     ligand_density: float = 0.5, strength: int = 2, seed: int = 4,
+                     r_range=(12.0, 24.0)):
+    """Precision-study channel: a shear channel at Re with n_particles
+    circles or equal-area ellipses (AR 2 or 3) near the bottom wall.  Drawn
+    with PCG64(seed): equal-area radius uniform in r_range, shape uniform over
+    {circle, ar2, ar3}, gap between the lowest point and the wall uniform in
+    [3e-3 H, 3 r] (and the top of the particle below 3/4 H); x positions rejection-sampled so that neighbouring
+    centroids are at least 2.5 (r_i + r_j) / 2 apart and clear of each other's
+    extent.  One simulation with several particles: (config, [particles])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cfg = shear_channel(nx, ny, Re, seed=seed, sim_id=0)
+    H = ny - 1
+    ap = adhesion_params(H, (cfg["tau"] - 0.5) / 3.0, strength)
+    sigma = ap.pop("sigma")
+    cfg.update(ap)
+    shapes = ("circle", "ar2", "ar3")
+    placed = []
+    parts = []
+    tries = 0
+    while len(parts) < n_particles:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place the particles")
+        r = float(rng.uniform(*r_range))
+        shape = shapes[int(rng.integers(0, 3))]
+        half_w = r if shape == "circle" else r / math.sqrt(float(shape[2:]))
+        # the particle stays at least a quarter of the channel below the top
+        room = 0.75 * H - 2.0 * half_height(shape, r)
+        if room <= Y0_OVER_H * H:
+            continue
+        gap = float(rng.uniform(Y0_OVER_H * H, min(3.0 * r, room)))
+        x = float(rng.uniform(2.0 * r, nx - 2.0 * r))
+        if any(abs(x - px) < max(2.5 * (r + pr) / 2.0, half_w + pw + 2.0)
+               for px, pr, pw in placed):
+            continue
+        p = adhesion_particle(cfg, shape, r, x=x, ligand_density=ligand_density,
+                              sigma=sigma, gap_over_h=gap / H)
+        placed.append((x, r, half_w))
+        parts.append(p)
+    return cfg, parts
+
+
 def poiseuille_circle(nx: int = 200, ny: int = 50, radius: float = 10.0, tau: float = 0.8,
                       Re: float = 0.1, n: int = 63, ligand_density: float = 0.5,
                       strength: int = 1, seed: int = 1):
