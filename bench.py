@@ -122,10 +122,10 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def build_workload(L, W, storage, stream, allocator):
+def build_workload(L, W, storage, stream, allocator, rounding="stochastic"):
     sims = []
     for cfg, parts in W.single_ellipse_sweep():
-        s = L.Sim(storage=storage, stream=stream, allocator=allocator, **cfg)
+        s = L.Sim(storage=storage, stream=stream, allocator=allocator, rounding=rounding, **cfg)
         for p in parts:
             s.add_particle(**p)
         sims.append(s)
@@ -199,6 +199,65 @@ def run_reference(args):
 
 
 # ---- GPU arm -------------------------------------------------------------------
+
+def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="stochastic"):
+    """The same workload with another storage format: step time, MLUPS and
+    the bulk lattice pass against the HBM roofline at its bytes per update."""
+    import torch
+    sims = build_workload(lbib, W, storage, stream.cuda_stream, alloc, rounding)
+    nodes = sum(s.nx * s.ny for s in sims)
+    b = lbib.Batch(sims)
+    b.set_timing(16)
+    b.step(warmup)
+    torch.cuda.synchronize()
+    b.kernel_times()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = b.kernel_times()
+    pn = b.pass_nodes()
+    b.synchronize()
+    bpu = BYTES_PER_UPDATE[storage]
+    value = nodes * steps / (ms * 1e-3) / 1e6
+    ach = pn["bulk"] * bpu / (kt["lattice_ms"] * 1e-3) / 1e9 if kt["lattice_ms"] > 0 else None
+    b.close()
+    for s in sims:
+        s.close()
+    return {"storage": storage, "rounding": rounding, "value": value, "unit": "MLUPS",
+            "steps": steps, "ms_per_step": ms / steps, "bytes_per_update": bpu,
+            "hbm_roofline_frac_of_step": value * 1e6 * bpu / (peak * 1e9),
+            "lattice_kernel_ms": kt["lattice_ms"], "particle_kernel_ms": kt["particle_ms"],
+            "near_kernel_ms": kt["near_ms"],
+            "roofline_achieved_gbs": ach, "roofline_frac": ach / peak if ach else None}
+
+
+def serving_leg(lbib, W, n_requests, alloc, quantum):
+    """The serving loop on the first n_requests of the request trace (Poisson
+    arrivals at 20/s, lattices 256x64 .. 2048x512, 1-4 particles, FP32 or
+    FP16, 5k-50k steps) on the wall clock: p50 / p99 latency from arrival to
+    result, served and offered update rates."""
+    import torch
+    from paper_1808_01448_gb300 import serve
+    trace = W.serving_trace(n_requests)
+    streams = {"f32": torch.cuda.Stream(), "f16": torch.cuda.Stream()}
+    eng = serve.LbibEngine(lbib, {k: v.cuda_stream for k, v in streams.items()}, alloc)
+    srv = serve.Server(eng, budget_bytes=150 << 30, quantum=quantum)
+    t0 = time.perf_counter()
+    res = srv.run(trace, t0=t0)
+    wall = time.perf_counter() - t0
+    eng.close()
+    p50, p99 = serve.latency_stats(res)
+    total = sum(r["steps"] * r["config"]["nx"] * r["config"]["ny"] for r in trace)
+    return {"requests": len(res), "p50_s": p50, "p99_s": p99, "wall_s": wall,
+            "served_mlups": srv.updates / wall / 1e6,
+            "offered_mlups": total / trace[-1]["arrival_s"] / 1e6,
+            "arrival_window_s": trace[-1]["arrival_s"], "rebuilds": srv.rebuilds,
+            "rounds": srv.rounds, "quantum": quantum, "budget_gb": 150,
+            "trace": f"first {n_requests} requests of the 20/s Poisson trace (PCG64 seed 5)"}
+
 
 def run_gpu(args):
     import torch
@@ -285,8 +344,17 @@ def run_gpu(args):
         for s in e2e_sims:
             s.close()
 
+    peak, peak_kind = read_peaks()
+    legs = {}
+    if rank == 0 and args.storage == "f32" and args.storage_steps > 0:
+        legs["fp16_storage"] = storage_leg(lbib, W, "f16", stream, alloc, args.storage_steps,
+                                           args.warmup, peak)
+        legs["bf16_storage"] = storage_leg(lbib, W, "bf16", stream, alloc, args.storage_steps,
+                                           args.warmup, peak)
+    if rank == 0 and args.serve_requests > 0:
+        legs["latency"] = serving_leg(lbib, W, args.serve_requests, alloc, args.serve_quantum)
+
     if rank == 0:
-        peak, peak_kind = read_peaks()
         bpu = BYTES_PER_UPDATE[args.storage]
         lat_ms = kt["lattice_ms"]
         # algorithmic bytes of one bulk-pass launch: the nodes it updates
@@ -312,6 +380,7 @@ def run_gpu(args):
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": base,
         }
+        line.update(legs)
         print(json.dumps(line))
     batch.close()
     for s in sims:
@@ -330,6 +399,11 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--cpu-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage-steps", type=int, default=2000,
+                    help="steps of the FP16 / BF16 storage legs (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=60,
+                    help="requests of the serving leg (0: skip)")
+    ap.add_argument("--serve-quantum", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -63,6 +63,14 @@ typedef enum lbib_wall { LBIB_WALL_ZOU_HE = 0, LBIB_WALL_BOUNCE_BACK = 1,
 typedef enum lbib_storage { LBIB_STORE_F32 = 0, LBIB_STORE_F64 = 1,
                             LBIB_STORE_F16 = 2, LBIB_STORE_BF16 = 3 } lbib_storage;
 
+/* Rounding of the 16-bit stores (F16, BF16; ignored otherwise).
+ * STOCHASTIC (the default): round up with probability equal to the dropped
+ * fraction, from a hash of the node index and of the value (the same bits
+ * alone or in a batch), so that increments smaller than half a unit in the
+ * last place are not lost on average.  NEAREST: round to nearest even; slow
+ * transients then stall where the per-step change is below half an ulp. */
+typedef enum lbib_rounding { LBIB_ROUND_STOCHASTIC = 0, LBIB_ROUND_NEAREST = 1 } lbib_rounding;
+
 /* Optional device allocator hook (e.g. a framework's caching allocator).
  * alloc returns device memory of at least `bytes` bytes usable on `stream`,
  * or NULL; free releases it.  When NULL the library uses cudaMalloc. */
@@ -85,6 +93,7 @@ typedef void (*lbib_free_fn)(void *ptr, void *stream, void *ctx);
  *  seed, sim_id      key of the counter-based bond draws
  * Device-side settings:
  *  storage           lbib_storage
+ *  rounding          lbib_rounding of F16 / BF16 stores
  *  f16_scale         F16 only: power-of-two scale of f - w (0 = automatic)
  *  cuda_stream       cudaStream_t to run on (NULL = the legacy default)
  *  alloc, free, alloc_ctx   optional allocator hook */
@@ -100,7 +109,7 @@ typedef struct lbib_config {
     double receptor_bottom, receptor_top;
     uint64_t seed, sim_id;
     int32_t storage;
-    int32_t reserved0;
+    int32_t rounding;
     double f16_scale;
     void *cuda_stream;
     lbib_alloc_fn alloc;

@@ -165,6 +165,7 @@ SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
     d.cur = s->d_cur; d.step = s->d_step; d.err = s->d_err;
     // vector path: whole groups of four nodes per row, buffers 32-byte aligned
     d.vec4 = c.nx % 4 == 0 && ((uintptr_t)s->pop[0] % 32) == 0 && ((uintptr_t)s->pop[1] % 32) == 0;
+    d.sround = c.rounding == LBIB_ROUND_STOCHASTIC;
     return d;
 }
 
@@ -546,7 +547,7 @@ cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
             if ((e = launch_lattice(b->kind, b->bd, f, 0, b->stream))) return e;
             if (k == 0 && (e = mark(1, b->stream))) return e;
             if (k == 0 && (e = mark(2, b->stream))) return e;
-            if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->stream))) return e;
+            if ((e = launch_particles(b->kind, b->bd, f ^ 1, 2, b->smem, b->stream))) return e;
             if (k == 0 && (e = mark(3, b->stream))) return e;
             if (ev && k == 0 && ((e = mark(4, b->stream)) || (e = mark(5, b->stream)))) return e;
         }
@@ -672,6 +673,8 @@ lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out) {
     if ((c.wall_bottom == LBIB_WALL_PERIODIC) != (c.wall_top == LBIB_WALL_PERIODIC))
         return fail(LBIB_E_ARG, "periodic walls must be set on both sides");
     if (c.storage < 0 || c.storage > 3) return fail(LBIB_E_ARG, "unknown storage %d", c.storage);
+    if (c.rounding != LBIB_ROUND_NEAREST && c.rounding != LBIB_ROUND_STOCHASTIC)
+        return fail(LBIB_E_ARG, "unknown rounding %d", c.rounding);
     if (!(c.kBT > 0) || c.k_f < 0 || c.k_r0 < 0 || c.y_cr < 0 || c.eps_min <= 0 ||
         c.receptor_bottom < 0 || c.receptor_top < 0)
         return fail(LBIB_E_ARG, "bond / wall-force parameters out of range");

@@ -35,7 +35,8 @@ struct SimDev {
     int nx, ny, wall_b, wall_t;
     int p0, np;          // particle range in the batch's particle table
     int tile0, ntiles;   // lattice work tiles of this simulation
-    int vec4, pad0;      // rows in whole groups of four aligned nodes
+    int vec4;            // rows in whole groups of four aligned nodes
+    int sround;          // 16-bit storage: stochastic rounding of the stores
     double tau, u_b, u_t, gx, gy;
     double k_f, k_r0, kBT, sigma_star_ratio, y_cr, y_eq_ratio;
     double hamaker, eps_min, rec_b, rec_t;
@@ -93,6 +94,35 @@ struct BatchDev {
     int nsims, nparts, total_tiles;
 };
 
+// Stochastic rounding of 16-bit stores.  A node's dither word is a hash of
+// its index and of the bits of its first post-collision deviation (so it is
+// deterministic and independent of the batch), spread over the nine planes
+// by multiplicative hashing; the top bits of r_i dither the bits that the
+// conversion drops: FP32 -> FP16 (normal range) drops 13 mantissa bits,
+// FP32 -> BF16 drops 16.  Adding a uniform integer below 2^b to the FP32
+// bit pattern and truncating rounds up with probability equal to the
+// dropped fraction, for either sign.
+__device__ __forceinline__ unsigned mix32(unsigned x) {   // "lowbias32" (C. Wellons)
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ unsigned dither_word(int k, float d0) {
+    return mix32((unsigned)k * 0x9e3779b9u ^ __float_as_uint(d0));
+}
+__device__ __forceinline__ unsigned dither_plane(unsigned h, int i) {
+    return (h ^ ((unsigned)i * 0x632be5abu)) * 0x85ebca6bu;
+}
+__device__ __forceinline__ __half half_sr(float x, unsigned r) {
+    return __float2half_rz(__uint_as_float(__float_as_uint(x) + (r >> 19)));
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, unsigned r) {
+    return __ushort_as_bfloat16((unsigned short)((__float_as_uint(x) + (r >> 16)) >> 16));
+}
+
 // Storage traits: load a deviation into the compute type, store one back.
 template <typename S> struct Store;
 template <> struct Store<float> {
@@ -102,12 +132,20 @@ template <> struct Store<float> {
     // the particle data and code out of L2
     static __device__ __forceinline__ float ld_cs(const float *p, int i, float) { return __ldcs(p + i); }
     static __device__ __forceinline__ void st_cs(float *p, int i, float v, float) { __stcs(p + i, v); }
+    template <bool STREAM>
+    static __device__ __forceinline__ void st_r(float *p, int i, float v, float sc, unsigned) {
+        if constexpr (STREAM) st_cs(p, i, v, sc); else st(p, i, v, sc);
+    }
 };
 template <> struct Store<double> {
     static __device__ __forceinline__ double ld(const double *p, int i, float) { return __ldg(p + i); }
     static __device__ __forceinline__ void st(double *p, int i, double v, float) { p[i] = v; }
     static __device__ __forceinline__ double ld_cs(const double *p, int i, float) { return __ldcs(p + i); }
     static __device__ __forceinline__ void st_cs(double *p, int i, double v, float) { __stcs(p + i, v); }
+    template <bool STREAM>
+    static __device__ __forceinline__ void st_r(double *p, int i, double v, float sc, unsigned) {
+        if constexpr (STREAM) st_cs(p, i, v, sc); else st(p, i, v, sc);
+    }
 };
 template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half *p, int i, float inv) {
@@ -122,6 +160,11 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ void st_cs(__half *p, int i, float v, float scale) {
         __stcs(p + i, __float2half_rn(v * scale));
     }
+    template <bool STREAM>
+    static __device__ __forceinline__ void st_r(__half *p, int i, float v, float scale, unsigned r) {
+        const __half h = half_sr(v * scale, r);
+        if constexpr (STREAM) __stcs(p + i, h); else p[i] = h;
+    }
 };
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, int i, float inv) {
@@ -135,6 +178,12 @@ template <> struct Store<__nv_bfloat16> {
     }
     static __device__ __forceinline__ void st_cs(__nv_bfloat16 *p, int i, float v, float scale) {
         __stcs(p + i, __float2bfloat16_rn(v * scale));
+    }
+    template <bool STREAM>
+    static __device__ __forceinline__ void st_r(__nv_bfloat16 *p, int i, float v, float scale,
+                                                unsigned r) {
+        const __nv_bfloat16 h = bf16_sr(v * scale, r);
+        if constexpr (STREAM) __stcs(p + i, h); else p[i] = h;
     }
 };
 
@@ -157,6 +206,10 @@ template <bool STREAM> struct Vec4<float, STREAM> {
     static __device__ __forceinline__ void st(float *p, const float o[4], float) {
         stv<STREAM>((float4 *)p, make_float4(o[0], o[1], o[2], o[3]));
     }
+    static __device__ __forceinline__ void st_r(float *p, const float o[4], float sc,
+                                                const unsigned *) {
+        st(p, o, sc);
+    }
 };
 template <bool STREAM> struct Vec4<double, STREAM> {
     static __device__ __forceinline__ void ld(const double *p, float, double o[4]) {
@@ -166,6 +219,10 @@ template <bool STREAM> struct Vec4<double, STREAM> {
     static __device__ __forceinline__ void st(double *p, const double o[4], float) {
         stv<STREAM>((double2 *)p, make_double2(o[0], o[1]));
         stv<STREAM>((double2 *)p + 1, make_double2(o[2], o[3]));
+    }
+    static __device__ __forceinline__ void st_r(double *p, const double o[4], float sc,
+                                                const unsigned *) {
+        st(p, o, sc);
     }
 };
 template <bool STREAM> struct Vec4<__half, STREAM> {
@@ -185,6 +242,15 @@ template <bool STREAM> struct Vec4<__half, STREAM> {
         memcpy(&u.y, &b, 4);
         stv<STREAM>((uint2 *)p, u);
     }
+    static __device__ __forceinline__ void st_r(__half *p, const float o[4], float sc,
+                                                const unsigned *r) {
+        const __half2 a = __halves2half2(half_sr(o[0] * sc, r[0]), half_sr(o[1] * sc, r[1]));
+        const __half2 b = __halves2half2(half_sr(o[2] * sc, r[2]), half_sr(o[3] * sc, r[3]));
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        stv<STREAM>((uint2 *)p, u);
+    }
 };
 template <bool STREAM> struct Vec4<__nv_bfloat16, STREAM> {
     static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float inv, float o[4]) {
@@ -198,6 +264,15 @@ template <bool STREAM> struct Vec4<__nv_bfloat16, STREAM> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, const float o[4], float sc) {
         const __nv_bfloat162 a = __floats2bfloat162_rn(o[0] * sc, o[1] * sc);
         const __nv_bfloat162 b = __floats2bfloat162_rn(o[2] * sc, o[3] * sc);
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        stv<STREAM>((uint2 *)p, u);
+    }
+    static __device__ __forceinline__ void st_r(__nv_bfloat16 *p, const float o[4], float sc,
+                                                const unsigned *r) {
+        const __nv_bfloat162 a = __halves2bfloat162(bf16_sr(o[0] * sc, r[0]), bf16_sr(o[1] * sc, r[1]));
+        const __nv_bfloat162 b = __halves2bfloat162(bf16_sr(o[2] * sc, r[2]), bf16_sr(o[3] * sc, r[3]));
         uint2 u;
         memcpy(&u.x, &a, 4);
         memcpy(&u.y, &b, 4);
@@ -320,8 +395,10 @@ __device__ __forceinline__ void tile_force(const SimDev &s, ParticleDev *const *
 // Launchers (defined in the .cu files), one instantiation per storage kind.
 // mode: 0 every node; 1 bulk (nodes outside the near boxes); 2 near boxes only
 cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st);
-// pdl: launched as a programmatic dependent of the previous kernel on st
-cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int init, int smem,
+// mode: 0 overlapped step, 1 init (IB forcing at the current pose), 2 step
+// without the near-box pass.  pdl: launched as a programmatic dependent of
+// the previous kernel on st
+cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int mode, int smem,
                              cudaStream_t st, bool pdl = false);
 cudaError_t launch_fields(int kind, const SimDev &s, ParticleDev *const *parts, double *rho,
                           double *ux, double *uy, cudaStream_t st);

@@ -54,6 +54,13 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
 template <typename S, typename R, bool STREAM = false>
 __device__ __forceinline__ void store_node(const SimDev &s, S *__restrict__ dst, int N, int k,
                                            const R d[9]) {
+    if (sizeof(S) == 2 && s.sround) {
+        const unsigned h = dither_word(k, (float)d[0]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            Store<S>::template st_r<STREAM>(dst, i * N + k, d[i], s.scale, dither_plane(h, i));
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         if constexpr (STREAM) Store<S>::st_cs(dst, i * N + k, d[i], s.scale);
@@ -195,7 +202,18 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int fli
             if (!BULK && s.np) tile_force<R>(s, b.parts, x0 + j, y, Fx, Fy);
             collide_node<R>(s, d[j], Fx, Fy);
         }
-        if (keep == 0xFu) {
+        if (keep == 0xFu && sizeof(S) == 2 && s.sround) {
+            unsigned h[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) h[j] = dither_word(k + j, (float)d[j][0]);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
+                const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
+                                       dither_plane(h[2], i), dither_plane(h[3], i)};
+                Vec4<S, BULK>::st_r(dst + i * N + k, o, s.scale, r);
+            }
+        } else if (keep == 0xFu) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};

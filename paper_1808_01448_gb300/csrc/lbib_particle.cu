@@ -296,7 +296,11 @@ __device__ __noinline__ double prob_reverse(double k_r0, double dsig, double kBT
 }
 
 template <typename S, typename R>
-__global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int flip, int init) {
+__global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int flip, int mode) {
+    // mode bit 0: init (IB forcing only, at the current pose); bit 1: a step
+    // without the near-box lattice pass
+    const int init = mode & 1;
+    const bool plain = (mode & 2) != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // descriptors copied to shared memory once: later reads do not wait on
     // global memory, nor get reloaded after the kernel's own global stores
@@ -750,13 +754,13 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         }
         P->pend_ox = bx;
         P->pend_oy = by;
-        if (init) {
-            // before the first step both lattice steps use the initial pose
+        if (init || plain) {
+            // before the first step (or when no near pass publishes boxes)
+            // both lattice steps use the box around the latest pose
             P->box_ox[0] = P->box_ox[1] = bx;
             P->box_oy[0] = P->box_oy[1] = by;
-        } else {
-            P->step = Pc.step + 1;
         }
+        if (!init) P->step = Pc.step + 1;
     }
 }
 
@@ -808,7 +812,7 @@ cudaError_t particle_kernel_setup(int kind, int smem) {
     });
 }
 
-cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int init, int smem,
+cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int mode, int smem,
                              cudaStream_t st, bool pdl) {
     if (b.nparts == 0) return cudaSuccess;
     return by_kind(kind, [&](auto sv, auto rv) {
@@ -824,7 +828,7 @@ cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int init, in
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = pdl ? 1 : 0;
-        return cudaLaunchKernelEx(&cfg, particle_kernel<S, R>, b, flip, init);
+        return cudaLaunchKernelEx(&cfg, particle_kernel<S, R>, b, flip, mode);
     });
 }
 

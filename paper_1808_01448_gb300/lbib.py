@@ -44,7 +44,7 @@ class Config(C.Structure):
         ("hamaker", C.c_double), ("eps_min", C.c_double),
         ("receptor_bottom", C.c_double), ("receptor_top", C.c_double),
         ("seed", C.c_uint64), ("sim_id", C.c_uint64),
-        ("storage", C.c_int32), ("reserved0", C.c_int32),
+        ("storage", C.c_int32), ("rounding", C.c_int32),
         ("f16_scale", C.c_double),
         ("cuda_stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
@@ -145,11 +145,13 @@ def make_config(storage="f32", stream=None, allocator=None, **kw) -> Config:
                     tau=0.8, u_bottom=0.0, u_top=0.0, gx=0.0, gy=0.0, k_f=0.85,
                     k_r0=1e-4, kBT=0.1, sigma_star_ratio=0.5, y_cr=1.36,
                     y_eq_ratio=0.5, hamaker=0.0, eps_min=0.1, receptor_bottom=1.0,
-                    receptor_top=0.0, seed=1, sim_id=0, f16_scale=0.0)
+                    receptor_top=0.0, seed=1, sim_id=0, f16_scale=0.0, rounding="stochastic")
     defaults.update(kw)
     for k, v in defaults.items():
         if k in ("wall_bottom", "wall_top") and isinstance(v, str):
             v = WALL[v]
+        if k == "rounding" and isinstance(v, str):
+            v = {"stochastic": 0, "nearest": 1}[v]
         setattr(c, k, v)
     c.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     c.cuda_stream = stream
@@ -310,6 +312,11 @@ class Batch:
 
     def set_timing(self, nsamples):
         _check(lib().lbib_batch_set_timing(self._h, int(nsamples)))
+
+    def synchronize(self):
+        """Wait for the batch's work; raises on a member's device error."""
+        for s in self.sims:
+            s.synchronize()
 
     def kernel_times(self):
         ms = (C.c_double * 3)(); cnt = (C.c_int64 * 3)()

@@ -219,6 +219,46 @@ def particle_cluster(nx: int = 4096, ny: int = 1024, n_particles: int = 8, Re: f
     return cfg, parts
 
 
+def serving_trace(n_requests: int = 600, rate: float = 20.0, seed: int = 5,
+                  steps_range=(5000, 50000)):
+    """Simulation requests for the serving loop, drawn with PCG64(seed):
+    Poisson arrivals at `rate` per second; nx = 2^U[8, 11] rounded to a
+    multiple of 32, ny = nx / 4; 1-4 particles of aspect ratio U[1, 3]
+    (equal-area radius 0.09 ny, at most 20, major axis normal to the wall,
+    spread evenly along x near the bottom wall); ligand density U[0.3, 0.9]; bond strength
+    1 or 2; Re log-uniform in [0.01, 1]; steps log-uniform in steps_range;
+    FP32 or FP16 storage with equal probability.  Returns a list of dicts
+    with 'arrival_s', 'steps', 'storage', 'config' and 'particles'."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for rid in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        nx = int(round(2.0 ** rng.uniform(8.0, 11.0) / 32.0)) * 32
+        ny = nx // 4
+        k = int(rng.integers(1, 5))
+        rl = float(rng.uniform(0.3, 0.9))
+        strength = int(rng.integers(1, 3))
+        Re = float(10.0 ** rng.uniform(-2.0, 0.0))
+        steps = int(round(math.exp(rng.uniform(math.log(steps_range[0]),
+                                               math.log(steps_range[1])))))
+        storage = "f32" if rng.uniform() < 0.5 else "f16"
+        ars = [float(rng.uniform(1.0, 3.0)) for _ in range(k)]
+        cfg = shear_channel(nx, ny, Re, seed=seed, sim_id=rid)
+        ap = adhesion_params(ny - 1, (cfg["tau"] - 0.5) / 3.0, strength)
+        sigma = ap.pop("sigma")
+        cfg.update(ap)
+        parts = []
+        for i, ar in enumerate(ars):
+            shape = f"ar{ar:.6f}"
+            parts.append(adhesion_particle(cfg, shape, min(0.09 * ny, 20.0),
+                                           x=nx * (i + 1) / (k + 1),
+                                           ligand_density=rl, sigma=sigma))
+        out.append(dict(rid=rid, arrival_s=t, steps=steps, storage=storage, config=cfg,
+                        particles=parts))
+    return out
+
+
 def poiseuille_circle(nx: int = 200, ny: int = 50, radius: float = 10.0, tau: float = 0.8,
                       Re: float = 0.1, n: int = 63, ligand_density: float = 0.5,
                       strength: int = 1, seed: int = 1):

@@ -1,0 +1,93 @@
+"""Reduced-precision storage against the FP64 oracle.
+
+Populations are stored as f - w_i in FP16 (times a power-of-two scale) or
+BF16 and collided in FP32.  Stated errors (relative L2 of the velocity field,
+largest centroid error in lattice units), with stochastic rounding of the
+stores (the default):
+  FP16: velocity <= 1e-3, trajectory <= 1e-5
+  BF16: velocity <= 1e-2, trajectory <= 1e-4
+and with round-to-nearest, where transients slower than half an ulp per step
+stall, velocity <= 5e-2 (FP16) and <= 0.5 (BF16).  Bond states equal the
+oracle's in every case below.
+"""
+import numpy as np
+import pytest
+
+from paper_1808_01448_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BOUND = {("f16", "stochastic"): (1e-3, 1e-5), ("bf16", "stochastic"): (1e-2, 1e-4),
+         ("f16", "nearest"): (5e-2, 1e-3), ("bf16", "nearest"): (0.5, 1e-3)}
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1808_01448_gb300 import build, lbib
+    build.build()
+    return lbib
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = {
+    # first member of the design sweep: 896 x 112, circle, Re 0.01
+    "sweep0": (lambda: W.design_sweep()[0], 500),
+    # two particles near the bottom wall of a 512 x 128 channel at Re 1
+    "cluster": (lambda: W.particle_cluster(512, 128, 2), 1000),
+    # Couette start-up, 256 x 64, Re 1 (no particle)
+    "couette": (lambda: (W.shear_channel(256, 64, 1.0), []), 2000),
+}
+
+
+@pytest.fixture(scope="module")
+def oracle_runs(O):
+    out = {}
+    for name, (make, steps) in CASES.items():
+        cfg, parts = make()
+        o = O.OracleSim(**cfg)
+        for p in parts:
+            o.add_particle(**p)
+        o.step(steps)
+        out[name] = (cfg, parts, steps, o.fields(), [o.particle(k) for k in range(len(parts))],
+                     [o.bonds(k)[0] for k in range(len(parts))])
+    return out
+
+
+@pytest.mark.parametrize("rounding", ["stochastic", "nearest"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_reduced_storage_error(L, oracle_runs, case, storage, rounding):
+    cfg, parts, steps, (ro, uo, vo), po, bo = oracle_runs[case]
+    g = L.Sim(storage=storage, rounding=rounding, **cfg)
+    for p in parts:
+        g.add_particle(**p)
+    g.step(steps)
+    g.synchronize()
+    rg, ug, vg = g.fields()
+    vel_bound, traj_bound = BOUND[(storage, rounding)]
+    err = rel_l2(np.stack([ug, vg]), np.stack([uo, vo]))
+    assert err < vel_bound, err
+    for k in range(len(parts)):
+        pg = g.particle(k)
+        for q in ("xc", "yc"):
+            assert abs(pg[q] - po[k][q]) < traj_bound, (q, pg[q] - po[k][q])
+        np.testing.assert_array_equal(g.bonds(k)[0], bo[k])
+    g.close()
+
+
+def test_stochastic_rounding_is_deterministic_and_batch_invariant(L):
+    cfg, parts = W.design_sweep()[0]
+    runs = []
+    for _ in range(2):
+        g = L.Sim(storage="f16", **cfg)
+        for p in parts:
+            g.add_particle(**p)
+        runs.append(g)
+    runs[0].step(77)
+    b = L.Batch([runs[1]])
+    b.step(77)
+    np.testing.assert_array_equal(runs[0].populations(), runs[1].populations())
+    b.close()

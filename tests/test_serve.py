@@ -1,0 +1,159 @@
+"""Serving-loop scheduling on the host (no GPU): admission by memory budget,
+quanta that stop at the nearest completion, exact step counts, latency
+accounting, and the trace generator's recipe."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1808_01448_gb300 import serve, workloads as W
+
+
+class FakeEngine:
+    """Advances a virtual clock by the work of each step call (updates /
+    rate) and records what the scheduler asks for."""
+
+    def __init__(self, rate=1e9):
+        self.t = 0.0
+        self.rate = rate
+        self.members = []
+        self.steps_done = {}
+        self.calls = []
+        self.max_active = 0
+
+    def clock(self):
+        return self.t
+
+    def create(self, req):
+        self.steps_done[req["rid"]] = 0
+        return req["rid"]
+
+    def rebuild(self, members):
+        self.members = [m[1] for m in members]
+        self.max_active = max(self.max_active, len(self.members))
+
+    def step(self, n):
+        self.calls.append((n, tuple(self.members)))
+        work = 0
+        for rid in self.members:
+            self.steps_done[rid] += n
+            work += self.nodes[rid] * n
+        self.t += work / self.rate
+
+    def result(self, h):
+        return [{"steps": self.steps_done[h]}]
+
+    def destroy(self, h):
+        self.members = [m for m in self.members if m != h]
+
+    def idle(self, s):
+        self.t += s
+
+
+def small_trace(n=12, seed=7):
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for rid in range(n):
+        t += rng.exponential(0.05)
+        nx = int(rng.choice([64, 128, 256]))
+        out.append(dict(rid=rid, arrival_s=t, steps=int(rng.integers(10, 400)),
+                        storage="f32" if rid % 2 else "f16",
+                        config=dict(nx=nx, ny=nx // 4), particles=[{}]))
+    return out
+
+
+def run(trace, **kw):
+    eng = FakeEngine(rate=kw.pop("rate", 2e7))
+    eng.nodes = {r["rid"]: r["config"]["nx"] * r["config"]["ny"] for r in trace}
+    srv = serve.Server(eng, clock=eng.clock, **kw)
+    res = srv.run(trace, t0=0.0)
+    return eng, srv, res
+
+
+def test_every_request_gets_exactly_its_steps():
+    trace = small_trace()
+    eng, srv, res = run(trace, quantum=64)
+    assert sorted(r.rid for r in res) == list(range(len(trace)))
+    for r in res:
+        assert r.particles[0]["steps"] == r.steps
+        assert eng.steps_done[r.rid] == r.steps
+    assert all(n <= 64 for n, _ in eng.calls)
+    assert srv.updates == sum(r["steps"] * r["config"]["nx"] * r["config"]["ny"] for r in trace)
+
+
+def test_latency_is_arrival_to_result_and_ordered():
+    trace = small_trace()
+    eng, srv, res = run(trace, quantum=50)
+    done = [r.done_s for r in res]
+    assert done == sorted(done)
+    for r in res:
+        assert r.admitted_s >= r.arrival_s - 1e-12
+        assert r.done_s > r.admitted_s
+        assert r.latency_s == pytest.approx(r.done_s - r.arrival_s)
+    p50, p99 = serve.latency_stats(res)
+    lat = sorted(r.latency_s for r in res)
+    assert p50 == lat[math.ceil(0.5 * len(lat)) - 1]
+    assert p99 == lat[-1]
+
+
+def test_admission_respects_the_memory_budget():
+    trace = small_trace(20)
+    sizes = {r["rid"]: serve.request_bytes(r) for r in trace}
+    budget = 3 * max(sizes.values())
+    eng = FakeEngine(rate=1e6)
+    eng.nodes = {r["rid"]: r["config"]["nx"] * r["config"]["ny"] for r in trace}
+    srv = serve.Server(eng, budget_bytes=budget, quantum=32, clock=eng.clock)
+    res = srv.run(trace, t0=0.0)
+    assert len(res) == len(trace)
+    for n, members in eng.calls:
+        assert sum(sizes[m] for m in members) <= budget
+    # requests are admitted in arrival order
+    adm = sorted(res, key=lambda r: r.rid)
+    assert all(a.admitted_s <= b.admitted_s for a, b in zip(adm, adm[1:]))
+
+
+def test_oversized_request_is_rejected():
+    trace = small_trace(2)
+    eng = FakeEngine()
+    eng.nodes = {r["rid"]: 1 for r in trace}
+    srv = serve.Server(eng, budget_bytes=1000, clock=eng.clock)
+    with pytest.raises(ValueError):
+        srv.run(trace, t0=0.0)
+
+
+def test_max_active_caps_the_batch():
+    trace = small_trace(15)
+    eng, srv, res = run(trace, quantum=40, max_active=3, rate=1e6)
+    assert eng.max_active <= 3
+    assert len(res) == len(trace)
+
+
+def test_batches_continue_while_requests_arrive():
+    # a long request keeps running while short ones arrive, join and leave
+    trace = [dict(rid=0, arrival_s=0.0, steps=1000, storage="f32",
+                  config=dict(nx=64, ny=16), particles=[{}])]
+    for i in range(1, 5):
+        trace.append(dict(rid=i, arrival_s=0.01 * i, steps=50, storage="f32",
+                          config=dict(nx=64, ny=16), particles=[{}]))
+    eng, srv, res = run(trace, quantum=100, rate=1e7)
+    assert res[-1].rid == 0
+    assert any(len(m) > 1 and 0 in m for _, m in eng.calls)
+
+
+def test_serving_trace_recipe():
+    tr = W.serving_trace(200)
+    arr = np.array([r["arrival_s"] for r in tr])
+    assert np.all(np.diff(arr) > 0)
+    assert 200 / arr[-1] == pytest.approx(20.0, rel=0.2)
+    for r in tr:
+        c = r["config"]
+        assert 256 <= c["nx"] <= 2048 and c["nx"] % 32 == 0 and c["ny"] == c["nx"] // 4
+        assert 1 <= len(r["particles"]) <= 4
+        assert 5000 <= r["steps"] <= 50000
+        assert r["storage"] in ("f32", "f16")
+        assert 0.3 <= r["particles"][0]["ligand_density"] <= 0.9
+        for p in r["particles"]:
+            assert p["yc"] - np.min(p["vy"]) > 0          # above the bottom wall
+            assert p["yc"] + np.max(p["vy"]) < c["ny"] - 1
+            # within the library's particle size limit (LBIB_MAX_PARTICLE_RADIUS)
+            assert np.max(np.hypot(p["vx"], p["vy"])) <= 44.0
