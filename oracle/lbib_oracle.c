@@ -306,6 +306,15 @@ static void row_limits(const or_config *c, int *lo, int *hi) {
     *hi = c->ny - 1;
 }
 
+/* Wall lines: y = 0 and ny - 1 for Zou-He (wall nodes), -1/2 and ny - 1/2 for
+ * half-way bounce-back. */
+static double wall_line(const or_config *c, int top) {
+    int kind = top ? c->wall_top : c->wall_bottom;
+    double y = top ? (double)(c->ny - 1) : 0.0;
+    if (kind == OR_WALL_BOUNCE_BACK) y += top ? 0.5 : -0.5;
+    return y;
+}
+
 /* Gaussian elimination with partial pivoting on a 3x3 system. */
 static int solve3(const double A[3][3], const double *b, double *x) {
     double M[3][4];
@@ -343,6 +352,11 @@ static int mls_support(const or_config *c, double X, double Y, int32_t *ix, int3
     int lo, hi;
     row_limits(c, &lo, &hi);
     int periodic_y = c->wall_bottom == OR_WALL_PERIODIC;
+    /* a point beyond a wall line (a probe or marker of a particle pressed
+     * against the wall) is outside the fluid: no fit (reading of the paper,
+     * which places probes 1.2 dx along the normal without saying what happens
+     * at a wall) */
+    if (!periodic_y && (Y < wall_line(c, 0) || Y > wall_line(c, 1))) return 0;
     int x0 = (int)floor(X) - 1, y0 = (int)floor(Y) - 1;
     int nrow = 0, ncol = 0, n = 0;
     for (int a = 0; a < 4; ++a)

@@ -252,7 +252,9 @@ lbib_status check_err_word(lbib_sim *s) {
     int err = 0;
     CK(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err & ERR_UNSTABLE)
-        return fail(LBIB_E_UNSTABLE, "simulation %llu became unstable (non-finite or |u| >= 0.5)",
+        return fail(LBIB_E_UNSTABLE,
+                    "simulation %llu became unstable (a node's state non-finite, |rho - 1| >= 1 "
+                    "or |ux| + |uy| >= 10)",
                     (unsigned long long)s->cfg.sim_id);
     return LBIB_OK;
 }

@@ -25,9 +25,10 @@
 // gradient sum w_k d'_k u_k / (W v).
 //
 // GB300 has little FP64 throughput, so per-particle scalars (sincos, P_f,
-// Eq. 12, the update) run on one thread, per-point setup on one lane per
-// half-warp (broadcast by shuffles), and the FP64 sums on one warp over
-// per-element contributions kept in shared memory.
+// Eq. 12, the update) run on one thread, per-point setup on one thread per
+// point (kept in shared memory), and the FP64 sums on one warp per quantity
+// over per-element contributions kept in shared memory.  Each point's 4 x 4
+// support is summed by a quarter-warp (two nodes per lane, three shuffles).
 #include "lbib_internal.cuh"
 
 namespace lbib {
@@ -36,7 +37,7 @@ namespace {
 
 constexpr int P_THREADS = 512;   // >= LBIB_MAX_MARKERS: one marker per thread
 
-// Cubic B-spline of radius 2, branch-free (lanes of a half-warp straddle the
+// Cubic B-spline of radius 2, branch-free (lanes of a quarter-warp straddle the
 // two pieces).
 template <typename R>
 __device__ __forceinline__ R bspline(R r) {
@@ -177,6 +178,22 @@ __device__ __forceinline__ void setup_point(const SimDev &s, int bx, int by, R X
     const bool periodic = s.wall_b == LBIB_WALL_PERIODIC;
     unsigned rows = 0;
     int nz = 0;
+    // a point beyond a wall line (y = 0 / ny - 1 for Zou-He, -1/2 / ny - 1/2
+    // for bounce-back) is outside the fluid and has no fit
+    const int iy = iy0 + 1;
+    const bool below = s.wall_b == LBIB_WALL_BOUNCE_BACK ? (iy < -1 || (iy == -1 && fy < (R)0.5))
+                                                         : iy < 0;
+    const bool above = s.wall_t == LBIB_WALL_BOUNCE_BACK
+                           ? (iy > s.ny - 1 || (iy == s.ny - 1 && fy > (R)0.5))
+                           : (iy > s.ny - 1 || (iy == s.ny - 1 && fy > (R)0));
+    if (!periodic && (below || above)) {
+        pt.ix0[l] = ix0;
+        pt.iy0[l] = iy0;
+        pt.rows[l] = 0;
+        pt.fx[l] = fx;
+        pt.fy[l] = fy;
+        return;
+    }
     for (int b = 0; b < 4; ++b) {
         const int yy = iy0 + b;
         if (periodic || (yy >= 0 && yy <= s.ny - 1)) {
@@ -197,10 +214,11 @@ __device__ __forceinline__ void setup_point(const SimDev &s, int bx, int by, R X
     pt.inv_v[l] = inv_v;
 }
 
+// Sum over the eight lanes of a quarter-warp.
 template <typename T>
-__device__ __forceinline__ T hw_sum(T v) {
+__device__ __forceinline__ T qw_sum(T v) {
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
@@ -234,8 +252,8 @@ __device__ __noinline__ void pull_moments(const SimDev &s, const S *pop, int x, 
     node_moments(d, drho, jx, jy);
 }
 
-// Lane (a, b) of a half-warp: weights of its support node and the node's
-// moments (staged region, else pulled).  false when the node has no weight.
+// Support node (a, b) of point l: its weight and the node's moments (staged
+// region, else pulled).  false when the node has no weight.
 template <typename S, typename R>
 __device__ __forceinline__ bool lane_moments(const SimDev &s, const S *pop, const Points<R> &pt,
                                              int l, int a, int b, const R *mr, const R *mjx,
@@ -360,10 +378,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     int *nflag = (int *)take(16);
 
     const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
-    const int tid = threadIdx.x, lane = tid & 31, hl = lane & 15, warp = tid >> 5;
-    const int half = tid >> 4;
-    constexpr int NHALF = P_THREADS / 16;
-    const int a = hl & 3, bb = hl >> 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // a point's 4 x 4 support is taken by a quarter-warp: lane q holds
+    // nodes (q & 3, q >> 2) and (q & 3, (q >> 2) + 2)
+    const int qw = tid >> 3, ql = lane & 7;
+    constexpr int NQ = P_THREADS / 8;
+    const int a = ql & 3, bb = ql >> 2;
     const double yb = s.wall_b == LBIB_WALL_BOUNCE_BACK ? -0.5 : 0.0;
     const double yt = s.wall_t == LBIB_WALL_BOUNCE_BACK ? (double)s.ny - 0.5 : (double)(s.ny - 1);
 
@@ -512,28 +532,31 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         __syncthreads();
         const R nu = pick<R>(s.f_nu, s.d_nu);
 #pragma unroll 1
-        for (int base = 0; base < nl; base += NHALF) {
-            const int l = base + half;
+        for (int base = 0; base < nl; base += NQ) {
+            const int l = base + qw;
             const bool act = l < nl;
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-            R dx, dy, w, drho, jx, jy;
-            if (act && lane_moments<S, R>(s, pop, pt, l, a, bb, mr, mjx, mjy, flag, Tm, rx0, ry0, dx,
-                                          dy, w, drho, jx, jy)) {
-                const R irho = recip((R)1 + drho);
-                const R ux = jx * irho, uy = jy * irho;
-                const R dyc = dy - pt.mu[l];
-                s_rho = w * ((R)1 - dyc * pt.mu_v[l]) * drho;
-                s_ux = w * dx * ux;
-                s_uy = w * dyc * ux;
-                s_vx = w * dx * uy;
-                s_vy = w * dyc * uy;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                R dx, dy, w, drho, jx, jy;
+                if (act && lane_moments<S, R>(s, pop, pt, l, a, bb + 2 * h, mr, mjx, mjy, flag, Tm,
+                                              rx0, ry0, dx, dy, w, drho, jx, jy)) {
+                    const R irho = recip((R)1 + drho);
+                    const R ux = jx * irho, uy = jy * irho;
+                    const R dyc = dy - pt.mu[l];
+                    s_rho += w * ((R)1 - dyc * pt.mu_v[l]) * drho;
+                    s_ux += w * dx * ux;
+                    s_uy += w * dyc * ux;
+                    s_vx += w * dx * uy;
+                    s_vy += w * dyc * uy;
+                }
             }
-            s_rho = hw_sum(s_rho);
-            s_ux = hw_sum(s_ux);
-            s_uy = hw_sum(s_uy);
-            s_vx = hw_sum(s_vx);
-            s_vy = hw_sum(s_vy);
-            if (act && hl == 0) {
+            s_rho = qw_sum(s_rho);
+            s_ux = qw_sum(s_ux);
+            s_uy = qw_sum(s_uy);
+            s_vx = qw_sum(s_vx);
+            s_vy = qw_sum(s_vy);
+            if (act && ql == 0) {
                 R tx = 0, ty = 0;
                 if (pt.rows[l] & 16) {
                     const R iv = pt.inv_v[l];
@@ -680,23 +703,26 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     __syncthreads();
     const R ghx = (R)0.5 * pick<R>(s.f_gx, s.gx), ghy = (R)0.5 * pick<R>(s.f_gy, s.gy);
 #pragma unroll 1
-    for (int base = 0; base < nl; base += NHALF) {
-        const int l = base + half;
+    for (int base = 0; base < nl; base += NQ) {
+        const int l = base + qw;
         const bool act = l < nl;
         R s_rho = 0, s_u = 0, s_v = 0;
-        R dx, dy, w, drho, jx, jy;
-        if (act && lane_moments<S, R>(s, pop, pt, l, a, bb, mr, mjx, mjy, flag, Tm, rx0, ry0, dx, dy,
-                                      w, drho, jx, jy)) {
-            const R irho = recip((R)1 + drho);
-            const R phi = w * ((R)1 - (dy - pt.mu[l]) * pt.mu_v[l]);
-            s_rho = phi * drho;
-            s_u = phi * ((jx + ghx) * irho);
-            s_v = phi * ((jy + ghy) * irho);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            R dx, dy, w, drho, jx, jy;
+            if (act && lane_moments<S, R>(s, pop, pt, l, a, bb + 2 * h, mr, mjx, mjy, flag, Tm, rx0,
+                                          ry0, dx, dy, w, drho, jx, jy)) {
+                const R irho = recip((R)1 + drho);
+                const R phi = w * ((R)1 - (dy - pt.mu[l]) * pt.mu_v[l]);
+                s_rho += phi * drho;
+                s_u += phi * ((jx + ghx) * irho);
+                s_v += phi * ((jy + ghy) * irho);
+            }
         }
-        s_rho = hw_sum(s_rho);
-        s_u = hw_sum(s_u);
-        s_v = hw_sum(s_v);
-        if (act && hl == 0) {
+        s_rho = qw_sum(s_rho);
+        s_u = qw_sum(s_u);
+        s_v = qw_sum(s_v);
+        if (act && ql == 0) {
             R Fx = 0, Fy = 0;
             if (pt.rows[l] & 16) {
                 const R rl = (R)1 + s_rho;

@@ -59,9 +59,14 @@ class RecordingEngine(serve.LbibEngine):
     def idle(self, s):
         self.t += s
 
+    def create(self, req):
+        s = super().create(req)
+        s.rid = req["rid"]          # object ids are reused once a simulation is freed
+        return s
+
     def result(self, s):
         parts = super().result(s)
-        self.final[id(s)] = (s.populations(), [s.bonds(i)[0] for i in range(len(parts))], parts)
+        self.final[s.rid] = (s.populations(), [s.bonds(i)[0] for i in range(len(parts))], parts)
         return parts
 
 
@@ -71,15 +76,6 @@ def test_served_results_equal_solo_runs(L):
     streams = {"f32": torch.cuda.Stream(), "f16": torch.cuda.Stream()}
     alloc = L.torch_allocator()
     eng = RecordingEngine(L, {k: v.cuda_stream for k, v in streams.items()}, alloc)
-    handles = {}
-    orig_create = eng.create
-
-    def create(req):
-        h = orig_create(req)
-        handles[req["rid"]] = id(h)
-        return h
-
-    eng.create = create
     srv = serve.Server(eng, quantum=16, clock=eng.clock)
     res = srv.run(reqs, t0=0.0)
     assert sorted(r.rid for r in res) == list(range(len(reqs)))
@@ -91,7 +87,7 @@ def test_served_results_equal_solo_runs(L):
         for p in req["particles"]:
             solo.add_particle(**p)
         solo.step(req["steps"])
-        f_mix, bonds_mix, parts_mix = eng.final[handles[r.rid]]
+        f_mix, bonds_mix, parts_mix = eng.final[r.rid]
         np.testing.assert_array_equal(solo.populations(), f_mix)
         assert solo.particles() == parts_mix
         for i in range(len(req["particles"])):

@@ -55,18 +55,35 @@ def test_partition_of_unity_and_linear_reproduction(O, walls):
 
 def test_support_respects_walls(O):
     """Only lattice rows enter the support (wall nodes included, so a point
-    between the wall row and row 1 is inside its support's row span); a
-    support with a single usable row has no linear fit."""
-    for walls in ("zou_he", "bounce_back"):
+    between the wall row and row 1 is inside its support's row span); a point
+    beyond a wall line (y = 0 and ny - 1 for Zou-He, -1/2 and ny - 1/2 for
+    bounce-back) has no fit."""
+    for walls, yb, yt in (("zou_he", 0.0, 23.0), ("bounce_back", -0.5, 23.5)):
         c = cfg(O, wall_bottom=walls, wall_top=walls)
         ix, iy, phi = O.mls_shape(c, 10.3, 0.4)
         assert iy.min() == 0 and iy.max() == 2
         assert np.all(phi > -1e-12)                       # no extrapolation weights
         _, iy, _ = O.mls_shape(c, 10.3, c.ny - 1.4)
         assert iy.max() == c.ny - 1
-        assert len(O.mls_shape(c, 10.3, -1.9)[2]) == 0    # only row 0 is usable
-        assert len(O.mls_shape(c, 10.3, -1.0)[2]) == 0    # row 1 sits at |dy| = 2
-        assert len(O.mls_shape(c, 10.3, -0.8)[2]) > 0     # rows 0 and 1 remain
+        assert len(O.mls_shape(c, 10.3, yb)[2]) > 0       # on the wall line
+        assert len(O.mls_shape(c, 10.3, yt)[2]) > 0
+        assert len(O.mls_shape(c, 10.3, yb - 1e-9)[2]) == 0
+        assert len(O.mls_shape(c, 10.3, yt + 1e-9)[2]) == 0
+        assert len(O.mls_shape(c, 10.3, -1.9)[2]) == 0
+
+
+def test_fit_is_well_conditioned_up_to_the_walls(O):
+    """Everywhere in the fluid, wall lines included, the shape functions stay
+    bounded (no near-singular extrapolation from one usable row) and still
+    reproduce linear fields."""
+    for walls, yb, yt in (("zou_he", 0.0, 23.0), ("bounce_back", -0.5, 23.5)):
+        c = cfg(O, wall_bottom=walls, wall_top=walls)
+        for Y in np.concatenate([np.linspace(yb, yb + 2.0, 81), np.linspace(yt - 2.0, yt, 81)]):
+            ix, iy, phi = O.mls_shape(c, 17.37, Y)
+            assert len(phi) > 0
+            assert np.abs(phi).max() < 1.5
+            assert phi.sum() == pytest.approx(1.0, abs=1e-12)
+            assert (phi * iy).sum() == pytest.approx(Y, abs=1e-11)
 
 
 def test_fit_is_exact_on_linear_fields(O):
