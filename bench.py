@@ -207,6 +207,8 @@ def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="
     sims = build_workload(lbib, W, storage, stream.cuda_stream, alloc, rounding)
     nodes = sum(s.nx * s.ny for s in sims)
     b = lbib.Batch(sims)
+    b.step(2)
+    variant, _ = b.autotune(20)
     b.set_timing(16)
     b.step(warmup)
     torch.cuda.synchronize()
@@ -230,7 +232,7 @@ def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="
             "steps": steps, "ms_per_step": ms / steps, "bytes_per_update": bpu,
             "hbm_roofline_frac_of_step": value * 1e6 * bpu / (peak * 1e9),
             "lattice_kernel_ms": kt["lattice_ms"], "particle_kernel_ms": kt["particle_ms"],
-            "near_kernel_ms": kt["near_ms"],
+            "near_kernel_ms": kt["near_ms"], "lattice_variant": variant,
             "roofline_achieved_gbs": ach, "roofline_frac": ach / peak if ach else None}
 
 
@@ -281,6 +283,9 @@ def run_gpu(args):
     sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc)
     nodes = sum(s.nx * s.ny for s in sims)
     batch = lbib.Batch(sims)
+    # pick the lattice-pass kernel variant on this batch (timing runs only)
+    batch.step(2)
+    variant, variant_ms = batch.autotune(20)
     batch.set_timing(16)
     batch.step(args.warmup)
     torch.cuda.synchronize()
@@ -376,6 +381,8 @@ def run_gpu(args):
                          "kernel": "lattice_kernel", "bytes_per_update": bpu,
                          "lattice_kernel_ms": lat_ms, "particle_kernel_ms": kt["particle_ms"],
                          "near_kernel_ms": kt["near_ms"], "nodes_per_launch": pn["bulk"],
+                         "lattice_variant": variant,
+                         "variant_ms": [round(x, 5) for x in variant_ms],
                          "samples": kt["lattice_n"]},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": base,

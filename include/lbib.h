@@ -214,6 +214,22 @@ lbib_status lbib_batch_destroy(lbib_batch *b);
  * overlapped).  It synchronises the stream. */
 lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples);
 lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count);
+/* Kernel variants of the lattice pass (the bulk pass when particle work is
+ * overlapped), all on the same 1024-node tiles: 0 = 256 threads x one
+ * group of four nodes; 1 = the same, at most 64 registers (four CTAs per
+ * SM); 2 = 128 threads x two groups; 3 = the same, four CTAs per SM.  FP64
+ * storage and the plain (non-overlapped) pass always use variant 0.
+ * lbib_batch_autotune runs the lattice pass of each variant `reps` times on
+ * the batch's current state (timing runs: they write only the buffer the next
+ * step overwrites and leave step counters alone, so the simulation is
+ * unchanged), keeps the fastest for later steps, writes its index to
+ * *variant and the mean milliseconds of each variant to ms[] (either may be
+ * NULL).  Synchronises the stream.  lbib_batch_set_variant selects a variant
+ * directly (e.g. one tuned on an earlier batch of the same shape). */
+#define LBIB_LATTICE_VARIANTS 4
+lbib_status lbib_batch_autotune(lbib_batch *b, int32_t reps, int32_t *variant, double *ms);
+lbib_status lbib_batch_set_variant(lbib_batch *b, int32_t variant);
+
 /* Nodes each lattice pass of the next step updates, at the particles'
  * current near boxes: nodes[0] the lattice (bulk) pass, nodes[1] the
  * near-box pass (NB x NB per particle, rows outside the lattice left out; 0

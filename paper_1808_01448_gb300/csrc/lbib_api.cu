@@ -375,7 +375,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         for (auto &p : s->parts) {
             smem = std::max(smem, particle_smem_bytes(b->kind, p.T, p.nl));
             const int NB = near_edge(p.T);
-            near_tiles += (NB * NB + LB_TILE_NODES - 1) / LB_TILE_NODES;
+            near_tiles += (NB * NB + NEAR_TILE_NODES - 1) / NEAR_TILE_NODES;
             if (NB > s->cfg.nx || (s->cfg.wall_bottom == LBIB_WALL_PERIODIC && NB > s->cfg.ny))
                 boxes_fit = false;
         }
@@ -425,7 +425,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         for (auto &p : sims[i]->parts) {
             const int NB = near_edge(p.T);
             hnt0.push_back((int)hnp.size());
-            for (int t = 0; t < (NB * NB + LB_TILE_NODES - 1) / LB_TILE_NODES; ++t)
+            for (int t = 0; t < (NB * NB + NEAR_TILE_NODES - 1) / NEAR_TILE_NODES; ++t)
                 hnp.push_back((int)hnt0.size() - 1);
         }
     hnp.push_back(0);
@@ -467,6 +467,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->bd.near_part = dnpart;
     b->bd.near_tile0 = dntile0;
     b->bd.total_near_tiles = near_tiles;
+    b->bd.lat_variant = 0;
     b->d_curs = dcurs;
     b->overlap = nparts > 0 && boxes_fit;
     if (b->overlap) {
@@ -901,6 +902,65 @@ lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *cou
         count[k] = cnt[k];
     }
     return LBIB_OK;
+}
+
+// Captured graphs hold the kernel variant; a change of variant drops them.
+static lbib_status use_variant(lbib_batch *b, int variant) {
+    if (b->bd.lat_variant == variant) return LBIB_OK;
+    CK(cudaStreamSynchronize(b->stream));
+    b->bd.lat_variant = variant;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    if (b->nsamples > 0) return lbib_batch_set_timing(b, b->nsamples);
+    return LBIB_OK;
+}
+
+lbib_status lbib_batch_set_variant(lbib_batch *b, int32_t variant) {
+    if (!b) return fail(LBIB_E_ARG, "null batch");
+    if (variant < 0 || variant >= LBIB_LATTICE_VARIANTS)
+        return fail(LBIB_E_ARG, "lattice variant %d outside 0..%d", variant,
+                    LBIB_LATTICE_VARIANTS - 1);
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
+    return use_variant(b, variant);
+}
+
+lbib_status lbib_batch_autotune(lbib_batch *b, int32_t reps, int32_t *variant, double *ms) {
+    if (!b || reps < 1 || reps > 1000) return fail(LBIB_E_ARG, "reps must be 1..1000");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
+    for (lbib_sim *s : b->sims) {
+        lbib_status r = prime(s, b->stream);
+        if (r != LBIB_OK) return r;
+    }
+    const int mode = b->overlap ? 1 : 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    double best = 0.0;
+    int pick = 0;
+    const int saved = b->bd.lat_variant;
+    for (int v = 0; v < LBIB_LATTICE_VARIANTS && e == cudaSuccess; ++v) {
+        b->bd.lat_variant = v;
+        // one untimed run, then reps timed dry runs of the lattice pass
+        if ((e = launch_lattice(b->kind, b->bd, 2, mode, b->stream))) break;
+        if ((e = cudaEventRecord(e0, b->stream))) break;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = launch_lattice(b->kind, b->bd, 2, mode, b->stream);   // reads the current buffer only
+        if (e || (e = cudaEventRecord(e1, b->stream)) || (e = cudaEventSynchronize(e1))) break;
+        float t = 0.f;
+        if ((e = cudaEventElapsedTime(&t, e0, e1))) break;
+        const double mean = t / reps;
+        if (ms) ms[v] = mean;
+        if (v == 0 || mean < best) {
+            best = mean;
+            pick = v;
+        }
+    }
+    b->bd.lat_variant = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "lattice pass timing");
+    if (variant) *variant = pick;
+    return use_variant(b, pick);
 }
 
 lbib_status lbib_batch_pass_nodes(lbib_batch *b, int64_t *nodes) {

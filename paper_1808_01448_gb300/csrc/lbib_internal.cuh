@@ -26,6 +26,9 @@ enum StorageKind { ST_F32 = 0, ST_F64 = 1, ST_F16 = 2, ST_BF16 = 3 };
 constexpr int LB_THREADS = 256;
 constexpr int LB_NPT = 4;
 constexpr int LB_TILE_NODES = LB_THREADS * LB_NPT;
+// Near-box pass: one node per thread (short dependent-load chains, more CTAs).
+constexpr int NEAR_NPT = 1;
+constexpr int NEAR_TILE_NODES = LB_THREADS * NEAR_NPT;
 
 // Error bits of the per-simulation device error word.
 enum { ERR_UNSTABLE = 1 };
@@ -92,6 +95,7 @@ struct BatchDev {
     int *near_tile0;     // first near-box tile of each batch particle
     int total_near_tiles;
     int nsims, nparts, total_tiles;
+    int lat_variant;     // bulk-pass kernel variant (0 .. LBIB_LATTICE_VARIANTS - 1)
 };
 
 // Stochastic rounding of 16-bit stores.  A node's dither word is a hash of
@@ -393,7 +397,8 @@ __device__ __forceinline__ void tile_force(const SimDev &s, ParticleDev *const *
 }
 
 // Launchers (defined in the .cu files), one instantiation per storage kind.
-// mode: 0 every node; 1 bulk (nodes outside the near boxes); 2 near boxes only
+// mode: 0 every node; 1 bulk (nodes outside the near boxes); 2 near boxes only.
+// flip bit 1 marks a timing run of modes 0 / 1 (step counters untouched).
 cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st);
 // mode: 0 overlapped step, 1 init (IB forcing at the current pose), 2 step
 // without the near-box pass.  pdl: launched as a programmatic dependent of

@@ -32,21 +32,27 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
     const R uy = (jy + (R)0.5 * Fy) * irho;
     const R om = pick<R>(s.f_om, s.d_om);
     const R pref = pick<R>(s.f_pref, s.d_pref);
-    // f^eq - w_i = w_i [(rho - 1) - 1.5 rho u.u + rho (3 e.u + 4.5 (e.u)^2)]
+    // f^eq_i - w_i = w_i [A + 3 rho e.u + 4.5 rho (e.u)^2], A = (rho - 1) - 1.5 rho u.u
+    // Guo: S_i = (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
+    // Post-collision d_i (1 - om) + om (f^eq_i - w_i) + S_i, evaluated per pair
+    // of opposite directions (e -> -e flips e.u and e.F): a part even in e,
+    //   w [om A - 3 pref u.F] + 4.5 w (e.u) (om rho (e.u) + 2 pref (e.F)),
+    // and an odd part 3 w (om rho (e.u) + pref (e.F)).
     const R A = drho - (R)1.5 * rho * (ux * ux + uy * uy);
     const R uF = ux * Fx + uy * Fy;
-    constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    constexpr int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const R w = i == 0 ? (R)(4.0 / 9.0) : (i < 5 ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0));
-        const R eu = (R)EX[i] * ux + (R)EY[i] * uy;
-        const R eF = (R)EX[i] * Fx + (R)EY[i] * Fy;
-        const R deq = w * (A + rho * eu * ((R)3 + (R)4.5 * eu));
-        // Guo: (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
-        const R src_i = pref * w * ((R)3 * (eF - uF) + (R)9 * eu * eF);
-        d[i] = d[i] - om * (d[i] - deq) + src_i;
-    }
+    const R c = (R)1 - om, orho = om * rho, p2 = (R)2 * pref;
+    const R base = om * A - (R)3 * pref * uF;
+    d[0] = c * d[0] + (R)(4.0 / 9.0) * base;
+    auto pair = [&](int i, int j, R w, R eu, R eF) {
+        const R even = w * (base + (R)4.5 * eu * (orho * eu + p2 * eF));
+        const R odd = (R)3 * w * (orho * eu + pref * eF);
+        d[i] = c * d[i] + even + odd;
+        d[j] = c * d[j] + even - odd;
+    };
+    pair(1, 3, (R)(1.0 / 9.0), ux, Fx);
+    pair(2, 4, (R)(1.0 / 9.0), uy, Fy);
+    pair(5, 7, (R)(1.0 / 36.0), ux + uy, Fx + Fy);
+    pair(6, 8, (R)(1.0 / 36.0), uy - ux, Fy - Fx);
     // non-finite state or a density outside (0, 2): the run has broken down
     if (!(fabs(drho) < (R)1) || !(fabs(ux) + fabs(uy) < (R)10)) atomicOr(s.err, ERR_UNSTABLE);
 }
@@ -81,7 +87,7 @@ __device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ d
 // from the next group (x periodic).  Same values as pull_node per node.
 template <typename S, typename R, bool STREAM>
 __device__ __forceinline__ void pull_group(const SimDev &s, const S *__restrict__ src, int x0,
-                                           int y, R d[4][9]) {
+                                           int y, R (*d)[9]) {
     const int nx = s.nx, ny = s.ny, N = nx * ny;
     const float inv = s.inv_scale;
     const int ym = y == 0 ? ny - 1 : y - 1;
@@ -159,84 +165,105 @@ __device__ __forceinline__ unsigned outside_near_boxes4(const SimDev &s,
     return keep;
 }
 
-// One launch advances every simulation of a batch by one step.  A CTA owns
-// LB_TILE_NODES consecutive nodes (row-major) of one simulation.  With rows
-// in whole aligned groups of four, thread t takes nodes 4t .. 4t + 3 of the
-// tile (one row) with vector loads and stores; rows next to a wall take the
-// per-node pull.  Otherwise thread t takes nodes t, t + 256, ... (every
+// One launch advances every simulation of a batch by one step.  A CTA of
+// THREADS threads owns LB_TILE_NODES consecutive nodes (row-major) of one
+// simulation.  With rows in whole aligned groups of four, each thread takes
+// GROUPS groups of four consecutive nodes of one row (groups 4 * THREADS
+// nodes apart), with vector loads and stores; the loads of all its groups
+// are issued before any arithmetic.  Rows next to a wall take the per-node
+// pull.  Otherwise a thread takes 4 * GROUPS nodes, THREADS apart (every
 // scalar access of a warp still contiguous, the x - 1 / x + 1 pulls off by
-// one element).
+// one element).  MINB caps registers through the launch bounds.  The
+// variants share the tile, so a batch can switch between them.
 // BULK: skip the nodes of the particles' near boxes (they carry no IB force
 // and are updated by lattice_near_kernel, after the particle pass).
-template <typename S, typename R, bool BULK>
-__global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int flip) {
+// flip bit 1 (DRY): a timing run that leaves the step counter alone; it
+// writes only the buffer the next step overwrites.
+template <typename S, typename R, bool BULK, int THREADS, int GROUPS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int flip) {
+    static_assert(THREADS * 4 * GROUPS == LB_TILE_NODES, "tile size");
+    constexpr int NPT = 4 * GROUPS;
+    const bool dry = (flip & 2) != 0;
+    flip &= 1;
     const int tile = blockIdx.x;
     const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
     const int nx = s.nx;
     const int N = nx * s.ny;
-    if (tile == s.tile0 && threadIdx.x == 0) *s.step += 1;
+    if (!dry && tile == s.tile0 && threadIdx.x == 0) *s.step += 1;
     const int cur = *s.cur ^ flip;
     const S *__restrict__ src = (const S *)s.pop[cur];
     S *__restrict__ dst = (S *)s.pop[cur ^ 1];
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
-    R d[LB_NPT][9];
+    R d[NPT][9];
     if (s.vec4) {
-        const int k = (tile - s.tile0) * LB_TILE_NODES + 4 * (int)threadIdx.x;
-        if (k >= N) return;
-        const int y = k / nx, x0 = k - y * nx;
-        unsigned keep = 0xFu;
-        if (BULK && s.np) {
-            keep = outside_near_boxes4(s, b.parts, cur, x0, y);
-            if (!keep) return;
-        }
-        const bool wall_row = s.wall_b != LBIB_WALL_PERIODIC && (y == 0 || y == s.ny - 1);
-        if (wall_row) {
+        const int kt = (tile - s.tile0) * LB_TILE_NODES + 4 * (int)threadIdx.x;
+        int kg[GROUPS], yg[GROUPS], xg[GROUPS];
+        unsigned keep[GROUPS];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) pull_node<S, R, BULK>(s, src, x0 + j, y, d[j]);
-        } else {
-            pull_group<S, R, BULK>(s, src, x0, y, d);
+        for (int g = 0; g < GROUPS; ++g) {
+            kg[g] = kt + g * 4 * THREADS;
+            yg[g] = kg[g] / nx;
+            xg[g] = kg[g] - yg[g] * nx;
+            keep[g] = kg[g] < N ? 0xFu : 0u;
+            if (BULK && s.np && keep[g]) keep[g] = outside_near_boxes4(s, b.parts, cur, xg[g], yg[g]);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            R Fx = gx, Fy = gy;
-            if (!BULK && s.np) tile_force<R>(s, b.parts, x0 + j, y, Fx, Fy);
-            collide_node<R>(s, d[j], Fx, Fy);
-        }
-        if (keep == 0xFu && sizeof(S) == 2 && s.sround) {
-            unsigned h[4];
+        for (int g = 0; g < GROUPS; ++g) {
+            if (!keep[g]) continue;
+            const int y = yg[g];
+            if (s.wall_b != LBIB_WALL_PERIODIC && (y == 0 || y == s.ny - 1)) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) h[j] = dither_word(k + j, (float)d[j][0]);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
-                const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
-                                       dither_plane(h[2], i), dither_plane(h[3], i)};
-                Vec4<S, BULK>::st_r(dst + i * N + k, o, s.scale, r);
+                for (int j = 0; j < 4; ++j) pull_node<S, R, BULK>(s, src, xg[g] + j, y, d[4 * g + j]);
+            } else {
+                pull_group<S, R, BULK>(s, src, xg[g], y, &d[4 * g]);
             }
-        } else if (keep == 0xFu) {
+        }
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
-                Vec4<S, BULK>::st(dst + i * N + k, o, s.scale);
+        for (int g = 0; g < GROUPS; ++g) {
+            if (!keep[g]) continue;
+            const int k = kg[g];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                R Fx = gx, Fy = gy;
+                if (!BULK && s.np) tile_force<R>(s, b.parts, xg[g] + j, yg[g], Fx, Fy);
+                collide_node<R>(s, d[4 * g + j], Fx, Fy);
             }
-        } else {
+            if (keep[g] == 0xFu && sizeof(S) == 2 && s.sround) {
+                unsigned h[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (keep & (1u << j)) store_node<S, R, BULK>(s, dst, N, k + j, d[j]);
+                for (int j = 0; j < 4; ++j) h[j] = dither_word(k + j, (float)d[4 * g + j][0]);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
+                    const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
+                                           dither_plane(h[2], i), dither_plane(h[3], i)};
+                    Vec4<S, BULK>::st_r(dst + i * N + k, o, s.scale, r);
+                }
+            } else if (keep[g] == 0xFu) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
+                    Vec4<S, BULK>::st(dst + i * N + k, o, s.scale);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (keep[g] & (1u << j)) store_node<S, R, BULK>(s, dst, N, k + j, d[4 * g + j]);
+            }
         }
         return;
     }
     const int k0 = (tile - s.tile0) * LB_TILE_NODES + (int)threadIdx.x;
-    bool skip[LB_NPT];
-    // node coordinates: one division per thread, then step by LB_THREADS
-    int xs[LB_NPT], ys[LB_NPT];
+    bool skip[NPT];
+    // node coordinates: one division per thread, then step by THREADS
+    int xs[NPT], ys[NPT];
     {
         int y = k0 / nx, x = k0 - y * nx;
 #pragma unroll
-        for (int j = 0; j < LB_NPT; ++j) {
+        for (int j = 0; j < NPT; ++j) {
             xs[j] = x;
             ys[j] = y;
-            x += LB_THREADS;
+            x += THREADS;
             while (x >= nx) {
                 x -= nx;
                 ++y;
@@ -244,19 +271,19 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_kernel(BatchDev b, int fli
         }
     }
 #pragma unroll
-    for (int j = 0; j < LB_NPT; ++j) {
-        skip[j] = k0 + j * LB_THREADS >= N;
+    for (int j = 0; j < NPT; ++j) {
+        skip[j] = k0 + j * THREADS >= N;
         if (BULK && !skip[j] && s.np) skip[j] = in_near_box(s, b.parts, cur, xs[j], ys[j]);
     }
 #pragma unroll
-    for (int j = 0; j < LB_NPT; ++j)
+    for (int j = 0; j < NPT; ++j)
         if (!skip[j]) pull_node<S, R, BULK>(s, src, xs[j], ys[j], d[j]);
 #pragma unroll
-    for (int j = 0; j < LB_NPT; ++j) {
+    for (int j = 0; j < NPT; ++j) {
         if (!skip[j]) {
             R Fx = gx, Fy = gy;
             if (!BULK && s.np) tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
-            collide_store<S, R, BULK>(s, dst, N, k0 + j * LB_THREADS, d[j], Fx, Fy);
+            collide_store<S, R, BULK>(s, dst, N, k0 + j * THREADS, d[j], Fx, Fy);
         }
     }
 }
@@ -286,11 +313,11 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
     const S *__restrict__ src = (const S *)s.pop[cur];
     S *__restrict__ dst = (S *)s.pop[cur ^ 1];
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
-    const int k0 = (tile - t0) * LB_TILE_NODES + (int)threadIdx.x;
-    int xs[LB_NPT], ys[LB_NPT];
-    bool skip[LB_NPT];
+    const int k0 = (tile - t0) * NEAR_TILE_NODES + (int)threadIdx.x;
+    int xs[NEAR_NPT], ys[NEAR_NPT];
+    bool skip[NEAR_NPT];
 #pragma unroll
-    for (int j = 0; j < LB_NPT; ++j) {
+    for (int j = 0; j < NEAR_NPT; ++j) {
         const int k = k0 + j * LB_THREADS;
         const int by = k / NB, bx = k - by * NB;
         int x = ox + bx;
@@ -304,12 +331,12 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
         ys[j] = y;
         skip[j] = k >= NB * NB || y < 0 || y >= ny;
     }
-    R d[LB_NPT][9];
+    R d[NEAR_NPT][9];
 #pragma unroll
-    for (int j = 0; j < LB_NPT; ++j)
+    for (int j = 0; j < NEAR_NPT; ++j)
         if (!skip[j]) pull_node<S, R>(s, src, xs[j], ys[j], d[j]);
 #pragma unroll
-    for (int j = 0; j < LB_NPT; ++j) {
+    for (int j = 0; j < NEAR_NPT; ++j) {
         if (!skip[j]) {
             R Fx = gx, Fy = gy;
             tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
@@ -388,17 +415,45 @@ cudaError_t by_kind(int kind, F &&f) {
 
 }  // namespace
 
+// Bulk-pass variants (threads, groups of four nodes per thread, minimum
+// resident CTAs per SM); FP64 storage and the plain pass use variant 0.
+template <typename S, typename R, bool BULK>
+cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_t st) {
+    constexpr bool TUNED = BULK && sizeof(S) <= 4;
+    if (!TUNED) variant = 0;
+    switch (variant) {
+        case 1:
+            if constexpr (TUNED) {
+                lattice_kernel<S, R, BULK, 256, 1, 4><<<b.total_tiles, 256, 0, st>>>(b, flip);
+                break;
+            }
+            [[fallthrough]];
+        case 2:
+            if constexpr (TUNED) {
+                lattice_kernel<S, R, BULK, 128, 2, 1><<<b.total_tiles, 128, 0, st>>>(b, flip);
+                break;
+            }
+            [[fallthrough]];
+        case 3:
+            if constexpr (TUNED) {
+                lattice_kernel<S, R, BULK, 128, 2, 4><<<b.total_tiles, 128, 0, st>>>(b, flip);
+                break;
+            }
+            [[fallthrough]];
+        default:
+            lattice_kernel<S, R, BULK, 256, 1, 1><<<b.total_tiles, 256, 0, st>>>(b, flip);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st) {
     return by_kind(kind, [&](auto sv, auto rv) {
         using S = decltype(sv);
         using R = decltype(rv);
-        if (mode == 0) {
-            lattice_kernel<S, R, false><<<b.total_tiles, LB_THREADS, 0, st>>>(b, flip);
-        } else if (mode == 1) {
-            lattice_kernel<S, R, true><<<b.total_tiles, LB_THREADS, 0, st>>>(b, flip);
-        } else if (b.total_near_tiles > 0) {
+        if (mode == 0) return launch_variant<S, R, false>(b.lat_variant, b, flip, st);
+        if (mode == 1) return launch_variant<S, R, true>(b.lat_variant, b, flip, st);
+        if (b.total_near_tiles > 0)
             lattice_near_kernel<S, R><<<b.total_near_tiles, LB_THREADS, 0, st>>>(b, flip);
-        }
         return cudaGetLastError();
     });
 }

@@ -109,6 +109,8 @@ def lib():
                 "lbib_batch_set_timing": [vp, i32],
                 "lbib_batch_kernel_times": [vp, pd, C.POINTER(i64)],
                 "lbib_batch_pass_nodes": [vp, C.POINTER(i64)],
+                "lbib_batch_autotune": [vp, i32, C.POINTER(i32), pd],
+                "lbib_batch_set_variant": [vp, i32],
                 "lbib_synchronize": [vp],
                 "lbib_read_state": [vp, C.POINTER(State), C.POINTER(ParticleState), i32,
                                     pd, pd, pd, C.c_size_t],
@@ -323,6 +325,18 @@ class Batch:
         _check(lib().lbib_batch_kernel_times(self._h, ms, cnt))
         return {"lattice_ms": ms[0], "lattice_n": cnt[0], "particle_ms": ms[1],
                 "particle_n": cnt[1], "near_ms": ms[2], "near_n": cnt[2]}
+
+    def autotune(self, reps=20):
+        """Time the lattice-pass kernel variants on this batch (without
+        changing its state) and keep the fastest; returns (variant, ms per
+        variant)."""
+        v = C.c_int32()
+        ms = (C.c_double * 4)()
+        _check(lib().lbib_batch_autotune(self._h, int(reps), C.byref(v), ms))
+        return v.value, list(ms)
+
+    def set_variant(self, variant):
+        _check(lib().lbib_batch_set_variant(self._h, int(variant)))
 
     def pass_nodes(self):
         """Nodes updated per step by the bulk and near-box lattice passes at

@@ -163,6 +163,7 @@ class LbibEngine:
         self.alloc = allocator
         self.batches = {}               # storage -> Batch
         self.sims = {}                  # handle id -> Sim
+        self.variants = {}              # storage -> tuned lattice-pass variant
 
     def create(self, req):
         st = req["storage"]
@@ -173,12 +174,25 @@ class LbibEngine:
         return s
 
     def rebuild(self, members):
-        for b in self.batches.values():
-            b.close()
+        # only the storage groups whose membership changed get a new batch
         groups = {}
         for _, s, st in members:
             groups.setdefault(st, []).append(s)
-        self.batches = {st: self.L.Batch(ss) for st, ss in groups.items()}
+        for st in list(self.batches):
+            b = self.batches[st]
+            if st not in groups or [id(x) for x in b.sims] != [id(x) for x in groups[st]]:
+                b.close()
+                del self.batches[st]
+        for st, ss in groups.items():
+            if st not in self.batches:
+                b = self.L.Batch(ss)
+                # the lattice-pass variant is tuned on the first batch of each
+                # storage format and reused for the later ones
+                if st in self.variants:
+                    b.set_variant(self.variants[st])
+                else:
+                    self.variants[st] = b.autotune(10)[0]
+                self.batches[st] = b
 
     def step(self, n):
         for b in self.batches.values():
@@ -191,9 +205,10 @@ class LbibEngine:
 
     def destroy(self, s):
         # the batch holding s is rebuilt before the next step
-        for b in self.batches.values():
-            b.close()
-        self.batches = {}
+        for st, b in list(self.batches.items()):
+            if any(x is s for x in b.sims):
+                b.close()
+                del self.batches[st]
         self.sims.pop(id(s), None)
         s.close()
 

@@ -75,3 +75,33 @@ def test_design_sweep_smallest_member_vs_oracle(O, L):
     b.close()
     for s in sims:
         s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_lattice_variants_give_identical_bits(L, storage):
+    """Every lattice-pass kernel variant computes the same bits, and tuning
+    (timing runs of each variant) leaves the simulations unchanged."""
+    sweep = W.design_sweep()[:5]
+    runs = []
+    for v in range(4):
+        sims = [make(L, c, p, storage) for c, p in sweep]
+        b = L.Batch(sims)
+        b.step(3)
+        if v == 0:
+            before = [s.populations() for s in sims]
+            steps = [s.step_count for s in sims]
+            best, ms = b.autotune(3)
+            assert 0 <= best < 4 and all(m > 0 for m in ms)
+            for s, f, n in zip(sims, before, steps):
+                np.testing.assert_array_equal(s.populations(), f)
+                assert s.step_count == n
+        b.set_variant(v)
+        b.step(37)
+        runs.append([(s.populations(), s.particle(0)) for s in sims])
+        b.close()
+        for s in sims:
+            s.close()
+    for other in runs[1:]:
+        for (fa, pa), (fb, pb) in zip(runs[0], other):
+            np.testing.assert_array_equal(fa, fb)
+            assert pa == pb
