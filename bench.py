@@ -286,6 +286,9 @@ def run_gpu(args):
     # pick the lattice-pass kernel variant on this batch (timing runs only)
     batch.step(2)
     variant, variant_ms = batch.autotune(20)
+    if args.variant is not None:        # fixed choice (profiling runs)
+        variant = args.variant
+        batch.set_variant(variant)
     batch.set_timing(16)
     batch.step(args.warmup)
     torch.cuda.synchronize()
@@ -411,6 +414,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=60,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--serve-quantum", type=int, default=1000)
+    ap.add_argument("--variant", type=int, default=None,
+                    help="lattice-pass kernel variant instead of the autotuner's choice")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -147,7 +147,10 @@ typedef struct lbib_particle {
 
 /* Particle state after the last completed step: pose and velocities, the
  * loads of that step (hydrodynamic Eq. 7-8, bond Eq. 9, wall Eq. 12), mass
- * properties, and counts of elements, ligands, probing and bonded ligands. */
+ * properties, and counts of elements, ligands, probing and bonded ligands.
+ * p_adhesion is the probability of adhesion of the paper's Fig. 6 at this
+ * step: bonded ligands over the ligands close enough to a receptor wall to
+ * bond (n_bonded / n_probing; 0 when none is). */
 typedef struct lbib_particle_state {
     double xc, yc, theta, u, v, omega;
     double Fh[2], Mh;
@@ -155,6 +158,7 @@ typedef struct lbib_particle_state {
     double Fw[2];
     double area, mass, inertia, r_eq;
     int32_t nl, n_ligands, n_probing, n_bonded;
+    double p_adhesion;
 } lbib_particle_state;
 
 typedef struct lbib_state {

@@ -1041,6 +1041,7 @@ lbib_status lbib_read_state(lbib_sim *s, lbib_state *st, lbib_particle_state *pa
             o.area = p.area; o.mass = p.mass; o.inertia = p.inertia; o.r_eq = p.r_eq;
             o.nl = p.nl; o.n_ligands = p.n_ligands; o.n_probing = h.n_probing;
             o.n_bonded = h.n_bonded;
+            o.p_adhesion = h.n_probing > 0 ? (double)h.n_bonded / h.n_probing : 0.0;
         }
     }
     if (rho || ux || uy) {

@@ -28,7 +28,7 @@
 // Eq. 12, the update) run on one thread, per-point setup on one thread per
 // point (kept in shared memory), and the FP64 sums on one warp per quantity
 // over per-element contributions kept in shared memory.  Each point's 4 x 4
-// support is summed by a quarter-warp (two nodes per lane, three shuffles).
+// support is summed by the point's own thread from the staged moments.
 #include "lbib_internal.cuh"
 
 namespace lbib {
@@ -37,8 +37,8 @@ namespace {
 
 constexpr int P_THREADS = 512;   // >= LBIB_MAX_MARKERS: one marker per thread
 
-// Cubic B-spline of radius 2, branch-free (lanes of a quarter-warp straddle the
-// two pieces).
+// Cubic B-spline of radius 2, branch-free (the nodes of a support straddle
+// the two pieces).
 template <typename R>
 __device__ __forceinline__ R bspline(R r) {
     const R a = fabs(r);
@@ -214,14 +214,6 @@ __device__ __forceinline__ void setup_point(const SimDev &s, int bx, int by, R X
     pt.inv_v[l] = inv_v;
 }
 
-// Sum over the eight lanes of a quarter-warp.
-template <typename T>
-__device__ __forceinline__ T qw_sum(T v) {
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // FP64 sum of n values of an array by one warp.
 template <typename R>
 __device__ __forceinline__ double warp_sum_array(const R *a, int n) {
@@ -252,38 +244,60 @@ __device__ __noinline__ void pull_moments(const SimDev &s, const S *pop, int x, 
     node_moments(d, drho, jx, jy);
 }
 
-// Support node (a, b) of point l: its weight and the node's moments (staged
-// region, else pulled).  false when the node has no weight.
-template <typename S, typename R>
-__device__ __forceinline__ bool lane_moments(const SimDev &s, const S *pop, const Points<R> &pt,
-                                             int l, int a, int b, const R *mr, const R *mjx,
-                                             const R *mjy, const uint8_t *flag, int Tm,
-                                             int rx0, int ry0, R &dx,
-                                             R &dy, R &w, R &drho, R &jx, R &jy) {
+// Walks the 4 x 4 support of point l (after setup_point) in a fixed order,
+// calling f(w, dx, dyc, phi, drho, jx, jy) for every node of non-zero weight:
+// w = the normalised weight w_k / W, dx and dyc = the node's offsets in the
+// centred basis, phi = the MLS shape function, and the node's moments
+// (staged region, else pulled).  One thread per point: the staged region is
+// in shared memory, so the sixteen nodes are a short loop, not a reduction.
+template <typename S, typename R, typename F>
+__device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const Points<R> &pt,
+                                            int l, const R *mr, const R *mjx, const R *mjy,
+                                            const uint8_t *flag, int Tm, int rx0, int ry0,
+                                            F &&f) {
     const int rows = pt.rows[l];
-    if (!(rows & 16) || !(rows & (1 << b))) return false;
-    dx = (R)(a - 1) - pt.fx[l];
-    dy = (R)(b - 1) - pt.fy[l];
-    w = bspline(dx) * bspline(dy) * pt.invW[l];
-    if (w == (R)0) return false;
-    const int ix = pt.ix0[l] + a, iy = pt.iy0[l] + b;
-    const int u = ix - rx0, v = iy - ry0;
-    if ((unsigned)u < (unsigned)Tm && (unsigned)v < (unsigned)Tm && flag[v * Tm + u]) {
-        const int i = v * Tm + u;
-        drho = mr[i];
-        jx = mjx[i];
-        jy = mjy[i];
-    } else {
-        int xx = ix % s.nx;
-        if (xx < 0) xx += s.nx;
-        int yy = iy;
-        if (s.wall_b == LBIB_WALL_PERIODIC) {
-            yy %= s.ny;
-            if (yy < 0) yy += s.ny;
-        }
-        pull_moments<S, R>(s, pop, xx, yy, drho, jx, jy);
+    if (!(rows & 16)) return;
+    const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l], mu_v = pt.mu_v[l];
+    const int ix0 = pt.ix0[l], iy0 = pt.iy0[l];
+    R wx[4], dxa[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        dxa[a] = (R)(a - 1) - fx;
+        wx[a] = bspline(dxa[a]);
     }
-    return true;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        if (!(rows & (1 << b))) continue;
+        const R dy = (R)(b - 1) - fy;
+        const R wy = bspline(dy) * invW;
+        if (wy == (R)0) continue;
+        const R dyc = dy - mu;
+        const R py = wy * ((R)1 - dyc * mu_v);
+        const int v = iy0 + b - ry0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const R w = wx[a] * wy;
+            if (w == (R)0) continue;
+            const int u = ix0 + a - rx0;
+            R drho, jx, jy;
+            if ((unsigned)u < (unsigned)Tm && (unsigned)v < (unsigned)Tm && flag[v * Tm + u]) {
+                const int i = v * Tm + u;
+                drho = mr[i];
+                jx = mjx[i];
+                jy = mjy[i];
+            } else {
+                int xx = (ix0 + a) % s.nx;
+                if (xx < 0) xx += s.nx;
+                int yy = iy0 + b;
+                if (s.wall_b == LBIB_WALL_PERIODIC) {
+                    yy %= s.ny;
+                    if (yy < 0) yy += s.ny;
+                }
+                pull_moments<S, R>(s, pop, xx, yy, drho, jx, jy);
+            }
+            f(w, dxa[a], dyc, wx[a] * py, drho, jx, jy);
+        }
+    }
 }
 
 // Edge of the staged moment region: the force tile plus two nodes a side,
@@ -379,11 +393,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
 
     const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // a point's 4 x 4 support is taken by a quarter-warp: lane q holds
-    // nodes (q & 3, q >> 2) and (q & 3, (q >> 2) + 2)
-    const int qw = tid >> 3, ql = lane & 7;
-    constexpr int NQ = P_THREADS / 8;
-    const int a = ql & 3, bb = ql >> 2;
     const double yb = s.wall_b == LBIB_WALL_BOUNCE_BACK ? -0.5 : 0.0;
     const double yt = s.wall_t == LBIB_WALL_BOUNCE_BACK ? (double)s.ny - 0.5 : (double)(s.ny - 1);
 
@@ -525,53 +534,37 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     __syncthreads();
 
     if (!init) {
-        // ---- 2. hydrodynamic loads (Eq. 7-8) ------------------------------
-        if (tid < nl)
-            setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[tid] + (R)1.2 * nxw[tid],
-                           ps.fyc + ry[tid] + (R)1.2 * nyw[tid], pt, tid);
-        __syncthreads();
+        // ---- 2. hydrodynamic loads (Eq. 7-8), one thread per probe --------
         const R nu = pick<R>(s.f_nu, s.d_nu);
-#pragma unroll 1
-        for (int base = 0; base < nl; base += NQ) {
-            const int l = base + qw;
-            const bool act = l < nl;
+        if (tid < nl) {
+            const int l = tid;
+            setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l] + (R)1.2 * nxw[l],
+                           ps.fyc + ry[l] + (R)1.2 * nyw[l], pt, l);
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                R dx, dy, w, drho, jx, jy;
-                if (act && lane_moments<S, R>(s, pop, pt, l, a, bb + 2 * h, mr, mjx, mjy, flag, Tm,
-                                              rx0, ry0, dx, dy, w, drho, jx, jy)) {
-                    const R irho = recip((R)1 + drho);
-                    const R ux = jx * irho, uy = jy * irho;
-                    const R dyc = dy - pt.mu[l];
-                    s_rho += w * ((R)1 - dyc * pt.mu_v[l]) * drho;
-                    s_ux += w * dx * ux;
-                    s_uy += w * dyc * ux;
-                    s_vx += w * dx * uy;
-                    s_vy += w * dyc * uy;
-                }
+            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0,
+                              [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
+                                  const R irho = recip((R)1 + drho);
+                                  const R ux = jx * irho, uy = jy * irho;
+                                  s_rho += phi * drho;
+                                  s_ux += w * dx * ux;
+                                  s_uy += w * dyc * ux;
+                                  s_vx += w * dx * uy;
+                                  s_vy += w * dyc * uy;
+                              });
+            R tx = 0, ty = 0;
+            if (pt.rows[l] & 16) {
+                const R iv = pt.inv_v[l];
+                const R dudx = (R)3 * s_ux, dudy = s_uy * iv;
+                const R dvdx = (R)3 * s_vx, dvdy = s_vy * iv;
+                const R p = s_rho * (R)(1.0 / 3.0);
+                const R nxl = nxw[l], nyl = nyw[l];
+                const R txy = nu * (dudy + dvdx);
+                tx = (-p * nxl + nu * (R)2 * dudx * nxl + txy * nyl) * sS[l];
+                ty = (-p * nyl + txy * nxl + nu * (R)2 * dvdy * nyl) * sS[l];
             }
-            s_rho = qw_sum(s_rho);
-            s_ux = qw_sum(s_ux);
-            s_uy = qw_sum(s_uy);
-            s_vx = qw_sum(s_vx);
-            s_vy = qw_sum(s_vy);
-            if (act && ql == 0) {
-                R tx = 0, ty = 0;
-                if (pt.rows[l] & 16) {
-                    const R iv = pt.inv_v[l];
-                    const R dudx = (R)3 * s_ux, dudy = s_uy * iv;
-                    const R dvdx = (R)3 * s_vx, dvdy = s_vy * iv;
-                    const R p = s_rho * (R)(1.0 / 3.0);
-                    const R nxl = nxw[l], nyl = nyw[l];
-                    const R txy = nu * (dudy + dvdx);
-                    tx = (-p * nxl + nu * (R)2 * dudx * nxl + txy * nyl) * sS[l];
-                    ty = (-p * nyl + txy * nxl + nu * (R)2 * dvdy * nyl) * sS[l];
-                }
-                c[0][l] = tx;
-                c[1][l] = ty;
-                c[2][l] = rx[l] * ty - ry[l] * tx;
-            }
+            c[0][l] = tx;
+            c[1][l] = ty;
+            c[2][l] = rx[l] * ty - ry[l] * tx;
         }
 
         // ---- 3. bonds (Eq. 9-11), one element per thread -------------------
@@ -697,43 +690,30 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     }
 
     // ---- 6. IB direct forcing at the (new) pose ---------------------------
+    // (the tile is next touched by the spreading, after a barrier)
     for (int i = tid; i < 2 * T * T; i += P_THREADS) tile[i] = (R)0;
-    __syncthreads();
-    if (tid < nl) setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[tid], ps.fyc + ry[tid], pt, tid);
-    __syncthreads();
     const R ghx = (R)0.5 * pick<R>(s.f_gx, s.gx), ghy = (R)0.5 * pick<R>(s.f_gy, s.gy);
-#pragma unroll 1
-    for (int base = 0; base < nl; base += NQ) {
-        const int l = base + qw;
-        const bool act = l < nl;
+    if (tid < nl) {
+        const int l = tid;
+        setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l], ps.fyc + ry[l], pt, l);
         R s_rho = 0, s_u = 0, s_v = 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            R dx, dy, w, drho, jx, jy;
-            if (act && lane_moments<S, R>(s, pop, pt, l, a, bb + 2 * h, mr, mjx, mjy, flag, Tm, rx0,
-                                          ry0, dx, dy, w, drho, jx, jy)) {
-                const R irho = recip((R)1 + drho);
-                const R phi = w * ((R)1 - (dy - pt.mu[l]) * pt.mu_v[l]);
-                s_rho += phi * drho;
-                s_u += phi * ((jx + ghx) * irho);
-                s_v += phi * ((jy + ghy) * irho);
-            }
+        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0,
+                          [&](R, R, R, R phi, R drho, R jx, R jy) {
+                              const R irho = recip((R)1 + drho);
+                              s_rho += phi * drho;
+                              s_u += phi * ((jx + ghx) * irho);
+                              s_v += phi * ((jy + ghy) * irho);
+                          });
+        R Fx = 0, Fy = 0;
+        if (pt.rows[l] & 16) {
+            const R rl = (R)1 + s_rho;
+            const R udx = ps.uR - ps.omR * ry[l];
+            const R udy = ps.vR + ps.omR * rx[l];
+            Fx = (R)2 * rl * (udx - s_u) * sS[l];
+            Fy = (R)2 * rl * (udy - s_v) * sS[l];
         }
-        s_rho = qw_sum(s_rho);
-        s_u = qw_sum(s_u);
-        s_v = qw_sum(s_v);
-        if (act && ql == 0) {
-            R Fx = 0, Fy = 0;
-            if (pt.rows[l] & 16) {
-                const R rl = (R)1 + s_rho;
-                const R udx = ps.uR - ps.omR * ry[l];
-                const R udy = ps.vR + ps.omR * rx[l];
-                Fx = (R)2 * rl * (udx - s_u) * sS[l];
-                Fy = (R)2 * rl * (udy - s_v) * sS[l];
-            }
-            sFx[l] = Fx;
-            sFy[l] = Fy;
-        }
+        sFx[l] = Fx;
+        sFy[l] = Fy;
     }
     __syncthreads();
     // colour-ordered spreading into the tile; origin floor(X_c) - T/2

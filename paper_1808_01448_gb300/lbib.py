@@ -72,7 +72,7 @@ class ParticleState(C.Structure):
         ("area", C.c_double), ("mass", C.c_double), ("inertia", C.c_double),
         ("r_eq", C.c_double),
         ("nl", C.c_int32), ("n_ligands", C.c_int32), ("n_probing", C.c_int32),
-        ("n_bonded", C.c_int32),
+        ("n_bonded", C.c_int32), ("p_adhesion", C.c_double),
     ]
 
 

@@ -38,9 +38,13 @@ def hamaker_lu(H: float, nu: float) -> float:
 
 def thermal_energy(sigma: float, y_cr: float, y_eq_ratio: float = 0.5,
                    sigma_star_ratio: float = 0.5) -> float:
-    """k_B T such that the exponent of Eq. 11 is 1 at the critical length."""
+    """k_B T such that the exponent of Eq. 11 has magnitude 1 at the critical
+    length: +1 for slip bonds (sigma* < sigma), -1 for catch bonds
+    (sigma* > sigma).  For sigma* = sigma (ideal bonds) the exponent is 0 and
+    k_B T is taken as if sigma* were sigma / 2."""
     d = (1.0 - y_eq_ratio) * y_cr
-    return (1.0 - sigma_star_ratio) * sigma * d * d / 2.0
+    r = abs(1.0 - sigma_star_ratio) or 0.5
+    return r * sigma * d * d / 2.0
 
 
 def ramanujan_perimeter(a: float, b: float) -> float:
@@ -115,14 +119,19 @@ def adhesion_particle(cfg: dict, shape: str, radius_eq: float, x: float,
                 ligand_density=ligand_density, sigma=sigma)
 
 
-def adhesion_params(H: float, nu: float, strength: int) -> dict:
+def adhesion_params(H: float, nu: float, strength: int, sigma_star_ratio: float = 0.5,
+                    ycr_over_h: float = YCR_OVER_H) -> dict:
     """Bond and wall-force constants in lattice units for bond strength 1 or
     2: Table 1's dimensionless groups scaled by rho nu^2 / H (spring) and
-    rho nu^2 H (Hamaker), k_f / k_r0 = 8.5e3, k_B T from thermal_energy."""
+    rho nu^2 H (Hamaker), k_f / k_r0 = 8.5e3, k_B T from thermal_energy.
+    sigma_star_ratio = sigma* / sigma (Eq. 11): 0.5 slip bonds (the paper's
+    choice), above 1 catch bonds."""
     sigma = bond_sigma(strength, H, nu)
-    y_cr = YCR_OVER_H * H
+    y_cr = ycr_over_h * H
     return dict(sigma=sigma, y_cr=y_cr, k_r0=K_R0, k_f=KF_OVER_KR0 * K_R0,
-                kBT=thermal_energy(sigma, y_cr), hamaker=hamaker_lu(H, nu))
+                sigma_star_ratio=sigma_star_ratio,
+                kBT=thermal_energy(sigma, y_cr, sigma_star_ratio=sigma_star_ratio),
+                hamaker=hamaker_lu(H, nu))
 
 
 def single_ellipse_sweep(nx: int = 1024, ny: int = 256, radius_eq: float = 20.0,
@@ -145,6 +154,25 @@ def single_ellipse_sweep(nx: int = 1024, ny: int = 256, radius_eq: float = 20.0,
                                   ligand_density=ligand_density, sigma=sigma)
             out.append((cfg, [p]))
             sim_id += 1
+    return out
+
+
+def ycr_sweep(ycr_over_h=(3.4e-3, 6.8e-3, 1.36e-2), nx: int = 1024, ny: int = 256,
+              shape: str = "ar2", Re: float = 0.1, ligand_density: float = 0.7,
+              strength: int = 2, sigma_star_ratio: float = 0.5, seed: int = 7):
+    """Elliptical particle (equal area to a circle of radius 20) in the shear
+    channel for several critical bond lengths y_cr / H (the paper's Fig. 7
+    study; 6.8e-3 is its default), one simulation each; sigma_star_ratio
+    above 1 gives catch bonds.  Returns (config, [particle]) pairs."""
+    out = []
+    for sim_id, ycr in enumerate(ycr_over_h):
+        cfg = shear_channel(nx, ny, Re, seed=seed, sim_id=sim_id)
+        ap = adhesion_params(ny - 1, (cfg["tau"] - 0.5) / 3.0, strength, sigma_star_ratio, ycr)
+        sigma = ap.pop("sigma")
+        cfg.update(ap)
+        p = adhesion_particle(cfg, shape, 20.0, x=nx / 4.0, ligand_density=ligand_density,
+                              sigma=sigma)
+        out.append((cfg, [p]))
     return out
 
 

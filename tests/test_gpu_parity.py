@@ -142,6 +142,45 @@ def test_full_step_parity_f64_with_bonds(O, L):
     assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) < 1e-11
 
 
+def test_catch_bond_parity_f64(O, L):
+    """Catch bonds (sigma* = 2 sigma in Eq. 11: a stretched bond breaks less
+    often): bond states bit for bit with the oracle at every step, and the
+    adhesion probability n_bonded / n_probing of the oracle's counts."""
+    cfg, p = adhesion_case()
+    cfg["sigma_star_ratio"] = 2.0
+    o, g = pair(O, L, cfg, [p])
+    for t in range(100):
+        o.step(1)
+        g.step(1)
+        assert np.array_equal(o.bonds(0)[0], g.bonds(0)[0]), f"step {t + 1}"
+    po, pg = o.particle(0), g.particle(0)
+    assert pg["n_bonded"] > 0
+    assert pg["p_adhesion"] == po["n_bonded"] / po["n_probing"]
+    assert pg["xc"] == pytest.approx(po["xc"], abs=1e-10)
+
+
+def test_critical_length_sweep(L):
+    """The paper's Fig. 7 study: a longer critical bond length lets more
+    ligands probe the wall and more bonds form."""
+    sims = []
+    for cfg, parts in W.ycr_sweep():
+        s = L.Sim(storage="f32", **cfg)
+        for q in parts:
+            s.add_particle(**q)
+        sims.append(s)
+    b = L.Batch(sims)
+    probing, bonded = [0] * len(sims), [0] * len(sims)
+    for _ in range(20):
+        b.step(100)
+        for i, s in enumerate(sims):
+            st = s.particle(0)
+            probing[i] += st["n_probing"]
+            bonded[i] += st["n_bonded"]
+    assert probing[0] < probing[1] < probing[2]
+    assert bonded[0] < bonded[2]
+    b.close()
+
+
 @pytest.mark.parametrize("shape", ["circle", "ar3"])
 def test_full_step_parity_f32(O, L, shape):
     cfg, p = adhesion_case(shape=shape, Re=0.1, nx=128, ny=48, r=7.0)
