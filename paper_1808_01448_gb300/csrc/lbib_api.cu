@@ -169,9 +169,85 @@ SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
     return d;
 }
 
-// Polygon elements, mass properties, ligands and marker colouring.  Two
-// markers of one colour are at least 4 sqrt 2 apart, so their 4 x 4 supports
-// are disjoint in some axis for every rotation of the body.
+// Marker colouring for the spreading: two markers of one colour are at least
+// 4 sqrt 2 apart, so their 4 x 4 supports are disjoint in some axis for every
+// rotation of the body, and each colour is one pass of the spreading.  Markers
+// follow the outline, so colouring consecutive blocks of K or K + 1 markers
+// 0, 1, 2, ... (K + 1 colours, same-colour markers at least K apart along the
+// outline) usually needs fewer colours than a greedy pass, which leaves stray
+// colours where the outline closes; so does a cyclic greedy pass (each marker
+// takes the next free colour after its predecessor's).  The colouring with
+// the fewest colours is kept.  No heap use.
+// Returns the number of colours.
+int color_markers(const double *mx, const double *my, int n, int *color) {
+    const double D2 = 32.0 * (1.0 + 1e-9);
+    auto valid = [&](const int *c) {
+        for (int l = 0; l < n; ++l)
+            for (int q = l + 1; q < n; ++q)
+                if (c[l] == c[q]) {
+                    const double dx = mx[l] - mx[q], dy = my[l] - my[q];
+                    if (dx * dx + dy * dy < D2) return false;
+                }
+        return true;
+    };
+    // greedy in index order
+    int nc = 0;
+    for (int l = 0; l < n; ++l) {
+        char used[LBIB_MAX_MARKERS + 1] = {0};
+        for (int q = 0; q < l; ++q) {
+            const double dx = mx[l] - mx[q], dy = my[l] - my[q];
+            if (dx * dx + dy * dy < D2) used[color[q]] = 1;
+        }
+        int c = 0;
+        while (c < nc && used[c]) ++c;
+        color[l] = c;
+        if (c == nc) ++nc;
+    }
+    // blocks of consecutive markers
+    int blk[LBIB_MAX_MARKERS];
+    for (int K = 2; K + 1 < nc && K <= n; ++K) {
+        const int q = n / K, r = n % K;     // r blocks of K + 1, q - r of K
+        if (q < r) continue;
+        int l = 0;
+        for (int b = 0; b < q; ++b)
+            for (int j = 0; j < K + (b < r ? 1 : 0); ++j) blk[l++] = j;
+        if (!valid(blk)) continue;
+        for (int i = 0; i < n; ++i) color[i] = blk[i];
+        nc = K + (r > 0 ? 1 : 0);
+        break;
+    }
+    // cyclic greedy with C colours: each marker takes the first colour after
+    // its predecessor's, in cyclic order, that no marker already coloured
+    // within reach has
+    for (int C = 2; C < nc; ++C) {
+        bool ok = true;
+        int prev = C - 1;
+        for (int l = 0; l < n && ok; ++l) blk[l] = -1;
+        for (int l = 0; l < n && ok; ++l) {
+            char bad[LBIB_MAX_MARKERS + 1] = {0};
+            for (int q = 0; q < n; ++q) {
+                if (blk[q] < 0) continue;
+                const double dx = mx[l] - mx[q], dy = my[l] - my[q];
+                if (dx * dx + dy * dy < D2) bad[blk[q]] = 1;
+            }
+            int c = -1;
+            for (int k = 1; k <= C; ++k)
+                if (!bad[(prev + k) % C]) {
+                    c = (prev + k) % C;
+                    break;
+                }
+            if (c < 0) ok = false;
+            else blk[l] = prev = c;
+        }
+        if (!ok) continue;
+        for (int i = 0; i < n; ++i) color[i] = blk[i];
+        nc = C;
+        break;
+    }
+    return nc;
+}
+
+// Polygon elements, mass properties, ligands and marker colouring.
 void build_geometry(HostParticle &p) {
     const int n = (int)p.vx.size();
     p.nl = n;
@@ -203,20 +279,8 @@ void build_geometry(HostParticle &p) {
         p.ligand[l] = floor((double)(l + 1) * p.lig) > floor((double)l * p.lig);
         p.n_ligands += p.ligand[l];
     }
-    const double D2 = 32.0 * (1.0 + 1e-9);
     std::vector<int> color(n, -1);
-    int nc = 0;
-    for (int l = 0; l < n; ++l) {
-        std::vector<char> used(nc + 1, 0);
-        for (int q = 0; q < l; ++q) {
-            const double dx = p.mbx[l] - p.mbx[q], dy = p.mby[l] - p.mby[q];
-            if (dx * dx + dy * dy < D2) used[color[q]] = 1;
-        }
-        int c = 0;
-        while (c < nc && used[c]) ++c;
-        color[l] = c;
-        if (c == nc) ++nc;
-    }
+    const int nc = color_markers(p.mbx.data(), p.mby.data(), n, color.data());
     p.ncolors = nc;
     p.color_off.assign(nc + 1, 0);
     for (int l = 0; l < n; ++l) p.color_off[color[l] + 1]++;
@@ -1173,19 +1237,7 @@ void noalloc_geometry(const lbib_particle &in, NoAllocGeom &g) {
         g.ligand[l] = floor((double)(l + 1) * in.ligand_density) > floor((double)l * in.ligand_density);
         g.n_ligands += g.ligand[l];
     }
-    const double D2 = 32.0 * (1.0 + 1e-9);
-    int nc = 0;
-    for (int l = 0; l < n; ++l) {
-        char used[LBIB_MAX_MARKERS + 1] = {0};
-        for (int q = 0; q < l; ++q) {
-            const double dx = g.mbx[l] - g.mbx[q], dy = g.mby[l] - g.mby[q];
-            if (dx * dx + dy * dy < D2) used[g.color[q]] = 1;
-        }
-        int c = 0;
-        while (c < nc && used[c]) ++c;
-        g.color[l] = c;
-        if (c == nc) ++nc;
-    }
+    const int nc = color_markers(g.mbx, g.mby, n, g.color);
     g.ncolors = nc;
     for (int c = 0; c <= nc; ++c) g.coff[c] = 0;
     for (int l = 0; l < n; ++l) g.coff[g.color[l] + 1]++;

@@ -236,12 +236,18 @@ __device__ __forceinline__ R warp_min_array(const R *a, int n, R base, R sign) {
 }
 
 // Node moments pulled from the populations (outside the staged region).
+template <typename R>
+struct Moments {
+    R drho, jx, jy;
+};
+
 template <typename S, typename R>
-__device__ __noinline__ void pull_moments(const SimDev &s, const S *pop, int x, int y, R &drho,
-                                          R &jx, R &jy) {
+__device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, int x, int y) {
     R d[9];
     pull_node<S, R>(s, pop, x, y, d);
-    node_moments(d, drho, jx, jy);
+    Moments<R> m;
+    node_moments(d, m.drho, m.jx, m.jy);
+    return m;
 }
 
 // Walks the 4 x 4 support of point l (after setup_point) in a fixed order,
@@ -250,12 +256,16 @@ __device__ __noinline__ void pull_moments(const SimDev &s, const S *pop, int x, 
 // centred basis, phi = the MLS shape function, and the node's moments
 // (staged region, else pulled).  One thread per point: the staged region is
 // in shared memory, so the sixteen nodes are a short loop, not a reduction.
+// On return the shape function of node (a, b) is wxo[a] pyo[b] (pyo[b] = 0
+// for a row outside the lattice or of zero weight; all zero without a fit).
 template <typename S, typename R, typename F>
 __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const Points<R> &pt,
                                             int l, const R *mr, const R *mjx, const R *mjy,
                                             const uint8_t *flag, int Tm, int rx0, int ry0,
-                                            F &&f) {
+                                            R (&wxo)[4], R (&pyo)[4], F &&f) {
     const int rows = pt.rows[l];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) wxo[k] = pyo[k] = (R)0;
     if (!(rows & 16)) return;
     const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l], mu_v = pt.mu_v[l];
     const int ix0 = pt.ix0[l], iy0 = pt.iy0[l];
@@ -264,6 +274,7 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
     for (int a = 0; a < 4; ++a) {
         dxa[a] = (R)(a - 1) - fx;
         wx[a] = bspline(dxa[a]);
+        wxo[a] = wx[a];
     }
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -273,6 +284,7 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
         if (wy == (R)0) continue;
         const R dyc = dy - mu;
         const R py = wy * ((R)1 - dyc * mu_v);
+        pyo[b] = py;
         const int v = iy0 + b - ry0;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -293,7 +305,10 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
                     yy %= s.ny;
                     if (yy < 0) yy += s.ny;
                 }
-                pull_moments<S, R>(s, pop, xx, yy, drho, jx, jy);
+                const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy);
+                drho = m.drho;
+                jx = m.jx;
+                jy = m.jy;
             }
             f(w, dxa[a], dyc, wx[a] * py, drho, jx, jy);
         }
@@ -305,13 +320,29 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
 // below one node per step) fall inside it.
 __host__ __device__ __forceinline__ int region_edge(int T) { return T + 4; }
 
+template <typename R> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+// The spreading contributions (16 pairs per marker) reuse the staged
+// moments' space when they fit in it.
+template <typename R>
+__host__ __device__ __forceinline__ bool spread_in_moments(int nl, int Tm) {
+    const size_t m = ((sizeof(R) * (size_t)Tm * Tm + 15) & ~size_t(15)) * 3;
+    return 32 * sizeof(R) * (size_t)nl <= m;
+}
+
 template <typename R>
 size_t smem_bytes_for(int nl, int T) {
     auto up = [](size_t b) { return (b + 15) & ~size_t(15); };
     const size_t Tm = (size_t)region_edge(T);
-    return up(sizeof(Pose<R>)) + 23 * up(sizeof(R) * nl) + 3 * up(sizeof(int) * nl) + up(nl) +
+    // the staged moments (and, where they do not fit there, the spreading
+    // contributions) are laid out last
+    const size_t moments = 3 * up(sizeof(R) * Tm * Tm);
+    const size_t spread = spread_in_moments<R>(nl, (int)Tm) ? 0 : 32 * sizeof(R) * (size_t)nl;
+    return up(sizeof(Pose<R>)) + 21 * up(sizeof(R) * nl) + 3 * up(sizeof(int) * nl) + up(nl) +
            up(sizeof(int) * nl) + up(sizeof(int) * (nl + 1)) + up(sizeof(R) * 2 * T * T) +
-           3 * up(sizeof(R) * Tm * Tm) + up(Tm * Tm) + 16;
+           up(Tm * Tm) + 16 + moments + spread;
 }
 
 // Reverse probability of Eq. 11 (dt = 1): FP32 on the FP32 path, FP64 on the
@@ -367,10 +398,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     R *ry = (R *)take(sizeof(R) * nl);
     R *nxw = (R *)take(sizeof(R) * nl);     // outward normal
     R *nyw = (R *)take(sizeof(R) * nl);
-    R *c[6];                                // per-element loads and bond forces
-    for (int k = 0; k < 6; ++k) c[k] = (R *)take(sizeof(R) * nl);
-    R *sFx = (R *)take(sizeof(R) * nl);     // marker forces F_l eps_l
-    R *sFy = (R *)take(sizeof(R) * nl);
+    // per-element loads (0-2) and bond forces (3-5): quantity k at cq + k cstride
+    const int cstride = (int)(((sizeof(R) * nl + 15) & ~size_t(15)) / sizeof(R));
+    R *cq = (R *)take(6 * sizeof(R) * cstride);
     Points<R> pt;
     pt.ix0 = (int *)take(sizeof(int) * nl);
     pt.iy0 = (int *)take(sizeof(int) * nl);
@@ -384,12 +414,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     uint8_t *lig8 = (uint8_t *)take(nl);
     int *corder = (int *)take(sizeof(int) * nl);
     int *coff = (int *)take(sizeof(int) * (nl + 1));
-    R *tile = (R *)take(sizeof(R) * 2 * T * T);
-    R *mr = (R *)take(sizeof(R) * Tm * Tm);     // staged moments of the region
-    R *mjx = (R *)take(sizeof(R) * Tm * Tm);
-    R *mjy = (R *)take(sizeof(R) * Tm * Tm);
     uint8_t *flag = (uint8_t *)take(Tm * Tm);     // region node staged
     int *nflag = (int *)take(16);
+    R *tile = (R *)take(sizeof(R) * 2 * T * T);
+    // staged moments of the region, last (the spreading contributions follow
+    // them when they do not fit in their space)
+    const size_t mstride = (sizeof(R) * Tm * Tm + 15) / 16 * 16 / sizeof(R);
+    R *mr = (R *)take(sizeof(R) * Tm * Tm);
+    R *mjx = (R *)take(sizeof(R) * Tm * Tm);
+    R *mjy = (R *)take(sizeof(R) * Tm * Tm);
 
     const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -528,7 +561,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             d[8] = Store<S>::ld(pop, 8 * N + rp + xm, inv);
             node_moments(d, mr[i], mjx[i], mjy[i]);
         } else {
-            pull_moments<S, R>(s, pop, xx, yy, mr[i], mjx[i], mjy[i]);
+            const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy);
+            mr[i] = m.drho;
+            mjx[i] = m.jx;
+            mjy[i] = m.jy;
         }
     }
     __syncthreads();
@@ -541,7 +577,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l] + (R)1.2 * nxw[l],
                            ps.fyc + ry[l] + (R)1.2 * nyw[l], pt, l);
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0,
+            R wxo[4], pyo[4];    // not needed here
+            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0, wxo, pyo,
                               [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
                                   const R irho = recip((R)1 + drho);
                                   const R ux = jx * irho, uy = jy * irho;
@@ -562,9 +599,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
                 tx = (-p * nxl + nu * (R)2 * dudx * nxl + txy * nyl) * sS[l];
                 ty = (-p * nyl + txy * nxl + nu * (R)2 * dvdy * nyl) * sS[l];
             }
-            c[0][l] = tx;
-            c[1][l] = ty;
-            c[2][l] = rx[l] * ty - ry[l] * tx;
+            cq[0 * cstride + l] = tx;
+            cq[1 * cstride + l] = ty;
+            cq[2 * cstride + l] = rx[l] * ty - ry[l] * tx;
         }
 
         // ---- 3. bonds (Eq. 9-11), one element per thread -------------------
@@ -622,15 +659,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
                     }
                 }
             }
-            c[3][l] = fx;
-            c[4][l] = fy;
-            c[5][l] = rx[l] * fy - ry[l] * fx;
+            cq[3 * cstride + l] = fx;
+            cq[4 * cstride + l] = fy;
+            cq[5 * cstride + l] = rx[l] * fy - ry[l] * fx;
         }
         const int nbonded = __syncthreads_count(bonded);
 
         // ---- FP64 sums: one warp per quantity, gaps on warp 6 --------------
         if (warp < 6) {
-            const double v = warp_sum_array<R>(c[warp], nl);
+            const double v = warp_sum_array<R>(cq + warp * cstride, nl);
             if (lane == 0) ps.F[warp] = v;
         } else if (warp == 6) {
             const R gb = warp_min_array<R>(ry, nl, ps.gap0_b, (R)1);
@@ -693,18 +730,18 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     // (the tile is next touched by the spreading, after a barrier)
     for (int i = tid; i < 2 * T * T; i += P_THREADS) tile[i] = (R)0;
     const R ghx = (R)0.5 * pick<R>(s.f_gx, s.gx), ghy = (R)0.5 * pick<R>(s.f_gy, s.gy);
+    R Fx = 0, Fy = 0, wxo[4], pyo[4];
     if (tid < nl) {
         const int l = tid;
         setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l], ps.fyc + ry[l], pt, l);
         R s_rho = 0, s_u = 0, s_v = 0;
-        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0,
+        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0, wxo, pyo,
                           [&](R, R, R, R phi, R drho, R jx, R jy) {
                               const R irho = recip((R)1 + drho);
                               s_rho += phi * drho;
                               s_u += phi * ((jx + ghx) * irho);
                               s_v += phi * ((jy + ghy) * irho);
                           });
-        R Fx = 0, Fy = 0;
         if (pt.rows[l] & 16) {
             const R rl = (R)1 + s_rho;
             const R udx = ps.uR - ps.omR * ry[l];
@@ -712,11 +749,27 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             Fx = (R)2 * rl * (udx - s_u) * sS[l];
             Fy = (R)2 * rl * (udy - s_v) * sS[l];
         }
-        sFx[l] = Fx;
-        sFy[l] = Fy;
+    }
+    // each marker's sixteen contributions phi_k F_l eps_l, in the staged
+    // moments' space once every support has been read (or a buffer of their
+    // own when they do not fit there)
+    using R2 = typename Pair<R>::type;
+    R2 *ctb = spread_in_moments<R>(nl, Tm) ? (R2 *)mr : (R2 *)(mr + 3 * mstride);
+    __syncthreads();
+    if (tid < nl) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const R phi = wxo[j & 3] * pyo[j >> 2];
+            R2 c;
+            c.x = phi * Fx;
+            c.y = phi * Fy;
+            ctb[tid * 16 + j] = c;
+        }
     }
     __syncthreads();
-    // colour-ordered spreading into the tile; origin floor(X_c) - T/2
+    // colour-ordered spreading into the tile; origin floor(X_c) - T/2.
+    // Markers of one colour have disjoint supports, so each tile node takes
+    // its contributions in colour order (identical alone or in a batch).
     const int ox = ps.ixc - T / 2;
     const int oy = ps.iyc - T / 2;
 #pragma unroll 1
@@ -724,16 +777,13 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         const int m0 = coff[cl], m1 = coff[cl + 1];
         for (int t = tid; t < (m1 - m0) * 16; t += P_THREADS) {
             const int m = corder[m0 + (t >> 4)];
-            const int j = t & 15, ta = j & 3, tb = j >> 2;
-            const int rows = pt.rows[m];
-            if (!(rows & 16) || !(rows & (1 << tb))) continue;
-            const R dx = (R)(ta - 1) - pt.fx[m], dy = (R)(tb - 1) - pt.fy[m];
-            const R phi = bspline(dx) * bspline(dy) * pt.invW[m] *
-                          ((R)1 - (dy - pt.mu[m]) * pt.mu_v[m]);
-            const int tx = pt.ix0[m] + ta - ox, ty = pt.iy0[m] + tb - oy;
+            const int j = t & 15;
+            const R2 c = ctb[m * 16 + j];
+            if (c.x == (R)0 && c.y == (R)0) continue;
+            const int tx = pt.ix0[m] + (j & 3) - ox, ty = pt.iy0[m] + (j >> 2) - oy;
             if ((unsigned)tx < (unsigned)T && (unsigned)ty < (unsigned)T) {
-                tile[ty * T + tx] += phi * sFx[m];
-                tile[T * T + ty * T + tx] += phi * sFy[m];
+                tile[ty * T + tx] += c.x;
+                tile[T * T + ty * T + tx] += c.y;
             }
         }
         __syncthreads();
