@@ -84,6 +84,13 @@ struct ParticleDev {
     int8_t *anchor_wall;
     void *tile;              // IB force density, [2][T][T] of the compute type
     double *pf_tab;          // P_f by probing count, bottom [nl+1] then top [nl+1]
+    // Pose in the compute precision left by the last particle pass for the
+    // next one (pose_ok = 1), so that a pass starts without the FP64 pose
+    // arithmetic: the centroid's floor node, then its offset from it, cos and
+    // sin of the angle, the centroid's distances to the bottom and top wall
+    // lines, and the velocities u, v, omega.
+    int pose_ok, pose_ixc, pose_iyc, pose_pad;
+    double pose_r[9];
 };
 
 struct BatchDev {

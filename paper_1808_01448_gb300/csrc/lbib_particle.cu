@@ -48,9 +48,18 @@ __device__ __forceinline__ R bspline(R r) {
     return a < (R)1 ? inner : outer;
 }
 
+// 1 / rho for a density near 1: FP32 hardware approximation refined by one
+// Newton-Raphson step r (2 - x r) (within an ulp or two); exact division on
+// the FP64 path.
 template <typename R>
-__device__ __forceinline__ R recip(R x) {
-    if constexpr (sizeof(R) == 4) return __frcp_rn(x); else return (R)1 / x;
+__device__ __forceinline__ R recip_rho(R x) {
+    if constexpr (sizeof(R) == 4) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r * fmaf(-x, r, 2.f);
+    } else {
+        return (R)1 / x;
+    }
 }
 
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers and Weyl
@@ -146,8 +155,11 @@ __device__ __noinline__ void clipped_axis(R fy, unsigned rows, R &invW, R &mu_o,
     double W0 = 0.0, W1 = 0.0, W2 = 0.0;
     for (int b = 0; b < 4; ++b) {
         if (!(rows & (1u << b))) continue;
-        const double dy = (double)((R)(b - 1) - fy);
-        const double w = bspline(dy);
+        // offset and weight in the compute precision (the point itself is
+        // known to it); moments and solve in FP64
+        const R dyr = (R)(b - 1) - fy;
+        const double dy = (double)dyr;
+        const double w = (double)bspline(dyr);
         W0 += w;
         W1 += w * dy;
         W2 += w * dy * dy;
@@ -342,7 +354,7 @@ size_t smem_bytes_for(int nl, int T) {
     const size_t spread = spread_in_moments<R>(nl, (int)Tm) ? 0 : 32 * sizeof(R) * (size_t)nl;
     return up(sizeof(Pose<R>)) + 21 * up(sizeof(R) * nl) + 3 * up(sizeof(int) * nl) + up(nl) +
            up(sizeof(int) * nl) + up(sizeof(int) * (nl + 1)) + up(sizeof(R) * 2 * T * T) +
-           up(Tm * Tm) + 16 + moments + spread;
+           up(Tm * Tm) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread;
 }
 
 // Reverse probability of Eq. 11 (dt = 1): FP32 on the FP32 path, FP64 on the
@@ -415,7 +427,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     int *corder = (int *)take(sizeof(int) * nl);
     int *coff = (int *)take(sizeof(int) * (nl + 1));
     uint8_t *flag = (uint8_t *)take(Tm * Tm);     // region node staged
-    int *nflag = (int *)take(16);
+    int4 *span = (int4 *)take(sizeof(int4) * Tm);       // staged spans per region row
+    int *pre = (int *)take(sizeof(int) * (Tm + 1));     // staged nodes before each row
     R *tile = (R *)take(sizeof(R) * 2 * T * T);
     // staged moments of the region, last (the spreading contributions follow
     // them when they do not fit in their space)
@@ -432,7 +445,17 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     if (tid == 0) {
         ps.xc = Pc.xc; ps.yc = Pc.yc; ps.th = Pc.th;
         ps.u = Pc.u; ps.v = Pc.v; ps.om = Pc.om;
-        set_pose(ps, yb, yt);
+        if (Pc.pose_ok) {
+            // left by the last pass: the same values set_pose gives
+            ps.ixc = Pc.pose_ixc;
+            ps.iyc = Pc.pose_iyc;
+            ps.fxc = (R)Pc.pose_r[0]; ps.fyc = (R)Pc.pose_r[1];
+            ps.cs = (R)Pc.pose_r[2]; ps.sn = (R)Pc.pose_r[3];
+            ps.gap0_b = (R)Pc.pose_r[4]; ps.gap0_t = (R)Pc.pose_r[5];
+            ps.uR = (R)Pc.pose_r[6]; ps.vR = (R)Pc.pose_r[7]; ps.omR = (R)Pc.pose_r[8];
+        } else {
+            set_pose(ps, yb, yt);
+        }
     }
     if (tid < nl) {
         gbx[tid] = (R)Pc.mbx[tid];
@@ -461,76 +484,86 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     place();
     const int rx0 = ps.ixc - Tm / 2, ry0 = ps.iyc - Tm / 2;
     for (int i = tid; i < (Tm * Tm + 3) / 4; i += P_THREADS) ((int *)flag)[i] = 0;
-    if (tid == 0) *nflag = 0;
+    for (int v = tid; v < Tm; v += P_THREADS) span[v] = make_int4(Tm, -1, Tm, -1);
     __syncthreads();
 
     // ---- stage the moments of the nodes the supports can touch ------------
-    // each marker flags its probe's 4 x 4 support and a 6 x 6 box around its
-    // own support (one node of motion either way); flagged nodes are
-    // compacted into a list (kept in the force-tile buffer) and pulled.
+    // The supports of a marker's probe and of the marker itself after a move
+    // below one node lie in the bounding box of the probe's 4 x 4 support and
+    // a 6 x 6 box around the marker's own.  Per region row, the boxes of the
+    // markers whose outward normal points left (the outline runs down there)
+    // make one span and the others a second; along a convex outline each of
+    // these chains is monotone in y, so a span is an interval of the row (any
+    // support node outside the staged nodes is pulled directly, with the same
+    // arithmetic).  The spans are listed, flagged and pulled.
     if (tid < nl) {
         const R X = ps.fxc + rx[tid], Y = ps.fyc + ry[tid];
-        const int mx0 = (int)floor(X) - 2 + ps.ixc - rx0, my0 = (int)floor(Y) - 2 + ps.iyc - ry0;
-#pragma unroll 1
-        for (int v = 0; v < 6; ++v)
-#pragma unroll 1
-            for (int u = 0; u < 6; ++u)
-                if ((unsigned)(mx0 + u) < (unsigned)Tm && (unsigned)(my0 + v) < (unsigned)Tm)
-                    flag[(my0 + v) * Tm + mx0 + u] = 1;
+        int bx0 = (int)floor(X) - 2, by0 = (int)floor(Y) - 2;
+        int bx1 = bx0 + 5, by1 = by0 + 5;
         if (!init) {
-            const int px0 = (int)floor(X + (R)1.2 * nxw[tid]) - 1 + ps.ixc - rx0;
-            const int py0 = (int)floor(Y + (R)1.2 * nyw[tid]) - 1 + ps.iyc - ry0;
+            const int px0 = (int)floor(X + (R)1.2 * nxw[tid]) - 1;
+            const int py0 = (int)floor(Y + (R)1.2 * nyw[tid]) - 1;
+            bx0 = min(bx0, px0);
+            by0 = min(by0, py0);
+            bx1 = max(bx1, px0 + 3);
+            by1 = max(by1, py0 + 3);
+        }
+        const int h = Tm / 2;       // region coordinate of the centroid's floor node
+        const int ulo = max(bx0 + h, 0), uhi = min(bx1 + h, Tm - 1);
+        int *sp = (int *)span + (nxw[tid] < (R)0 ? 0 : 2);
+        if (ulo <= uhi) {
 #pragma unroll 1
-            for (int v = 0; v < 4; ++v)
-#pragma unroll 1
-                for (int u = 0; u < 4; ++u)
-                    if ((unsigned)(px0 + u) < (unsigned)Tm && (unsigned)(py0 + v) < (unsigned)Tm)
-                        flag[(py0 + v) * Tm + px0 + u] = 1;
+            for (int v = max(by0 + h, 0); v <= min(by1 + h, Tm - 1); ++v) {
+                const int yy = ry0 + v;
+                if (s.wall_b != LBIB_WALL_PERIODIC && (yy < 0 || yy >= s.ny)) continue;
+                atomicMin(sp + 4 * v, ulo);
+                atomicMax(sp + 4 * v + 1, uhi);
+            }
         }
     }
     __syncthreads();
-    int *list = (int *)tile;
-    const int nwords = (Tm * Tm + 3) / 4;
-    for (int base = 0; base < nwords; base += P_THREADS) {
-        // four flags per thread; one shared atomic per warp
-        const int wi = base + tid;
-        int idx[4], cnt = 0;
-        if (wi < nwords) {
-            const unsigned fw = ((const unsigned *)flag)[wi];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = 4 * wi + q;
-                if (i >= Tm * Tm || !((fw >> (8 * q)) & 0xFFu)) continue;
-                int yy = ry0 + i / Tm;
-                if (s.wall_b == LBIB_WALL_PERIODIC) {
-                    yy %= s.ny;
-                    if (yy < 0) yy += s.ny;
-                }
-                if (yy < 0 || yy >= s.ny) {
-                    flag[i] = 0;        // outside the lattice rows: never read
-                    continue;
-                }
-                idx[cnt++] = i;
+    // merge overlapping spans, count the nodes of each row, prefix sum (one warp)
+    if (warp == 0) {
+        int carry = 0;
+        for (int base = 0; base < Tm; base += 32) {
+            const int v = base + lane;
+            int cnt = 0;
+            if (v < Tm) {
+                int4 q = span[v];
+                if (q.y >= q.x && q.w >= q.z && q.z <= q.y + 1 && q.x <= q.w + 1)
+                    q = make_int4(min(q.x, q.z), max(q.y, q.w), Tm, -1);
+                span[v] = q;
+                cnt = max(q.y - q.x + 1, 0) + max(q.w - q.z + 1, 0);
             }
-        }
-        int incl = cnt;
+            int incl = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (v < Tm) pre[v] = carry + incl - cnt;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int wbase = 0;
-        if (lane == 31 && total) wbase = atomicAdd(nflag, total);
-        wbase = __shfl_sync(0xffffffffu, wbase, 31);
-        const int at = wbase + incl - cnt;
-        for (int q = 0; q < cnt; ++q) list[at + q] = idx[q];
+        if (lane == 0) pre[Tm] = carry;
+    }
+    __syncthreads();
+    // list (kept in the force-tile buffer) and flags of the staged nodes, one
+    // warp per row
+    int *list = (int *)tile;
+    for (int v = warp; v < Tm; v += P_THREADS / 32) {
+        const int4 q = span[v];
+        const int n0 = max(q.y - q.x + 1, 0), p0 = pre[v], n = pre[v + 1] - p0;
+        for (int i = lane; i < n; i += 32) {
+            const int u = i < n0 ? q.x + i : q.z + (i - n0);
+            list[p0 + i] = v * Tm + u;
+            flag[v * Tm + u] = 1;
+        }
     }
     __syncthreads();
     // populations of this step come from the lattice pass just before: wait
     // for it here (everything above reads only particle and geometry data)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int nlist = *nflag;
+    const int nlist = pre[Tm];
 #pragma unroll 2
     for (int k = tid; k < nlist; k += P_THREADS) {
         const int i = list[k];
@@ -580,7 +613,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             R wxo[4], pyo[4];    // not needed here
             support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0, wxo, pyo,
                               [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
-                                  const R irho = recip((R)1 + drho);
+                                  const R irho = recip_rho((R)1 + drho);
                                   const R ux = jx * irho, uy = jy * irho;
                                   s_rho += phi * drho;
                                   s_ux += w * dx * ux;
@@ -737,7 +770,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         R s_rho = 0, s_u = 0, s_v = 0;
         support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0, wxo, pyo,
                           [&](R, R, R, R phi, R drho, R jx, R jy) {
-                              const R irho = recip((R)1 + drho);
+                              const R irho = recip_rho((R)1 + drho);
                               s_rho += phi * drho;
                               s_u += phi * ((jx + ghx) * irho);
                               s_v += phi * ((jy + ghy) * irho);
@@ -817,6 +850,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             P->box_oy[0] = P->box_oy[1] = by;
         }
         if (!init) P->step = Pc.step + 1;
+        // the pose of the next pass (unchanged for a fixed particle)
+        P->pose_ixc = ps.ixc;
+        P->pose_iyc = ps.iyc;
+        P->pose_r[0] = (double)ps.fxc; P->pose_r[1] = (double)ps.fyc;
+        P->pose_r[2] = (double)ps.cs; P->pose_r[3] = (double)ps.sn;
+        P->pose_r[4] = (double)ps.gap0_b; P->pose_r[5] = (double)ps.gap0_t;
+        P->pose_r[6] = (double)ps.uR; P->pose_r[7] = (double)ps.vR; P->pose_r[8] = (double)ps.omR;
+        P->pose_ok = 1;
     }
 }
 
