@@ -328,7 +328,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     const size_t rsz = compute_size(s->kind);
     const size_t bytes = sizeof(ParticleDev) + 5 * n * 8 + n + 4 * n + 4 * (p.ncolors + 1) + n +
                          16 * (size_t)(n + 1) +
-                         8 * n + n + 2 * rsz * p.T * p.T + 16 * 16;
+                         8 * n + n + 2 * rsz * p.T * p.T + ECACHE * rsz * (size_t)n + 16 * 16;
     unsigned char *blk = (unsigned char *)dalloc(s->cfg, s->stream, bytes);
     if (!blk) return fail(LBIB_E_OOM, "device allocation of %zu bytes for a particle failed", bytes);
     p.d_block = blk;
@@ -349,6 +349,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     int8_t *aw = (int8_t *)take(n);
     void *tile = take(2 * rsz * p.T * p.T);
     double *pft = (double *)take(16 * (size_t)(n + 1));
+    void *ecache = take(ECACHE * rsz * (size_t)n);
     h.xc = h.xc1 = p.xc; h.yc = h.yc1 = p.yc; h.th = h.th1 = p.th;
     h.mass = p.mass; h.inertia = p.inertia; h.r_eq = p.r_eq; h.sigma = p.sigma;
     h.inv_mass = 1.0 / p.mass; h.inv_inertia = 1.0 / p.inertia;
@@ -358,6 +359,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     h.mbx = mbx; h.mby = mby; h.nbx = nbx; h.nby = nby; h.S = S;
     h.ligand = lig; h.color_order = co; h.color_off = coff;
     h.bond = bond; h.anchor_x = ax; h.anchor_wall = aw; h.tile = tile; h.pf_tab = pft;
+    h.ecache = ecache;      // filled by the first pass (pose_ok = 0 until then)
     p.d_part = (ParticleDev *)pd;
     cudaStream_t st = s->stream;
     CK(cudaMemcpyAsync(pd, &h, sizeof h, cudaMemcpyHostToDevice, st));

@@ -91,7 +91,14 @@ struct ParticleDev {
     // lines, and the velocities u, v, omega.
     int pose_ok, pose_ixc, pose_iyc, pose_pad;
     double pose_r[9];
+    // Per-element record of the compute type, [nl][ECACHE] (or null), rewritten
+    // by every pass for the next one (valid with pose_ok): body-frame centroid
+    // x, y, normal x, y, length, the marker offset x, y and normal x, y at the
+    // pose above, ligand flag, colour order entry, colour offset (entries
+    // 0 .. ncolors - 1).  Rewriting keeps it in L2 between passes.
+    void *ecache;
 };
+constexpr int ECACHE = 12;
 
 struct BatchDev {
     SimDev *sims;

@@ -113,28 +113,42 @@ struct Pose {
     int nprobe, nbonded;
 };
 
+// The pose in the compute precision, one degree of freedom at a time (so that
+// the three lanes of the rigid update can each finish their own): 0 the
+// centroid's x (floor node, offset, u), 1 its y (floor node, offset, wall
+// distances, v), 2 the angle (cos and sin, omega).
+template <typename R>
+__device__ __forceinline__ void set_pose_dof(Pose<R> &ps, int k, double yb, double yt) {
+    if (k == 0) {
+        const double fx = floor(ps.xc);
+        ps.ixc = (int)fx;
+        ps.fxc = (R)(ps.xc - fx);
+        ps.uR = (R)ps.u;
+    } else if (k == 1) {
+        const double fy = floor(ps.yc);
+        ps.iyc = (int)fy;
+        ps.fyc = (R)(ps.yc - fy);
+        ps.gap0_b = (R)(ps.yc - yb);
+        ps.gap0_t = (R)(yt - ps.yc);
+        ps.vR = (R)ps.v;
+    } else {
+        R sn, cs;
+        if constexpr (sizeof(R) == 4) {
+            // angle reduced to [-pi, pi] in FP64, then the FP32 sine and cosine
+            const double t = ps.th - 6.283185307179586 * rint(ps.th * 0.15915494309189535);
+            sincosf((float)t, &sn, &cs);
+        } else {
+            sincos(ps.th, &sn, &cs);
+        }
+        ps.cs = cs;
+        ps.sn = sn;
+        ps.omR = (R)ps.om;
+    }
+}
+
 template <typename R>
 __device__ __noinline__ void set_pose(Pose<R> &ps, double yb, double yt) {
-    R sn, cs;
-    if constexpr (sizeof(R) == 4) {
-        // angle reduced to [-pi, pi] in FP64, then the FP32 sine and cosine
-        const double t = ps.th - 6.283185307179586 * rint(ps.th * 0.15915494309189535);
-        sincosf((float)t, &sn, &cs);
-    } else {
-        sincos(ps.th, &sn, &cs);
-    }
-    const double fx = floor(ps.xc), fy = floor(ps.yc);
-    ps.ixc = (int)fx;
-    ps.iyc = (int)fy;
-    ps.fxc = (R)(ps.xc - fx);
-    ps.fyc = (R)(ps.yc - fy);
-    ps.cs = cs;
-    ps.sn = sn;
-    ps.gap0_b = (R)(ps.yc - yb);
-    ps.gap0_t = (R)(yt - ps.yc);
-    ps.uR = (R)ps.u;
-    ps.vR = (R)ps.v;
-    ps.omR = (R)ps.om;
+    for (int k = 0; k < 3; ++k) set_pose_dof(ps, k, yb, yt);
 }
 
 // MLS support parameters of the points (probes or markers), one slot per
@@ -148,10 +162,16 @@ struct Points {
     R *invW, *mu, *mu_v, *inv_v;   // y-axis moments: 1 / W0, mu, mu / v, 1 / v
 };
 
-// Moments of a wall-clipped y axis, summed and solved in FP64.
+// Moments of a wall-clipped y axis, summed and solved in FP64: 1 / W0, mu,
+// mu / v and 1 / v (returned by value, so that the caller's point stays in
+// registers).
 template <typename R>
-__device__ __noinline__ void clipped_axis(R fy, unsigned rows, R &invW, R &mu_o, R &mu_v,
-                                          R &inv_v) {
+struct AxisMoments {
+    R invW, mu, mu_v, inv_v;
+};
+
+template <typename R>
+__device__ __noinline__ AxisMoments<R> clipped_axis(R fy, unsigned rows) {
     double W0 = 0.0, W1 = 0.0, W2 = 0.0;
     for (int b = 0; b < 4; ++b) {
         if (!(rows & (1u << b))) continue;
@@ -164,21 +184,21 @@ __device__ __noinline__ void clipped_axis(R fy, unsigned rows, R &invW, R &mu_o,
         W1 += w * dy;
         W2 += w * dy * dy;
     }
-    // reciprocals: FP32 seed, two Newton-Raphson steps r <- r (2 - a r) in
+    // reciprocal: FP32 seed, two Newton-Raphson steps r <- r (2 - a r) in
     // FP64 (relative error ~1e-7 squares to below FP64 rounding)
     auto rcp = [](double a) {
         double r = (double)__frcp_rn((float)a);
         r = r * (2.0 - a * r);
         return r * (2.0 - a * r);
     };
-    const double iW = rcp(W0);
-    const double mu = W1 * iW;
-    const double v = W2 * iW - mu * mu;
-    const double iv = rcp(v);
-    invW = (R)iW;
-    mu_o = (R)mu;
-    mu_v = (R)(mu * iv);
-    inv_v = (R)iv;
+    // with D = W0 W2 - W1^2 = W0^2 v and r = 1 / (W0 D), one reciprocal gives
+    // 1 / W0 = D r, mu = W1 / W0, 1 / v = W0^2 / D = W0^3 r and
+    // mu / v = W1 W0 / D = W1 W0^2 r
+    const double D = W0 * W2 - W1 * W1;
+    const double r = rcp(W0 * D);
+    const double iW = D * r;
+    const double W0r = W0 * W0 * r;
+    return AxisMoments<R>{(R)iW, (R)(W1 * iW), (R)(W1 * W0r), (R)(W0 * W0r)};
 }
 
 template <typename R>
@@ -214,7 +234,13 @@ __device__ __forceinline__ void setup_point(const SimDev &s, int bx, int by, R X
         }
     }
     R invW = (R)1, mu = (R)0, mu_v = (R)0, inv_v = (R)3;
-    if (nz >= 2 && rows != 0xFu) clipped_axis<R>(fy, rows, invW, mu, mu_v, inv_v);
+    if (nz >= 2 && rows != 0xFu) {
+        const AxisMoments<R> m = clipped_axis<R>(fy, rows);
+        invW = m.invW;
+        mu = m.mu;
+        mu_v = m.mu_v;
+        inv_v = m.inv_v;
+    }
     pt.ix0[l] = ix0;
     pt.iy0[l] = iy0;
     pt.rows[l] = (int)rows | (nz >= 2 ? 16 : 0);
@@ -457,16 +483,34 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             set_pose(ps, yb, yt);
         }
     }
+    // element data: from the record the last pass left (marker positions at
+    // this pose included), else from the geometry arrays
+    const bool cached = Pc.pose_ok && Pc.ecache;
+    R *erec = (R *)Pc.ecache;
     if (tid < nl) {
-        gbx[tid] = (R)Pc.mbx[tid];
-        gby[tid] = (R)Pc.mby[tid];
-        gnx[tid] = (R)Pc.nbx[tid];
-        gny[tid] = (R)Pc.nby[tid];
-        sS[tid] = (R)Pc.S[tid];
-        lig8[tid] = Pc.ligand[tid];
-        corder[tid] = Pc.color_order[tid];
+        if (cached) {
+            const R *e = erec + (size_t)tid * ECACHE;
+            R v[ECACHE];
+#pragma unroll
+            for (int k = 0; k < ECACHE; ++k) v[k] = e[k];
+            gbx[tid] = v[0]; gby[tid] = v[1]; gnx[tid] = v[2]; gny[tid] = v[3];
+            sS[tid] = v[4];
+            rx[tid] = v[5]; ry[tid] = v[6]; nxw[tid] = v[7]; nyw[tid] = v[8];
+            lig8[tid] = (uint8_t)v[9];
+            corder[tid] = (int)v[10];
+            if (tid < Pc.ncolors) coff[tid] = (int)v[11];
+        } else {
+            gbx[tid] = (R)Pc.mbx[tid];
+            gby[tid] = (R)Pc.mby[tid];
+            gnx[tid] = (R)Pc.nbx[tid];
+            gny[tid] = (R)Pc.nby[tid];
+            sS[tid] = (R)Pc.S[tid];
+            lig8[tid] = Pc.ligand[tid];
+            corder[tid] = Pc.color_order[tid];
+            if (tid < Pc.ncolors) coff[tid] = Pc.color_off[tid];
+        }
     }
-    if (tid <= Pc.ncolors) coff[tid] = Pc.color_off[tid];
+    if (tid == 0) coff[Pc.ncolors] = nl;     // the last colour ends at nl
     __syncthreads();
 
     // markers (offsets from the centroid) at the current pose
@@ -481,7 +525,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             nyw[tid] = sn * nbx + cs * nby;
         }
     };
-    place();
+    if (!cached) place();
     const int rx0 = ps.ixc - Tm / 2, ry0 = ps.iyc - Tm / 2;
     for (int i = tid; i < (Tm * Tm + 3) / 4; i += P_THREADS) ((int *)flag)[i] = 0;
     for (int v = tid; v < Tm; v += P_THREADS) span[v] = make_int4(Tm, -1, Tm, -1);
@@ -564,7 +608,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     // for it here (everything above reads only particle and geometry data)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nlist = pre[Tm];
-#pragma unroll 2
+#pragma unroll 4
     for (int k = tid; k < nlist; k += P_THREADS) {
         const int i = list[k];
         const int v = i / Tm, u = i - v * Tm;
@@ -745,6 +789,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             if (k == 0) { ps.u = un; ps.xc = xn; }
             if (k == 1) { ps.v = un; ps.yc = xn; }
             if (k == 2) { ps.om = un; ps.th = xn; }
+            set_pose_dof(ps, k, yb, yt);     // this lane's part of the new pose
         }
         if (tid == 32) {
             P->Fh[0] = ps.F[0]; P->Fh[1] = ps.F[1]; P->Mh = ps.F[2];
@@ -754,28 +799,68 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             P->n_bonded = ps.nbonded;
         }
         __syncthreads();
-        if (tid == 0 && !Pc.fixed) set_pose(ps, yb, yt);
-        __syncthreads();
         place();
     }
 
     // ---- 6. IB direct forcing at the (new) pose ---------------------------
-    // (the tile is next touched by the spreading, after a barrier)
-    for (int i = tid; i < 2 * T * T; i += P_THREADS) tile[i] = (R)0;
     const R ghx = (R)0.5 * pick<R>(s.f_gx, s.gx), ghy = (R)0.5 * pick<R>(s.f_gy, s.gy);
     R Fx = 0, Fy = 0, wxo[4], pyo[4];
     if (tid < nl) {
         const int l = tid;
         setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l], ps.fyc + ry[l], pt, l);
+        // interpolation of rho and u* = (j + g/2) / rho over the 4 x 4 support
+        // (same node order and weights as support_sum)
+        const int rows = pt.rows[l];
+        const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l], mu_v = pt.mu_v[l];
+        const int ix0 = pt.ix0[l], iy0 = pt.iy0[l];
         R s_rho = 0, s_u = 0, s_v = 0;
-        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0, wxo, pyo,
-                          [&](R, R, R, R phi, R drho, R jx, R jy) {
-                              const R irho = recip_rho((R)1 + drho);
-                              s_rho += phi * drho;
-                              s_u += phi * ((jx + ghx) * irho);
-                              s_v += phi * ((jy + ghy) * irho);
-                          });
-        if (pt.rows[l] & 16) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            wxo[a] = (rows & 16) ? bspline((R)(a - 1) - fx) : (R)0;
+            pyo[a] = (R)0;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (!(rows & 16) || !(rows & (1 << b))) continue;
+            const R dy = (R)(b - 1) - fy;
+            const R wy = bspline(dy) * invW;
+            if (wy == (R)0) continue;
+            const R py = wy * ((R)1 - (dy - mu) * mu_v);
+            pyo[b] = py;
+            const int v = iy0 + b - ry0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (wxo[a] * wy == (R)0) continue;
+                const int u = ix0 + a - rx0;
+                R drho, jx, jy;
+                const bool st = (unsigned)u < (unsigned)Tm && (unsigned)v < (unsigned)Tm &&
+                                flag[v * Tm + u];
+                if (st) {
+                    const int i = v * Tm + u;
+                    drho = mr[i];
+                    jx = mjx[i];
+                    jy = mjy[i];
+                } else {
+                    int xx = (ix0 + a) % s.nx;
+                    if (xx < 0) xx += s.nx;
+                    int yy = iy0 + b;
+                    if (s.wall_b == LBIB_WALL_PERIODIC) {
+                        yy %= s.ny;
+                        if (yy < 0) yy += s.ny;
+                    }
+                    const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy);
+                    drho = m.drho;
+                    jx = m.jx;
+                    jy = m.jy;
+                }
+                const R irho = recip_rho((R)1 + drho);
+                const R phi = wxo[a] * py;
+                s_rho += phi * drho;
+                s_u += phi * ((jx + ghx) * irho);
+                s_v += phi * ((jy + ghy) * irho);
+            }
+        }
+        if (rows & 16) {
             const R rl = (R)1 + s_rho;
             const R udx = ps.uR - ps.omR * ry[l];
             const R udy = ps.vR + ps.omR * rx[l];
@@ -788,6 +873,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     // own when they do not fit there)
     using R2 = typename Pair<R>::type;
     R2 *ctb = spread_in_moments<R>(nl, Tm) ? (R2 *)mr : (R2 *)(mr + 3 * mstride);
+    // a zero tile for the spreading (T is even: whole 16-byte words)
+    for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += P_THREADS)
+        ((uint4 *)tile)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     if (tid < nl) {
 #pragma unroll
@@ -822,7 +910,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         __syncthreads();
     }
     R *gt = (R *)Pc.tile;
-    for (int i = tid; i < 2 * T * T; i += P_THREADS) gt[i] = tile[i];
+    for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += P_THREADS)
+        ((uint4 *)gt)[i] = ((const uint4 *)tile)[i];
     if (tid == 0) {
         int oxw = ox % s.nx;
         if (oxw < 0) oxw += s.nx;
@@ -858,6 +947,18 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         P->pose_r[4] = (double)ps.gap0_b; P->pose_r[5] = (double)ps.gap0_t;
         P->pose_r[6] = (double)ps.uR; P->pose_r[7] = (double)ps.vR; P->pose_r[8] = (double)ps.omR;
         P->pose_ok = 1;
+    }
+    // the element record for the next pass (markers placed at the latest pose)
+    if (erec && tid < nl) {
+        R *e = erec + (size_t)tid * ECACHE;
+        R v[ECACHE];
+        v[0] = gbx[tid]; v[1] = gby[tid]; v[2] = gnx[tid]; v[3] = gny[tid]; v[4] = sS[tid];
+        v[5] = rx[tid]; v[6] = ry[tid]; v[7] = nxw[tid]; v[8] = nyw[tid];
+        v[9] = (R)lig8[tid];
+        v[10] = (R)corder[tid];
+        v[11] = tid < Pc.ncolors ? (R)coff[tid] : (R)0;
+#pragma unroll
+        for (int k = 0; k < ECACHE; ++k) e[k] = v[k];
     }
 }
 
