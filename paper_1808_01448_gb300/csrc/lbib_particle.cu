@@ -294,16 +294,12 @@ __device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, i
 // centred basis, phi = the MLS shape function, and the node's moments
 // (staged region, else pulled).  One thread per point: the staged region is
 // in shared memory, so the sixteen nodes are a short loop, not a reduction.
-// On return the shape function of node (a, b) is wxo[a] pyo[b] (pyo[b] = 0
-// for a row outside the lattice or of zero weight; all zero without a fit).
 template <typename S, typename R, typename F>
 __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const Points<R> &pt,
                                             int l, const R *mr, const R *mjx, const R *mjy,
                                             const uint8_t *flag, int Tm, int rx0, int ry0,
-                                            R (&wxo)[4], R (&pyo)[4], F &&f) {
+                                            F &&f) {
     const int rows = pt.rows[l];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) wxo[k] = pyo[k] = (R)0;
     if (!(rows & 16)) return;
     const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l], mu_v = pt.mu_v[l];
     const int ix0 = pt.ix0[l], iy0 = pt.iy0[l];
@@ -312,9 +308,10 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
     for (int a = 0; a < 4; ++a) {
         dxa[a] = (R)(a - 1) - fx;
         wx[a] = bspline(dxa[a]);
-        wxo[a] = wx[a];
     }
-#pragma unroll
+    // rows as a loop: the pass runs each instruction about once, so compact
+    // code (fewer instruction fetches) beats unrolled code here
+#pragma unroll 1
     for (int b = 0; b < 4; ++b) {
         if (!(rows & (1 << b))) continue;
         const R dy = (R)(b - 1) - fy;
@@ -322,7 +319,6 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
         if (wy == (R)0) continue;
         const R dyc = dy - mu;
         const R py = wy * ((R)1 - dyc * mu_v);
-        pyo[b] = py;
         const int v = iy0 + b - ry0;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -529,7 +525,21 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     const int rx0 = ps.ixc - Tm / 2, ry0 = ps.iyc - Tm / 2;
     for (int i = tid; i < (Tm * Tm + 3) / 4; i += P_THREADS) ((int *)flag)[i] = 0;
     for (int v = tid; v < Tm; v += P_THREADS) span[v] = make_int4(Tm, -1, Tm, -1);
-    __syncthreads();
+    // ---- 3. bonds (Eq. 9-11), one element per thread: they need only the
+    // pose, so they run with the staging, before the wait on the lattice pass
+    const bool has_b = s.wall_b != LBIB_WALL_PERIODIC && s.rec_b > 0.0;
+    const bool has_t = s.wall_t != LBIB_WALL_PERIODIC && s.rec_t > 0.0;
+    const R ycr = pick<R>((float)s.y_cr, s.y_cr);
+    bool lig = false, pb = false, ptop = false;
+    R gapb = (R)0, gapt = (R)0;
+    if (!init && tid < nl) {
+        lig = lig8[tid] != 0;
+        gapb = ps.gap0_b + ry[tid];
+        gapt = ps.gap0_t - ry[tid];
+        pb = lig && has_b && gapb < ycr;
+        ptop = lig && has_t && gapt < ycr;
+    }
+    const int nprobe = __syncthreads_count(pb || ptop);
 
     // ---- stage the moments of the nodes the supports can touch ------------
     // The supports of a marker's probe and of the marker itself after a move
@@ -565,7 +575,52 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             }
         }
     }
-    __syncthreads();
+    bool bonded = false;
+    if (!init && tid < nl) {
+        const int l = tid;
+        R fx = 0, fy = 0;
+        if (lig) {
+            // one draw per (step, element); the step is this particle's count
+            const double U = bond_uniform(s, Pc.step, (int)blockIdx.x - s.p0, l);
+            uint8_t bnd = P->bond[l];
+            double ax = P->anchor_x[l];
+            int8_t aw = P->anchor_wall[l];
+            const R y_eq = pick<R>((float)(s.y_eq_ratio * s.y_cr), s.y_eq_ratio * s.y_cr);
+            if (bnd) {
+                // bond vector anchor - X_l; the anchor lies on a wall line
+                const R dx = (R)(ax - ps.xc) - rx[l];
+                const R dy = aw ? gapt : -gapb;
+                const R y = sqrt(dx * dx + dy * dy);
+                const double Pr = prob_reverse<R>(s.k_r0, Pc.sigma * (1.0 - s.sigma_star_ratio),
+                                                  2.0 * s.kBT, y - y_eq);
+                if (U < Pr) bnd = 0;
+            } else if (pb || ptop) {
+                if (U < Pc.pf_tab[pb ? nprobe : nl + 1 + nprobe]) {
+                    bnd = 1;
+                    ax = ps.xc + (double)rx[l];
+                    aw = pb ? 0 : 1;
+                    P->anchor_x[l] = ax;
+                    P->anchor_wall[l] = aw;
+                }
+            }
+            P->bond[l] = bnd;
+            if (bnd) {
+                bonded = true;
+                const R dx = (R)(ax - ps.xc) - rx[l];
+                const R dy = aw ? gapt : -gapb;
+                const R y = sqrt(dx * dx + dy * dy);
+                if (y > (R)0) {
+                    const R mag = (R)Pc.sigma * (y - y_eq) / y;
+                    fx = mag * dx;
+                    fy = mag * dy;
+                }
+            }
+        }
+        cq[3 * cstride + l] = fx;
+        cq[4 * cstride + l] = fy;
+        cq[5 * cstride + l] = rx[l] * fy - ry[l] * fx;
+    }
+    const int nbonded = __syncthreads_count(bonded);
     // merge overlapping spans, count the nodes of each row, prefix sum (one warp)
     if (warp == 0) {
         int carry = 0;
@@ -589,6 +644,30 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             carry += __shfl_sync(0xffffffffu, incl, 31);
         }
         if (lane == 0) pre[Tm] = carry;
+    } else if (!init && warp <= 3) {
+        // FP64 sums of the bond loads, one warp per quantity
+        const double v = warp_sum_array<R>(cq + (2 + warp) * cstride, nl);
+        if (lane == 0) ps.F[2 + warp] = v;
+    } else if (!init && warp == 4) {
+        const R gb = warp_min_array<R>(ry, nl, ps.gap0_b, (R)1);
+        const R gt = warp_min_array<R>(ry, nl, ps.gap0_t, (R)-1);
+        if (lane == 0) {
+            ps.gmin_b = gb;
+            ps.gmin_t = gt;
+            ps.nprobe = nprobe;
+            ps.nbonded = nbonded;
+            // ---- 4. wall force (Eq. 12) -------------------------------
+            R Fw = 0;
+            if (s.wall_b != LBIB_WALL_PERIODIC && s.hamaker != 0.0) {
+                const R em = pick<R>((float)s.eps_min, s.eps_min);
+                const R eb = fmax(gb, em), et = fmax(gt, em);
+                const R k = pick<R>((float)(s.hamaker / (8.0 * 1.4142135623730951)),
+                                    s.hamaker / (8.0 * 1.4142135623730951));
+                const R r = pick<R>((float)Pc.r_eq, Pc.r_eq);
+                Fw = k * sqrt(r / (eb * eb * eb * eb * eb)) - k * sqrt(r / (et * et * et * et * et));
+            }
+            ps.Fw = (double)Fw;
+        }
     }
     __syncthreads();
     // list (kept in the force-tile buffer) and flags of the staged nodes, one
@@ -608,7 +687,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     // for it here (everything above reads only particle and geometry data)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nlist = pre[Tm];
-#pragma unroll 4
+#pragma unroll 1
     for (int k = tid; k < nlist; k += P_THREADS) {
         const int i = list[k];
         const int v = i / Tm, u = i - v * Tm;
@@ -654,8 +733,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l] + (R)1.2 * nxw[l],
                            ps.fyc + ry[l] + (R)1.2 * nyw[l], pt, l);
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-            R wxo[4], pyo[4];    // not needed here
-            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0, wxo, pyo,
+            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0,
                               [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
                                   const R irho = recip_rho((R)1 + drho);
                                   const R ux = jx * irho, uy = jy * irho;
@@ -681,91 +759,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             cq[2 * cstride + l] = rx[l] * ty - ry[l] * tx;
         }
 
-        // ---- 3. bonds (Eq. 9-11), one element per thread -------------------
-        const bool has_b = s.wall_b != LBIB_WALL_PERIODIC && s.rec_b > 0.0;
-        const bool has_t = s.wall_t != LBIB_WALL_PERIODIC && s.rec_t > 0.0;
-        const R ycr = pick<R>((float)s.y_cr, s.y_cr);
-        bool lig = false, pb = false, ptop = false;
-        R gapb = (R)0, gapt = (R)0;
-        if (tid < nl) {
-            lig = lig8[tid] != 0;
-            gapb = ps.gap0_b + ry[tid];
-            gapt = ps.gap0_t - ry[tid];
-            pb = lig && has_b && gapb < ycr;
-            ptop = lig && has_t && gapt < ycr;
-        }
-        const int nprobe = __syncthreads_count(pb || ptop);
-        bool bonded = false;
-        if (tid < nl) {
-            const int l = tid;
-            R fx = 0, fy = 0;
-            if (lig) {
-                // one draw per (step, element); the step is this particle's count
-                const double U = bond_uniform(s, Pc.step, (int)blockIdx.x - s.p0, l);
-                uint8_t bnd = P->bond[l];
-                double ax = P->anchor_x[l];
-                int8_t aw = P->anchor_wall[l];
-                const R y_eq = pick<R>((float)(s.y_eq_ratio * s.y_cr), s.y_eq_ratio * s.y_cr);
-                if (bnd) {
-                    // bond vector anchor - X_l; the anchor lies on a wall line
-                    const R dx = (R)(ax - ps.xc) - rx[l];
-                    const R dy = aw ? gapt : -gapb;
-                    const R y = sqrt(dx * dx + dy * dy);
-                    const double Pr = prob_reverse<R>(s.k_r0, Pc.sigma * (1.0 - s.sigma_star_ratio),
-                                                      2.0 * s.kBT, y - y_eq);
-                    if (U < Pr) bnd = 0;
-                } else if (pb || ptop) {
-                    if (U < Pc.pf_tab[pb ? nprobe : nl + 1 + nprobe]) {
-                        bnd = 1;
-                        ax = ps.xc + (double)rx[l];
-                        aw = pb ? 0 : 1;
-                        P->anchor_x[l] = ax;
-                        P->anchor_wall[l] = aw;
-                    }
-                }
-                P->bond[l] = bnd;
-                if (bnd) {
-                    bonded = true;
-                    const R dx = (R)(ax - ps.xc) - rx[l];
-                    const R dy = aw ? gapt : -gapb;
-                    const R y = sqrt(dx * dx + dy * dy);
-                    if (y > (R)0) {
-                        const R mag = (R)Pc.sigma * (y - y_eq) / y;
-                        fx = mag * dx;
-                        fy = mag * dy;
-                    }
-                }
-            }
-            cq[3 * cstride + l] = fx;
-            cq[4 * cstride + l] = fy;
-            cq[5 * cstride + l] = rx[l] * fy - ry[l] * fx;
-        }
-        const int nbonded = __syncthreads_count(bonded);
-
-        // ---- FP64 sums: one warp per quantity, gaps on warp 6 --------------
-        if (warp < 6) {
+        __syncthreads();
+        // ---- FP64 sums of the loads, one warp per quantity (the bond loads
+        // and the wall force were summed during the staging) ---------------
+        if (warp < 3) {
             const double v = warp_sum_array<R>(cq + warp * cstride, nl);
             if (lane == 0) ps.F[warp] = v;
-        } else if (warp == 6) {
-            const R gb = warp_min_array<R>(ry, nl, ps.gap0_b, (R)1);
-            const R gt = warp_min_array<R>(ry, nl, ps.gap0_t, (R)-1);
-            if (lane == 0) {
-                ps.gmin_b = gb;
-                ps.gmin_t = gt;
-                ps.nprobe = nprobe;
-                ps.nbonded = nbonded;
-                // ---- 4. wall force (Eq. 12) -------------------------------
-                R Fw = 0;
-                if (s.wall_b != LBIB_WALL_PERIODIC && s.hamaker != 0.0) {
-                    const R em = pick<R>((float)s.eps_min, s.eps_min);
-                    const R eb = fmax(gb, em), et = fmax(gt, em);
-                    const R k = pick<R>((float)(s.hamaker / (8.0 * 1.4142135623730951)),
-                                        s.hamaker / (8.0 * 1.4142135623730951));
-                    const R r = pick<R>((float)Pc.r_eq, Pc.r_eq);
-                    Fw = k * sqrt(r / (eb * eb * eb * eb * eb)) - k * sqrt(r / (et * et * et * et * et));
-                }
-                ps.Fw = (double)Fw;
-            }
         }
         __syncthreads();
         // ---- 5. rigid update (Eq. 13-16), one lane per degree of freedom ---
@@ -804,63 +803,19 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
 
     // ---- 6. IB direct forcing at the (new) pose ---------------------------
     const R ghx = (R)0.5 * pick<R>(s.f_gx, s.gx), ghy = (R)0.5 * pick<R>(s.f_gy, s.gy);
-    R Fx = 0, Fy = 0, wxo[4], pyo[4];
+    R Fx = 0, Fy = 0;
     if (tid < nl) {
         const int l = tid;
         setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l], ps.fyc + ry[l], pt, l);
-        // interpolation of rho and u* = (j + g/2) / rho over the 4 x 4 support
-        // (same node order and weights as support_sum)
-        const int rows = pt.rows[l];
-        const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l], mu_v = pt.mu_v[l];
-        const int ix0 = pt.ix0[l], iy0 = pt.iy0[l];
         R s_rho = 0, s_u = 0, s_v = 0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            wxo[a] = (rows & 16) ? bspline((R)(a - 1) - fx) : (R)0;
-            pyo[a] = (R)0;
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            if (!(rows & 16) || !(rows & (1 << b))) continue;
-            const R dy = (R)(b - 1) - fy;
-            const R wy = bspline(dy) * invW;
-            if (wy == (R)0) continue;
-            const R py = wy * ((R)1 - (dy - mu) * mu_v);
-            pyo[b] = py;
-            const int v = iy0 + b - ry0;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                if (wxo[a] * wy == (R)0) continue;
-                const int u = ix0 + a - rx0;
-                R drho, jx, jy;
-                const bool st = (unsigned)u < (unsigned)Tm && (unsigned)v < (unsigned)Tm &&
-                                flag[v * Tm + u];
-                if (st) {
-                    const int i = v * Tm + u;
-                    drho = mr[i];
-                    jx = mjx[i];
-                    jy = mjy[i];
-                } else {
-                    int xx = (ix0 + a) % s.nx;
-                    if (xx < 0) xx += s.nx;
-                    int yy = iy0 + b;
-                    if (s.wall_b == LBIB_WALL_PERIODIC) {
-                        yy %= s.ny;
-                        if (yy < 0) yy += s.ny;
-                    }
-                    const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy);
-                    drho = m.drho;
-                    jx = m.jx;
-                    jy = m.jy;
-                }
-                const R irho = recip_rho((R)1 + drho);
-                const R phi = wxo[a] * py;
-                s_rho += phi * drho;
-                s_u += phi * ((jx + ghx) * irho);
-                s_v += phi * ((jy + ghy) * irho);
-            }
-        }
-        if (rows & 16) {
+        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0,
+                          [&](R, R, R, R phi, R drho, R jx, R jy) {
+                              const R irho = recip_rho((R)1 + drho);
+                              s_rho += phi * drho;
+                              s_u += phi * ((jx + ghx) * irho);
+                              s_v += phi * ((jy + ghy) * irho);
+                          });
+        if (pt.rows[l] & 16) {
             const R rl = (R)1 + s_rho;
             const R udx = ps.uR - ps.omR * ry[l];
             const R udy = ps.vR + ps.omR * rx[l];
@@ -878,13 +833,31 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         ((uint4 *)tile)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     if (tid < nl) {
+        // phi_(a,b) = wx[a] py[b] as in support_sum (zero without a fit or
+        // for a row outside the lattice)
+        const int rows = pt.rows[tid];
+        const R fx = pt.fx[tid], fy = pt.fy[tid], invW = pt.invW[tid], mu = pt.mu[tid];
+        const R mu_v = pt.mu_v[tid];
+        R wx[4];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const R phi = wxo[j & 3] * pyo[j >> 2];
-            R2 c;
-            c.x = phi * Fx;
-            c.y = phi * Fy;
-            ctb[tid * 16 + j] = c;
+        for (int a = 0; a < 4; ++a) wx[a] = (rows & 16) ? bspline((R)(a - 1) - fx) : (R)0;
+#pragma unroll 1
+        for (int b = 0; b < 4; ++b) {
+            R py = (R)0;
+            if ((rows & 16) && (rows & (1 << b))) {
+                const R dy = (R)(b - 1) - fy;
+                const R wy = bspline(dy) * invW;
+                const R dyc = dy - mu;
+                py = wy * ((R)1 - dyc * mu_v);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const R phi = wx[a] * py;
+                R2 c;
+                c.x = phi * Fx;
+                c.y = phi * Fy;
+                ctb[tid * 16 + b * 4 + a] = c;
+            }
         }
     }
     __syncthreads();
