@@ -376,7 +376,7 @@ size_t smem_bytes_for(int nl, int T) {
     const size_t spread = spread_in_moments<R>(nl, (int)Tm) ? 0 : 32 * sizeof(R) * (size_t)nl;
     return up(sizeof(Pose<R>)) + 21 * up(sizeof(R) * nl) + 3 * up(sizeof(int) * nl) + up(nl) +
            up(sizeof(int) * nl) + up(sizeof(int) * (nl + 1)) + up(sizeof(R) * 2 * T * T) +
-           up(Tm * Tm) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread;
+           up(Tm * Tm) + up(sizeof(double) * 3 * (P_THREADS / 32)) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread;
 }
 
 // Reverse probability of Eq. 11 (dt = 1): FP32 on the FP32 path, FP64 on the
@@ -449,6 +449,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     int *corder = (int *)take(sizeof(int) * nl);
     int *coff = (int *)take(sizeof(int) * (nl + 1));
     uint8_t *flag = (uint8_t *)take(Tm * Tm);     // region node staged
+    double *lpart = (double *)take(sizeof(double) * 3 * (P_THREADS / 32));   // load partials
     int4 *span = (int4 *)take(sizeof(int4) * Tm);       // staged spans per region row
     int *pre = (int *)take(sizeof(int) * (Tm + 1));     // staged nodes before each row
     R *tile = (R *)take(sizeof(R) * 2 * T * T);
@@ -728,6 +729,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     if (!init) {
         // ---- 2. hydrodynamic loads (Eq. 7-8), one thread per probe --------
         const R nu = pick<R>(s.f_nu, s.d_nu);
+        R tx = 0, ty = 0, tq = 0;
         if (tid < nl) {
             const int l = tid;
             setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l] + (R)1.2 * nxw[l],
@@ -743,7 +745,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
                                   s_vx += w * dx * uy;
                                   s_vy += w * dyc * uy;
                               });
-            R tx = 0, ty = 0;
             if (pt.rows[l] & 16) {
                 const R iv = pt.inv_v[l];
                 const R dudx = (R)3 * s_ux, dudy = s_uy * iv;
@@ -754,20 +755,33 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
                 tx = (-p * nxl + nu * (R)2 * dudx * nxl + txy * nyl) * sS[l];
                 ty = (-p * nyl + txy * nxl + nu * (R)2 * dvdy * nyl) * sS[l];
             }
-            cq[0 * cstride + l] = tx;
-            cq[1 * cstride + l] = ty;
-            cq[2 * cstride + l] = rx[l] * ty - ry[l] * tx;
+            tq = rx[l] * ty - ry[l] * tx;
         }
-
-        __syncthreads();
-        // ---- FP64 sums of the loads, one warp per quantity (the bond loads
-        // and the wall force were summed during the staging) ---------------
-        if (warp < 3) {
-            const double v = warp_sum_array<R>(cq + warp * cstride, nl);
-            if (lane == 0) ps.F[warp] = v;
+        // FP64 sums of the loads: a tree over each warp's probes, the warps'
+        // partial sums added in warp order by the update lanes below (the
+        // bond loads and the wall force were summed during the staging)
+        if (warp < (nl + 31) / 32) {
+            double a0 = (double)tx, a1 = (double)ty, a2 = (double)tq;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            }
+            if (lane == 0) {
+                lpart[3 * warp] = a0;
+                lpart[3 * warp + 1] = a1;
+                lpart[3 * warp + 2] = a2;
+            }
         }
         __syncthreads();
         // ---- 5. rigid update (Eq. 13-16), one lane per degree of freedom ---
+        if (tid < 3) {
+            double h = 0.0;
+            for (int w = 0; w < (nl + 31) / 32; ++w) h += lpart[3 * w + tid];
+            ps.F[tid] = h;
+            if (tid == 2) P->Mh = h; else P->Fh[tid] = h;
+        }
         if (tid < 3 && !Pc.fixed) {
             const int k = tid;
             const double F = k == 0 ? ps.F[0] + ps.F[3]
@@ -791,7 +805,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             set_pose_dof(ps, k, yb, yt);     // this lane's part of the new pose
         }
         if (tid == 32) {
-            P->Fh[0] = ps.F[0]; P->Fh[1] = ps.F[1]; P->Mh = ps.F[2];
             P->Fb[0] = ps.F[3]; P->Fb[1] = ps.F[4]; P->Mb = ps.F[5];
             P->Fw[0] = 0.0; P->Fw[1] = ps.Fw;
             P->n_probing = ps.nprobe;
