@@ -531,12 +531,16 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     const bool has_b = s.wall_b != LBIB_WALL_PERIODIC && s.rec_b > 0.0;
     const bool has_t = s.wall_t != LBIB_WALL_PERIODIC && s.rec_t > 0.0;
     const R ycr = pick<R>((float)s.y_cr, s.y_cr);
+    // element of this thread's bond: the upper half of the block takes the
+    // bonds when both halves fit the elements, so that they run beside the
+    // staging work of the lower half
+    const int kb = 2 * nl <= P_THREADS ? tid - P_THREADS / 2 : tid;
     bool lig = false, pb = false, ptop = false;
     R gapb = (R)0, gapt = (R)0;
-    if (!init && tid < nl) {
-        lig = lig8[tid] != 0;
-        gapb = ps.gap0_b + ry[tid];
-        gapt = ps.gap0_t - ry[tid];
+    if (!init && (unsigned)kb < (unsigned)nl) {
+        lig = lig8[kb] != 0;
+        gapb = ps.gap0_b + ry[kb];
+        gapt = ps.gap0_t - ry[kb];
         pb = lig && has_b && gapb < ycr;
         ptop = lig && has_t && gapt < ycr;
     }
@@ -577,8 +581,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         }
     }
     bool bonded = false;
-    if (!init && tid < nl) {
-        const int l = tid;
+    if (!init && (unsigned)kb < (unsigned)nl) {
+        const int l = kb;
         R fx = 0, fy = 0;
         if (lig) {
             // one draw per (step, element); the step is this particle's count
