@@ -297,7 +297,7 @@ __device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, i
 template <typename S, typename R, typename F>
 __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const Points<R> &pt,
                                             int l, const R *mr, const R *mjx, const R *mjy,
-                                            const uint8_t *flag, int Tm, int rx0, int ry0,
+                                            const int4 *span, int Tm, int rx0, int ry0,
                                             F &&f) {
     const int rows = pt.rows[l];
     if (!(rows & 16)) return;
@@ -320,13 +320,15 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
         const R dyc = dy - mu;
         const R py = wy * ((R)1 - dyc * mu_v);
         const int v = iy0 + b - ry0;
+        // the row's staged spans (none outside the region)
+        const int4 q = (unsigned)v < (unsigned)Tm ? span[v] : make_int4(0, -1, 0, -1);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const R w = wx[a] * wy;
             if (w == (R)0) continue;
             const int u = ix0 + a - rx0;
             R drho, jx, jy;
-            if ((unsigned)u < (unsigned)Tm && (unsigned)v < (unsigned)Tm && flag[v * Tm + u]) {
+            if ((u >= q.x && u <= q.y) || (u >= q.z && u <= q.w)) {
                 const int i = v * Tm + u;
                 drho = mr[i];
                 jx = mjx[i];
@@ -376,7 +378,7 @@ size_t smem_bytes_for(int nl, int T) {
     const size_t spread = spread_in_moments<R>(nl, (int)Tm) ? 0 : 32 * sizeof(R) * (size_t)nl;
     return up(sizeof(Pose<R>)) + 21 * up(sizeof(R) * nl) + 3 * up(sizeof(int) * nl) + up(nl) +
            up(sizeof(int) * nl) + up(sizeof(int) * (nl + 1)) + up(sizeof(R) * 2 * T * T) +
-           up(Tm * Tm) + up(sizeof(double) * 3 * (P_THREADS / 32)) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread;
+           up(sizeof(double) * 3 * (P_THREADS / 32)) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread;
 }
 
 // Reverse probability of Eq. 11 (dt = 1): FP32 on the FP32 path, FP64 on the
@@ -448,7 +450,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     uint8_t *lig8 = (uint8_t *)take(nl);
     int *corder = (int *)take(sizeof(int) * nl);
     int *coff = (int *)take(sizeof(int) * (nl + 1));
-    uint8_t *flag = (uint8_t *)take(Tm * Tm);     // region node staged
     double *lpart = (double *)take(sizeof(double) * 3 * (P_THREADS / 32));   // load partials
     int4 *span = (int4 *)take(sizeof(int4) * Tm);       // staged spans per region row
     int *pre = (int *)take(sizeof(int) * (Tm + 1));     // staged nodes before each row
@@ -524,7 +525,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     };
     if (!cached) place();
     const int rx0 = ps.ixc - Tm / 2, ry0 = ps.iyc - Tm / 2;
-    for (int i = tid; i < (Tm * Tm + 3) / 4; i += P_THREADS) ((int *)flag)[i] = 0;
     for (int v = tid; v < Tm; v += P_THREADS) span[v] = make_int4(Tm, -1, Tm, -1);
     // ---- 3. bonds (Eq. 9-11), one element per thread: they need only the
     // pose, so they run with the staging, before the wait on the lattice pass
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     // make one span and the others a second; along a convex outline each of
     // these chains is monotone in y, so a span is an interval of the row (any
     // support node outside the staged nodes is pulled directly, with the same
-    // arithmetic).  The spans are listed, flagged and pulled.
+    // arithmetic).  The nodes of the spans are counted per row and pulled.
     if (tid < nl) {
         const R X = ps.fxc + rx[tid], Y = ps.fyc + ry[tid];
         int bx0 = (int)floor(X) - 2, by0 = (int)floor(Y) - 2;
@@ -675,27 +675,23 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         }
     }
     __syncthreads();
-    // list (kept in the force-tile buffer) and flags of the staged nodes, one
-    // warp per row
-    int *list = (int *)tile;
-    for (int v = warp; v < Tm; v += P_THREADS / 32) {
-        const int4 q = span[v];
-        const int n0 = max(q.y - q.x + 1, 0), p0 = pre[v], n = pre[v + 1] - p0;
-        for (int i = lane; i < n; i += 32) {
-            const int u = i < n0 ? q.x + i : q.z + (i - n0);
-            list[p0 + i] = v * Tm + u;
-            flag[v * Tm + u] = 1;
-        }
-    }
-    __syncthreads();
     // populations of this step come from the lattice pass just before: wait
     // for it here (everything above reads only particle and geometry data)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nlist = pre[Tm];
 #pragma unroll 1
     for (int k = tid; k < nlist; k += P_THREADS) {
-        const int i = list[k];
-        const int v = i / Tm, u = i - v * Tm;
+        // staged node k: row v is the last with pre[v] <= k, then its spans
+        int lo = 0, hi = Tm;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pre[mid] <= k) lo = mid; else hi = mid;
+        }
+        const int v = lo;
+        const int4 q = span[v];
+        const int n0 = max(q.y - q.x + 1, 0), o = k - pre[v];
+        const int u = o < n0 ? q.x + o : q.z + (o - n0);
+        const int i = v * Tm + u;
         int xx = (rx0 + u) % s.nx;
         if (xx < 0) xx += s.nx;
         int yy = ry0 + v;
@@ -739,7 +735,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l] + (R)1.2 * nxw[l],
                            ps.fyc + ry[l] + (R)1.2 * nyw[l], pt, l);
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0,
+            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, Tm, rx0, ry0,
                               [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
                                   const R irho = recip_rho((R)1 + drho);
                                   const R ux = jx * irho, uy = jy * irho;
@@ -825,7 +821,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         const int l = tid;
         setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l], ps.fyc + ry[l], pt, l);
         R s_rho = 0, s_u = 0, s_v = 0;
-        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, flag, Tm, rx0, ry0,
+        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, Tm, rx0, ry0,
                           [&](R, R, R, R phi, R drho, R jx, R jy) {
                               const R irho = recip_rho((R)1 + drho);
                               s_rho += phi * drho;
