@@ -775,36 +775,36 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             }
         }
         __syncthreads();
-        // ---- 5. rigid update (Eq. 13-16), one lane per degree of freedom ---
-        if (tid < 3) {
+        // ---- 5. rigid update (Eq. 13-16), one degree of freedom per warp ---
+        // (lane 0 of warps 0, 1, 2: the three chains of FP64 arithmetic run
+        // side by side instead of one after another in a divergent warp)
+        if ((tid & 31) == 0 && tid < 96) {
+            const int k = tid >> 5;
             double h = 0.0;
-            for (int w = 0; w < (nl + 31) / 32; ++w) h += lpart[3 * w + tid];
-            ps.F[tid] = h;
-            if (tid == 2) P->Mh = h; else P->Fh[tid] = h;
+            for (int w = 0; w < (nl + 31) / 32; ++w) h += lpart[3 * w + k];
+            ps.F[k] = h;
+            if (k == 2) P->Mh = h; else P->Fh[k] = h;
+            if (!Pc.fixed) {
+                const double F = k == 0 ? h + ps.F[3] : (k == 1 ? h + ps.F[4] + ps.Fw : h + ps.F[5]);
+                const double im = k == 2 ? Pc.inv_inertia : Pc.inv_mass;
+                const double u0 = k == 0 ? ps.u : (k == 1 ? ps.v : ps.om);
+                const double u1 = k == 0 ? Pc.u1 : (k == 1 ? Pc.v1 : Pc.om1);
+                const double x0 = k == 0 ? ps.xc : (k == 1 ? ps.yc : ps.th);
+                const double x1 = k == 0 ? Pc.xc1 : (k == 1 ? Pc.yc1 : Pc.th1);
+                const double un = 2.0 / 3.0 * (2.0 * u0 - 0.5 * u1 + F * im);
+                const double xn = (4.0 * x0 - x1 + 2.0 * un) * (1.0 / 3.0);
+                double *Pu = k == 0 ? &P->u : (k == 1 ? &P->v : &P->om);
+                double *Pu1 = k == 0 ? &P->u1 : (k == 1 ? &P->v1 : &P->om1);
+                double *Px = k == 0 ? &P->xc : (k == 1 ? &P->yc : &P->th);
+                double *Px1 = k == 0 ? &P->xc1 : (k == 1 ? &P->yc1 : &P->th1);
+                *Pu1 = u0; *Pu = un; *Px1 = x0; *Px = xn;
+                if (k == 0) { ps.u = un; ps.xc = xn; }
+                if (k == 1) { ps.v = un; ps.yc = xn; }
+                if (k == 2) { ps.om = un; ps.th = xn; }
+                set_pose_dof(ps, k, yb, yt);     // this degree of freedom of the new pose
+            }
         }
-        if (tid < 3 && !Pc.fixed) {
-            const int k = tid;
-            const double F = k == 0 ? ps.F[0] + ps.F[3]
-                           : (k == 1 ? ps.F[1] + ps.F[4] + ps.Fw : ps.F[2] + ps.F[5]);
-            const double im = k == 2 ? Pc.inv_inertia : Pc.inv_mass;
-            const double u0 = k == 0 ? ps.u : (k == 1 ? ps.v : ps.om);
-            const double u1 = k == 0 ? Pc.u1 : (k == 1 ? Pc.v1 : Pc.om1);
-            const double x0 = k == 0 ? ps.xc : (k == 1 ? ps.yc : ps.th);
-            const double x1 = k == 0 ? Pc.xc1 : (k == 1 ? Pc.yc1 : Pc.th1);
-            const double un = 2.0 / 3.0 * (2.0 * u0 - 0.5 * u1 + F * im);
-            const double xn = (4.0 * x0 - x1 + 2.0 * un) * (1.0 / 3.0);
-            double *Pu = k == 0 ? &P->u : (k == 1 ? &P->v : &P->om);
-            double *Pu1 = k == 0 ? &P->u1 : (k == 1 ? &P->v1 : &P->om1);
-            double *Px = k == 0 ? &P->xc : (k == 1 ? &P->yc : &P->th);
-            double *Px1 = k == 0 ? &P->xc1 : (k == 1 ? &P->yc1 : &P->th1);
-            *Pu1 = u0; *Pu = un; *Px1 = x0; *Px = xn;
-            __syncwarp(0x7u);
-            if (k == 0) { ps.u = un; ps.xc = xn; }
-            if (k == 1) { ps.v = un; ps.yc = xn; }
-            if (k == 2) { ps.om = un; ps.th = xn; }
-            set_pose_dof(ps, k, yb, yt);     // this lane's part of the new pose
-        }
-        if (tid == 32) {
+        if (tid == 96) {
             P->Fb[0] = ps.F[3]; P->Fb[1] = ps.F[4]; P->Mb = ps.F[5];
             P->Fw[0] = 0.0; P->Fw[1] = ps.Fw;
             P->n_probing = ps.nprobe;
