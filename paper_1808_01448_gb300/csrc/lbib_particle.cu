@@ -560,6 +560,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         int bx0 = (int)floor(X) - 2, by0 = (int)floor(Y) - 2;
         int bx1 = bx0 + 5, by1 = by0 + 5;
         if (!init) {
+            // the probe's MLS support needs only the pose: set up here, beside
+            // the bond kinetics of the upper half of the block
+            setup_point<R>(s, ps.ixc, ps.iyc, X + (R)1.2 * nxw[tid], Y + (R)1.2 * nyw[tid], pt, tid);
             const int px0 = (int)floor(X + (R)1.2 * nxw[tid]) - 1;
             const int py0 = (int)floor(Y + (R)1.2 * nyw[tid]) - 1;
             bx0 = min(bx0, px0);
@@ -732,8 +735,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         R tx = 0, ty = 0, tq = 0;
         if (tid < nl) {
             const int l = tid;
-            setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l] + (R)1.2 * nxw[l],
-                           ps.fyc + ry[l] + (R)1.2 * nyw[l], pt, l);
+            // (its support was set up with the staging)
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
             support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, Tm, rx0, ry0,
                               [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
