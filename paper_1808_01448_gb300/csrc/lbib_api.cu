@@ -640,7 +640,10 @@ cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
         if ((e = cudaEventRecord(b->evb[k & 1], b->s2))) return e;
         if (k > 0 && (e = cudaStreamWaitEvent(b->s1, b->evb[(k - 1) & 1], 0))) return e;
         if (k == 0 && (e = mark(4, b->s1))) return e;
-        if ((e = launch_lattice(b->kind, b->bd, f, 2, b->s1))) return e;
+        // programmatic dependent of the particle pass of the step before
+        // (its CTAs are resident when that pass ends), unless an event record
+        // sits between them
+        if ((e = launch_lattice(b->kind, b->bd, f, 2, b->s1, k > 0 && !(ev && k == 1)))) return e;
         if (k == 0 && (e = mark(5, b->s1))) return e;
         if ((e = cudaEventRecord(b->evn[k & 1], b->s1))) return e;
         if (k == 0 && (e = mark(2, b->s1))) return e;

@@ -295,13 +295,18 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
 // the next step but one.
 template <typename S, typename R>
 __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, int flip) {
-    // let the particle pass that follows start its prologue now; it waits
-    // for this grid to complete before reading the populations
-    asm volatile("griddepcontrol.launch_dependents;");
     const int tile = blockIdx.x;
     const int pi = __ldg(b.near_part + tile);
     ParticleDev *P = b.parts[pi];
     const SimDev &s = b.sims[b.part_sim[pi]];
+    // when launched as a programmatic dependent of the particle pass before
+    // it, wait for that pass here: it wrote the force tiles and the next box
+    // (everything read above is fixed for the batch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // then let the particle pass that follows start its prologue (which
+    // reads what the particle pass before wrote); it waits for this grid to
+    // complete before reading the populations
+    asm volatile("griddepcontrol.launch_dependents;");
     const int cur = *s.cur ^ flip;
     const int NB = P->NB, ox = P->box_ox[cur], oy = P->box_oy[cur];
     const int t0 = __ldg(b.near_tile0 + pi);
@@ -446,15 +451,24 @@ cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st) {
+cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st,
+                           bool pdl) {
     return by_kind(kind, [&](auto sv, auto rv) {
         using S = decltype(sv);
         using R = decltype(rv);
         if (mode == 0) return launch_variant<S, R, false>(b.lat_variant, b, flip, st);
         if (mode == 1) return launch_variant<S, R, true>(b.lat_variant, b, flip, st);
-        if (b.total_near_tiles > 0)
-            lattice_near_kernel<S, R><<<b.total_near_tiles, LB_THREADS, 0, st>>>(b, flip);
-        return cudaGetLastError();
+        if (b.total_near_tiles == 0) return cudaSuccess;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(b.total_near_tiles);
+        cfg.blockDim = dim3(LB_THREADS);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = pdl ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, lattice_near_kernel<S, R>, b, flip);
     });
 }
 

@@ -838,6 +838,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
             Fy = (R)2 * rl * (udy - s_v) * sS[l];
         }
     }
+    // the near-box pass of the next step may be scheduled from here on (it
+    // waits for this pass to end before it reads the tiles)
+    asm volatile("griddepcontrol.launch_dependents;");
     // each marker's sixteen contributions phi_k F_l eps_l, in the staged
     // moments' space once every support has been read (or a buffer of their
     // own when they do not fit there)
