@@ -64,6 +64,7 @@ struct HostParticle {
     std::vector<uint8_t> ligand;
     std::vector<int> color_order, color_off;
     ParticleDev *d_part = nullptr;   // device struct
+    void *d_ecache = nullptr;        // its element record (inside d_block)
     void *d_block = nullptr;         // geometry, bonds, tile
 };
 
@@ -360,6 +361,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     h.ligand = lig; h.color_order = co; h.color_off = coff;
     h.bond = bond; h.anchor_x = ax; h.anchor_wall = aw; h.tile = tile; h.pf_tab = pft;
     h.ecache = ecache;      // filled by the first pass (pose_ok = 0 until then)
+    p.d_ecache = ecache;
     p.d_part = (ParticleDev *)pd;
     cudaStream_t st = s->stream;
     CK(cudaMemcpyAsync(pd, &h, sizeof h, cudaMemcpyHostToDevice, st));
@@ -447,6 +449,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         }
     }
     const size_t bytes = sizeof(SimDev) * n + sizeof(ParticleDev *) * (nparts + 1) +
+                         sizeof(PartRec) * (nparts + 1) +
                          sizeof(int) * (nparts + 1) + sizeof(int *) * n +
                          sizeof(int) * (size_t)tiles + sizeof(int) * (size_t)(near_tiles + nparts) +
                          256;
@@ -461,6 +464,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     };
     SimDev *dsims = (SimDev *)take(sizeof(SimDev) * n);
     ParticleDev **dparts = (ParticleDev **)take(sizeof(ParticleDev *) * (nparts + 1));
+    PartRec *dprec = (PartRec *)take(sizeof(PartRec) * (nparts + 1));
     int *dpsim = (int *)take(sizeof(int) * (nparts + 1));
     int **dcurs = (int **)take(sizeof(int *) * n);
     int *dtsim = (int *)take(sizeof(int) * (size_t)tiles);
@@ -468,6 +472,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     int *dntile0 = (int *)take(sizeof(int) * (size_t)(nparts + 1));
     std::vector<SimDev> hs;
     std::vector<ParticleDev *> hp;
+    std::vector<PartRec> hpr;
     std::vector<int> hps;
     std::vector<int *> hc;
     int tile0 = 0;
@@ -477,11 +482,13 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         tile0 += hs.back().ntiles;
         for (auto &p : s->parts) {
             hp.push_back(p.d_part);
+            hpr.push_back(PartRec{p.d_ecache, p.nl, 0});
             hps.push_back(i);
         }
         hc.push_back(s->d_cur);
     }
     hp.push_back(nullptr);
+    hpr.push_back(PartRec{nullptr, 0, 0});
     hps.push_back(0);
     std::vector<int> hts((size_t)tiles);
     for (int i = 0; i < n; ++i)
@@ -500,6 +507,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     cudaError_t e;
     if ((e = cudaMemcpyAsync(dsims, hs.data(), sizeof(SimDev) * n, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dparts, hp.data(), sizeof(ParticleDev *) * hp.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(dprec, hpr.data(), sizeof(PartRec) * hpr.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dpsim, hps.data(), sizeof(int) * hps.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dcurs, hc.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dtsim, hts.data(), sizeof(int) * hts.size(), cudaMemcpyHostToDevice, st)) ||
@@ -525,6 +533,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->smem = smem;
     b->bd.sims = dsims;
     b->bd.parts = dparts;
+    b->bd.prec = dprec;
     b->bd.part_sim = dpsim;
     b->bd.tile_sim = dtsim;
     b->bd.nsims = n;

@@ -100,9 +100,18 @@ struct ParticleDev {
 };
 constexpr int ECACHE = 12;
 
+// Per batch particle: its element record (ParticleDev::ecache) and element
+// count, so that a particle pass can load the record in the same round as the
+// descriptor.
+struct PartRec {
+    void *erec;
+    int nl, pad;
+};
+
 struct BatchDev {
     SimDev *sims;
     ParticleDev **parts;
+    const PartRec *prec;     // [nparts] or null
     int *part_sim;
     int *tile_sim;       // lattice work tile -> simulation index
     int *near_part;      // near-box work tile -> batch particle index

@@ -406,6 +406,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     __shared__ __align__(16) unsigned char s_sim_raw[sizeof(SimDev)];
     __shared__ __align__(16) unsigned char s_par_raw[sizeof(ParticleDev)];
     ParticleDev *P = b.parts[blockIdx.x];
+    // this thread's element record, loaded beside the descriptor (used only
+    // if the descriptor says it is valid)
+    R ev[ECACHE];
+    const PartRec prec = b.prec ? b.prec[blockIdx.x] : PartRec{nullptr, 0, 0};
+    if (prec.erec && (int)threadIdx.x < prec.nl) {
+        const R *e = (const R *)prec.erec + (size_t)threadIdx.x * ECACHE;
+#pragma unroll
+        for (int k = 0; k < ECACHE; ++k) ev[k] = e[k];
+    }
     {
         const int *src_s = (const int *)&b.sims[b.part_sim[blockIdx.x]];
         const int *src_p = (const int *)P;
@@ -483,14 +492,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     }
     // element data: from the record the last pass left (marker positions at
     // this pose included), else from the geometry arrays
-    const bool cached = Pc.pose_ok && Pc.ecache;
+    const bool cached = Pc.pose_ok && Pc.ecache && prec.erec == Pc.ecache;
     R *erec = (R *)Pc.ecache;
     if (tid < nl) {
         if (cached) {
-            const R *e = erec + (size_t)tid * ECACHE;
-            R v[ECACHE];
-#pragma unroll
-            for (int k = 0; k < ECACHE; ++k) v[k] = e[k];
+            const R *v = ev;
             gbx[tid] = v[0]; gby[tid] = v[1]; gnx[tid] = v[2]; gny[tid] = v[3];
             sS[tid] = v[4];
             rx[tid] = v[5]; ry[tid] = v[6]; nxw[tid] = v[7]; nyw[tid] = v[8];
@@ -682,7 +688,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     // for it here (everything above reads only particle and geometry data)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nlist = pre[Tm];
-#pragma unroll 1
+#pragma unroll 2
     for (int k = tid; k < nlist; k += P_THREADS) {
         // staged node k: row v is the last with pre[v] <= k, then its spans
         int lo = 0, hi = Tm;
