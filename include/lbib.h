@@ -221,8 +221,14 @@ lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *cou
 /* Kernel variants of the lattice pass (the bulk pass when particle work is
  * overlapped), all on the same 1024-node tiles: 0 = 256 threads x one
  * group of four nodes; 1 = the same, at most 64 registers (four CTAs per
- * SM); 2 = 128 threads x two groups; 3 = the same, four CTAs per SM.  FP64
- * storage and the plain (non-overlapped) pass always use variant 0.
+ * SM); 2 = 128 threads x two groups; 3 = the same, four CTAs per SM;
+ * 4 = variant 1 with each plane's source range staged in shared memory by
+ * bulk asynchronous copies (copy engine, mbarrier completion); 5 = the same
+ * with two tiles per CTA in two stages (the second tile's copies in flight
+ * while the first is computed).  Variants 4 and 5 need FP32/FP16/BF16 storage, rows of
+ * whole 16-byte words and walls that are not periodic in every member (else
+ * they run as variant 1).  FP64 storage and the plain (non-overlapped) pass
+ * always use variant 0.
  * lbib_batch_autotune runs the lattice pass of each variant `reps` times on
  * the batch's current state (timing runs: they write only the buffer the next
  * step overwrites and leave step counters alone, so the simulation is
@@ -230,7 +236,7 @@ lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *cou
  * *variant and the mean milliseconds of each variant to ms[] (either may be
  * NULL).  Synchronises the stream.  lbib_batch_set_variant selects a variant
  * directly (e.g. one tuned on an earlier batch of the same shape). */
-#define LBIB_LATTICE_VARIANTS 4
+#define LBIB_LATTICE_VARIANTS 6
 lbib_status lbib_batch_autotune(lbib_batch *b, int32_t reps, int32_t *variant, double *ms);
 lbib_status lbib_batch_set_variant(lbib_batch *b, int32_t variant);
 

@@ -316,6 +316,9 @@ void ellipse_outline(double ax, double by, int n, std::vector<double> &vx,
 lbib_status check_err_word(lbib_sim *s) {
     int err = 0;
     CK(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & ERR_TIMEOUT)
+        return fail(LBIB_E_TIMEOUT, "simulation %llu: a bounded device wait of the lattice pass ran out",
+                    (unsigned long long)s->cfg.sim_id);
     if (err & ERR_UNSTABLE)
         return fail(LBIB_E_UNSTABLE,
                     "simulation %llu became unstable (a node's state non-finite, |rho - 1| >= 1 "
@@ -543,6 +546,18 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->bd.near_tile0 = dntile0;
     b->bd.total_near_tiles = near_tiles;
     b->bd.lat_variant = 0;
+    // copy-engine staging (variants 4, 5): rows of whole 16-byte words,
+    // walls that are not periodic, 4- or 2-byte storage
+    int tma_ok = b->kind != ST_F64;
+    for (int i = 0; i < n; ++i) {
+        const int per16 = 16 / (int)storage_size(b->kind);
+        if (!hs[i].vec4 || hs[i].nx % per16 != 0 || hs[i].wall_b == LBIB_WALL_PERIODIC) tma_ok = 0;
+    }
+    b->bd.tma_ok = tma_ok;
+    if (tma_ok && (e = lattice_kernel_setup(b->kind)) != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e, "lattice kernel setup");
+    }
     b->d_curs = dcurs;
     b->overlap = nparts > 0 && boxes_fit;
     if (b->overlap) {

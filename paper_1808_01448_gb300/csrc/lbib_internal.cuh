@@ -31,7 +31,7 @@ constexpr int NEAR_NPT = 1;
 constexpr int NEAR_TILE_NODES = LB_THREADS * NEAR_NPT;
 
 // Error bits of the per-simulation device error word.
-enum { ERR_UNSTABLE = 1 };
+enum { ERR_UNSTABLE = 1, ERR_TIMEOUT = 2 };
 
 // Per-simulation descriptor as seen by the kernels of one batch.
 struct SimDev {
@@ -119,6 +119,7 @@ struct BatchDev {
     int total_near_tiles;
     int nsims, nparts, total_tiles;
     int lat_variant;     // bulk-pass kernel variant (0 .. LBIB_LATTICE_VARIANTS - 1)
+    int tma_ok;          // every lattice suits the copy-engine variants (4, 5)
 };
 
 // Stochastic rounding of 16-bit stores.  A node's dither word is a hash of
@@ -431,6 +432,9 @@ cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cuda
 // the previous kernel on st
 cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int mode, int smem,
                              cudaStream_t st, bool pdl = false);
+// Allows the lattice-pass variants their dynamic shared memory (once per
+// storage kind and device, before the first launch).
+cudaError_t lattice_kernel_setup(int kind);
 cudaError_t launch_fields(int kind, const SimDev &s, ParticleDev *const *parts, double *rho,
                           double *ux, double *uy, cudaStream_t st);
 cudaError_t launch_populations(int kind, const SimDev &s, double *out, cudaStream_t st);

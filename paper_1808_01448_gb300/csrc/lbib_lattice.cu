@@ -350,6 +350,250 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
     }
 }
 
+// ---- bulk pass with copy-engine staging (variants 4 and 5) -----------------
+// Same 1024-node tiles and arithmetic as lattice_kernel (BULK, vector path).
+// Thread 0 has the copy engine bring, for each of the nine population planes,
+// the node range the tile pulls from -- the tile's range shifted by the
+// plane's row offset, with a 16-byte margin on each side -- into shared memory
+// with one bulk copy each, all completing on one mbarrier; the threads then
+// take their groups of four nodes from shared memory.  Groups in the wall rows
+// or at either end of a row (where x wraps) pull from global memory as in the
+// other variants.  Only for storage of 4 or 2 bytes on lattices whose rows
+// are whole 16-byte words and whose walls are not periodic (tma_ok).  The
+// wait on the mbarrier is bounded: past the limit the simulation's error word
+// gets ERR_TIMEOUT and the CTA leaves its tile unwritten.
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Waits for phase 0 of the mbarrier, at most `limit` polls; true if it completed.
+__device__ __forceinline__ bool mbar_wait0(const uint64_t *bar, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar))
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Four consecutive staged values (p 16-byte aligned) and one staged value, in
+// the compute type.
+template <typename S> struct Staged4;
+template <> struct Staged4<float> {
+    static __device__ __forceinline__ void ld4(const float *p, float, float o[4]) {
+        const float4 v = *(const float4 *)p;
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    static __device__ __forceinline__ float ld1(const float *p, float) { return *p; }
+};
+template <> struct Staged4<__half> {
+    static __device__ __forceinline__ void ld4(const __half *p, float inv, float o[4]) {
+        const uint2 u = *(const uint2 *)p;
+        __half2 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        o[0] = fa.x * inv; o[1] = fa.y * inv; o[2] = fb.x * inv; o[3] = fb.y * inv;
+    }
+    static __device__ __forceinline__ float ld1(const __half *p, float inv) {
+        return __half2float(*p) * inv;
+    }
+};
+template <> struct Staged4<__nv_bfloat16> {
+    static __device__ __forceinline__ void ld4(const __nv_bfloat16 *p, float inv, float o[4]) {
+        const uint2 u = *(const uint2 *)p;
+        __nv_bfloat162 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        o[0] = fa.x * inv; o[1] = fa.y * inv; o[2] = fb.x * inv; o[3] = fb.y * inv;
+    }
+    static __device__ __forceinline__ float ld1(const __nv_bfloat16 *p, float inv) {
+        return __bfloat162float(*p) * inv;
+    }
+};
+
+template <typename S>
+__host__ __device__ constexpr int tma_margin() { return 16 / (int)sizeof(S); }
+template <typename S>
+__host__ __device__ constexpr int tma_width() { return LB_TILE_NODES + 2 * tma_margin<S>(); }
+template <typename S>
+__host__ __device__ constexpr size_t tma_stage_bytes() {
+    return 9 * (size_t)tma_width<S>() * sizeof(S);
+}
+template <typename S, int TILES>
+__host__ __device__ constexpr size_t tma_smem_bytes() {
+    return TILES * (tma_stage_bytes<S>() + 16);
+}
+
+// Thread 0: the bulk copies of one tile's nine source ranges into a stage,
+// completing on its mbarrier (phase 0).
+template <typename S>
+__device__ __forceinline__ void tma_issue(const BatchDev &b, int flip, int tile, S *stg,
+                                          uint64_t *bar) {
+    constexpr int H = tma_margin<S>(), W = tma_width<S>();
+    constexpr int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
+    const int nx = s.nx, N = nx * s.ny;
+    const S *src = (const S *)s.pop[*s.cur ^ flip];
+    const int k0 = (tile - s.tile0) * LB_TILE_NODES;
+    // plane i of node k comes from node k - EY[i] nx - EX[i]: stage nodes
+    // [k0 - EY[i] nx - H, + W), clipped to the lattice (the clipped part is
+    // only ever needed by wall-row groups, which pull from global memory)
+    int lo[9], bytes[9];
+    unsigned total = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int g0 = k0 - EY[i] * nx - H;
+        const int a = max(g0, 0), e = min(g0 + W, N);
+        lo[i] = a;
+        bytes[i] = e > a ? (e - a) * (int)sizeof(S) : 0;
+        total += (unsigned)bytes[i];
+    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(total) : "memory");
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (!bytes[i]) continue;
+        const int g0 = k0 - EY[i] * nx - H;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+            ::"r"(smem_addr(stg + i * W + (lo[i] - g0))), "l"(src + (size_t)i * N + lo[i]),
+              "r"(bytes[i]), "r"(smem_addr(bar))
+            : "memory");
+    }
+}
+
+// One tile from its stage (every thread: one group of four nodes).  Returns
+// false if the stage's copies did not complete within the bounded wait.
+template <typename S, typename R>
+__device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, int tile,
+                                         const S *stg, const uint64_t *bar) {
+    constexpr int H = tma_margin<S>(), W = tma_width<S>();
+    constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
+    const int nx = s.nx, ny = s.ny, N = nx * ny;
+    if (!dry && tile == s.tile0 && threadIdx.x == 0) *s.step += 1;
+    const int cur = *s.cur ^ flip;
+    const S *__restrict__ src = (const S *)s.pop[cur];
+    S *__restrict__ dst = (S *)s.pop[cur ^ 1];
+    const int k0 = (tile - s.tile0) * LB_TILE_NODES;
+    // this thread's group of four nodes (decided while the copies run)
+    const int kt = k0 + 4 * (int)threadIdx.x;
+    const int y = kt / nx, x0 = kt - y * nx;
+    unsigned keep = kt < N ? 0xFu : 0u;
+    if (s.np && keep) keep = outside_near_boxes4(s, b.parts, cur, x0, y);
+    const bool wall = y == 0 || y == ny - 1;
+    const bool global_pull = wall || x0 == 0 || x0 + 4 == nx;
+    R d[4][9];
+    if (keep && global_pull) {
+        if (wall) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pull_node<S, R, true>(s, src, x0 + j, y, d[j]);
+        } else {
+            pull_group<S, R, true>(s, src, x0, y, d);
+        }
+    }
+    if (!mbar_wait0(bar, 1 << 16)) {
+        if (threadIdx.x == 0) atomicOr(s.err, ERR_TIMEOUT);
+        return false;
+    }
+    if (!keep) return true;
+    if (!global_pull) {
+        const float inv = s.inv_scale;
+        const int j0 = kt - k0 + H;                 // staged index of node kt (no x shift)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const S *p = stg + i * W + j0;          // nodes kt .. kt + 3 of plane i's source row
+            R v[4];
+            Staged4<S>::ld4(p, inv, v);
+            if (EX[i] == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) d[j][i] = v[j];
+            } else if (EX[i] > 0) {                 // pulls from x - 1
+                d[0][i] = Staged4<S>::ld1(p - 1, inv);
+#pragma unroll
+                for (int j = 1; j < 4; ++j) d[j][i] = v[j - 1];
+            } else {                                // pulls from x + 1
+#pragma unroll
+                for (int j = 0; j < 3; ++j) d[j][i] = v[j + 1];
+                d[3][i] = Staged4<S>::ld1(p + 4, inv);
+            }
+        }
+    }
+    const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) collide_node<R>(s, d[j], gx, gy);
+    if (keep == 0xFu && sizeof(S) == 2 && s.sround) {
+        unsigned h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = dither_word(kt + j, (float)d[j][0]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
+            const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
+                                   dither_plane(h[2], i), dither_plane(h[3], i)};
+            Vec4<S, true>::st_r(dst + (size_t)i * N + kt, o, s.scale, r);
+        }
+    } else if (keep == 0xFu) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
+            Vec4<S, true>::st(dst + (size_t)i * N + kt, o, s.scale);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (keep & (1u << j)) store_node<S, R, true>(s, dst, N, kt + j, d[j]);
+    }
+    return true;
+}
+
+// TILES consecutive tiles per CTA, each in its own stage: the copies of all
+// of them are issued at once, so the later tiles' data arrive while the first
+// is computed.
+template <typename S, typename R, int MINB, int TILES>
+__global__ void __launch_bounds__(256, MINB) lattice_tma_kernel(BatchDev b, int flip) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const bool dry = (flip & 2) != 0;
+    flip &= 1;
+    auto stage = [&](int t) { return (S *)(smem_raw + t * (tma_stage_bytes<S>() + 16)); };
+    auto barrier = [&](int t) {
+        return (uint64_t *)(smem_raw + t * (tma_stage_bytes<S>() + 16) + tma_stage_bytes<S>());
+    };
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < TILES; ++t)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(barrier(t))) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int first = blockIdx.x * TILES;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < TILES; ++t)
+            if (first + t < b.total_tiles) tma_issue<S>(b, flip, first + t, stage(t), barrier(t));
+    }
+#pragma unroll
+    for (int t = 0; t < TILES; ++t) {
+        if (first + t >= b.total_tiles) break;
+        if (!tma_tile<S, R>(b, flip, dry, first + t, stage(t), barrier(t))) {
+            // copies that did not complete in time: one more bounded wait on
+            // each stage still in flight (they write this CTA's shared
+            // memory), then leave the remaining tiles
+            for (int u = t; u < TILES && first + u < b.total_tiles; ++u) mbar_wait0(barrier(u), 1 << 16);
+            return;
+        }
+    }
+}
+
 template <typename S, typename R>
 __global__ void fields_kernel(SimDev s, ParticleDev *const *parts, double *rho_o, double *ux_o,
                               double *uy_o) {
@@ -426,7 +670,22 @@ template <typename S, typename R, bool BULK>
 cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_t st) {
     constexpr bool TUNED = BULK && sizeof(S) <= 4;
     if (!TUNED) variant = 0;
+    if (variant >= 4 && !b.tma_ok) variant = 1;     // lattices unsuited to staging
     switch (variant) {
+        case 4:
+            if constexpr (TUNED) {
+                lattice_tma_kernel<S, R, 4, 1>
+                    <<<b.total_tiles, 256, tma_smem_bytes<S, 1>(), st>>>(b, flip);
+                break;
+            }
+            [[fallthrough]];
+        case 5:
+            if constexpr (TUNED) {
+                lattice_tma_kernel<S, R, 3, 2>
+                    <<<(b.total_tiles + 1) / 2, 256, tma_smem_bytes<S, 2>(), st>>>(b, flip);
+                break;
+            }
+            [[fallthrough]];
         case 1:
             if constexpr (TUNED) {
                 lattice_kernel<S, R, BULK, 256, 1, 4><<<b.total_tiles, 256, 0, st>>>(b, flip);
@@ -449,6 +708,18 @@ cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_
             lattice_kernel<S, R, BULK, 256, 1, 1><<<b.total_tiles, 256, 0, st>>>(b, flip);
     }
     return cudaGetLastError();
+}
+
+cudaError_t lattice_kernel_setup(int kind) {
+    return by_kind(kind, [&](auto sv, auto rv) -> cudaError_t {
+        using S = decltype(sv);
+        using R = decltype(rv);
+        if constexpr (sizeof(S) <= 4)
+            return cudaFuncSetAttribute(lattice_tma_kernel<S, R, 3, 2>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tma_smem_bytes<S, 2>());
+        return cudaSuccess;
+    });
 }
 
 cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st,

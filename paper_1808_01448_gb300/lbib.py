@@ -16,6 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "liblbib.so")
+LATTICE_VARIANTS = 6        # LBIB_LATTICE_VARIANTS of include/lbib.h
 
 WALL = {"zou_he": 0, "bounce_back": 1, "periodic": 2}
 STORAGE = {"f32": 0, "f64": 1, "f16": 2, "bf16": 3}
@@ -331,7 +332,7 @@ class Batch:
         changing its state) and keep the fastest; returns (variant, ms per
         variant)."""
         v = C.c_int32()
-        ms = (C.c_double * 4)()
+        ms = (C.c_double * LATTICE_VARIANTS)()
         _check(lib().lbib_batch_autotune(self._h, int(reps), C.byref(v), ms))
         return v.value, list(ms)
 

@@ -83,7 +83,7 @@ def test_lattice_variants_give_identical_bits(L, storage):
     (timing runs of each variant) leaves the simulations unchanged."""
     sweep = W.design_sweep()[:5]
     runs = []
-    for v in range(4):
+    for v in range(L.LATTICE_VARIANTS):
         sims = [make(L, c, p, storage) for c, p in sweep]
         b = L.Batch(sims)
         b.step(3)
@@ -91,7 +91,7 @@ def test_lattice_variants_give_identical_bits(L, storage):
             before = [s.populations() for s in sims]
             steps = [s.step_count for s in sims]
             best, ms = b.autotune(3)
-            assert 0 <= best < 4 and all(m > 0 for m in ms)
+            assert 0 <= best < L.LATTICE_VARIANTS and all(m > 0 for m in ms)
             for s, f, n in zip(sims, before, steps):
                 np.testing.assert_array_equal(s.populations(), f)
                 assert s.step_count == n
