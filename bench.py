@@ -1,19 +1,22 @@
 """Throughput of the LB-IB-MLS adhesion step on GB300 (one JSON line).
 
-Workload (default): single elliptical particle, aspect ratio 2 and 3
-(equal area to a circle of radius 20), channel 1024 x 256 D2Q9, Re in
-{0.01, 0.1, 1.0}, ligand density 0.7, bond strength 2, FP32 populations
-with FP64 MLS solves and rigid-body update: six independent simulations
-stepped together (one lattice kernel and one particle kernel per step).
-A "step" is one time step of all six.  The working set (6 x 2 x 9.4 MB of
-populations) is larger than L2, so no flush is needed between steps.
+Workload (default): the batched design sweep, 72 independent channels
+(shape circle / ellipse AR2 / AR3 x ligand density {0.3, 0.5, 0.7, 0.9} x
+bond strength {1, 2} x Re {0.01, 0.1, 1.0}), lattices drawn from 256 x 64 to
+1024 x 256 (7.43 M nodes in all), one particle each, FP32 populations with
+FP64 MLS solves and rigid-body update, all stepped together (per step one
+bulk lattice launch, one near-box launch and one particle launch, replayed
+from CUDA graphs).  A "step" is one time step of all 72.  The inputs are
+larger than L2: 535 MB of FP32 populations (two buffers) against a 129 MiB
+L2, 268 MB in FP16 / BF16, so no flush is needed between steps.
 
 Metric: aggregate MLUPS = sum(nx * ny) * steps / time, with the fraction of
 the HBM roofline at 72 B per FP32 lattice update.  Under torchrun every rank
-runs the same six simulations on its own GPU (independent replicas, no
+runs the same 72 simulations on its own GPU (independent replicas, no
 collective on the data path); value is the total over ranks.
 
---impl reference times the FP64 CPU oracle on the same workload.
+--impl reference times the FP64 CPU oracle on a sample of the same
+workload.
 """
 from __future__ import annotations
 
@@ -32,8 +35,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_UPDATE = {"f32": 72, "f64": 144, "f16": 36, "bf16": 36}
-WORKLOAD = ("single ellipse AR2/AR3 x Re{0.01,0.1,1}, 1024x256 D2Q9, ligand 0.7, sigma 2, "
-            "6 sims batched")
+WORKLOAD = ("batched design sweep: 72 sims (circle/AR2/AR3 x ligand {0.3,0.5,0.7,0.9} x "
+            "sigma {1,2} x Re {0.01,0.1,1}), lattices 256x64..1024x256, 7.43 M nodes, "
+            "one particle each")
 
 
 def env_int(k, d):
@@ -124,7 +128,7 @@ class ClockSampler:
 
 def build_workload(L, W, storage, stream, allocator, rounding="stochastic"):
     sims = []
-    for cfg, parts in W.single_ellipse_sweep():
+    for cfg, parts in W.design_sweep():
         s = L.Sim(storage=storage, stream=stream, allocator=allocator, rounding=rounding, **cfg)
         for p in parts:
             s.add_particle(**p)
@@ -139,7 +143,7 @@ def _oracle_worker(args):
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
     from paper_1808_01448_gb300 import workloads as W
-    cfg, parts = W.single_ellipse_sweep()[idx]
+    cfg, parts = W.design_sweep()[idx]
     s = O.OracleSim(**cfg)
     for p in parts:
         s.add_particle(**p)
@@ -150,34 +154,38 @@ def _oracle_worker(args):
     return cfg["nx"] * cfg["ny"] * steps, dt
 
 
-def cpu_baseline(steps_per_sim, nsims=6):
+def cpu_baseline(steps_per_sim, nsims=12):
     """The oracle as it stands (single-threaded C, FP64), one process per
-    simulation of the workload, started with spawn."""
+    simulation of an evenly spaced sample of the workload's 72, started with
+    spawn; the rate is the sample's node updates over the slowest process's
+    time."""
     from oracle import oracle as O
     O.build()
     cores = min(nsims, os.cpu_count() or 1)
+    pick = [round(i * 72 / nsims) for i in range(nsims)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_worker, [(i, steps_per_sim) for i in range(nsims)])
+        res = pool.map(_oracle_worker, [(i, steps_per_sim) for i in pick])
     wall = time.perf_counter() - t0
     updates = sum(r[0] for r in res)
-    busy = max(r[1] for r in res)
+    busy = max(r[1] for r in res) if cores >= nsims else sum(r[1] for r in res) / cores
     return {"value": updates / busy / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{nsims} sims x {steps_per_sim} steps of the 1024x256 workload, "
+            "sample": f"{nsims} of the 72 sims (every {72 // nsims}th) x {steps_per_sim} steps, "
                       f"{cores} processes (wall {wall:.1f} s incl. setup)"}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on the workload, K timed steps of
-    the six simulations (one worker process each)."""
+    """Reference arm: the FP64 CPU oracle on a sample of the workload (12 of
+    the 72 simulations, one worker process each), K timed steps or as many as
+    fit in a few minutes."""
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
     from oracle import oracle as O
     O.build()
     # bounded sample: cap the oracle work so that K steps end within minutes
-    per_step_s = 0.06
+    per_step_s = 0.06               # the largest sim (1024 x 256) per oracle step
     cap = max(1, int(150.0 / per_step_s))
     k_run = min(args.steps, cap)
     base = cpu_baseline(k_run + args.warmup * 0)
@@ -185,7 +193,7 @@ def run_reference(args):
         "metric": "aggregate MLUPS + % HBM roofline (FP32 vs FP16-storage), p50/p99 sim latency",
         "impl": "reference", "value": base["value"], "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 6 * 1024 * 256 / (base["value"] * 1e6) * 1e3,
+        "ms_per_step": 7432960 / (base["value"] * 1e6) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "storage": "f64 (oracle)"},
         "cpu_baseline": base,
@@ -326,14 +334,17 @@ def run_gpu(args):
     e2e = None
     if rank == 0 or world > 1:
         e2e_sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc)
-        f0 = torch.empty((9, 256, 1024), dtype=torch.float64).pin_memory()
-        f0.copy_(torch.tensor([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4,
-                              dtype=torch.float64)[:, None, None].expand(9, 256, 1024))
-        f0_np = f0.numpy()
+        w9 = torch.tensor([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, dtype=torch.float64)
+        f0 = {}                     # pinned initial populations, one per lattice shape
+        for s in e2e_sims:
+            if (s.ny, s.nx) not in f0:
+                t = torch.empty((9, s.ny, s.nx), dtype=torch.float64).pin_memory()
+                t.copy_(w9[:, None, None].expand(9, s.ny, s.nx))
+                f0[(s.ny, s.nx)] = t.numpy()
         barrier()
         t0 = time.perf_counter()
         for s in e2e_sims:
-            s.set_populations(f0_np)
+            s.set_populations(f0[(s.ny, s.nx)])
         eb = lbib.Batch(e2e_sims)
         chunk, done, d2h = 100, 0, 0
         while done < args.steps:
@@ -364,6 +375,7 @@ def run_gpu(args):
 
     if rank == 0:
         bpu = BYTES_PER_UPDATE[args.storage]
+        l2_mib = torch.cuda.get_device_properties(local).L2_cache_size / 2**20
         lat_ms = kt["lattice_ms"]
         # algorithmic bytes of one bulk-pass launch: the nodes it updates
         achieved = pn["bulk"] * bpu / (lat_ms * 1e-3) / 1e9 if lat_ms > 0 else None
@@ -374,8 +386,11 @@ def run_gpu(args):
             "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": 1024, "ny": 256, "sims": len(sims),
-                       "storage": args.storage, "l2": "working set 226 MB > L2, no flush",
+            "config": {"workload": WORKLOAD, "lattices": "256x64..1024x256", "nodes": nodes,
+                       "sims": len(sims),
+                       "storage": args.storage,
+                       "l2": (f"inputs larger than L2, no flush: {nodes * bpu / 1e6:.0f} MB of "
+                              f"populations (two buffers) vs {l2_mib:.0f} MiB L2"),
                        "parallelism": f"replicas x{world}"},
             "hbm_roofline_frac_of_step": value * 1e6 * bpu / (peak * 1e9) / world,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -218,6 +218,22 @@ lbib_status lbib_batch_destroy(lbib_batch *b);
  * overlapped).  It synchronises the stream. */
 lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples);
 lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count);
+/* Benchmark form of lbib_batch_step: advances the batch nsteps steps with
+ * the same results, with the L2 cache flushed before every step, and times
+ * the steps alone.  Before each step the library overwrites the caller's
+ * device buffer `flush` (flush_bytes bytes; 16-byte aligned, a multiple of
+ * 16 bytes and at least the device's L2 size, else LBIB_E_ARG) and, when
+ * clean = 1, reads it back, so that the step starts with none of its inputs
+ * in L2 and (clean = 1) no dirty line to write back.  The buffer's contents
+ * are destroyed.  Steps run as graphs of up to 32 steps, each step joined
+ * before the next flush (no overlap between steps).  If ms is not NULL it
+ * receives, summed over the steps, the device time (CUDA events) of
+ * [0] each step from the end of its flush to the end of its last kernel,
+ * [1] its bulk lattice pass, [2] its flush, [3] its near-box and particle
+ * passes (the particle pass alone when not overlapped): ms[4].  Synchronises
+ * the stream after every graph. */
+lbib_status lbib_batch_step_flushed(lbib_batch *b, int64_t nsteps, void *flush,
+                                    size_t flush_bytes, int32_t clean, double *ms);
 /* Kernel variants of the lattice pass (the bulk pass when particle work is
  * overlapped), all on the same 1024-node tiles: 0 = 256 threads x one
  * group of four nodes; 1 = the same, at most 64 registers (four CTAs per

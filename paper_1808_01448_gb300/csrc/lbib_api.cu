@@ -45,6 +45,35 @@ lbib_status cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);             \
     } while (0)
 
+// L2 clearing before a timed step: writing a buffer larger than L2 evicts
+// every line the step could reuse; reading it back then replaces the dirty
+// lines of the write with clean ones.
+__global__ void __launch_bounds__(512) l2_fill_kernel(uint4 *buf, size_t n, unsigned v) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        buf[i] = make_uint4(v, v + 1, v + 2, v + 3);
+}
+
+__global__ void __launch_bounds__(512) l2_read_kernel(uint4 *buf, size_t n, unsigned v) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    unsigned acc = 0;
+    for (size_t i = i0; i < n; i += stride) {
+        const uint4 q = buf[i];
+        acc |= (q.x ^ v) | (q.y ^ (v + 1)) | (q.z ^ (v + 2)) | (q.w ^ (v + 3));
+    }
+    if (acc && i0 < n) buf[i0].x = acc;     // never taken; keeps the loads
+}
+
+cudaError_t launch_l2_flush(void *buf, size_t bytes, bool clean, unsigned tag, cudaStream_t st) {
+    const size_t n = bytes / sizeof(uint4);
+    const int grid = (int)std::min<size_t>((n + 511) / 512, 4096);
+    const unsigned v = 0x5a5a0000u ^ (tag << 2);
+    l2_fill_kernel<<<grid, 512, 0, st>>>((uint4 *)buf, n, v);
+    if (clean) l2_read_kernel<<<grid, 512, 0, st>>>((uint4 *)buf, n, v);
+    return cudaGetLastError();
+}
+
 size_t compute_size(int kind) { return kind == ST_F64 ? 8 : 4; }
 size_t storage_size(int kind) {
     switch (kind) {
@@ -120,6 +149,13 @@ struct lbib_batch {
     cudaStream_t s1 = nullptr, s2 = nullptr;
     cudaEvent_t evb[2] = {nullptr, nullptr}, evn[2] = {nullptr, nullptr};
     cudaEvent_t evfork = nullptr, evjoin = nullptr, evjoin1 = nullptr;
+    // flushed stepping: a graph of GRAPH_STEPS steps, each after an L2 flush
+    // of fbuf, with FEV events per step
+    cudaGraphExec_t fgraph = nullptr;
+    void *fbuf = nullptr;
+    size_t fbytes = 0;
+    int fclean = -1;
+    std::vector<cudaEvent_t> fev;
 };
 
 namespace {
@@ -406,6 +442,8 @@ void free_batch(lbib_batch *b) {
     for (auto g : b->tgraphs)
         if (g) cudaGraphExecDestroy(g);
     for (auto e : b->ev) cudaEventDestroy(e);
+    if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
+    for (auto e : b->fev) cudaEventDestroy(e);
     if (b->d_block) dfree(b->acfg, b->orphan ? nullptr : b->stream, b->d_block);
     delete b;
 }
@@ -683,10 +721,67 @@ cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
     return e;
 }
 
-lbib_status capture(lbib_batch *b, cudaEvent_t *ev, cudaGraphExec_t *out) {
+// Events per step of flushed stepping: flush start, step start, bulk-pass
+// start and end, step end, near-pass start, particle-pass end.
+constexpr int FEV = 7;
+
+// Enqueue nsteps steps (inside a capture only), each after an L2 flush and
+// bracketed by event records ev[FEV * k + ...]; ends with a parity flip when
+// nsteps is odd.  The kernels are those of enqueue_steps; the L2 flush is a
+// join point between steps.
+cudaError_t enqueue_flushed_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
+    const unsigned fl = cudaEventRecordExternal;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nsteps; ++k) {
+        const int f = k & 1;
+        cudaEvent_t *E = ev + FEV * k;
+        if ((e = cudaEventRecordWithFlags(E[0], b->stream, fl)) ||
+            (e = launch_l2_flush(b->fbuf, b->fbytes, b->fclean, (unsigned)k, b->stream)) ||
+            (e = cudaEventRecordWithFlags(E[1], b->stream, fl)))
+            return e;
+        if (!b->overlap) {
+            if ((e = cudaEventRecordWithFlags(E[2], b->stream, fl)) ||
+                (e = launch_lattice(b->kind, b->bd, f, 0, b->stream)) ||
+                (e = cudaEventRecordWithFlags(E[3], b->stream, fl)) ||
+                (e = cudaEventRecordWithFlags(E[5], b->stream, fl)) ||
+                (e = launch_particles(b->kind, b->bd, f ^ 1, 2, b->smem, b->stream)) ||
+                (e = cudaEventRecordWithFlags(E[6], b->stream, fl)))
+                return e;
+        } else {
+            // near pass first; the particle pass follows it as a programmatic
+            // dependent and the bulk pass is released when it ends, so that
+            // the particle pass's CTAs are resident before the bulk pass
+            // fills the SMs (as in the overlapped graph, where both wait on
+            // the near pass)
+            if ((e = cudaEventRecord(b->evfork, b->stream)) ||
+                (e = cudaStreamWaitEvent(b->s1, b->evfork, 0)) ||
+                (e = cudaStreamWaitEvent(b->s2, b->evfork, 0)) ||
+                (e = cudaEventRecordWithFlags(E[5], b->s1, fl)) ||
+                (e = launch_lattice(b->kind, b->bd, f, 2, b->s1)) ||
+                (e = cudaEventRecord(b->evn[0], b->s1)) ||
+                (e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->s1, true)) ||
+                (e = cudaEventRecordWithFlags(E[6], b->s1, fl)) ||
+                (e = cudaEventRecord(b->evjoin1, b->s1)) ||
+                (e = cudaStreamWaitEvent(b->s2, b->evn[0], 0)) ||
+                (e = cudaEventRecordWithFlags(E[2], b->s2, fl)) ||
+                (e = launch_lattice(b->kind, b->bd, f, 1, b->s2)) ||
+                (e = cudaEventRecordWithFlags(E[3], b->s2, fl)) ||
+                (e = cudaEventRecord(b->evjoin, b->s2)) ||
+                (e = cudaStreamWaitEvent(b->stream, b->evjoin, 0)) ||
+                (e = cudaStreamWaitEvent(b->stream, b->evjoin1, 0)))
+                return e;
+        }
+        if ((e = cudaEventRecordWithFlags(E[4], b->stream, fl))) return e;
+    }
+    if (nsteps & 1) e = launch_flip(b->d_curs, (int)b->sims.size(), b->stream);
+    return e;
+}
+
+template <class Enqueue>
+lbib_status capture_with(lbib_batch *b, Enqueue &&enqueue, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_steps(b, GRAPH_STEPS, ev);
+    cudaError_t e = enqueue();
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -698,6 +793,10 @@ lbib_status capture(lbib_batch *b, cudaEvent_t *ev, cudaGraphExec_t *out) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     return LBIB_OK;
+}
+
+lbib_status capture(lbib_batch *b, cudaEvent_t *ev, cudaGraphExec_t *out) {
+    return capture_with(b, [&] { return enqueue_steps(b, GRAPH_STEPS, ev); }, out);
 }
 
 lbib_status batch_step_impl(lbib_batch *b, int64_t n) {
@@ -997,6 +1096,71 @@ lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *cou
     return LBIB_OK;
 }
 
+lbib_status lbib_batch_step_flushed(lbib_batch *b, int64_t n, void *flush, size_t flush_bytes,
+                                    int32_t clean, double *ms) {
+    if (!b) return fail(LBIB_E_ARG, "null batch");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
+    if (n < 0) return fail(LBIB_E_ARG, "nsteps must be >= 0");
+    if (!flush || ((uintptr_t)flush & 15) || (flush_bytes & 15))
+        return fail(LBIB_E_ARG, "flush buffer must be 16-byte aligned, a multiple of 16 bytes");
+    if (clean != 0 && clean != 1) return fail(LBIB_E_ARG, "clean must be 0 or 1");
+    int dev = 0, l2 = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    if (flush_bytes < (size_t)l2)
+        return fail(LBIB_E_ARG, "flush buffer of %zu bytes is smaller than L2 (%d bytes)",
+                    flush_bytes, l2);
+    double acc[4] = {0, 0, 0, 0};
+    if (ms) ms[0] = ms[1] = ms[2] = ms[3] = 0;
+    if (n == 0) return LBIB_OK;
+    for (lbib_sim *s : b->sims) {
+        lbib_status r = prime(s, b->stream);
+        if (r != LBIB_OK) return r;
+    }
+    if (b->fev.empty()) {
+        b->fev.assign(FEV * GRAPH_STEPS, nullptr);
+        for (auto &e : b->fev) CK(cudaEventCreate(&e));
+    }
+    if (b->fgraph && (b->fbuf != flush || b->fbytes != flush_bytes || b->fclean != clean)) {
+        CK(cudaStreamSynchronize(b->stream));
+        cudaGraphExecDestroy(b->fgraph);
+        b->fgraph = nullptr;
+    }
+    b->fbuf = flush;
+    b->fbytes = flush_bytes;
+    b->fclean = clean;
+    for (int64_t done = 0; done < n;) {
+        const int m = (int)std::min<int64_t>(n - done, GRAPH_STEPS);
+        cudaGraphExec_t g = b->fgraph, tmp = nullptr;
+        auto enq = [&] { return enqueue_flushed_steps(b, m, b->fev.data()); };
+        lbib_status r = LBIB_OK;
+        if (m < GRAPH_STEPS) r = capture_with(b, enq, &tmp), g = tmp;
+        else if (!g) r = capture_with(b, enq, &b->fgraph), g = b->fgraph;
+        if (r != LBIB_OK) return r;
+        cudaError_t e = cudaGraphLaunch(g, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (tmp) cudaGraphExecDestroy(tmp);
+        if (e != cudaSuccess) return cuda_fail(e, "flushed steps");
+        for (lbib_sim *s : b->sims) {
+            s->step += m;
+            s->cur ^= m & 1;
+        }
+        for (int k = 0; k < m; ++k) {
+            const cudaEvent_t *E = &b->fev[FEV * k];
+            float t[4] = {0, 0, 0, 0};
+            CK(cudaEventElapsedTime(&t[0], E[1], E[4]));
+            CK(cudaEventElapsedTime(&t[1], E[2], E[3]));
+            CK(cudaEventElapsedTime(&t[2], E[0], E[1]));
+            CK(cudaEventElapsedTime(&t[3], E[5], E[6]));
+            for (int j = 0; j < 4; ++j) acc[j] += t[j];
+        }
+        done += m;
+    }
+    if (ms)
+        for (int j = 0; j < 4; ++j) ms[j] = acc[j];
+    return LBIB_OK;
+}
+
 // Captured graphs hold the kernel variant; a change of variant drops them.
 static lbib_status use_variant(lbib_batch *b, int variant) {
     if (b->bd.lat_variant == variant) return LBIB_OK;
@@ -1004,6 +1168,8 @@ static lbib_status use_variant(lbib_batch *b, int variant) {
     b->bd.lat_variant = variant;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
+    b->fgraph = nullptr;
     if (b->nsamples > 0) return lbib_batch_set_timing(b, b->nsamples);
     return LBIB_OK;
 }

@@ -110,6 +110,7 @@ def lib():
                 "lbib_batch_set_timing": [vp, i32],
                 "lbib_batch_kernel_times": [vp, pd, C.POINTER(i64)],
                 "lbib_batch_pass_nodes": [vp, C.POINTER(i64)],
+                "lbib_batch_step_flushed": [vp, i64, vp, C.c_size_t, i32, pd],
                 "lbib_batch_autotune": [vp, i32, C.POINTER(i32), pd],
                 "lbib_batch_set_variant": [vp, i32],
                 "lbib_synchronize": [vp],
@@ -312,6 +313,17 @@ class Batch:
 
     def step(self, n=1):
         _check(lib().lbib_batch_step(self._h, int(n)))
+
+    def step_flushed(self, n, flush_ptr, flush_bytes, clean=True):
+        """Step n times with the L2 flushed (device buffer at ``flush_ptr``
+        overwritten, and read back when ``clean``) before every step; returns
+        the summed device ms of the steps, their bulk lattice passes and the
+        flushes, and of the near-box plus particle passes
+        (``lbib_batch_step_flushed``)."""
+        ms = (C.c_double * 4)()
+        _check(lib().lbib_batch_step_flushed(self._h, int(n), C.c_void_p(int(flush_ptr)),
+                                             int(flush_bytes), 1 if clean else 0, ms))
+        return {"step_ms": ms[0], "bulk_ms": ms[1], "flush_ms": ms[2], "chain_ms": ms[3]}
 
     def set_timing(self, nsamples):
         _check(lib().lbib_batch_set_timing(self._h, int(nsamples)))

@@ -105,3 +105,35 @@ def test_lattice_variants_give_identical_bits(L, storage):
         for (fa, pa), (fb, pb) in zip(runs[0], other):
             np.testing.assert_array_equal(fa, fb)
             assert pa == pb
+
+
+@pytest.mark.parametrize("clean", [False, True])
+def test_flushed_steps_equal_plain_steps(L, clean):
+    """Stepping with an L2 flush before every step (the cold-L2 timing form)
+    gives the same bits as plain stepping, over a full graph and an odd
+    remainder, and reports positive step, bulk-pass and flush times."""
+    import torch
+    sweep = W.design_sweep()[:4]
+    plain = [make(L, c, p) for c, p in sweep]
+    flushed = [make(L, c, p) for c, p in sweep]
+    bp, bf = L.Batch(plain), L.Batch(flushed)
+    bp.step(37)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    buf = torch.empty(2 * l2 + 4096, dtype=torch.uint8, device="cuda")
+    t = bf.step_flushed(37, buf.data_ptr(), buf.numel(), clean)
+    assert t["step_ms"] > 0 and t["bulk_ms"] > 0 and t["flush_ms"] > 0
+    assert t["bulk_ms"] <= t["step_ms"]
+    for a, b in zip(plain, flushed):
+        assert a.step_count == b.step_count == 37
+        np.testing.assert_array_equal(a.populations(), b.populations())
+        assert a.particle(0) == b.particle(0)
+    with pytest.raises(L.LbibError):
+        bf.step_flushed(1, buf.data_ptr(), 1 << 20, clean)     # smaller than L2
+    bf.step(5)
+    bp.step(5)
+    for a, b in zip(plain, flushed):
+        np.testing.assert_array_equal(a.populations(), b.populations())
+    bp.close()
+    bf.close()
+    for s in plain + flushed:
+        s.close()
