@@ -21,17 +21,30 @@ __device__ __forceinline__ R recip(R x) {
 
 // BGK collision with the Guo source (Eq. 1, 2, 4-6) of one node, in
 // deviation form: d holds the pre-collision deviations on entry and the
-// post-collision ones on return.
-template <typename R>
+// post-collision ones on return.  SC: d holds the deviations times the
+// storage scale (16-bit storage, as loaded and stored without conversion):
+// the three moments are scaled down, and omega and the Guo prefactor, which
+// enter only the terms added to d, are scaled up once per thread, instead
+// of nine multiplications on load and nine on store.  The scale is a power
+// of two (unless the caller set another), so every rounding is the same as
+// in the unscaled form.
+template <typename R, bool SC = false>
 __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy) {
     R drho, jx, jy;
     node_moments(d, drho, jx, jy);
+    if constexpr (SC) {
+        const R inv = s.inv_scale;
+        drho *= inv;
+        jx *= inv;
+        jy *= inv;
+    }
     const R rho = (R)1 + drho;
     const R irho = recip(rho);
     const R ux = (jx + (R)0.5 * Fx) * irho;
     const R uy = (jy + (R)0.5 * Fy) * irho;
     const R om = pick<R>(s.f_om, s.d_om);
-    const R pref = pick<R>(s.f_pref, s.d_pref);
+    const R pref0 = pick<R>(s.f_pref, s.d_pref);
+    const R oms = SC ? om * (R)s.scale : om, pref = SC ? pref0 * (R)s.scale : pref0;
     // f^eq_i - w_i = w_i [A + 3 rho e.u + 4.5 rho (e.u)^2], A = (rho - 1) - 1.5 rho u.u
     // Guo: S_i = (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
     // Post-collision d_i (1 - om) + om (f^eq_i - w_i) + S_i, evaluated per pair
@@ -40,8 +53,8 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
     // and an odd part 3 w (om rho (e.u) + pref (e.F)).
     const R A = drho - (R)1.5 * rho * (ux * ux + uy * uy);
     const R uF = ux * Fx + uy * Fy;
-    const R c = (R)1 - om, orho = om * rho, p2 = (R)2 * pref;
-    const R base = om * A - (R)3 * pref * uF;
+    const R c = (R)1 - om, orho = oms * rho, p2 = (R)2 * pref;
+    const R base = oms * A - (R)3 * pref * uF;
     d[0] = c * d[0] + (R)(4.0 / 9.0) * base;
     auto pair = [&](int i, int j, R w, R eu, R eF) {
         const R even = w * (base + (R)4.5 * eu * (orho * eu + p2 * eF));
@@ -57,20 +70,23 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
     if (!(fabs(drho) < (R)1) || !(fabs(ux) + fabs(uy) < (R)10)) atomicOr(s.err, ERR_UNSTABLE);
 }
 
-template <typename S, typename R, bool STREAM = false>
+// SC: d is scaled (see collide_node); the dither hash takes the unscaled
+// first deviation either way.
+template <typename S, typename R, bool STREAM = false, bool SC = false>
 __device__ __forceinline__ void store_node(const SimDev &s, S *__restrict__ dst, int N, int k,
                                            const R d[9]) {
+    const float sc = SC ? 1.f : s.scale;
     if (sizeof(S) == 2 && s.sround) {
-        const unsigned h = dither_word(k, (float)d[0]);
+        const unsigned h = dither_word(k, SC ? (float)d[0] * s.inv_scale : (float)d[0]);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            Store<S>::template st_r<STREAM>(dst, i * N + k, d[i], s.scale, dither_plane(h, i));
+            Store<S>::template st_r<STREAM>(dst, i * N + k, d[i], sc, dither_plane(h, i));
         return;
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        if constexpr (STREAM) Store<S>::st_cs(dst, i * N + k, d[i], s.scale);
-        else Store<S>::st(dst, i * N + k, d[i], s.scale);
+        if constexpr (STREAM) Store<S>::st_cs(dst, i * N + k, d[i], sc);
+        else Store<S>::st(dst, i * N + k, d[i], sc);
     }
 }
 
@@ -87,9 +103,8 @@ __device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ d
 // from the next group (x periodic).  Same values as pull_node per node.
 template <typename S, typename R, bool STREAM>
 __device__ __forceinline__ void pull_group(const SimDev &s, const S *__restrict__ src, int x0,
-                                           int y, R (*d)[9]) {
+                                           int y, R (*d)[9], float inv) {
     const int nx = s.nx, ny = s.ny, N = nx * ny;
-    const float inv = s.inv_scale;
     const int ym = y == 0 ? ny - 1 : y - 1;
     const int yp = y == ny - 1 ? 0 : y + 1;
     const int r0 = y * nx, rm = ym * nx, rp = yp * nx;
@@ -196,6 +211,8 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
     R d[NPT][9];
     if (s.vec4) {
+        // 16-bit storage: groups collide in the scaled form (collide_node)
+        constexpr bool SC = sizeof(S) == 2;
         const int kt = (tile - s.tile0) * LB_TILE_NODES + 4 * (int)threadIdx.x;
         int kg[GROUPS], yg[GROUPS], xg[GROUPS];
         unsigned keep[GROUPS];
@@ -213,9 +230,15 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             const int y = yg[g];
             if (s.wall_b != LBIB_WALL_PERIODIC && (y == 0 || y == s.ny - 1)) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) pull_node<S, R, BULK>(s, src, xg[g] + j, y, d[4 * g + j]);
+                for (int j = 0; j < 4; ++j) {
+                    pull_node<S, R, BULK>(s, src, xg[g] + j, y, d[4 * g + j]);
+                    if constexpr (SC) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) d[4 * g + j][i] *= s.scale;
+                    }
+                }
             } else {
-                pull_group<S, R, BULK>(s, src, xg[g], y, &d[4 * g]);
+                pull_group<S, R, BULK>(s, src, xg[g], y, &d[4 * g], SC ? 1.f : s.inv_scale);
             }
         }
 #pragma unroll
@@ -226,29 +249,33 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             for (int j = 0; j < 4; ++j) {
                 R Fx = gx, Fy = gy;
                 if (!BULK && s.np) tile_force<R>(s, b.parts, xg[g] + j, yg[g], Fx, Fy);
-                collide_node<R>(s, d[4 * g + j], Fx, Fy);
+                collide_node<R, SC>(s, d[4 * g + j], Fx, Fy);
             }
+            const float sc = SC ? 1.f : s.scale;
             if (keep[g] == 0xFu && sizeof(S) == 2 && s.sround) {
                 unsigned h[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) h[j] = dither_word(k + j, (float)d[4 * g + j][0]);
+                for (int j = 0; j < 4; ++j)
+                    h[j] = dither_word(k + j, SC ? (float)d[4 * g + j][0] * s.inv_scale
+                                                 : (float)d[4 * g + j][0]);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
                     const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
                                            dither_plane(h[2], i), dither_plane(h[3], i)};
-                    Vec4<S, BULK>::st_r(dst + i * N + k, o, s.scale, r);
+                    Vec4<S, BULK>::st_r(dst + i * N + k, o, sc, r);
                 }
             } else if (keep[g] == 0xFu) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
-                    Vec4<S, BULK>::st(dst + i * N + k, o, s.scale);
+                    Vec4<S, BULK>::st(dst + i * N + k, o, sc);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (keep[g] & (1u << j)) store_node<S, R, BULK>(s, dst, N, k + j, d[4 * g + j]);
+                    if (keep[g] & (1u << j))
+                        store_node<S, R, BULK, SC>(s, dst, N, k + j, d[4 * g + j]);
             }
         }
         return;
@@ -492,13 +519,21 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     if (s.np && keep) keep = outside_near_boxes4(s, b.parts, cur, x0, y);
     const bool wall = y == 0 || y == ny - 1;
     const bool global_pull = wall || x0 == 0 || x0 + 4 == nx;
+    // 16-bit storage: the group collides in the scaled form (collide_node)
+    constexpr bool SC = sizeof(S) == 2;
     R d[4][9];
     if (keep && global_pull) {
         if (wall) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) pull_node<S, R, true>(s, src, x0 + j, y, d[j]);
+            for (int j = 0; j < 4; ++j) {
+                pull_node<S, R, true>(s, src, x0 + j, y, d[j]);
+                if constexpr (SC) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) d[j][i] *= s.scale;
+                }
+            }
         } else {
-            pull_group<S, R, true>(s, src, x0, y, d);
+            pull_group<S, R, true>(s, src, x0, y, d, SC ? 1.f : s.inv_scale);
         }
     }
     if (!mbar_wait0(bar, 1 << 16)) {
@@ -507,7 +542,7 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     }
     if (!keep) return true;
     if (!global_pull) {
-        const float inv = s.inv_scale;
+        const float inv = SC ? 1.f : s.inv_scale;
         const int j0 = kt - k0 + H;                 // staged index of node kt (no x shift)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -530,28 +565,30 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     }
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) collide_node<R>(s, d[j], gx, gy);
+    for (int j = 0; j < 4; ++j) collide_node<R, SC>(s, d[j], gx, gy);
+    const float sc = SC ? 1.f : s.scale;
     if (keep == 0xFu && sizeof(S) == 2 && s.sround) {
         unsigned h[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) h[j] = dither_word(kt + j, (float)d[j][0]);
+        for (int j = 0; j < 4; ++j)
+            h[j] = dither_word(kt + j, SC ? (float)d[j][0] * s.inv_scale : (float)d[j][0]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
             const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
                                    dither_plane(h[2], i), dither_plane(h[3], i)};
-            Vec4<S, true>::st_r(dst + (size_t)i * N + kt, o, s.scale, r);
+            Vec4<S, true>::st_r(dst + (size_t)i * N + kt, o, sc, r);
         }
     } else if (keep == 0xFu) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
-            Vec4<S, true>::st(dst + (size_t)i * N + kt, o, s.scale);
+            Vec4<S, true>::st(dst + (size_t)i * N + kt, o, sc);
         }
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (keep & (1u << j)) store_node<S, R, true>(s, dst, N, kt + j, d[j]);
+            if (keep & (1u << j)) store_node<S, R, true, SC>(s, dst, N, kt + j, d[j]);
     }
     return true;
 }
