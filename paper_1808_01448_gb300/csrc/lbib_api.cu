@@ -181,6 +181,13 @@ SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
     SimDev d{};
     const lbib_config &c = s->cfg;
     d.nx = c.nx; d.ny = c.ny; d.wall_b = c.wall_bottom; d.wall_t = c.wall_top;
+    {
+        int t = 0;
+        while ((1 << t) < c.nx) ++t;
+        const unsigned long long p2 = 1ull << (31 + t);
+        d.nx_m = (unsigned)((p2 + (unsigned long long)c.nx - 1) / (unsigned long long)c.nx);
+        d.nx_s = t - 1;
+    }
     d.p0 = p0; d.np = (int)s->parts.size();
     d.tile0 = tile0;
     d.ntiles = (int)((s->N + LB_TILE_NODES - 1) / LB_TILE_NODES);

@@ -40,6 +40,9 @@ struct SimDev {
     int tile0, ntiles;   // lattice work tiles of this simulation
     int vec4;            // rows in whole groups of four aligned nodes
     int sround;          // 16-bit storage: stochastic rounding of the stores
+    // k / nx = umulhi(k, nx_m) >> nx_s for 0 <= k < 2^31 (div_nx below)
+    unsigned nx_m;
+    int nx_s;
     double tau, u_b, u_t, gx, gy;
     double k_f, k_r0, kBT, sigma_star_ratio, y_cr, y_eq_ratio;
     double hamaker, eps_min, rec_b, rec_t;
@@ -56,6 +59,14 @@ struct SimDev {
     long long *step;          // device: completed steps
     int *err;                 // device: error bits
 };
+
+// Row of node index k: with t = ceil(log2 nx), m = ceil(2^(31+t) / nx) < 2^32
+// and k = q nx + r, k m / 2^(31+t) = q + r / nx + k e / (nx 2^(31+t)) with
+// e = m nx - 2^(31+t) < nx, and the last two terms stay below 1 for k < 2^31,
+// so the shifted high product is exactly q.
+__device__ __forceinline__ int div_nx(const SimDev &s, int k) {
+    return (int)(__umulhi((unsigned)k, s.nx_m) >> s.nx_s);
+}
 
 // Rigid particle, resident in device memory (FP64 state and loads).
 struct ParticleDev {

@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
 #pragma unroll
         for (int g = 0; g < GROUPS; ++g) {
             kg[g] = kt + g * 4 * THREADS;
-            yg[g] = kg[g] / nx;
+            yg[g] = div_nx(s, kg[g]);
             xg[g] = kg[g] - yg[g] * nx;
             keep[g] = kg[g] < N ? 0xFu : 0u;
             if (BULK && s.np && keep[g]) keep[g] = outside_near_boxes4(s, b.parts, cur, xg[g], yg[g]);
@@ -514,7 +514,7 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     const int k0 = (tile - s.tile0) * LB_TILE_NODES;
     // this thread's group of four nodes (decided while the copies run)
     const int kt = k0 + 4 * (int)threadIdx.x;
-    const int y = kt / nx, x0 = kt - y * nx;
+    const int y = div_nx(s, kt), x0 = kt - y * nx;
     unsigned keep = kt < N ? 0xFu : 0u;
     if (s.np && keep) keep = outside_near_boxes4(s, b.parts, cur, x0, y);
     const bool wall = y == 0 || y == ny - 1;
