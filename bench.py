@@ -330,7 +330,7 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers: fresh simulations, the
     # initial populations uploaded from pinned host memory, K steps in chunks
-    # of 100 with the particle states read back to the host after each chunk
+    # of 100 with all particle states read back to the host after each chunk
     e2e = None
     if rank == 0 or world > 1:
         e2e_sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc)
@@ -350,9 +350,8 @@ def run_gpu(args):
         while done < args.steps:
             n = min(chunk, args.steps - done)
             eb.step(n)
-            for s in e2e_sims:
-                s.particles()
-                d2h += 160
+            eb.particles()          # every member's particle states, one readback
+            d2h += eb.last_d2h_bytes
             done += n
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0

@@ -218,6 +218,16 @@ lbib_status lbib_batch_destroy(lbib_batch *b);
  * overlapped).  It synchronises the stream. */
 lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples);
 lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count);
+/* Particle states of every member of the batch, in member order (each
+ * member's particles in pid order), as lbib_read_state gives them: one
+ * gather kernel, one copy to pinned host memory and one synchronisation of
+ * the batch's stream for the whole batch.  out receives up to cap states;
+ * *count (if not NULL) the batch's particle count; *d2h_bytes (if not NULL)
+ * the bytes copied from the device (the particles' device records and one
+ * error word per member).  Reports a member's deferred device error
+ * (E_UNSTABLE, E_TIMEOUT) like lbib_read_state. */
+lbib_status lbib_batch_read_particles(lbib_batch *b, lbib_particle_state *out, int32_t cap,
+                                      int32_t *count, size_t *d2h_bytes);
 /* Benchmark form of lbib_batch_step: advances the batch nsteps steps with
  * the same results, with the L2 cache flushed before every step, and times
  * the steps alone.  Before each step the library overwrites the caller's
@@ -244,7 +254,7 @@ lbib_status lbib_batch_step_flushed(lbib_batch *b, int64_t nsteps, void *flush,
  * while the first is computed).  Variants 4 and 5 need FP32/FP16/BF16 storage, rows of
  * whole 16-byte words and walls that are not periodic in every member (else
  * they run as variant 1).  FP64 storage and the plain (non-overlapped) pass
- * always use variant 0.
+ * always use variant 0.  A new batch starts with variant 1.
  * lbib_batch_autotune runs the lattice pass of each variant `reps` times on
  * the batch's current state (timing runs: they write only the buffer the next
  * step overwrites and leave step counters alone, so the simulation is

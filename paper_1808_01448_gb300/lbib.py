@@ -111,6 +111,8 @@ def lib():
                 "lbib_batch_kernel_times": [vp, pd, C.POINTER(i64)],
                 "lbib_batch_pass_nodes": [vp, C.POINTER(i64)],
                 "lbib_batch_step_flushed": [vp, i64, vp, C.c_size_t, i32, pd],
+                "lbib_batch_read_particles": [vp, C.POINTER(ParticleState), i32, C.POINTER(i32),
+                                              C.POINTER(C.c_size_t)],
                 "lbib_batch_autotune": [vp, i32, C.POINTER(i32), pd],
                 "lbib_batch_set_variant": [vp, i32],
                 "lbib_synchronize": [vp],
@@ -313,6 +315,28 @@ class Batch:
 
     def step(self, n=1):
         _check(lib().lbib_batch_step(self._h, int(n)))
+
+    def particles(self):
+        """Particle states of all members in member order, one readback for
+        the batch (``lbib_batch_read_particles``); a list per member.  The
+        bytes the readback copied are left in ``last_d2h_bytes``."""
+        total = sum(s.n_particles for s in self.sims)
+        arr = (ParticleState * max(total, 1))()
+        cnt = C.c_int32()
+        nb = C.c_size_t()
+        _check(lib().lbib_batch_read_particles(self._h, arr, total, C.byref(cnt), C.byref(nb)))
+        self.last_d2h_bytes = nb.value
+        out, k = [], 0
+        for s in self.sims:
+            row = []
+            for _ in range(s.n_particles):
+                d = {name: getattr(arr[k], name) for name, _ in ParticleState._fields_}
+                for key in ("Fh", "Fb", "Fw"):
+                    d[key] = tuple(d[key])
+                row.append(d)
+                k += 1
+            out.append(row)
+        return out
 
     def step_flushed(self, n, flush_ptr, flush_bytes, clean=True):
         """Step n times with the L2 flushed (device buffer at ``flush_ptr``

@@ -137,3 +137,20 @@ def test_flushed_steps_equal_plain_steps(L, clean):
     bf.close()
     for s in plain + flushed:
         s.close()
+
+
+def test_batch_readback_equals_per_sim_readback(L):
+    """One batched readback of every member's particle states gives exactly
+    what each simulation's own readback gives, and counts its bytes."""
+    sweep = W.design_sweep()[:7]
+    sims = [make(L, c, p) for c, p in sweep]
+    b = L.Batch(sims)
+    b.step(35)
+    rows = b.particles()
+    assert len(rows) == len(sims)
+    for s, row in zip(sims, rows):
+        assert row == s.particles()
+    assert b.last_d2h_bytes > 0
+    b.close()
+    for s in sims:
+        s.close()
