@@ -628,6 +628,15 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     // variant 1 (256 threads, 64-register cap) is the fastest untuned choice
     // on every measured workload; FP64 storage runs variant 0 regardless
     b->bd.lat_variant = 1;
+    // particle CTA width: 256 threads when every particle fits and there are
+    // enough particles that the SMs their CTAs hold matter to the bulk pass
+    // (the narrow CTA holds half an SM's registers, a little longer)
+    {
+        int max_nl = 0;
+        for (int i = 0; i < n; ++i)
+            for (auto &p : sims[i]->parts) max_nl = std::max(max_nl, p.nl);
+        b->bd.pthreads = (b->kind != ST_F64 && max_nl <= 256 && nparts >= 32) ? 256 : 512;
+    }
     // copy-engine staging (variants 4, 5): rows of whole 16-byte words,
     // walls that are not periodic, 4- or 2-byte storage
     int tma_ok = b->kind != ST_F64;
@@ -1244,6 +1253,28 @@ lbib_status lbib_batch_read_particles(lbib_batch *b, lbib_particle_state *out, i
             ++k;
         }
     }
+    return LBIB_OK;
+}
+
+lbib_status lbib_batch_set_particle_threads(lbib_batch *b, int32_t threads) {
+    if (!b) return fail(LBIB_E_ARG, "null batch");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
+    if (threads != 256 && threads != 512) return fail(LBIB_E_ARG, "threads must be 256 or 512");
+    if (threads == 256) {
+        if (b->kind == ST_F64) return fail(LBIB_E_ARG, "FP64 storage runs 512-thread particle CTAs");
+        for (lbib_sim *s : b->sims)
+            for (auto &p : s->parts)
+                if (p.nl > 256) return fail(LBIB_E_ARG, "a particle has %d elements (> 256)", p.nl);
+    }
+    if (b->bd.pthreads == threads) return LBIB_OK;
+    CK(cudaStreamSynchronize(b->stream));
+    b->bd.pthreads = threads;
+    // captured graphs hold the launch configuration
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
+    b->fgraph = nullptr;
+    if (b->nsamples > 0) return lbib_batch_set_timing(b, b->nsamples);
     return LBIB_OK;
 }
 

@@ -131,6 +131,7 @@ struct BatchDev {
     int nsims, nparts, total_tiles;
     int lat_variant;     // bulk-pass kernel variant (0 .. LBIB_LATTICE_VARIANTS - 1)
     int tma_ok;          // every lattice suits the copy-engine variants (4, 5)
+    int pthreads;        // particle CTA width: 256 (every particle fits) or 512
 };
 
 // Stochastic rounding of 16-bit stores.  A node's dither word is a hash of

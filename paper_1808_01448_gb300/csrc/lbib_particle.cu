@@ -35,7 +35,10 @@ namespace lbib {
 
 namespace {
 
-constexpr int P_THREADS = 512;   // >= LBIB_MAX_MARKERS: one marker per thread
+// Threads of a particle CTA: one marker per thread, so at least the
+// particle's element count; P_THREADS (>= LBIB_MAX_MARKERS) always fits, the
+// 256-thread form holds half the registers of an SM while it runs.
+constexpr int P_THREADS = 512;
 
 // Cubic B-spline of radius 2, branch-free (the nodes of a support straddle
 // the two pieces).
@@ -394,8 +397,8 @@ __device__ __noinline__ double prob_reverse(double k_r0, double dsig, double kBT
     }
 }
 
-template <typename S, typename R>
-__global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int flip, int mode) {
+template <typename S, typename R, int PT>
+__global__ void __launch_bounds__(PT, 1) particle_kernel(BatchDev b, int flip, int mode) {
     // mode bit 0: init (IB forcing only, at the current pose); bit 1: a step
     // without the near-box lattice pass
     const int init = mode & 1;
@@ -418,9 +421,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     {
         const int *src_s = (const int *)&b.sims[b.part_sim[blockIdx.x]];
         const int *src_p = (const int *)P;
-        for (int i = threadIdx.x; i < (int)(sizeof(SimDev) / 4); i += P_THREADS)
+        for (int i = threadIdx.x; i < (int)(sizeof(SimDev) / 4); i += PT)
             ((int *)s_sim_raw)[i] = src_s[i];
-        for (int i = threadIdx.x; i < (int)(sizeof(ParticleDev) / 4); i += P_THREADS)
+        for (int i = threadIdx.x; i < (int)(sizeof(ParticleDev) / 4); i += PT)
             ((int *)s_par_raw)[i] = src_p[i];
     }
     __syncthreads();
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     uint8_t *lig8 = (uint8_t *)take(nl);
     int *corder = (int *)take(sizeof(int) * nl);
     int *coff = (int *)take(sizeof(int) * (nl + 1));
-    double *lpart = (double *)take(sizeof(double) * 3 * (P_THREADS / 32));   // load partials
+    double *lpart = (double *)take(sizeof(double) * 3 * (PT / 32));   // load partials
     int4 *span = (int4 *)take(sizeof(int4) * Tm);       // staged spans per region row
     int *pre = (int *)take(sizeof(int) * (Tm + 1));     // staged nodes before each row
     R *tile = (R *)take(sizeof(R) * 2 * T * T);
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     };
     if (!cached) place();
     const int rx0 = ps.ixc - Tm / 2, ry0 = ps.iyc - Tm / 2;
-    for (int v = tid; v < Tm; v += P_THREADS) span[v] = make_int4(Tm, -1, Tm, -1);
+    for (int v = tid; v < Tm; v += PT) span[v] = make_int4(Tm, -1, Tm, -1);
     // ---- 3. bonds (Eq. 9-11), one element per thread: they need only the
     // pose, so they run with the staging, before the wait on the lattice pass
     const bool has_b = s.wall_b != LBIB_WALL_PERIODIC && s.rec_b > 0.0;
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     // element of this thread's bond: the upper half of the block takes the
     // bonds when both halves fit the elements, so that they run beside the
     // staging work of the lower half
-    const int kb = 2 * nl <= P_THREADS ? tid - P_THREADS / 2 : tid;
+    const int kb = 2 * nl <= PT ? tid - PT / 2 : tid;
     bool lig = false, pb = false, ptop = false;
     R gapb = (R)0, gapt = (R)0;
     if (!init && (unsigned)kb < (unsigned)nl) {
@@ -689,7 +692,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nlist = pre[Tm];
 #pragma unroll 2
-    for (int k = tid; k < nlist; k += P_THREADS) {
+    for (int k = tid; k < nlist; k += PT) {
         // staged node k: row v is the last with pre[v] <= k, then its spans
         int lo = 0, hi = Tm;
         while (hi - lo > 1) {
@@ -853,7 +856,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
     using R2 = typename Pair<R>::type;
     R2 *ctb = spread_in_moments<R>(nl, Tm) ? (R2 *)mr : (R2 *)(mr + 3 * mstride);
     // a zero tile for the spreading (T is even: whole 16-byte words)
-    for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += P_THREADS)
+    for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += PT)
         ((uint4 *)tile)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     if (tid < nl) {
@@ -893,7 +896,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
 #pragma unroll 1
     for (int cl = 0; cl < Pc.ncolors; ++cl) {
         const int m0 = coff[cl], m1 = coff[cl + 1];
-        for (int t = tid; t < (m1 - m0) * 16; t += P_THREADS) {
+        for (int t = tid; t < (m1 - m0) * 16; t += PT) {
             const int m = corder[m0 + (t >> 4)];
             const int j = t & 15;
             const R2 c = ctb[m * 16 + j];
@@ -907,7 +910,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) particle_kernel(BatchDev b, int 
         __syncthreads();
     }
     R *gt = (R *)Pc.tile;
-    for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += P_THREADS)
+    for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += PT)
         ((uint4 *)gt)[i] = ((const uint4 *)tile)[i];
     if (tid == 0) {
         int oxw = ox % s.nx;
@@ -989,7 +992,7 @@ int particle_smem_limit(int kind) {
     cudaError_t e = by_kind(kind, [&](auto sv, auto rv) {
         using S = decltype(sv);
         using R = decltype(rv);
-        return cudaFuncGetAttributes(&fa, particle_kernel<S, R>);
+        return cudaFuncGetAttributes(&fa, particle_kernel<S, R, P_THREADS>);
     });
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1002,8 +1005,14 @@ cudaError_t particle_kernel_setup(int kind, int smem) {
     return by_kind(kind, [&](auto sv, auto rv) {
         using S = decltype(sv);
         using R = decltype(rv);
-        return cudaFuncSetAttribute(particle_kernel<S, R>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(particle_kernel<S, R, P_THREADS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if constexpr (sizeof(S) <= 4) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(particle_kernel<S, R, 256>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        }
+        return e;
     });
 }
 
@@ -1013,9 +1022,11 @@ cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int mode, in
     return by_kind(kind, [&](auto sv, auto rv) {
         using S = decltype(sv);
         using R = decltype(rv);
+        // the 256-thread form when every particle fits (FP32 / 16-bit storage)
+        const bool narrow = sizeof(S) <= 4 && b.pthreads == 256;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(b.nparts);
-        cfg.blockDim = dim3(P_THREADS);
+        cfg.blockDim = dim3(narrow ? 256 : P_THREADS);
         cfg.dynamicSmemBytes = (size_t)smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
@@ -1023,7 +1034,10 @@ cudaError_t launch_particles(int kind, const BatchDev &b, int flip, int mode, in
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = pdl ? 1 : 0;
-        return cudaLaunchKernelEx(&cfg, particle_kernel<S, R>, b, flip, mode);
+        if constexpr (sizeof(S) <= 4) {
+            if (narrow) return cudaLaunchKernelEx(&cfg, particle_kernel<S, R, 256>, b, flip, mode);
+        }
+        return cudaLaunchKernelEx(&cfg, particle_kernel<S, R, P_THREADS>, b, flip, mode);
     });
 }
 

@@ -111,6 +111,7 @@ def lib():
                 "lbib_batch_kernel_times": [vp, pd, C.POINTER(i64)],
                 "lbib_batch_pass_nodes": [vp, C.POINTER(i64)],
                 "lbib_batch_step_flushed": [vp, i64, vp, C.c_size_t, i32, pd],
+                "lbib_batch_set_particle_threads": [vp, i32],
                 "lbib_batch_read_particles": [vp, C.POINTER(ParticleState), i32, C.POINTER(i32),
                                               C.POINTER(C.c_size_t)],
                 "lbib_batch_autotune": [vp, i32, C.POINTER(i32), pd],
@@ -374,6 +375,10 @@ class Batch:
 
     def set_variant(self, variant):
         _check(lib().lbib_batch_set_variant(self._h, int(variant)))
+
+    def set_particle_threads(self, threads):
+        """256 or 512 threads per particle CTA (``lbib_batch_set_particle_threads``)."""
+        _check(lib().lbib_batch_set_particle_threads(self._h, int(threads)))
 
     def pass_nodes(self):
         """Nodes updated per step by the bulk and near-box lattice passes at

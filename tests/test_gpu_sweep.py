@@ -154,3 +154,26 @@ def test_batch_readback_equals_per_sim_readback(L):
     b.close()
     for s in sims:
         s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_particle_cta_widths_give_identical_bits(L, storage):
+    """256- and 512-thread particle CTAs compute the same bits (over a full
+    graph and an odd remainder); widths that do not fit are refused."""
+    sweep = W.design_sweep()[:6]
+    runs = []
+    for width in (512, 256):
+        sims = [make(L, c, p, storage) for c, p in sweep]
+        b = L.Batch(sims)
+        b.set_particle_threads(width)
+        b.step(37)
+        runs.append([(s.populations(), s.particles(), s.bonds(0)[0]) for s in sims])
+        with pytest.raises(L.LbibError):
+            b.set_particle_threads(384)
+        b.close()
+        for s in sims:
+            s.close()
+    for (fa, pa, ba), (fb, pb, bb) in zip(*runs):
+        np.testing.assert_array_equal(fa, fb)
+        assert pa == pb
+        np.testing.assert_array_equal(ba, bb)
