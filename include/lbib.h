@@ -220,8 +220,8 @@ lbib_status lbib_batch_set_timing(lbib_batch *b, int32_t nsamples);
 lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *count);
 /* Threads per particle CTA (one element per thread): 512 fits every
  * particle; 256 (FP32 / 16-bit storage, every particle with at most 256
- * elements) holds half an SM's registers while the particle pass runs, so
- * the bulk lattice pass keeps more of the GPU.  Same results either way.  A
+ * elements) holds a quarter of an SM's registers while the particle pass
+ * runs, so the bulk lattice pass keeps more of the GPU.  Same results either way.  A
  * new batch takes 256 when it can and has at least 32 particles, else 512.
  * Errors: E_ARG (other widths, or 256 where a particle does not fit). */
 lbib_status lbib_batch_set_particle_threads(lbib_batch *b, int32_t threads);

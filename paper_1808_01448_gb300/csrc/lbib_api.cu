@@ -630,7 +630,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->bd.lat_variant = 1;
     // particle CTA width: 256 threads when every particle fits and there are
     // enough particles that the SMs their CTAs hold matter to the bulk pass
-    // (the narrow CTA holds half an SM's registers, a little longer)
+    // (the narrow CTA holds a quarter of an SM's registers, a little longer)
     {
         int max_nl = 0;
         for (int i = 0; i < n; ++i)

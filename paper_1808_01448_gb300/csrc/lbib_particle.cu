@@ -37,7 +37,7 @@ namespace {
 
 // Threads of a particle CTA: one marker per thread, so at least the
 // particle's element count; P_THREADS (>= LBIB_MAX_MARKERS) always fits, the
-// 256-thread form holds half the registers of an SM while it runs.
+// 256-thread form holds a quarter of an SM's registers while it runs.
 constexpr int P_THREADS = 512;
 
 // Cubic B-spline of radius 2, branch-free (the nodes of a support straddle
@@ -397,8 +397,11 @@ __device__ __noinline__ double prob_reverse(double k_r0, double dsig, double kBT
     }
 }
 
+// The 256-thread form is capped at 64 registers (a quarter of an SM's), so
+// that three bulk-pass CTAs fit beside it.
 template <typename S, typename R, int PT>
-__global__ void __launch_bounds__(PT, 1) particle_kernel(BatchDev b, int flip, int mode) {
+__global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDev b, int flip,
+                                                                         int mode) {
     // mode bit 0: init (IB forcing only, at the current pose); bit 1: a step
     // without the near-box lattice pass
     const int init = mode & 1;
