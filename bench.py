@@ -330,7 +330,7 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers: fresh simulations, the
     # initial populations uploaded from pinned host memory, K steps in chunks
-    # of 100 with all particle states read back to the host after each chunk
+    # of 128 with all particle states read back to the host after each chunk
     e2e = None
     if rank == 0 or world > 1:
         e2e_sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc)
@@ -346,13 +346,20 @@ def run_gpu(args):
         for s in e2e_sims:
             s.set_populations(f0[(s.ny, s.nx)])
         eb = lbib.Batch(e2e_sims)
-        chunk, done, d2h = 100, 0, 0
+        # every member's particle states after each chunk, one readback per
+        # chunk, collected while the next chunk runs
+        chunk, done, d2h, pending = 128, 0, 0, False
         while done < args.steps:
             n = min(chunk, args.steps - done)
             eb.step(n)
-            eb.particles()          # every member's particle states, one readback
-            d2h += eb.last_d2h_bytes
             done += n
+            if pending:
+                eb.particles()
+                d2h += eb.last_d2h_bytes
+            eb.read_particles_async()
+            pending = True
+        eb.particles()
+        d2h += eb.last_d2h_bytes
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         e2e = {"value": nodes * args.steps / dt / 1e6, "unit": "MLUPS",

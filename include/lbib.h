@@ -227,14 +227,20 @@ lbib_status lbib_batch_kernel_times(lbib_batch *b, double *mean_ms, int64_t *cou
 lbib_status lbib_batch_set_particle_threads(lbib_batch *b, int32_t threads);
 /* Particle states of every member of the batch, in member order (each
  * member's particles in pid order), as lbib_read_state gives them: one
- * gather kernel, one copy to pinned host memory and one synchronisation of
- * the batch's stream for the whole batch.  out receives up to cap states;
+ * gather kernel and one copy to pinned host memory for the whole batch.
+ * lbib_batch_read_particles_async only enqueues them on the batch's stream
+ * (the states after all work enqueued so far) and returns; the next
+ * lbib_batch_read_particles then waits for that copy alone (work enqueued
+ * in between keeps running) and converts it.  Without a started readback,
+ * lbib_batch_read_particles starts one and waits.  Starting a second one
+ * before collecting the first is E_STATE.  out receives up to cap states;
  * *count (if not NULL) the batch's particle count; *d2h_bytes (if not NULL)
  * the bytes copied from the device (the particles' device records and one
  * error word per member).  Reports a member's deferred device error
  * (E_UNSTABLE, E_TIMEOUT) like lbib_read_state. */
 lbib_status lbib_batch_read_particles(lbib_batch *b, lbib_particle_state *out, int32_t cap,
                                       int32_t *count, size_t *d2h_bytes);
+lbib_status lbib_batch_read_particles_async(lbib_batch *b);
 /* Benchmark form of lbib_batch_step: advances the batch nsteps steps with
  * the same results, with the L2 cache flushed before every step, and times
  * the steps alone.  Before each step the library overwrites the caller's

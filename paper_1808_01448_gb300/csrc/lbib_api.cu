@@ -108,6 +108,7 @@ struct HostParticle {
     std::vector<int> color_order, color_off;
     ParticleDev *d_part = nullptr;   // device struct
     void *d_ecache = nullptr;        // its element record (inside d_block)
+    double *d_pftab = nullptr;       // its P_f table (inside d_block)
     void *d_block = nullptr;         // geometry, bonds, tile
 };
 
@@ -173,6 +174,8 @@ struct lbib_batch {
     // batched state readback: the members' particle records and error words
     // gathered on the device, then one copy into pinned host memory
     void *d_rb = nullptr, *h_rb = nullptr;
+    cudaEvent_t ev_rb = nullptr;        // the staged copy has landed
+    bool rb_pending = false;            // a started readback awaits collection
 };
 
 namespace {
@@ -441,6 +444,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     h.bond = bond; h.anchor_x = ax; h.anchor_wall = aw; h.tile = tile; h.pf_tab = pft;
     h.ecache = ecache;      // filled by the first pass (pose_ok = 0 until then)
     p.d_ecache = ecache;
+    p.d_pftab = pft;
     p.d_part = (ParticleDev *)pd;
     cudaStream_t st = s->stream;
     CK(cudaMemcpyAsync(pd, &h, sizeof h, cudaMemcpyHostToDevice, st));
@@ -486,6 +490,7 @@ void free_batch(lbib_batch *b) {
     for (auto e : b->fev) cudaEventDestroy(e);
     if (b->d_rb) dfree(b->acfg, b->orphan ? nullptr : b->stream, b->d_rb);
     if (b->h_rb) cudaFreeHost(b->h_rb);
+    if (b->ev_rb) cudaEventDestroy(b->ev_rb);
     if (b->d_block) dfree(b->acfg, b->orphan ? nullptr : b->stream, b->d_block);
     delete b;
 }
@@ -691,9 +696,7 @@ lbib_status upload_pf_tables(lbib_sim *s) {
             tab[k] = 1.0 - exp(-(s->cfg.k_f * s->cfg.receptor_bottom) * Nl);
             tab[n + 1 + k] = 1.0 - exp(-(s->cfg.k_f * s->cfg.receptor_top) * Nl);
         }
-        ParticleDev h;
-        CK(cudaMemcpy(&h, p.d_part, sizeof h, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(h.pf_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p.d_pftab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
     }
     return LBIB_OK;
 }
@@ -711,6 +714,40 @@ lbib_status prime(lbib_sim *s, cudaStream_t st) {
         if (e != cudaSuccess) return cuda_fail(e, "particle kernel (init)");
     }
     s->primed = true;
+    return LBIB_OK;
+}
+
+// Prime the members of a batch.  A fresh user batch (no member primed yet)
+// takes one initial IB launch over all its particles instead of one launch
+// and one private batch per simulation; otherwise each member is primed on
+// its own.
+lbib_status prime_members(lbib_batch *b) {
+    bool none = true, all = true;
+    for (lbib_sim *s : b->sims) {
+        if (s->primed) none = false;
+        else all = false;
+    }
+    if (all) return LBIB_OK;
+    if (!none || b->is_self) {
+        for (lbib_sim *s : b->sims) {
+            lbib_status r = prime(s, b->stream);
+            if (r != LBIB_OK) return r;
+        }
+        return LBIB_OK;
+    }
+    // the particles' uploads run on their simulations' streams
+    CK(cudaStreamSynchronize(b->stream));
+    for (lbib_sim *s : b->sims)
+        if (s->stream != b->stream) CK(cudaStreamSynchronize(s->stream));
+    for (lbib_sim *s : b->sims) {
+        lbib_status r = upload_pf_tables(s);
+        if (r != LBIB_OK) return r;
+    }
+    if (b->bd.nparts > 0) {
+        cudaError_t e = launch_particles(b->kind, b->bd, 0, 1, b->smem, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "particle kernel (init)");
+    }
+    for (lbib_sim *s : b->sims) s->primed = true;
     return LBIB_OK;
 }
 
@@ -856,8 +893,8 @@ lbib_status batch_step_impl(lbib_batch *b, int64_t n) {
     if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
     if (n < 0) return fail(LBIB_E_ARG, "nsteps must be >= 0");
     if (n == 0) return LBIB_OK;
-    for (lbib_sim *s : b->sims) {
-        lbib_status r = prime(s, b->stream);
+    {
+        lbib_status r = prime_members(b);
         if (r != LBIB_OK) return r;
     }
     const int64_t full = n / GRAPH_STEPS;
@@ -1166,8 +1203,8 @@ lbib_status lbib_batch_step_flushed(lbib_batch *b, int64_t n, void *flush, size_
     double acc[4] = {0, 0, 0, 0};
     if (ms) ms[0] = ms[1] = ms[2] = ms[3] = 0;
     if (n == 0) return LBIB_OK;
-    for (lbib_sim *s : b->sims) {
-        lbib_status r = prime(s, b->stream);
+    {
+        lbib_status r = prime_members(b);
         if (r != LBIB_OK) return r;
     }
     if (b->fev.empty()) {
@@ -1214,15 +1251,11 @@ lbib_status lbib_batch_step_flushed(lbib_batch *b, int64_t n, void *flush, size_
     return LBIB_OK;
 }
 
-lbib_status lbib_batch_read_particles(lbib_batch *b, lbib_particle_state *out, int32_t cap,
-                                     int32_t *count, size_t *d2h_bytes) {
-    if (!b) return fail(LBIB_E_ARG, "null batch");
-    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
-    if (cap < 0 || (cap > 0 && !out)) return fail(LBIB_E_ARG, "cap must be >= 0, out non-null");
+// Enqueue the gather of every member's particle record and error word and
+// their copy into the pinned staging buffer, then record ev_rb.
+static lbib_status readback_start(lbib_batch *b) {
     const int np = b->bd.nparts, ns = b->bd.nsims;
-    if (count) *count = np;
     const size_t pbytes = sizeof(ParticleDev) * (size_t)np, bytes = pbytes + sizeof(int) * ns;
-    if (d2h_bytes) *d2h_bytes = bytes;
     if (!b->d_rb) {
         b->d_rb = dalloc(b->acfg, b->stream, bytes);
         if (!b->d_rb) return fail(LBIB_E_OOM, "device allocation of %zu bytes failed", bytes);
@@ -1230,9 +1263,10 @@ lbib_status lbib_batch_read_particles(lbib_batch *b, lbib_particle_state *out, i
             b->h_rb = nullptr;
             return fail(LBIB_E_OOM, "pinned host allocation of %zu bytes failed", bytes);
         }
+        CK(cudaEventCreateWithFlags(&b->ev_rb, cudaEventDisableTiming));
     }
-    for (lbib_sim *s : b->sims) {
-        lbib_status r = prime(s, b->stream);
+    {
+        lbib_status r = prime_members(b);
         if (r != LBIB_OK) return r;
     }
     int *derr = (int *)((char *)b->d_rb + pbytes);
@@ -1240,7 +1274,33 @@ lbib_status lbib_batch_read_particles(lbib_batch *b, lbib_particle_state *out, i
                                                         (ParticleDev *)b->d_rb, derr);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(b->h_rb, b->d_rb, bytes, cudaMemcpyDeviceToHost, b->stream));
-    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaEventRecord(b->ev_rb, b->stream));
+    b->rb_pending = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_batch_read_particles_async(lbib_batch *b) {
+    if (!b) return fail(LBIB_E_ARG, "null batch");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
+    if (b->rb_pending) return fail(LBIB_E_STATE, "a started readback has not been collected");
+    return readback_start(b);
+}
+
+lbib_status lbib_batch_read_particles(lbib_batch *b, lbib_particle_state *out, int32_t cap,
+                                     int32_t *count, size_t *d2h_bytes) {
+    if (!b) return fail(LBIB_E_ARG, "null batch");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
+    if (cap < 0 || (cap > 0 && !out)) return fail(LBIB_E_ARG, "cap must be >= 0, out non-null");
+    const int np = b->bd.nparts, ns = b->bd.nsims;
+    if (count) *count = np;
+    const size_t pbytes = sizeof(ParticleDev) * (size_t)np;
+    if (d2h_bytes) *d2h_bytes = pbytes + sizeof(int) * ns;
+    if (!b->rb_pending) {
+        lbib_status r = readback_start(b);
+        if (r != LBIB_OK) return r;
+    }
+    b->rb_pending = false;
+    CK(cudaEventSynchronize(b->ev_rb));
     const ParticleDev *hp = (const ParticleDev *)b->h_rb;
     const int *herr = (const int *)((const char *)b->h_rb + pbytes);
     int k = 0;
@@ -1303,8 +1363,8 @@ lbib_status lbib_batch_set_variant(lbib_batch *b, int32_t variant) {
 lbib_status lbib_batch_autotune(lbib_batch *b, int32_t reps, int32_t *variant, double *ms) {
     if (!b || reps < 1 || reps > 1000) return fail(LBIB_E_ARG, "reps must be 1..1000");
     if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
-    for (lbib_sim *s : b->sims) {
-        lbib_status r = prime(s, b->stream);
+    {
+        lbib_status r = prime_members(b);
         if (r != LBIB_OK) return r;
     }
     const int mode = b->overlap ? 1 : 0;
@@ -1391,6 +1451,7 @@ lbib_status lbib_read_state(lbib_sim *s, lbib_state *st, lbib_particle_state *pa
     lbib_status r = LBIB_OK;
     if (rho || ux || uy) {
         r = prime(s, s->stream);   // the fields include the IB force of this step
+        if (r == LBIB_OK) r = ensure_self(s);
         if (r != LBIB_OK) return r;
     }
     CK(cudaStreamSynchronize(s->stream));
@@ -1452,6 +1513,7 @@ lbib_status lbib_read_bonds(lbib_sim *s, int32_t pid, uint8_t *bond, double *ax,
 lbib_status lbib_read_ib_force(lbib_sim *s, double *fx, double *fy) {
     if (!s || !fx || !fy) return fail(LBIB_E_ARG, "null argument");
     lbib_status r = prime(s, s->stream);
+    if (r == LBIB_OK) r = ensure_self(s);
     if (r != LBIB_OK) return r;
     r = ensure_scratch(s, 2 * s->N * sizeof(double));
     if (r != LBIB_OK) return r;

@@ -112,6 +112,7 @@ def lib():
                 "lbib_batch_pass_nodes": [vp, C.POINTER(i64)],
                 "lbib_batch_step_flushed": [vp, i64, vp, C.c_size_t, i32, pd],
                 "lbib_batch_set_particle_threads": [vp, i32],
+                "lbib_batch_read_particles_async": [vp],
                 "lbib_batch_read_particles": [vp, C.POINTER(ParticleState), i32, C.POINTER(i32),
                                               C.POINTER(C.c_size_t)],
                 "lbib_batch_autotune": [vp, i32, C.POINTER(i32), pd],
@@ -319,8 +320,9 @@ class Batch:
 
     def particles(self):
         """Particle states of all members in member order, one readback for
-        the batch (``lbib_batch_read_particles``); a list per member.  The
-        bytes the readback copied are left in ``last_d2h_bytes``."""
+        the batch (``lbib_batch_read_particles``; collects a readback started
+        by ``read_particles_async``); a list per member.  The bytes the
+        readback copied are left in ``last_d2h_bytes``."""
         total = sum(s.n_particles for s in self.sims)
         arr = (ParticleState * max(total, 1))()
         cnt = C.c_int32()
@@ -338,6 +340,11 @@ class Batch:
                 k += 1
             out.append(row)
         return out
+
+    def read_particles_async(self):
+        """Enqueue the readback of every member's particle states (after the
+        work enqueued so far); the next ``particles()`` collects it."""
+        _check(lib().lbib_batch_read_particles_async(self._h))
 
     def step_flushed(self, n, flush_ptr, flush_bytes, clean=True):
         """Step n times with the L2 flushed (device buffer at ``flush_ptr``

@@ -177,3 +177,26 @@ def test_particle_cta_widths_give_identical_bits(L, storage):
         np.testing.assert_array_equal(fa, fb)
         assert pa == pb
         np.testing.assert_array_equal(ba, bb)
+
+
+def test_async_readback_gives_the_states_when_started(L):
+    """A readback started after 35 steps and collected after 10 more gives
+    the states after 35 steps; a second start before collection is refused."""
+    sweep = W.design_sweep()[:5]
+    a = [make(L, c, p) for c, p in sweep]
+    b = [make(L, c, p) for c, p in sweep]
+    ba, bb = L.Batch(a), L.Batch(b)
+    ba.step(35)
+    ba.read_particles_async()
+    with pytest.raises(L.LbibError):
+        ba.read_particles_async()
+    ba.step(10)
+    late = ba.particles()
+    bb.step(35)
+    assert late == bb.particles()
+    bb.step(10)
+    assert ba.particles() == bb.particles()
+    ba.close()
+    bb.close()
+    for s in a + b:
+        s.close()
