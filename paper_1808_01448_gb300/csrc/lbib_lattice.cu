@@ -29,7 +29,7 @@ __device__ __forceinline__ R recip(R x) {
 // of two (unless the caller set another), so every rounding is the same as
 // in the unscaled form.
 template <typename R, bool SC = false>
-__device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy) {
+__device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy, bool &bad) {
     R drho, jx, jy;
     node_moments(d, drho, jx, jy);
     if constexpr (SC) {
@@ -67,7 +67,15 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
     pair(5, 7, (R)(1.0 / 36.0), ux + uy, Fx + Fy);
     pair(6, 8, (R)(1.0 / 36.0), uy - ux, Fy - Fx);
     // non-finite state or a density outside (0, 2): the run has broken down
-    if (!(fabs(drho) < (R)1) || !(fabs(ux) + fabs(uy) < (R)10)) atomicOr(s.err, ERR_UNSTABLE);
+    // (the caller raises the error bit once for all its nodes)
+    bad |= !(fabs(drho) < (R)1) | !(fabs(ux) + fabs(uy) < (R)10);
+}
+
+template <typename R, bool SC = false>
+__device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy) {
+    bool bad = false;
+    collide_node<R, SC>(s, d, Fx, Fy, bad);
+    if (bad) atomicOr(s.err, ERR_UNSTABLE);
 }
 
 // SC: d is scaled (see collide_node); the dither hash takes the unscaled
@@ -241,6 +249,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
                 pull_group<S, R, BULK>(s, src, xg[g], y, &d[4 * g], SC ? 1.f : s.inv_scale);
             }
         }
+        bool bad = false;
 #pragma unroll
         for (int g = 0; g < GROUPS; ++g) {
             if (!keep[g]) continue;
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             for (int j = 0; j < 4; ++j) {
                 R Fx = gx, Fy = gy;
                 if (!BULK && s.np) tile_force<R>(s, b.parts, xg[g] + j, yg[g], Fx, Fy);
-                collide_node<R, SC>(s, d[4 * g + j], Fx, Fy);
+                collide_node<R, SC>(s, d[4 * g + j], Fx, Fy, bad);
             }
             const float sc = SC ? 1.f : s.scale;
             if (keep[g] == 0xFu && sizeof(S) == 2 && s.sround) {
@@ -278,6 +287,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
                         store_node<S, R, BULK, SC>(s, dst, N, k + j, d[4 * g + j]);
             }
         }
+        if (bad) atomicOr(s.err, ERR_UNSTABLE);
         return;
     }
     const int k0 = (tile - s.tile0) * LB_TILE_NODES + (int)threadIdx.x;
@@ -565,7 +575,10 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     }
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) collide_node<R, SC>(s, d[j], gx, gy);
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) collide_node<R, SC>(s, d[j], gx, gy, bad);
+    if (bad) atomicOr(s.err, ERR_UNSTABLE);
     const float sc = SC ? 1.f : s.scale;
     if (keep == 0xFu && sizeof(S) == 2 && s.sround) {
         unsigned h[4];
