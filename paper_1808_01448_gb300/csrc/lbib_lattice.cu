@@ -574,7 +574,6 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
         }
     }
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
-#pragma unroll
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) collide_node<R, SC>(s, d[j], gx, gy, bad);
