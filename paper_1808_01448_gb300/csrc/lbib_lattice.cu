@@ -98,13 +98,6 @@ __device__ __forceinline__ void store_node(const SimDev &s, S *__restrict__ dst,
     }
 }
 
-template <typename S, typename R, bool STREAM = false>
-__device__ __forceinline__ void collide_store(const SimDev &s, S *__restrict__ dst, int N,
-                                              int k, R d[9], R Fx, R Fy) {
-    collide_node<R>(s, d, Fx, Fy);
-    store_node<S, R, STREAM>(s, dst, N, k, d);
-}
-
 // Pre-collision deviations of the four nodes (x0 .. x0 + 3, y) of a row away
 // from the walls (or of a lattice periodic in y): one vector load per
 // population plane, plus one scalar load for the node the x shift brings in
@@ -315,14 +308,17 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
 #pragma unroll
     for (int j = 0; j < NPT; ++j)
         if (!skip[j]) pull_node<S, R, BULK>(s, src, xs[j], ys[j], d[j]);
+    bool bad = false;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         if (!skip[j]) {
             R Fx = gx, Fy = gy;
             if (!BULK && s.np) tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
-            collide_store<S, R, BULK>(s, dst, N, k0 + j * THREADS, d[j], Fx, Fy);
+            collide_node<R>(s, d[j], Fx, Fy, bad);
+            store_node<S, R, BULK>(s, dst, N, k0 + j * THREADS, d[j]);
         }
     }
+    if (bad) atomicOr(s.err, ERR_UNSTABLE);
 }
 
 // The nodes of the near boxes (one box per particle; NB x NB nodes, rows
@@ -377,14 +373,17 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
 #pragma unroll
     for (int j = 0; j < NEAR_NPT; ++j)
         if (!skip[j]) pull_node<S, R>(s, src, xs[j], ys[j], d[j]);
+    bool bad = false;
 #pragma unroll
     for (int j = 0; j < NEAR_NPT; ++j) {
         if (!skip[j]) {
             R Fx = gx, Fy = gy;
             tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
-            collide_store<S, R>(s, dst, N, ys[j] * nx + xs[j], d[j], Fx, Fy);
+            collide_node<R>(s, d[j], Fx, Fy, bad);
+            store_node<S, R>(s, dst, N, ys[j] * nx + xs[j], d[j]);
         }
     }
+    if (bad) atomicOr(s.err, ERR_UNSTABLE);
 }
 
 // ---- bulk pass with copy-engine staging (variants 4 and 5) -----------------
