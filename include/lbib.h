@@ -115,6 +115,14 @@ typedef struct lbib_config {
     lbib_alloc_fn alloc;
     lbib_free_fn free;
     void *alloc_ctx;
+    /* Direct-forcing passes per step (multi-direct forcing; 0 or 1: the
+     * single pass of Sec. "The combined LB-IB method").  With M > 1 each
+     * marker's force is corrected M - 1 times by the slip left after its own
+     * particle's force is spread: F <- F + F0 - I[spread(F)], I the MLS
+     * interpolation at the marker and F0 the first pass's force; the last F
+     * is spread.  0 .. 16, else E_ARG. */
+    int32_t ib_iterations;
+    int32_t reserved1;
 } lbib_config;
 
 /* A rigid particle (Sec. "Pressure and viscous stresses"): a closed polygon

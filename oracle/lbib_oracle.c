@@ -699,7 +699,14 @@ static void moments(const or_sim *s, double *rho, double *ux, double *uy, double
 /* IB direct forcing (Favier et al. [38] with MLS [13], [39]).  Reading: the
  * desired marker velocity is the rigid motion U_c + omega x (X_l - X_c); the
  * force density that makes the Guo half-step velocity u* + F/(2 rho) match it
- * is F_l = 2 rho_l (U^d_l - u*_l) / dt; spread with eps_l = S_l dx. */
+ * is F_l = 2 rho_l (U^d_l - u*_l) / dt; spread with eps_l = S_l dx.
+ * Multi-direct forcing (ib_iterations = M > 1): the velocity a marker sees
+ * after its own particle's force is spread, u^m_l = u*_l + I_l[f^(m-1)] /
+ * (2 rho_l) (I_l: the MLS interpolation at X_l, rho_l the marker's
+ * interpolated density), is corrected again, F^m_l = F^(m-1)_l +
+ * 2 rho_l (U^d_l - u^m_l) = F^(m-1)_l + F^0_l - I_l[f^(m-1)], for
+ * m = 1 .. M-1, and F^(M-1) is spread.  Each particle iterates against its
+ * own spread force only. */
 static void ib_force(or_sim *s) {
     size_t n = NN(s);
     memset(s->fibx, 0, n * sizeof(double));
@@ -723,6 +730,28 @@ static void ib_force(or_sim *s) {
             double udy = p->v + p->omega * (mx[l] - p->xc);
             Fx[l] = 2.0 * rl[l] * (udx - ul[l]);
             Fy[l] = 2.0 * rl[l] * (udy - vl[l]);
+        }
+        if (s->c.ib_iterations > 1) {
+            /* F^0 kept in rl / ul (no longer needed), the particle's own
+             * spread field in tx / ty */
+            double *tx = (double *)malloc(2 * n * sizeof(double)), *ty = tx + n;
+            double *Ix = (double *)malloc(2 * nv * sizeof(double)), *Iy = Ix + nv;
+            for (int l = 0; l < nv; ++l) {
+                rl[l] = Fx[l];
+                ul[l] = Fy[l];
+            }
+            for (int m = 1; m < s->c.ib_iterations; ++m) {
+                memset(tx, 0, 2 * n * sizeof(double));
+                or_spread(&s->c, nv, mx, my, Fx, Fy, S, tx, ty);
+                or_interp(&s->c, tx, nv, mx, my, Ix);
+                or_interp(&s->c, ty, nv, mx, my, Iy);
+                for (int l = 0; l < nv; ++l) {
+                    Fx[l] = Fx[l] + rl[l] - Ix[l];
+                    Fy[l] = Fy[l] + ul[l] - Iy[l];
+                }
+            }
+            free(Ix);
+            free(tx);
         }
         or_spread(&s->c, nv, mx, my, Fx, Fy, S, s->fibx, s->fiby);
         free(buf);

@@ -38,6 +38,8 @@ typedef struct or_config {
     double hamaker, eps_min;         /* Eq. 12 constant, lower clamp of the gap */
     double receptor_bottom, receptor_top; /* receptor density on each wall */
     uint64_t seed, sim_id;           /* Philox key */
+    int32_t ib_iterations;           /* direct-forcing passes per step (<= 1: one) */
+    int32_t reserved;
 } or_config;
 
 typedef struct or_particle_in {

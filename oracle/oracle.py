@@ -52,6 +52,7 @@ class OrConfig(C.Structure):
         ("hamaker", C.c_double), ("eps_min", C.c_double),
         ("receptor_bottom", C.c_double), ("receptor_top", C.c_double),
         ("seed", C.c_uint64), ("sim_id", C.c_uint64),
+        ("ib_iterations", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -136,7 +137,7 @@ def make_config(**kw) -> OrConfig:
                     tau=0.8, u_bottom=0.0, u_top=0.0, gx=0.0, gy=0.0, k_f=0.85,
                     k_r0=1e-4, kBT=0.1, sigma_star_ratio=0.5, y_cr=1.36,
                     y_eq_ratio=0.5, hamaker=0.0, eps_min=0.1, receptor_bottom=1.0,
-                    receptor_top=0.0, seed=1, sim_id=0)
+                    receptor_top=0.0, seed=1, sim_id=0, ib_iterations=1)
     defaults.update(kw)
     for k, v in defaults.items():
         if k in ("wall_bottom", "wall_top") and isinstance(v, str):

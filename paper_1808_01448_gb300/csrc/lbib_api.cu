@@ -230,6 +230,7 @@ SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
     // vector path: whole groups of four nodes per row, buffers 32-byte aligned
     d.vec4 = c.nx % 4 == 0 && ((uintptr_t)s->pop[0] % 32) == 0 && ((uintptr_t)s->pop[1] % 32) == 0;
     d.sround = c.rounding == LBIB_ROUND_STOCHASTIC;
+    d.ib_iters = c.ib_iterations > 1 ? c.ib_iterations : 1;
     return d;
 }
 
@@ -952,6 +953,8 @@ lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out) {
     const lbib_config &c = *cfg;
     if (c.nx < 8 || c.ny < 4 || (int64_t)c.nx * c.ny >= (1ll << 31) / 9)
         return fail(LBIB_E_ARG, "lattice %d x %d outside 8 x 4 .. 2^31/9 nodes", c.nx, c.ny);
+    if (c.ib_iterations < 0 || c.ib_iterations > 16)
+        return fail(LBIB_E_ARG, "ib_iterations %d outside 0 .. 16", c.ib_iterations);
     if (!(c.tau > 0.5) || !isfinite(c.tau)) return fail(LBIB_E_ARG, "tau must be > 1/2");
     for (int w : {c.wall_bottom, c.wall_top})
         if (w < 0 || w > 2) return fail(LBIB_E_ARG, "unknown wall kind %d", w);
@@ -1621,6 +1624,8 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
     const lbib_config &c = *cfg;
     if (c.nx < 8 || c.ny < 4 || (int64_t)c.nx * c.ny >= (1ll << 31) / 9)
         return fail(LBIB_E_ARG, "lattice %d x %d outside 8 x 4 .. 2^31/9 nodes", c.nx, c.ny);
+    if (c.ib_iterations < 0 || c.ib_iterations > 16)
+        return fail(LBIB_E_ARG, "ib_iterations %d outside 0 .. 16", c.ib_iterations);
     if (!(c.tau > 0.5) || c.wall_bottom < 0 || c.wall_bottom > 2 || c.wall_top < 0 || c.wall_top > 2 ||
         (c.wall_bottom == LBIB_WALL_PERIODIC) != (c.wall_top == LBIB_WALL_PERIODIC))
         return fail(LBIB_E_ARG, "invalid channel configuration");
@@ -1692,6 +1697,7 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
     hs.p0 = 0; hs.np = 1; hs.tile0 = 0; hs.ntiles = 0;
     hs.tau = c.tau; hs.u_b = c.u_bottom; hs.u_t = c.u_top; hs.gx = c.gx; hs.gy = c.gy;
     hs.scale = 1.f; hs.inv_scale = 1.f;
+    hs.ib_iters = c.ib_iterations > 1 ? c.ib_iterations : 1;
     const double om = 1.0 / c.tau;
     hs.d_om = om; hs.d_pref = 1.0 - 0.5 * om; hs.d_ub6 = c.u_bottom / 6.0; hs.d_ut6 = c.u_top / 6.0;
     hs.f_om = (float)om; hs.f_pref = (float)hs.d_pref; hs.f_gx = (float)c.gx; hs.f_gy = (float)c.gy;

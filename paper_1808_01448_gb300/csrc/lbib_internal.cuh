@@ -40,6 +40,8 @@ struct SimDev {
     int tile0, ntiles;   // lattice work tiles of this simulation
     int vec4;            // rows in whole groups of four aligned nodes
     int sround;          // 16-bit storage: stochastic rounding of the stores
+    int ib_iters;        // direct-forcing passes per step (>= 1)
+    int pad_ib;
     // k / nx = umulhi(k, nx_m) >> nx_s for 0 <= k < 2^31 (div_nx below)
     unsigned nx_m;
     int nx_s;

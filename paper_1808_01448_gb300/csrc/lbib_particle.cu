@@ -853,64 +853,103 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     // the near-box pass of the next step may be scheduled from here on (it
     // waits for this pass to end before it reads the tiles)
     asm volatile("griddepcontrol.launch_dependents;");
-    // each marker's sixteen contributions phi_k F_l eps_l, in the staged
-    // moments' space once every support has been read (or a buffer of their
-    // own when they do not fit there)
     using R2 = typename Pair<R>::type;
     R2 *ctb = spread_in_moments<R>(nl, Tm) ? (R2 *)mr : (R2 *)(mr + 3 * mstride);
-    // a zero tile for the spreading (T is even: whole 16-byte words)
-    for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += PT)
-        ((uint4 *)tile)[i] = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
-    if (tid < nl) {
-        // phi_(a,b) = wx[a] py[b] as in support_sum (zero without a fit or
-        // for a row outside the lattice)
-        const int rows = pt.rows[tid];
-        const R fx = pt.fx[tid], fy = pt.fy[tid], invW = pt.invW[tid], mu = pt.mu[tid];
-        const R mu_v = pt.mu_v[tid];
-        R wx[4];
+    const int ox = ps.ixc - T / 2;
+    const int oy = ps.iyc - T / 2;
+    // phi_(a,b) = wx[a] py[b] of marker l, as in support_sum (zero without a
+    // fit or for a row outside the lattice)
+    auto marker_phi = [&](int l, R wx[4], R py[4]) {
+        const int rows = pt.rows[l];
+        const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l];
+        const R mu_v = pt.mu_v[l];
 #pragma unroll
         for (int a = 0; a < 4; ++a) wx[a] = (rows & 16) ? bspline((R)(a - 1) - fx) : (R)0;
-#pragma unroll 1
+#pragma unroll
         for (int b = 0; b < 4; ++b) {
-            R py = (R)0;
+            py[b] = (R)0;
             if ((rows & 16) && (rows & (1 << b))) {
                 const R dy = (R)(b - 1) - fy;
                 const R wy = bspline(dy) * invW;
                 const R dyc = dy - mu;
-                py = wy * ((R)1 - dyc * mu_v);
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const R phi = wx[a] * py;
-                R2 c;
-                c.x = phi * Fx;
-                c.y = phi * Fy;
-                ctb[tid * 16 + b * 4 + a] = c;
+                py[b] = wy * ((R)1 - dyc * mu_v);
             }
         }
-    }
-    __syncthreads();
-    // colour-ordered spreading into the tile; origin floor(X_c) - T/2.
-    // Markers of one colour have disjoint supports, so each tile node takes
-    // its contributions in colour order (identical alone or in a batch).
-    const int ox = ps.ixc - T / 2;
-    const int oy = ps.iyc - T / 2;
+    };
+    // one spreading pass of the markers' forces (Fx, Fy) into a zeroed tile
+    auto spread_pass = [&]() {
+        // a zero tile for the spreading (T is even: whole 16-byte words)
+        for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += PT)
+            ((uint4 *)tile)[i] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        // each marker's sixteen contributions phi_k F_l eps_l, in the staged
+        // moments' space once every support has been read (or a buffer of
+        // their own when they do not fit there)
+        if (tid < nl) {
+            R wx[4], py[4];
+            marker_phi(tid, wx, py);
 #pragma unroll 1
-    for (int cl = 0; cl < Pc.ncolors; ++cl) {
-        const int m0 = coff[cl], m1 = coff[cl + 1];
-        for (int t = tid; t < (m1 - m0) * 16; t += PT) {
-            const int m = corder[m0 + (t >> 4)];
-            const int j = t & 15;
-            const R2 c = ctb[m * 16 + j];
-            if (c.x == (R)0 && c.y == (R)0) continue;
-            const int tx = pt.ix0[m] + (j & 3) - ox, ty = pt.iy0[m] + (j >> 2) - oy;
-            if ((unsigned)tx < (unsigned)T && (unsigned)ty < (unsigned)T) {
-                tile[ty * T + tx] += c.x;
-                tile[T * T + ty * T + tx] += c.y;
+            for (int b = 0; b < 4; ++b) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const R phi = wx[a] * py[b];
+                    R2 c;
+                    c.x = phi * Fx;
+                    c.y = phi * Fy;
+                    ctb[tid * 16 + b * 4 + a] = c;
+                }
             }
         }
         __syncthreads();
+        // colour-ordered spreading into the tile; origin floor(X_c) - T/2.
+        // Markers of one colour have disjoint supports, so each tile node
+        // takes its contributions in colour order (identical alone or in a
+        // batch).
+#pragma unroll 1
+        for (int cl = 0; cl < Pc.ncolors; ++cl) {
+            const int m0 = coff[cl], m1 = coff[cl + 1];
+            for (int t = tid; t < (m1 - m0) * 16; t += PT) {
+                const int m = corder[m0 + (t >> 4)];
+                const int j = t & 15;
+                const R2 c = ctb[m * 16 + j];
+                if (c.x == (R)0 && c.y == (R)0) continue;
+                const int tx = pt.ix0[m] + (j & 3) - ox, ty = pt.iy0[m] + (j >> 2) - oy;
+                if ((unsigned)tx < (unsigned)T && (unsigned)ty < (unsigned)T) {
+                    tile[ty * T + tx] += c.x;
+                    tile[T * T + ty * T + tx] += c.y;
+                }
+            }
+            __syncthreads();
+        }
+    };
+    spread_pass();
+    // multi-direct forcing: the slip each marker sees once this particle's
+    // force is spread, corrected M - 1 more times, F <- F + F0 - eps_l I_l[f]
+    // (F carries eps_l = S_l; I_l[f] = sum_k phi_k f_k over the tile)
+    const R F0x = Fx, F0y = Fy;
+#pragma unroll 1
+    for (int it = 1; it < s.ib_iters; ++it) {
+        if (tid < nl && (pt.rows[tid] & 16)) {
+            R wx[4], py[4];
+            marker_phi(tid, wx, py);
+            R ix = 0, iy = 0;
+#pragma unroll 1
+            for (int b = 0; b < 4; ++b) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int tx = pt.ix0[tid] + a - ox, ty = pt.iy0[tid] + b - oy;
+                    if ((unsigned)tx < (unsigned)T && (unsigned)ty < (unsigned)T) {
+                        const R phi = wx[a] * py[b];
+                        ix += phi * tile[ty * T + tx];
+                        iy += phi * tile[T * T + ty * T + tx];
+                    }
+                }
+            }
+            Fx += F0x - sS[tid] * ix;
+            Fy += F0y - sS[tid] * iy;
+        }
+        __syncthreads();    // every read of the tile before it is zeroed
+        spread_pass();
     }
     R *gt = (R *)Pc.tile;
     for (int i = tid; i < (int)(2 * sizeof(R) * T * T / 16); i += PT)

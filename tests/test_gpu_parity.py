@@ -355,3 +355,60 @@ def test_torch_allocator_and_stream(O, L):
     o.step(40)
     assert abs(g.particle(0)["xc"] - o.particle(0)["xc"]) < 1e-11
     g.close()
+
+
+@pytest.mark.parametrize("walls", ["zou_he", "periodic"])
+def test_multi_direct_forcing_parity_f64(O, L, walls):
+    """Three direct-forcing passes (multi-direct forcing): the IB force field
+    of the GPU's FP64 path equals the oracle's to rounding."""
+    nx, ny = 80, 44
+    cfg = dict(nx=nx, ny=ny, wall_bottom=walls, wall_top=walls, tau=0.9,
+               u_top=0.0 if walls == "periodic" else 0.02, ib_iterations=3)
+    f0 = random_start(O, nx, ny, 4, amp=0.01)
+    vx, vy = W.particle_outline("ar2", 7.0)
+    p = dict(vx=vx, vy=vy, xc=40.6, yc=14.3 if walls != "periodic" else 2.2, theta=0.2,
+             ligand_density=0.0, sigma=0.0)
+    o, g = pair(O, L, cfg, [p], f_post=f0)
+    fo = o.ib_force()
+    fg = g.ib_force()
+    scale = max(np.abs(fo[0]).max(), np.abs(fo[1]).max())
+    assert scale > 1e-4
+    np.testing.assert_allclose(fg[0], fo[0], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(fg[1], fo[1], rtol=0, atol=1e-12 * scale)
+    # the passes change the force (against a single pass)
+    o1, g1 = pair(O, L, dict(cfg, ib_iterations=1), [p], f_post=f0)
+    assert np.abs(g1.ib_force()[0] - fg[0]).max() > 1e-3 * scale
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_multi_direct_forcing_full_step(O, L, storage):
+    """Coupled steps with three direct-forcing passes against the oracle:
+    FP64 to rounding with bond states equal at every step; FP32 within the
+    stated tolerances (velocity 1e-5 relative L2, trajectory 1e-4)."""
+    cfg, p = adhesion_case(shape="circle", Re=0.1, nx=112, ny=44, r=6.5)
+    cfg["ib_iterations"] = 3
+    o, g = pair(O, L, cfg, [p], storage=storage)
+    steps = 60 if storage == "f64" else 150
+    for t in range(steps):
+        o.step(1)
+        g.step(1)
+        if storage == "f64":
+            assert np.array_equal(o.bonds(0)[0], g.bonds(0)[0]), f"step {t + 1}"
+    ro, uo, vo = o.fields()
+    rg, ug, vg = g.fields()
+    err = rel_l2(np.stack([ug, vg]), np.stack([uo, vo]))
+    po, pg = o.particle(0), g.particle(0)
+    if storage == "f64":
+        assert err < 1e-11
+        for k in ("xc", "yc", "theta", "u", "v", "omega"):
+            assert pg[k] == pytest.approx(po[k], abs=1e-10), k
+    else:
+        assert err < 1e-5
+        for k in ("xc", "yc", "theta"):
+            assert abs(pg[k] - po[k]) < 1e-4, k
+        assert np.array_equal(o.bonds(0)[0], g.bonds(0)[0])
+
+
+def test_ib_iterations_out_of_range_is_refused(L):
+    with pytest.raises(L.LbibError):
+        L.Sim(nx=32, ny=16, ib_iterations=17)
