@@ -249,6 +249,10 @@ lbib_status lbib_batch_set_particle_threads(lbib_batch *b, int32_t threads);
 lbib_status lbib_batch_read_particles(lbib_batch *b, lbib_particle_state *out, int32_t cap,
                                       int32_t *count, size_t *d2h_bytes);
 lbib_status lbib_batch_read_particles_async(lbib_batch *b);
+/* Wait for all work enqueued on the batch and report a member's deferred
+ * device error (E_UNSTABLE, E_TIMEOUT): one copy of every member's error
+ * word.  A started readback stays pending. */
+lbib_status lbib_batch_synchronize(lbib_batch *b);
 /* Benchmark form of lbib_batch_step: advances the batch nsteps steps with
  * the same results, with the L2 cache flushed before every step, and times
  * the steps alone.  Before each step the library overwrites the caller's

@@ -176,6 +176,7 @@ struct lbib_batch {
     void *d_rb = nullptr, *h_rb = nullptr;
     cudaEvent_t ev_rb = nullptr;        // the staged copy has landed
     bool rb_pending = false;            // a started readback awaits collection
+    int *d_errs = nullptr, *h_errs = nullptr;   // members' error words (synchronize)
 };
 
 namespace {
@@ -492,6 +493,8 @@ void free_batch(lbib_batch *b) {
     if (b->d_rb) dfree(b->acfg, b->orphan ? nullptr : b->stream, b->d_rb);
     if (b->h_rb) cudaFreeHost(b->h_rb);
     if (b->ev_rb) cudaEventDestroy(b->ev_rb);
+    if (b->d_errs) dfree(b->acfg, b->orphan ? nullptr : b->stream, b->d_errs);
+    if (b->h_errs) cudaFreeHost(b->h_errs);
     if (b->d_block) dfree(b->acfg, b->orphan ? nullptr : b->stream, b->d_block);
     delete b;
 }
@@ -1279,6 +1282,31 @@ static lbib_status readback_start(lbib_batch *b) {
     CK(cudaMemcpyAsync(b->h_rb, b->d_rb, bytes, cudaMemcpyDeviceToHost, b->stream));
     CK(cudaEventRecord(b->ev_rb, b->stream));
     b->rb_pending = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_batch_synchronize(lbib_batch *b) {
+    if (!b) return fail(LBIB_E_ARG, "null batch");
+    if (b->orphan) return fail(LBIB_E_STATE, "a member of this batch was destroyed");
+    const int ns = b->bd.nsims;
+    if (!b->d_errs) {
+        b->d_errs = (int *)dalloc(b->acfg, b->stream, sizeof(int) * ns);
+        if (!b->d_errs) return fail(LBIB_E_OOM, "device allocation of %zu bytes failed", sizeof(int) * ns);
+        if (cudaHostAlloc((void **)&b->h_errs, sizeof(int) * ns, cudaHostAllocDefault) != cudaSuccess) {
+            b->h_errs = nullptr;
+            return fail(LBIB_E_OOM, "pinned host allocation failed");
+        }
+    }
+    // the error words of every member in one copy, after all enqueued work
+    gather_states_kernel<<<1, 128, 0, b->stream>>>(b->bd.parts, 0, b->bd.sims, ns, nullptr,
+                                                   b->d_errs);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(b->h_errs, b->d_errs, sizeof(int) * ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < ns; ++i) {
+        lbib_status r = err_status(b->sims[i], b->h_errs[i]);
+        if (r != LBIB_OK) return r;
+    }
     return LBIB_OK;
 }
 

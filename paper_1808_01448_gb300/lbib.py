@@ -114,6 +114,7 @@ def lib():
                 "lbib_batch_step_flushed": [vp, i64, vp, C.c_size_t, i32, pd],
                 "lbib_batch_set_particle_threads": [vp, i32],
                 "lbib_batch_read_particles_async": [vp],
+                "lbib_batch_synchronize": [vp],
                 "lbib_batch_read_particles": [vp, C.POINTER(ParticleState), i32, C.POINTER(i32),
                                               C.POINTER(C.c_size_t)],
                 "lbib_batch_autotune": [vp, i32, C.POINTER(i32), pd],
@@ -363,9 +364,9 @@ class Batch:
         _check(lib().lbib_batch_set_timing(self._h, int(nsamples)))
 
     def synchronize(self):
-        """Wait for the batch's work; raises on a member's device error."""
-        for s in self.sims:
-            s.synchronize()
+        """Wait for the batch's work; raises on a member's device error (one
+        copy of the members' error words, ``lbib_batch_synchronize``)."""
+        _check(lib().lbib_batch_synchronize(self._h))
 
     def kernel_times(self):
         ms = (C.c_double * 3)(); cnt = (C.c_int64 * 3)()

@@ -200,3 +200,29 @@ def test_async_readback_gives_the_states_when_started(L):
     bb.close()
     for s in a + b:
         s.close()
+
+
+def test_batch_synchronize_reports_a_member_error(L):
+    """A batch's synchronize (one copy of the members' error words) reports
+    an unstable member and stays quiet for a stable batch, and it leaves a
+    started readback pending."""
+    sweep = W.design_sweep()[:3]
+    good = [make(L, c, p) for c, p in sweep]
+    b = L.Batch(good)
+    b.step(5)
+    b.read_particles_async()
+    b.step(5)
+    b.synchronize()
+    at5 = b.particles()             # the readback started after 5 steps
+    at10 = b.particles()
+    assert len(at5) == len(at10) == 3 and at5 != at10
+    b.close()
+    bad = L.Sim(nx=32, ny=16, wall_bottom="periodic", wall_top="periodic", tau=0.51, gx=0.2)
+    mixed = L.Batch([good[0], bad])
+    mixed.step(300)
+    with pytest.raises(L.LbibError) as e:
+        mixed.synchronize()
+    assert e.value.status == "E_UNSTABLE"
+    mixed.close()
+    for s in good + [bad]:
+        s.close()
