@@ -139,7 +139,7 @@ struct BatchDev {
 // Stochastic rounding of 16-bit stores.  A node's dither word is a hash of
 // its index and of the bits of its first post-collision deviation (so it is
 // deterministic and independent of the batch), spread over the nine planes
-// by multiplicative hashing; the top bits of r_i dither the bits that the
+// by one affine map each; the top bits of r_i dither the bits that the
 // conversion drops: FP32 -> FP16 (normal range) drops 13 mantissa bits,
 // FP32 -> BF16 drops 16.  Adding a uniform integer below 2^b to the FP32
 // bit pattern and truncating rounds up with probability equal to the
@@ -156,7 +156,8 @@ __device__ __forceinline__ unsigned dither_word(int k, float d0) {
     return mix32((unsigned)k * 0x9e3779b9u ^ __float_as_uint(d0));
 }
 __device__ __forceinline__ unsigned dither_plane(unsigned h, int i) {
-    return (h ^ ((unsigned)i * 0x632be5abu)) * 0x85ebca6bu;
+    // an affine bijection per plane (odd multiplier): one multiply-add
+    return h * (0x9e3779b1u + 0x3c6ef372u * (unsigned)i) + 0x7f4a7c15u * (unsigned)(i + 1);
 }
 __device__ __forceinline__ __half half_sr(float x, unsigned r) {
     return __float2half_rz(__uint_as_float(__float_as_uint(x) + (r >> 19)));
