@@ -208,6 +208,24 @@ def run_reference(args):
 
 # ---- GPU arm -------------------------------------------------------------------
 
+def max_over_ranks(x, device):
+    """The largest x over the ranks of the default process group (x itself
+    without one): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(world, nodes, steps, ms):
+    """Whole-job rate: every rank updates `nodes` nodes per step (replicas),
+    all ranks within the slowest rank's `ms`."""
+    return world * nodes * steps / (ms * 1e-3) / 1e6
+
+
 def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="stochastic"):
     """The same workload with another storage format: step time, MLUPS and
     the bulk lattice pass against the HBM roofline at its bytes per update."""
@@ -322,11 +340,8 @@ def run_gpu(args):
     pn = batch.pass_nodes()
     for s in sims:
         s.synchronize()             # raises on a device-side error
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, "cuda")
+    value = aggregate_mlups(world, nodes, args.steps, ms)
 
     # end to end through the C ABI with host buffers: fresh simulations, the
     # initial populations uploaded from pinned host memory, K steps in chunks
@@ -361,10 +376,10 @@ def run_gpu(args):
         eb.particles()
         d2h += eb.last_d2h_bytes
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        e2e = {"value": nodes * args.steps / dt / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": 9 * nodes * 8 / args.steps,
-               "d2h_bytes_per_step": d2h / args.steps}
+        dt = max_over_ranks(time.perf_counter() - t0, "cuda")
+        e2e = {"value": aggregate_mlups(world, nodes, args.steps, dt * 1e3), "unit": "MLUPS",
+               "h2d_bytes_per_step": world * 9 * nodes * 8 / args.steps,
+               "d2h_bytes_per_step": world * d2h / args.steps}
         eb.close()
         for s in e2e_sims:
             s.close()
