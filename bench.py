@@ -35,9 +35,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_UPDATE = {"f32": 72, "f64": 144, "f16": 36, "bf16": 36}
-WORKLOAD = ("batched design sweep: 72 sims (circle/AR2/AR3 x ligand {0.3,0.5,0.7,0.9} x "
-            "sigma {1,2} x Re {0.01,0.1,1}), lattices 256x64..1024x256, 7.43 M nodes, "
-            "one particle each")
+WORKLOADS = {
+    "sweep72": ("batched design sweep: 72 sims (circle/AR2/AR3 x ligand {0.3,0.5,0.7,0.9} x "
+                "sigma {1,2} x Re {0.01,0.1,1}), lattices 256x64..1024x256, 7.43 M nodes, "
+                "one particle each", "256x64..1024x256"),
+    "ellipse6": ("single ellipse AR2/AR3 x Re{0.01,0.1,1}, 1024x256 D2Q9, ligand 0.7, sigma 2, "
+                 "6 sims batched", "1024x256"),
+}
+
+
+def workload_cases(name):
+    from paper_1808_01448_gb300 import workloads as W
+    return W.design_sweep() if name == "sweep72" else W.single_ellipse_sweep()
 
 
 def env_int(k, d):
@@ -126,9 +135,9 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def build_workload(L, W, storage, stream, allocator, rounding="stochastic"):
+def build_workload(L, W, storage, stream, allocator, rounding="stochastic", name="sweep72"):
     sims = []
-    for cfg, parts in W.design_sweep():
+    for cfg, parts in workload_cases(name):
         s = L.Sim(storage=storage, stream=stream, allocator=allocator, rounding=rounding, **cfg)
         for p in parts:
             s.add_particle(**p)
@@ -139,11 +148,10 @@ def build_workload(L, W, storage, stream, allocator, rounding="stochastic"):
 # ---- CPU oracle baseline -----------------------------------------------------
 
 def _oracle_worker(args):
-    idx, steps = args
+    name, idx, steps = args
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
-    from paper_1808_01448_gb300 import workloads as W
-    cfg, parts = W.design_sweep()[idx]
+    cfg, parts = workload_cases(name)[idx]
     s = O.OracleSim(**cfg)
     for p in parts:
         s.add_particle(**p)
@@ -154,25 +162,27 @@ def _oracle_worker(args):
     return cfg["nx"] * cfg["ny"] * steps, dt
 
 
-def cpu_baseline(steps_per_sim, nsims=12):
+def cpu_baseline(steps_per_sim, name="sweep72", nsims=12):
     """The oracle as it stands (single-threaded C, FP64), one process per
-    simulation of an evenly spaced sample of the workload's 72, started with
-    spawn; the rate is the sample's node updates over the slowest process's
-    time."""
+    simulation of an evenly spaced sample of the workload's simulations (at
+    most nsims), started with spawn; the rate is the sample's node updates
+    over the slowest process's time."""
     from oracle import oracle as O
     O.build()
+    total = len(workload_cases(name))
+    nsims = min(nsims, total)
     cores = min(nsims, os.cpu_count() or 1)
-    pick = [round(i * 72 / nsims) for i in range(nsims)]
+    pick = [round(i * total / nsims) for i in range(nsims)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_worker, [(i, steps_per_sim) for i in pick])
+        res = pool.map(_oracle_worker, [(name, i, steps_per_sim) for i in pick])
     wall = time.perf_counter() - t0
     updates = sum(r[0] for r in res)
     busy = max(r[1] for r in res) if cores >= nsims else sum(r[1] for r in res) / cores
     return {"value": updates / busy / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{nsims} of the 72 sims (every {72 // nsims}th) x {steps_per_sim} steps, "
-                      f"{cores} processes (wall {wall:.1f} s incl. setup)"}
+            "sample": f"{nsims} of the {total} sims (every {total // nsims}th) x "
+                      f"{steps_per_sim} steps, {cores} processes (wall {wall:.1f} s incl. setup)"}
 
 
 def run_reference(args):
@@ -188,14 +198,16 @@ def run_reference(args):
     per_step_s = 0.06               # the largest sim (1024 x 256) per oracle step
     cap = max(1, int(150.0 / per_step_s))
     k_run = min(args.steps, cap)
-    base = cpu_baseline(k_run + args.warmup * 0)
+    base = cpu_baseline(k_run + args.warmup * 0, args.workload)
+    nodes = sum(c["nx"] * c["ny"] for c, _ in workload_cases(args.workload))
     line = {
         "metric": "aggregate MLUPS + % HBM roofline (FP32 vs FP16-storage), p50/p99 sim latency",
         "impl": "reference", "value": base["value"], "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 7432960 / (base["value"] * 1e6) * 1e3,
+        "ms_per_step": nodes / (base["value"] * 1e6) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "storage": "f64 (oracle)"},
+        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0],
+                                        "storage": "f64 (oracle)"},
         "cpu_baseline": base,
         "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -226,11 +238,12 @@ def aggregate_mlups(world, nodes, steps, ms):
     return world * nodes * steps / (ms * 1e-3) / 1e6
 
 
-def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="stochastic"):
+def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="stochastic",
+                name="sweep72"):
     """The same workload with another storage format: step time, MLUPS and
     the bulk lattice pass against the HBM roofline at its bytes per update."""
     import torch
-    sims = build_workload(lbib, W, storage, stream.cuda_stream, alloc, rounding)
+    sims = build_workload(lbib, W, storage, stream.cuda_stream, alloc, rounding, name)
     nodes = sum(s.nx * s.ny for s in sims)
     b = lbib.Batch(sims)
     b.step(2)
@@ -302,11 +315,11 @@ def run_gpu(args):
     # the oracle pool is spawned before any GPU work
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(args.cpu_steps)
+        base = cpu_baseline(args.cpu_steps, args.workload)
     lbib.lib()
     stream = torch.cuda.Stream()
     alloc = lbib.torch_allocator()
-    sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc)
+    sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc, name=args.workload)
     nodes = sum(s.nx * s.ny for s in sims)
     batch = lbib.Batch(sims)
     # pick the lattice-pass kernel variant on this batch (timing runs only)
@@ -348,7 +361,8 @@ def run_gpu(args):
     # of 128 with all particle states read back to the host after each chunk
     e2e = None
     if rank == 0 or world > 1:
-        e2e_sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc)
+        e2e_sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc,
+                                  name=args.workload)
         w9 = torch.tensor([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, dtype=torch.float64)
         f0 = {}                     # pinned initial populations, one per lattice shape
         for s in e2e_sims:
@@ -388,9 +402,9 @@ def run_gpu(args):
     legs = {}
     if rank == 0 and args.storage == "f32" and args.storage_steps > 0:
         legs["fp16_storage"] = storage_leg(lbib, W, "f16", stream, alloc, args.storage_steps,
-                                           args.warmup, peak)
+                                           args.warmup, peak, name=args.workload)
         legs["bf16_storage"] = storage_leg(lbib, W, "bf16", stream, alloc, args.storage_steps,
-                                           args.warmup, peak)
+                                           args.warmup, peak, name=args.workload)
     if rank == 0 and args.serve_requests > 0:
         legs["latency"] = serving_leg(lbib, W, args.serve_requests, alloc, args.serve_quantum)
 
@@ -407,11 +421,16 @@ def run_gpu(args):
             "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattices": "256x64..1024x256", "nodes": nodes,
+            "config": {"workload": WORKLOADS[args.workload][0],
+                       "lattices": WORKLOADS[args.workload][1], "nodes": nodes,
                        "sims": len(sims),
                        "storage": args.storage,
                        "l2": (f"inputs larger than L2, no flush: {nodes * bpu / 1e6:.0f} MB of "
-                              f"populations (two buffers) vs {l2_mib:.0f} MiB L2"),
+                              f"populations (two buffers) vs {l2_mib:.0f} MiB L2"
+                              if nodes * bpu > l2_mib * 2**20 else
+                              f"inputs smaller than L2 ({nodes * bpu / 1e6:.0f} MB of populations "
+                              f"vs {l2_mib:.0f} MiB), steps back to back without a flush: "
+                              f"not a cold-cache timing"),
                        "parallelism": f"replicas x{world}"},
             "hbm_roofline_frac_of_step": value * 1e6 * bpu / (peak * 1e9) / world,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -450,6 +469,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=60,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--serve-quantum", type=int, default=1000)
+    ap.add_argument("--workload", default="sweep72", choices=sorted(WORKLOADS),
+                    help="sweep72: the 72-channel design sweep (inputs larger than L2); "
+                         "ellipse6: six 1024x256 channels (inputs fit in L2)")
     ap.add_argument("--variant", type=int, default=None,
                     help="lattice-pass kernel variant instead of the autotuner's choice")
     args = ap.parse_args()
