@@ -300,8 +300,8 @@ __device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, i
 template <typename S, typename R, typename F>
 __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const Points<R> &pt,
                                             int l, const R *mr, const R *mjx, const R *mjy,
-                                            const int4 *span, int Tm, int rx0, int ry0,
-                                            F &&f) {
+                                            const int4 *span, const int *pre, int cap, int Tm,
+                                            int rx0, int ry0, F &&f) {
     const int rows = pt.rows[l];
     if (!(rows & 16)) return;
     const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l], mu_v = pt.mu_v[l];
@@ -324,15 +324,19 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
         const R py = wy * ((R)1 - dyc * mu_v);
         const int v = iy0 + b - ry0;
         // the row's staged spans (none outside the region)
-        const int4 q = (unsigned)v < (unsigned)Tm ? span[v] : make_int4(0, -1, 0, -1);
+        const bool inr = (unsigned)v < (unsigned)Tm;
+        const int4 q = inr ? span[v] : make_int4(0, -1, 0, -1);
+        const int p0 = inr ? pre[v] : 0, n0 = max(q.y - q.x + 1, 0);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const R w = wx[a] * wy;
             if (w == (R)0) continue;
             const int u = ix0 + a - rx0;
             R drho, jx, jy;
-            if ((u >= q.x && u <= q.y) || (u >= q.z && u <= q.w)) {
-                const int i = v * Tm + u;
+            // staging index of (u, v) in the row's spans (-1: not staged)
+            const int i = (u >= q.x && u <= q.y) ? p0 + (u - q.x)
+                          : (u >= q.z && u <= q.w) ? p0 + n0 + (u - q.z) : -1;
+            if (i >= 0 && i < cap) {
                 drho = mr[i];
                 jx = mjx[i];
                 jy = mjy[i];
@@ -365,9 +369,19 @@ template <> struct Pair<double> { using type = double2; };
 
 // The spreading contributions (16 pairs per marker) reuse the staged
 // moments' space when they fit in it.
+// Staged nodes a particle keeps in shared memory: its band's span nodes in
+// staging order (row by row, each row's spans in turn), at most this many;
+// nodes past it are pulled from global memory with the same arithmetic.  A
+// band is about ten nodes wide along the outline, so 16 per element plus 8
+// per region row covers it; a dense Tm x Tm box never needs more.
+__host__ __device__ __forceinline__ int stage_cap(int nl, int Tm) {
+    const long long c = 16ll * nl + 8ll * Tm, box = (long long)Tm * Tm;
+    return (int)(c < box ? c : box);
+}
+
 template <typename R>
-__host__ __device__ __forceinline__ bool spread_in_moments(int nl, int Tm) {
-    const size_t m = ((sizeof(R) * (size_t)Tm * Tm + 15) & ~size_t(15)) * 3;
+__host__ __device__ __forceinline__ bool spread_in_moments(int nl, int cap) {
+    const size_t m = ((sizeof(R) * (size_t)cap + 15) & ~size_t(15)) * 3;
     return 32 * sizeof(R) * (size_t)nl <= m;
 }
 
@@ -375,10 +389,11 @@ template <typename R>
 size_t smem_bytes_for(int nl, int T) {
     auto up = [](size_t b) { return (b + 15) & ~size_t(15); };
     const size_t Tm = (size_t)region_edge(T);
+    const size_t cap = (size_t)stage_cap(nl, (int)Tm);
     // the staged moments (and, where they do not fit there, the spreading
     // contributions) are laid out last
-    const size_t moments = 3 * up(sizeof(R) * Tm * Tm);
-    const size_t spread = spread_in_moments<R>(nl, (int)Tm) ? 0 : 32 * sizeof(R) * (size_t)nl;
+    const size_t moments = 3 * up(sizeof(R) * cap);
+    const size_t spread = spread_in_moments<R>(nl, (int)cap) ? 0 : 32 * sizeof(R) * (size_t)nl;
     return up(sizeof(Pose<R>)) + 21 * up(sizeof(R) * nl) + 3 * up(sizeof(int) * nl) + up(nl) +
            up(sizeof(int) * nl) + up(sizeof(int) * (nl + 1)) + up(sizeof(R) * 2 * T * T) +
            up(sizeof(double) * 3 * (P_THREADS / 32)) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread;
@@ -469,12 +484,14 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     int4 *span = (int4 *)take(sizeof(int4) * Tm);       // staged spans per region row
     int *pre = (int *)take(sizeof(int) * (Tm + 1));     // staged nodes before each row
     R *tile = (R *)take(sizeof(R) * 2 * T * T);
-    // staged moments of the region, last (the spreading contributions follow
-    // them when they do not fit in their space)
-    const size_t mstride = (sizeof(R) * Tm * Tm + 15) / 16 * 16 / sizeof(R);
-    R *mr = (R *)take(sizeof(R) * Tm * Tm);
-    R *mjx = (R *)take(sizeof(R) * Tm * Tm);
-    R *mjy = (R *)take(sizeof(R) * Tm * Tm);
+    // staged moments of the band's span nodes in staging order, at most cap of
+    // them, last (the spreading contributions follow them when they do not
+    // fit in their space)
+    const int cap = stage_cap(nl, Tm);
+    const size_t mstride = (sizeof(R) * (size_t)cap + 15) / 16 * 16 / sizeof(R);
+    R *mr = (R *)take(sizeof(R) * (size_t)cap);
+    R *mjx = (R *)take(sizeof(R) * (size_t)cap);
+    R *mjy = (R *)take(sizeof(R) * (size_t)cap);
 
     const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -693,7 +710,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     // populations of this step come from the lattice pass just before: wait
     // for it here (everything above reads only particle and geometry data)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int nlist = pre[Tm];
+    const int nlist = min(pre[Tm], cap);
 #pragma unroll 2
     for (int k = tid; k < nlist; k += PT) {
         // staged node k: row v is the last with pre[v] <= k, then its spans
@@ -706,7 +723,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
         const int4 q = span[v];
         const int n0 = max(q.y - q.x + 1, 0), o = k - pre[v];
         const int u = o < n0 ? q.x + o : q.z + (o - n0);
-        const int i = v * Tm + u;
+        const int i = k;
         int xx = (rx0 + u) % s.nx;
         if (xx < 0) xx += s.nx;
         int yy = ry0 + v;
@@ -749,7 +766,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             const int l = tid;
             // (its support was set up with the staging)
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, Tm, rx0, ry0,
+            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
                               [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
                                   const R irho = recip_rho((R)1 + drho);
                                   const R ux = jx * irho, uy = jy * irho;
@@ -835,7 +852,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
         const int l = tid;
         setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l], ps.fyc + ry[l], pt, l);
         R s_rho = 0, s_u = 0, s_v = 0;
-        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, Tm, rx0, ry0,
+        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
                           [&](R, R, R, R phi, R drho, R jx, R jy) {
                               const R irho = recip_rho((R)1 + drho);
                               s_rho += phi * drho;
@@ -854,7 +871,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     // waits for this pass to end before it reads the tiles)
     asm volatile("griddepcontrol.launch_dependents;");
     using R2 = typename Pair<R>::type;
-    R2 *ctb = spread_in_moments<R>(nl, Tm) ? (R2 *)mr : (R2 *)(mr + 3 * mstride);
+    R2 *ctb = spread_in_moments<R>(nl, cap) ? (R2 *)mr : (R2 *)(mr + 3 * mstride);
     const int ox = ps.ixc - T / 2;
     const int oy = ps.iyc - T / 2;
     // phi_(a,b) = wx[a] py[b] of marker l, as in support_sum (zero without a
