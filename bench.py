@@ -15,8 +15,9 @@ the HBM roofline at 72 B per FP32 lattice update.  Under torchrun every rank
 runs the same 72 simulations on its own GPU (independent replicas, no
 collective on the data path); value is the total over ranks.
 
---impl reference times the FP64 CPU oracle on a sample of the same
-workload.
+--workload ellipse6 times the six 1024 x 256 channels instead (their 113 MB
+of populations fit in L2, which the line's config says).  --impl reference
+times the FP64 CPU oracle on a sample of the same workload.
 """
 from __future__ import annotations
 
