@@ -87,6 +87,10 @@ typedef struct or_particle {
     double sigma, area, mass, inertia, r_eq;
     double Fh[2], Mh, Fb[2], Mb, Fw[2];
     int n_ligands, n_probing, n_bonded;
+    /* near-tie diagnostics of the last bond step (they change no result):
+     * the smallest |U - P| over the draws compared with a probability, and
+     * the smallest |gap - y_cr| over the ligands' probing tests */
+    double margin_p, margin_gap;
 } or_particle;
 
 struct or_sim {
@@ -214,6 +218,7 @@ int or_add_particle(or_sim *s, const or_particle_in *in) {
     p->inertia = in->rho_p * J;
     p->r_eq = sqrt(A / M_PI);
     p->sigma = in->sigma;
+    p->margin_p = p->margin_gap = INFINITY;
     p->xc = p->xc1 = in->xc;
     p->yc = p->yc1 = in->yc;
     p->theta = p->theta1 = in->theta;
@@ -573,12 +578,15 @@ static void bonds(or_sim *s, int pid, const double *mx, const double *my) {
     int has_t = c->wall_top != OR_WALL_PERIODIC && c->receptor_top > 0.0;
     double y_eq = c->y_eq_ratio * c->y_cr;
     double sigma_star = c->sigma_star_ratio * p->sigma;
+    double mp = INFINITY, mg = INFINITY;
     int nprobe = 0;
     for (int l = 0; l < p->nv; ++l) {
         if (!p->ligand[l]) continue;
         int pb = has_b && (my[l] - yb) < c->y_cr;
         int pt = has_t && (yt - my[l]) < c->y_cr;
         nprobe += (pb || pt);
+        if (has_b) mg = fmin(mg, fabs((my[l] - yb) - c->y_cr));
+        if (has_t) mg = fmin(mg, fabs((yt - my[l]) - c->y_cr));
     }
     double Nl = (double)nprobe / (double)p->nv;
     for (int l = 0; l < p->nv; ++l) {
@@ -589,6 +597,7 @@ static void bonds(or_sim *s, int pid, const double *mx, const double *my) {
             double dx = p->anchor_x[l] - mx[l], dy = wy - my[l];
             double y = sqrt(dx * dx + dy * dy);
             double Pr = or_prob_reverse(c->k_r0, p->sigma, sigma_star, y, y_eq, c->kBT);
+            mp = fmin(mp, fabs(U - Pr));
             if (U < Pr) p->bond[l] = 0;
         } else {
             int pb = has_b && (my[l] - yb) < c->y_cr;
@@ -596,6 +605,7 @@ static void bonds(or_sim *s, int pid, const double *mx, const double *my) {
             if (pb || pt) {
                 double dens = pb ? c->receptor_bottom : c->receptor_top;
                 double Pf = or_prob_forward(c->k_f * dens, Nl);
+                mp = fmin(mp, fabs(U - Pf));
                 if (U < Pf) {
                     p->bond[l] = 1;
                     p->anchor_x[l] = mx[l];
@@ -627,6 +637,8 @@ static void bonds(or_sim *s, int pid, const double *mx, const double *my) {
     p->Mb = M;
     p->n_probing = nprobe;
     p->n_bonded = nb;
+    p->margin_p = mp;
+    p->margin_gap = mg;
 }
 
 /* Eq. 12: F_w = H_k / (8 sqrt 2) sqrt(r / eps^5) along the wall normal into
@@ -834,13 +846,30 @@ int or_particle_get(const or_sim *s, int pid, or_particle_state *o) {
     o->area = p->area; o->mass = p->mass; o->inertia = p->inertia; o->r_eq = p->r_eq;
     o->nl = p->nv; o->n_ligands = p->n_ligands;
     o->n_probing = p->n_probing; o->n_bonded = p->n_bonded;
+    o->margin_p = p->margin_p; o->margin_gap = p->margin_gap;
     return 0;
 }
 
-int or_bonds_get(const or_sim *s, int pid, uint8_t *bond, double *anchor_x) {
+int or_bonds_get(const or_sim *s, int pid, uint8_t *bond, double *anchor_x,
+                 int8_t *anchor_wall) {
     if (!s || pid < 0 || pid >= s->np) return -1;
     const or_particle *p = &s->p[pid];
     if (bond) memcpy(bond, p->bond, p->nv);
     if (anchor_x) memcpy(anchor_x, p->anchor_x, p->nv * sizeof(double));
+    if (anchor_wall) memcpy(anchor_wall, p->anchor_wall, p->nv);
+    return 0;
+}
+
+/* Overwrites a particle's bond state (bond flag, anchor x and anchor wall of
+ * every element), e.g. to place a known bond before a step. */
+int or_bonds_set(or_sim *s, int pid, const uint8_t *bond, const double *anchor_x,
+                 const int8_t *anchor_wall) {
+    if (!s || pid < 0 || pid >= s->np || !bond || !anchor_x || !anchor_wall) return -1;
+    or_particle *p = &s->p[pid];
+    for (int l = 0; l < p->nv; ++l) {
+        p->bond[l] = bond[l] ? 1 : 0;
+        p->anchor_x[l] = anchor_x[l];
+        p->anchor_wall[l] = anchor_wall[l] ? 1 : 0;
+    }
     return 0;
 }

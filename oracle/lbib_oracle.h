@@ -59,6 +59,10 @@ typedef struct or_particle_state {
     double Fw[2];                    /* wall force (Eq. 12) */
     double area, mass, inertia, r_eq;
     int32_t nl, n_ligands, n_probing, n_bonded;
+    /* near-tie diagnostics of the last bond step (no effect on results):
+     * smallest |U - P| over the draws compared with P_f or P_r, and smallest
+     * |gap - y_cr| over the ligands' probing tests (inf when there was none) */
+    double margin_p, margin_gap;
 } or_particle_state;
 
 typedef struct or_sim or_sim;
@@ -78,7 +82,12 @@ int or_fields(or_sim *s, double *rho, double *ux, double *uy);
 /* current IB force density [ny][nx] for each component */
 int or_ib_force(or_sim *s, double *fx, double *fy);
 int or_particle_get(const or_sim *s, int pid, or_particle_state *out);
-int or_bonds_get(const or_sim *s, int pid, uint8_t *bond, double *anchor_x);
+/* bond flag, anchor x and anchor wall (0 bottom, 1 top) of every element;
+ * any pointer may be NULL */
+int or_bonds_get(const or_sim *s, int pid, uint8_t *bond, double *anchor_x,
+                 int8_t *anchor_wall);
+int or_bonds_set(or_sim *s, int pid, const uint8_t *bond, const double *anchor_x,
+                 const int8_t *anchor_wall);
 
 /* --- building blocks (used by the sim, exported for the pins) ------------ */
 void or_lattice(int32_t *ex, int32_t *ey, double *w, int32_t *opp);

@@ -76,6 +76,7 @@ class OrParticleState(C.Structure):
         ("r_eq", C.c_double),
         ("nl", C.c_int32), ("n_ligands", C.c_int32), ("n_probing", C.c_int32),
         ("n_bonded", C.c_int32),
+        ("margin_p", C.c_double), ("margin_gap", C.c_double),
     ]
 
 
@@ -101,7 +102,10 @@ def lib():
                 "or_fields": (C.c_int, [C.c_void_p, pd, pd, pd]),
                 "or_ib_force": (C.c_int, [C.c_void_p, pd, pd]),
                 "or_particle_get": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(OrParticleState)]),
-                "or_bonds_get": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint8), pd]),
+                "or_bonds_get": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint8), pd,
+                                           C.POINTER(C.c_int8)]),
+                "or_bonds_set": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint8), pd,
+                                           C.POINTER(C.c_int8)]),
                 "or_lattice": (None, [pi32, pi32, pd, pi32]),
                 "or_equilibrium": (None, [d, d, d, pd]),
                 "or_guo_source": (None, [d, d, d, d, d, pd]),
@@ -212,11 +216,25 @@ class OracleSim:
             out[k] = tuple(out[k])
         return out
 
-    def bonds(self, pid=0):
+    def bonds(self, pid=0, walls=False):
+        """Bond flags and anchor x of every element (and, with walls=True,
+        the anchor wall: 0 bottom, 1 top)."""
         n = self.particle(pid)["nl"]
-        b = np.zeros(n, dtype=np.uint8); ax = np.zeros(n)
-        lib().or_bonds_get(self._h, pid, b.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(ax))
-        return b, ax
+        b = np.zeros(n, dtype=np.uint8); ax = np.zeros(n); aw = np.zeros(n, dtype=np.int8)
+        lib().or_bonds_get(self._h, pid, b.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(ax),
+                           aw.ctypes.data_as(C.POINTER(C.c_int8)))
+        return (b, ax, aw) if walls else (b, ax)
+
+    def set_bonds(self, pid, bond, anchor_x, anchor_wall):
+        n = self.particle(pid)["nl"]
+        b = np.ascontiguousarray(bond, dtype=np.uint8)
+        ax = np.ascontiguousarray(anchor_x, dtype=np.float64)
+        aw = np.ascontiguousarray(anchor_wall, dtype=np.int8)
+        if not (len(b) == len(ax) == len(aw) == n):
+            raise ValueError(f"particle {pid} has {n} elements")
+        if lib().or_bonds_set(self._h, pid, b.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(ax),
+                              aw.ctypes.data_as(C.POINTER(C.c_int8))) != 0:
+            raise RuntimeError("or_bonds_set failed")
 
 
 # ---- building blocks -------------------------------------------------------
