@@ -239,6 +239,25 @@ def aggregate_mlups(world, nodes, steps, ms):
     return world * nodes * steps / (ms * 1e-3) / 1e6
 
 
+SAMPLE_GRAPHS = 16        # graph slots of the kernel-time sampler (lbib_batch_set_timing)
+MIN_IN_REGION = 8         # in-region samples needed before they alone give the roofline
+E2E_MIN_STEPS = 2048      # horizon of the end-to-end leg (a simulation request's length)
+
+
+def bulk_timing(batch, kt_region):
+    """Kernel times for the roofline: the samples taken inside the timed
+    region (CUDA events around the kernels of one step per graph replay, and
+    of the middle step of a call's steps outside a graph) when there are at
+    least MIN_IN_REGION, else a sampled run of SAMPLE_GRAPHS graphs of 32
+    steps right after the timed region, on the same batch and stream."""
+    if kt_region["lattice_n"] >= MIN_IN_REGION:
+        return kt_region, f"in the timed region ({kt_region['lattice_n']} sampled steps)"
+    batch.step(32 * SAMPLE_GRAPHS)
+    kt = batch.kernel_times()
+    return kt, (f"sampled run of {32 * SAMPLE_GRAPHS} steps after the timed region "
+                f"({kt['lattice_n']} sampled steps; {kt_region['lattice_n']} in the region)")
+
+
 def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="stochastic",
                 name="sweep72"):
     """The same workload with another storage format: step time, MLUPS and
@@ -249,7 +268,7 @@ def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="
     b = lbib.Batch(sims)
     b.step(2)
     variant, _ = b.autotune(20)
-    b.set_timing(16)
+    b.set_timing(SAMPLE_GRAPHS)
     b.step(warmup)
     torch.cuda.synchronize()
     b.kernel_times()
@@ -259,7 +278,7 @@ def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    kt = b.kernel_times()
+    kt, source = bulk_timing(b, b.kernel_times())
     pn = b.pass_nodes()
     b.synchronize()
     bpu = BYTES_PER_UPDATE[storage]
@@ -273,6 +292,7 @@ def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="
             "hbm_roofline_frac_of_step": value * 1e6 * bpu / (peak * 1e9),
             "lattice_kernel_ms": kt["lattice_ms"], "particle_kernel_ms": kt["particle_ms"],
             "near_kernel_ms": kt["near_ms"], "lattice_variant": variant,
+            "kernel_timing": source, "bulk_le_step": kt["lattice_ms"] <= ms / steps,
             "roofline_achieved_gbs": ach, "roofline_frac": ach / peak if ach else None}
 
 
@@ -329,7 +349,7 @@ def run_gpu(args):
     if args.variant is not None:        # fixed choice (profiling runs)
         variant = args.variant
         batch.set_variant(variant)
-    batch.set_timing(16)
+    batch.set_timing(SAMPLE_GRAPHS)
     batch.step(args.warmup)
     torch.cuda.synchronize()
     batch.kernel_times()            # drop samples taken during warm-up
@@ -350,7 +370,7 @@ def run_gpu(args):
     barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    kt = batch.kernel_times()
+    kt, kt_source = bulk_timing(batch, batch.kernel_times())
     pn = batch.pass_nodes()
     for s in sims:
         s.synchronize()             # raises on a device-side error
@@ -358,9 +378,11 @@ def run_gpu(args):
     value = aggregate_mlups(world, nodes, args.steps, ms)
 
     # end to end through the C ABI with host buffers: fresh simulations, the
-    # initial populations uploaded from pinned host memory, K steps in chunks
-    # of 128 with all particle states read back to the host after each chunk
+    # initial populations uploaded from pinned host memory, max(K, 2048) steps
+    # (a request's length) in chunks of 128 with all particle states read back
+    # to the host after each chunk
     e2e = None
+    e2e_steps = max(args.steps, E2E_MIN_STEPS)
     if rank == 0 or world > 1:
         e2e_sims = build_workload(lbib, W, args.storage, stream.cuda_stream, alloc,
                                   name=args.workload)
@@ -379,8 +401,8 @@ def run_gpu(args):
         # every member's particle states after each chunk, one readback per
         # chunk, collected while the next chunk runs
         chunk, done, d2h, pending = 128, 0, 0, False
-        while done < args.steps:
-            n = min(chunk, args.steps - done)
+        while done < e2e_steps:
+            n = min(chunk, e2e_steps - done)
             eb.step(n)
             done += n
             if pending:
@@ -392,9 +414,11 @@ def run_gpu(args):
         d2h += eb.last_d2h_bytes
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, "cuda")
-        e2e = {"value": aggregate_mlups(world, nodes, args.steps, dt * 1e3), "unit": "MLUPS",
-               "h2d_bytes_per_step": world * 9 * nodes * 8 / args.steps,
-               "d2h_bytes_per_step": world * d2h / args.steps}
+        e2e = {"value": aggregate_mlups(world, nodes, e2e_steps, dt * 1e3), "unit": "MLUPS",
+               "h2d_bytes_per_step": world * 9 * nodes * 8 / e2e_steps,
+               "d2h_bytes_per_step": world * d2h / e2e_steps, "steps": e2e_steps,
+               "includes": "simulation and batch set-up, initial populations uploaded from "
+                           "pinned host memory, all particle states read back every 128 steps"}
         eb.close()
         for s in e2e_sims:
             s.close()
@@ -442,7 +466,9 @@ def run_gpu(args):
                          "near_kernel_ms": kt["near_ms"], "nodes_per_launch": pn["bulk"],
                          "lattice_variant": variant,
                          "variant_ms": [round(x, 5) for x in variant_ms],
-                         "samples": kt["lattice_n"]},
+                         "alone_ms": round(variant_ms[variant], 5),
+                         "samples": kt["lattice_n"], "timing": kt_source,
+                         "bulk_le_step": lat_ms <= ms / args.steps},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": base,
         }

@@ -22,6 +22,10 @@
  *    synchronise that stream.  A device-side error (a non-finite state, a
  *    bounded wait that ran out) is reported by the next call.
  *  - A handle is not thread-safe; different handles are independent.
+ *  - Device waits are bounded: a wait of the lattice pass on its staged
+ *    copies gives up after LBIB_WAIT_POLLS polls (environment variable read
+ *    when a batch is created; default 65536) and the next call reports
+ *    LBIB_E_TIMEOUT.  Calls show as NVTX ranges in profiler timelines.
  *  - Lattice units: dx = dt = 1, c_s^2 = 1/3, nu = (tau - 1/2) / 3.
  *  - Node arrays are row-major [ny][nx]; populations [9][ny][nx] with the
  *    D2Q9 order e_0 = (0,0), e_1..4 = (1,0), (0,1), (-1,0), (0,-1),
@@ -218,8 +222,11 @@ lbib_status lbib_batch_create(lbib_sim *const *sims, int32_t n, lbib_batch **out
 lbib_status lbib_batch_step(lbib_batch *b, int64_t nsteps);
 lbib_status lbib_batch_destroy(lbib_batch *b);
 /* Kernel timing with CUDA events: when nsamples > 0, later batch steps
- * record the duration of sampled kernels (event records inside the replayed
- * graphs).  lbib_batch_kernel_times fills mean_ms[3] and count[3] with the
+ * record the duration of the kernels of one sampled step (event records
+ * inside the replayed graphs, around the middle step of each graph of up to
+ * nsamples graphs in turn, and around the middle step of the steps a call
+ * runs outside a graph), so every stepping call takes at least one sample.
+ * lbib_batch_kernel_times fills mean_ms[3] and count[3] with the
  * mean duration (ms) and number of samples taken since the last call:
  * [0] the lattice pass (the bulk pass when particle work is overlapped),
  * [1] the particle pass, [2] the near-box lattice pass (0 samples when not
@@ -322,11 +329,52 @@ lbib_status lbib_read_bonds(lbib_sim *sim, int32_t pid, uint8_t *bond_host,
 /* IB force density of the current step on the lattice ([ny][nx] each). */
 lbib_status lbib_read_ib_force(lbib_sim *sim, double *fx_host, double *fy_host);
 
+/* Kinematic record of a particle: pose and velocities after the last
+ * completed step and one step earlier (the two levels the second-order
+ * update of Eq. 13-16 reads), and the particle's completed step count, the
+ * counter of its bond draws (Eq. 10-11). */
+typedef struct lbib_particle_record {
+    double xc, yc, theta, u, v, omega;
+    double xc1, yc1, theta1, u1, v1, omega1;
+    int64_t step;
+} lbib_particle_record;
+
+/* Read a particle's record (synchronises).  Errors: E_ARG, E_CUDA and a
+ * deferred device error. */
+lbib_status lbib_get_particle_record(lbib_sim *sim, int32_t pid, lbib_particle_record *out);
+
+/* Overwrite a particle's record (synchronises): the next step starts from
+ * this pose and history, and the IB forcing of that step is recomputed at
+ * the new pose from the current populations (what the end of a step leaves).
+ * Bonds and anchors are kept.  Used to prescribe a particle's motion or to
+ * replay a trajectory.  Errors: E_ARG (bad pid, non-finite values, negative
+ * step), E_CUDA. */
+lbib_status lbib_set_particle_record(lbib_sim *sim, int32_t pid, const lbib_particle_record *in);
+
+/* Checkpoints.  A checkpoint is a host blob holding everything later steps
+ * depend on: the post-collision populations in the storage format, the
+ * completed step count, and per particle its record, last loads and counts,
+ * bond flags and anchors.  lbib_checkpoint_size gives its size;
+ * lbib_checkpoint_save writes it into host memory of at least that size
+ * (synchronises; E_ARG if too small); lbib_checkpoint_load restores it into
+ * a simulation created with the same lattice, storage (and F16 scale) and
+ * particles added with the same element counts (E_ARG otherwise; nothing is
+ * changed then), recomputes the IB forcing of the coming step, and
+ * synchronises.  Stepping on from a loaded checkpoint gives the same bits as
+ * stepping on from the saved simulation. */
+lbib_status lbib_checkpoint_size(lbib_sim *sim, size_t *bytes);
+lbib_status lbib_checkpoint_save(lbib_sim *sim, void *host, size_t bytes);
+lbib_status lbib_checkpoint_load(lbib_sim *sim, const void *host, size_t bytes);
+
+/* Device memory the simulation holds now (populations, particles, scratch
+ * and its own stepping tables), in bytes; for admission control. */
+lbib_status lbib_device_bytes(lbib_sim *sim, size_t *bytes);
+
 /* Allocation-free IB forcing (no counterpart in the paper: a service for
- * callers that cannot allocate device memory -- code in host callbacks or
- * stream-ordered sections where cudaMalloc/cudaFree would synchronise or is
- * not allowed, plugins whose host application owns every device allocation,
- * loops that must not touch an allocator after start-up).
+ * callers that cannot allocate device memory -- plugins and solvers inside a
+ * host application that owns every device allocation through its own arena,
+ * and real-time loops that must not call an allocator, which can
+ * synchronise the device or fail under memory pressure, once running).
  *
  * Computes the IB force density f_ib of one rigid particle (the MLS direct
  * forcing of lbib_step's first pass, with desired marker velocity
@@ -341,12 +389,15 @@ lbib_status lbib_read_ib_force(lbib_sim *sim, double *fx_host, double *fy_host);
  * Allocates no device or host heap memory: its only scratch is one static
  * device array of 256 KiB that every GPU loading the library keeps until the
  * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  Calls share the array and each rewrites
+ * address (cudaGetSymbolAddress, once per device) with the device current;
+ * make that first call before any stream capture.  The call copies nothing
+ * from host memory: it enqueues three kernels on the stream (one writes the
+ * descriptors and tables, passed as kernel parameters, into the array) and
+ * returns without waiting for them.  Calls share the array and each rewrites
  * what it reads; calls whose work overlaps on the GPU (different streams)
- * race.  The call is asynchronous on the stream.  Errors: E_ARG (bad
- * arguments, or the particle needs more than the 256 KiB scratch or the
- * shared memory of one SM), E_CUDA, E_UNSUPPORTED (device index >= 64). */
+ * race.  Errors: E_ARG (bad arguments, or the particle needs more than the
+ * 256 KiB scratch or the shared memory of one SM), E_CUDA, E_UNSUPPORTED
+ * (device index >= 64). */
 lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float *f_dev,
                                   const lbib_particle *p, double u, double v, double omega,
                                   double *fx_dev, double *fy_dev);

@@ -9,10 +9,15 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbib_internal.cuh"
 
@@ -44,6 +49,24 @@ lbib_status cuda_fail(cudaError_t e, const char *what) {
         cudaError_t e_ = (call);                                        \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);             \
     } while (0)
+
+// NVTX range around a C-ABI call (visible in profilers' timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Polls of a bounded device wait (the copy-engine staging of the lattice
+// pass) before it gives up and reports LBIB_E_TIMEOUT: LBIB_WAIT_POLLS from
+// the environment when a batch is created (0 .. 2^24), else 65536.
+int wait_polls_setting() {
+    const char *e = getenv("LBIB_WAIT_POLLS");
+    if (!e || !*e) return 1 << 16;
+    char *end = nullptr;
+    const long v = strtol(e, &end, 10);
+    if (end == e || v < 0) return 1 << 16;
+    return (int)std::min<long>(v, 1 << 24);
+}
 
 // L2 clearing before a timed step: writing a buffer larger than L2 evicts
 // every line the step could reuse; reading it back then replaces the dirty
@@ -110,6 +133,7 @@ struct HostParticle {
     void *d_ecache = nullptr;        // its element record (inside d_block)
     double *d_pftab = nullptr;       // its P_f table (inside d_block)
     void *d_block = nullptr;         // geometry, bonds, tile
+    size_t d_bytes = 0;              // size of d_block
 };
 
 }  // namespace
@@ -154,6 +178,7 @@ struct lbib_batch {
     std::vector<int> replayed;          // slot replayed since the last read
     int next_slot = 0;
     lbib_config acfg{};                 // allocator hook used for d_block
+    size_t d_bytes = 0;                 // size of d_block
     bool is_self = false;
     bool orphan = false;                // a member was destroyed: the batch is unusable
     // overlapped stepping: the bulk lattice pass runs on s2 while the particle
@@ -198,9 +223,14 @@ void dfree(const lbib_config &c, cudaStream_t st, void *p) {
     else cudaFree(p);
 }
 
-SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
+// Device descriptor of a channel from its configuration, its two population
+// buffers (f - w of the storage type), its device words (current buffer,
+// completed steps, error bits; step and err may be null for a pass that
+// writes neither), its storage scale and its particles' range [p0, p0 + np)
+// in a batch table.
+SimDev simdev_from(const lbib_config &c, void *pop0, void *pop1, int *cur, long long *step,
+                   int *err, float scale, int p0, int np, int tile0) {
     SimDev d{};
-    const lbib_config &c = s->cfg;
     d.nx = c.nx; d.ny = c.ny; d.wall_b = c.wall_bottom; d.wall_t = c.wall_top;
     {
         int t = 0;
@@ -209,15 +239,15 @@ SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
         d.nx_m = (unsigned)((p2 + (unsigned long long)c.nx - 1) / (unsigned long long)c.nx);
         d.nx_s = t - 1;
     }
-    d.p0 = p0; d.np = (int)s->parts.size();
+    d.p0 = p0; d.np = np;
     d.tile0 = tile0;
-    d.ntiles = (int)((s->N + LB_TILE_NODES - 1) / LB_TILE_NODES);
+    d.ntiles = (int)(((size_t)c.nx * c.ny + LB_TILE_NODES - 1) / LB_TILE_NODES);
     d.tau = c.tau; d.u_b = c.u_bottom; d.u_t = c.u_top; d.gx = c.gx; d.gy = c.gy;
     d.k_f = c.k_f; d.k_r0 = c.k_r0; d.kBT = c.kBT; d.sigma_star_ratio = c.sigma_star_ratio;
     d.y_cr = c.y_cr; d.y_eq_ratio = c.y_eq_ratio; d.hamaker = c.hamaker; d.eps_min = c.eps_min;
     d.rec_b = c.receptor_bottom; d.rec_t = c.receptor_top;
     d.seed = c.seed; d.sim_id = c.sim_id;
-    d.scale = s->scale; d.inv_scale = 1.f / s->scale;
+    d.scale = scale; d.inv_scale = 1.f / scale;
     const double om = 1.0 / c.tau;
     d.d_om = om; d.d_pref = 1.0 - 0.5 * om;
     d.d_ub6 = c.u_bottom / 6.0; d.d_ut6 = c.u_top / 6.0;
@@ -226,13 +256,18 @@ SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
     d.f_ub = (float)c.u_bottom; d.f_ut = (float)c.u_top;
     d.f_ub6 = (float)d.d_ub6; d.f_ut6 = (float)d.d_ut6;
     d.d_nu = (c.tau - 0.5) / 3.0; d.f_nu = (float)d.d_nu;
-    d.pop[0] = s->pop[0]; d.pop[1] = s->pop[1];
-    d.cur = s->d_cur; d.step = s->d_step; d.err = s->d_err;
+    d.pop[0] = pop0; d.pop[1] = pop1;
+    d.cur = cur; d.step = step; d.err = err;
     // vector path: whole groups of four nodes per row, buffers 32-byte aligned
-    d.vec4 = c.nx % 4 == 0 && ((uintptr_t)s->pop[0] % 32) == 0 && ((uintptr_t)s->pop[1] % 32) == 0;
+    d.vec4 = c.nx % 4 == 0 && ((uintptr_t)pop0 % 32) == 0 && ((uintptr_t)pop1 % 32) == 0;
     d.sround = c.rounding == LBIB_ROUND_STOCHASTIC;
     d.ib_iters = c.ib_iterations > 1 ? c.ib_iterations : 1;
     return d;
+}
+
+SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
+    return simdev_from(s->cfg, s->pop[0], s->pop[1], s->d_cur, s->d_step, s->d_err, s->scale, p0,
+                       (int)s->parts.size(), tile0);
 }
 
 // Marker colouring for the spreading: two markers of one colour are at least
@@ -417,6 +452,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     unsigned char *blk = (unsigned char *)dalloc(s->cfg, s->stream, bytes);
     if (!blk) return fail(LBIB_E_OOM, "device allocation of %zu bytes for a particle failed", bytes);
     p.d_block = blk;
+    p.d_bytes = bytes;
     size_t off = 0;
     auto take = [&](size_t b) {
         unsigned char *q = blk + off;
@@ -548,6 +584,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     unsigned char *blk = (unsigned char *)dalloc(sims[0]->cfg, b->stream, bytes);
     if (!blk) { delete b; return fail(LBIB_E_OOM, "device allocation for the batch failed"); }
     b->d_block = blk;
+    b->d_bytes = bytes;
     size_t off = 0;
     auto take = [&](size_t sz) {
         unsigned char *q = blk + off;
@@ -654,6 +691,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         if (!hs[i].vec4 || hs[i].nx % per16 != 0 || hs[i].wall_b == LBIB_WALL_PERIODIC) tma_ok = 0;
     }
     b->bd.tma_ok = tma_ok;
+    b->bd.wait_polls = wait_polls_setting();
     if (tma_ok && (e = lattice_kernel_setup(b->kind)) != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e, "lattice kernel setup");
@@ -721,6 +759,14 @@ lbib_status prime(lbib_sim *s, cudaStream_t st) {
     return LBIB_OK;
 }
 
+// IB forcing recomputed at the particles' current poses from the current
+// populations (the init-mode particle pass), after their state was changed
+// from the host: what the end of a step leaves for the next one.
+lbib_status reprime(lbib_sim *s) {
+    s->primed = false;
+    return prime(s, s->stream);
+}
+
 // Prime the members of a batch.  A fresh user batch (no member primed yet)
 // takes one initial IB launch over all its particles instead of one launch
 // and one private batch per simulation; otherwise each member is primed on
@@ -755,26 +801,28 @@ lbib_status prime_members(lbib_batch *b) {
     return LBIB_OK;
 }
 
-// Enqueue nsteps steps.  ev (inside a capture only) receives event records
-// around the first step's kernels: lattice / bulk [0, 1], particle [2, 3],
-// near boxes [4, 5].
-cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
+// Enqueue nsteps steps.  ev (or null) receives event records around the
+// kernels of the middle step ks = nsteps / 2 (a step in the steady state of
+// the two-stream schedule): lattice / bulk [0, 1], particle [2, 3], near
+// boxes [4, 5].  capturing: the enqueue is being captured into a graph (the
+// records become event-record nodes).
+cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev, bool capturing = true) {
     cudaError_t e = cudaSuccess;
-    // inside a capture, external records become event-record nodes
-    const unsigned fl = cudaEventRecordExternal;
+    const unsigned fl = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    const int ks = nsteps / 2;
     auto mark = [&](int i, cudaStream_t st) {
         return (ev) ? cudaEventRecordWithFlags(ev[i], st, fl) : cudaSuccess;
     };
     if (!b->overlap) {
         for (int k = 0; k < nsteps; ++k) {
             const int f = k & 1;
-            if (k == 0 && (e = mark(0, b->stream))) return e;
+            if (k == ks && (e = mark(0, b->stream))) return e;
             if ((e = launch_lattice(b->kind, b->bd, f, 0, b->stream))) return e;
-            if (k == 0 && (e = mark(1, b->stream))) return e;
-            if (k == 0 && (e = mark(2, b->stream))) return e;
+            if (k == ks && (e = mark(1, b->stream))) return e;
+            if (k == ks && (e = mark(2, b->stream))) return e;
             if ((e = launch_particles(b->kind, b->bd, f ^ 1, 2, b->smem, b->stream))) return e;
-            if (k == 0 && (e = mark(3, b->stream))) return e;
-            if (ev && k == 0 && ((e = mark(4, b->stream)) || (e = mark(5, b->stream)))) return e;
+            if (k == ks && (e = mark(3, b->stream))) return e;
+            if (ev && k == ks && ((e = mark(4, b->stream)) || (e = mark(5, b->stream)))) return e;
         }
         return e;
     }
@@ -790,23 +838,25 @@ cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
     for (int k = 0; k < nsteps; ++k) {
         const int f = k & 1;
         if (k > 0 && (e = cudaStreamWaitEvent(b->s2, b->evn[(k - 1) & 1], 0))) return e;
-        if (k == 0 && (e = mark(0, b->s2))) return e;
+        if (k == ks && (e = mark(0, b->s2))) return e;
         if ((e = launch_lattice(b->kind, b->bd, f, 1, b->s2))) return e;
-        if (k == 0 && (e = mark(1, b->s2))) return e;
+        if (k == ks && (e = mark(1, b->s2))) return e;
         if ((e = cudaEventRecord(b->evb[k & 1], b->s2))) return e;
         if (k > 0 && (e = cudaStreamWaitEvent(b->s1, b->evb[(k - 1) & 1], 0))) return e;
-        if (k == 0 && (e = mark(4, b->s1))) return e;
+        if (k == ks && (e = mark(4, b->s1))) return e;
         // programmatic dependent of the particle pass of the step before
         // (its CTAs are resident when that pass ends), unless an event record
         // sits between them
-        if ((e = launch_lattice(b->kind, b->bd, f, 2, b->s1, k > 0 && !(ev && k == 1)))) return e;
-        if (k == 0 && (e = mark(5, b->s1))) return e;
+        if ((e = launch_lattice(b->kind, b->bd, f, 2, b->s1,
+                                k > 0 && !(ev && (k == ks || k == ks + 1)))))
+            return e;
+        if (k == ks && (e = mark(5, b->s1))) return e;
         if ((e = cudaEventRecord(b->evn[k & 1], b->s1))) return e;
-        if (k == 0 && (e = mark(2, b->s1))) return e;
+        if (k == ks && (e = mark(2, b->s1))) return e;
         // programmatic dependent of the near pass (its prologue overlaps it),
         // unless an event record sits between them
-        if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->s1, !(ev && k == 0)))) return e;
-        if (k == 0 && (e = mark(3, b->s1))) return e;
+        if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->s1, !(ev && k == ks)))) return e;
+        if (k == ks && (e = mark(3, b->s1))) return e;
     }
     if ((e = cudaEventRecord(b->evjoin, b->s2)) || (e = cudaEventRecord(b->evjoin1, b->s1)) ||
         (e = cudaStreamWaitEvent(b->stream, b->evjoin, 0)) ||
@@ -919,7 +969,16 @@ lbib_status batch_step_impl(lbib_batch *b, int64_t n) {
         CK(cudaGraphLaunch(g, b->stream));
     }
     if (rem > 0) {
-        cudaError_t e = enqueue_steps(b, rem, nullptr);
+        // with timing on, the remainder's middle step is sampled too (the
+        // next slot's events), so that every call takes at least one sample
+        cudaEvent_t *ev = nullptr;
+        if (b->nsamples > 0) {
+            const int slot = b->next_slot;
+            b->next_slot = (slot + 1) % b->nsamples;
+            ev = &b->ev[6 * slot];
+            b->replayed[slot] = 1;
+        }
+        cudaError_t e = enqueue_steps(b, rem, ev, false);
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         if (rem & 1) {
             e = launch_flip(b->d_curs, (int)b->sims.size(), b->stream);
@@ -1123,6 +1182,7 @@ lbib_status lbib_set_populations(lbib_sim *s, const double *f) {
 }
 
 lbib_status lbib_step(lbib_sim *s, int64_t n) {
+    NvtxRange nv("lbib_step");
     if (!s) return fail(LBIB_E_ARG, "null simulation");
     lbib_status r = ensure_self(s);
     if (r != LBIB_OK) return r;
@@ -1137,6 +1197,7 @@ lbib_status lbib_batch_create(lbib_sim *const *sims, int32_t n, lbib_batch **out
 }
 
 lbib_status lbib_batch_step(lbib_batch *b, int64_t n) {
+    NvtxRange nv("lbib_batch_step");
     if (!b) return fail(LBIB_E_ARG, "null batch");
     return batch_step_impl(b, n);
 }
@@ -1476,6 +1537,7 @@ lbib_status lbib_synchronize(lbib_sim *s) {
 
 lbib_status lbib_read_state(lbib_sim *s, lbib_state *st, lbib_particle_state *parts,
                             int32_t n_parts, double *rho, double *ux, double *uy, size_t n_nodes) {
+    NvtxRange nv("lbib_read_state");
     if (!s) return fail(LBIB_E_ARG, "null simulation");
     if ((rho || ux || uy) && n_nodes != s->N)
         return fail(LBIB_E_ARG, "field buffers hold %zu nodes, lattice has %zu", n_nodes, s->N);
@@ -1556,20 +1618,225 @@ lbib_status lbib_read_ib_force(lbib_sim *s, double *fx, double *fy) {
     return LBIB_OK;
 }
 
+lbib_status lbib_get_particle_record(lbib_sim *s, int32_t pid, lbib_particle_record *out) {
+    if (!s || !out) return fail(LBIB_E_ARG, "null argument");
+    if (pid < 0 || pid >= (int)s->parts.size()) return fail(LBIB_E_ARG, "no particle %d", pid);
+    CK(cudaStreamSynchronize(s->stream));
+    ParticleDev h;
+    CK(cudaMemcpy(&h, s->parts[pid].d_part, sizeof h, cudaMemcpyDeviceToHost));
+    out->xc = h.xc; out->yc = h.yc; out->theta = h.th;
+    out->u = h.u; out->v = h.v; out->omega = h.om;
+    out->xc1 = h.xc1; out->yc1 = h.yc1; out->theta1 = h.th1;
+    out->u1 = h.u1; out->v1 = h.v1; out->omega1 = h.om1;
+    out->step = h.step;
+    return check_err_word(s);
+}
+
+lbib_status lbib_set_particle_record(lbib_sim *s, int32_t pid, const lbib_particle_record *in) {
+    NvtxRange nv("lbib_set_particle_record");
+    if (!s || !in) return fail(LBIB_E_ARG, "null argument");
+    if (pid < 0 || pid >= (int)s->parts.size()) return fail(LBIB_E_ARG, "no particle %d", pid);
+    const double v[12] = {in->xc, in->yc, in->theta, in->u, in->v, in->omega,
+                          in->xc1, in->yc1, in->theta1, in->u1, in->v1, in->omega1};
+    for (double x : v)
+        if (!isfinite(x)) return fail(LBIB_E_ARG, "non-finite particle record");
+    if (in->step < 0) return fail(LBIB_E_ARG, "negative particle step count");
+    CK(cudaStreamSynchronize(s->stream));
+    ParticleDev h;
+    CK(cudaMemcpy(&h, s->parts[pid].d_part, sizeof h, cudaMemcpyDeviceToHost));
+    h.xc = in->xc; h.yc = in->yc; h.th = in->theta;
+    h.u = in->u; h.v = in->v; h.om = in->omega;
+    h.xc1 = in->xc1; h.yc1 = in->yc1; h.th1 = in->theta1;
+    h.u1 = in->u1; h.v1 = in->v1; h.om1 = in->omega1;
+    h.step = in->step;
+    h.pose_ok = 0;          // the next pass derives its pose from these values
+    CK(cudaMemcpy(s->parts[pid].d_part, &h, sizeof h, cudaMemcpyHostToDevice));
+    return reprime(s);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoints: the whole state a later step depends on, as one host blob.
+// Layout: CkptHeader, the current post-collision populations in the storage
+// format ([9][ny][nx] of f - w, times the F16 scale), then per particle a
+// CkptParticle and its bond flags [nl], anchor x [nl] and anchor walls [nl],
+// each section padded to 8 bytes.  The IB force of the coming step is not
+// stored: loading recomputes it at the restored pose from the restored
+// populations, as the end of the saved step did.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t nx, ny, storage, n_particles;
+    int64_t step;
+    double scale;
+    uint64_t pop_bytes;
+};
+
+struct CkptParticle {
+    int32_t nl, n_probing, n_bonded, pad;
+    double xc, yc, th, u, v, om, xc1, yc1, th1, u1, v1, om1;
+    int64_t step;
+    double Fh[2], Mh, Fb[2], Mb, Fw[2];
+};
+
+const char CKPT_MAGIC[8] = {'L', 'B', 'I', 'B', 'C', 'K', 'P', 'T'};
+constexpr uint32_t CKPT_VERSION = 1;
+
+size_t pad8(size_t b) { return (b + 7) & ~size_t(7); }
+
+size_t ckpt_bytes(const lbib_sim *s) {
+    size_t b = sizeof(CkptHeader) + pad8(9 * s->N * storage_size(s->kind));
+    for (const HostParticle &p : s->parts)
+        b += sizeof(CkptParticle) + pad8(p.nl) + 8 * (size_t)p.nl + pad8(p.nl);
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbib_status lbib_checkpoint_size(lbib_sim *s, size_t *bytes) {
+    if (!s || !bytes) return fail(LBIB_E_ARG, "null argument");
+    *bytes = ckpt_bytes(s);
+    return LBIB_OK;
+}
+
+lbib_status lbib_checkpoint_save(lbib_sim *s, void *host, size_t bytes) {
+    NvtxRange nv("lbib_checkpoint_save");
+    if (!s || !host) return fail(LBIB_E_ARG, "null argument");
+    if (bytes < ckpt_bytes(s))
+        return fail(LBIB_E_ARG, "checkpoint needs %zu bytes, buffer holds %zu", ckpt_bytes(s), bytes);
+    CK(cudaStreamSynchronize(s->stream));
+    lbib_status r = check_err_word(s);
+    if (r != LBIB_OK) return r;
+    unsigned char *o = (unsigned char *)host;
+    CkptHeader hd{};
+    memcpy(hd.magic, CKPT_MAGIC, 8);
+    hd.version = CKPT_VERSION;
+    hd.header_bytes = sizeof(CkptHeader);
+    hd.nx = s->cfg.nx; hd.ny = s->cfg.ny; hd.storage = s->kind;
+    hd.n_particles = (int32_t)s->parts.size();
+    hd.step = s->step;
+    hd.scale = s->scale;
+    hd.pop_bytes = 9 * s->N * storage_size(s->kind);
+    memcpy(o, &hd, sizeof hd);
+    o += sizeof hd;
+    CK(cudaMemcpy(o, s->pop[s->cur], hd.pop_bytes, cudaMemcpyDeviceToHost));
+    o += pad8(hd.pop_bytes);
+    for (const HostParticle &p : s->parts) {
+        ParticleDev h;
+        CK(cudaMemcpy(&h, p.d_part, sizeof h, cudaMemcpyDeviceToHost));
+        CkptParticle c{};
+        c.nl = p.nl; c.n_probing = h.n_probing; c.n_bonded = h.n_bonded;
+        c.xc = h.xc; c.yc = h.yc; c.th = h.th; c.u = h.u; c.v = h.v; c.om = h.om;
+        c.xc1 = h.xc1; c.yc1 = h.yc1; c.th1 = h.th1; c.u1 = h.u1; c.v1 = h.v1; c.om1 = h.om1;
+        c.step = h.step;
+        c.Fh[0] = h.Fh[0]; c.Fh[1] = h.Fh[1]; c.Mh = h.Mh;
+        c.Fb[0] = h.Fb[0]; c.Fb[1] = h.Fb[1]; c.Mb = h.Mb;
+        c.Fw[0] = h.Fw[0]; c.Fw[1] = h.Fw[1];
+        memcpy(o, &c, sizeof c);
+        o += sizeof c;
+        CK(cudaMemcpy(o, h.bond, p.nl, cudaMemcpyDeviceToHost));
+        o += pad8(p.nl);
+        CK(cudaMemcpy(o, h.anchor_x, 8 * (size_t)p.nl, cudaMemcpyDeviceToHost));
+        o += 8 * (size_t)p.nl;
+        CK(cudaMemcpy(o, h.anchor_wall, p.nl, cudaMemcpyDeviceToHost));
+        o += pad8(p.nl);
+    }
+    return LBIB_OK;
+}
+
+lbib_status lbib_checkpoint_load(lbib_sim *s, const void *host, size_t bytes) {
+    NvtxRange nv("lbib_checkpoint_load");
+    if (!s || !host) return fail(LBIB_E_ARG, "null argument");
+    if (bytes < sizeof(CkptHeader)) return fail(LBIB_E_ARG, "checkpoint too short");
+    const unsigned char *o = (const unsigned char *)host;
+    CkptHeader hd;
+    memcpy(&hd, o, sizeof hd);
+    if (memcmp(hd.magic, CKPT_MAGIC, 8) != 0 || hd.version != CKPT_VERSION ||
+        hd.header_bytes != sizeof(CkptHeader))
+        return fail(LBIB_E_ARG, "not an lbib checkpoint of version %u", CKPT_VERSION);
+    if (hd.nx != s->cfg.nx || hd.ny != s->cfg.ny || hd.storage != s->kind ||
+        hd.n_particles != (int32_t)s->parts.size() || hd.scale != (double)s->scale ||
+        hd.pop_bytes != 9 * s->N * storage_size(s->kind) || hd.step < 0)
+        return fail(LBIB_E_ARG, "checkpoint of a %d x %d lattice (storage %d, %d particles) does "
+                    "not match this simulation", hd.nx, hd.ny, hd.storage, hd.n_particles);
+    if (bytes < ckpt_bytes(s)) return fail(LBIB_E_ARG, "checkpoint truncated");
+    {
+        // every particle's element count before anything is written
+        const unsigned char *q = o + sizeof hd + pad8(hd.pop_bytes);
+        for (const HostParticle &p : s->parts) {
+            CkptParticle c;
+            memcpy(&c, q, sizeof c);
+            if (c.nl != p.nl) return fail(LBIB_E_ARG, "checkpoint particle with %d elements, "
+                                          "simulation's has %d", c.nl, p.nl);
+            q += sizeof c + pad8(p.nl) + 8 * (size_t)p.nl + pad8(p.nl);
+        }
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    o += sizeof hd;
+    CK(cudaMemcpy(s->pop[s->cur], o, hd.pop_bytes, cudaMemcpyHostToDevice));
+    o += pad8(hd.pop_bytes);
+    for (HostParticle &p : s->parts) {
+        CkptParticle c;
+        memcpy(&c, o, sizeof c);
+        o += sizeof c;
+        ParticleDev h;
+        CK(cudaMemcpy(&h, p.d_part, sizeof h, cudaMemcpyDeviceToHost));
+        h.xc = c.xc; h.yc = c.yc; h.th = c.th; h.u = c.u; h.v = c.v; h.om = c.om;
+        h.xc1 = c.xc1; h.yc1 = c.yc1; h.th1 = c.th1; h.u1 = c.u1; h.v1 = c.v1; h.om1 = c.om1;
+        h.step = c.step;
+        h.Fh[0] = c.Fh[0]; h.Fh[1] = c.Fh[1]; h.Mh = c.Mh;
+        h.Fb[0] = c.Fb[0]; h.Fb[1] = c.Fb[1]; h.Mb = c.Mb;
+        h.Fw[0] = c.Fw[0]; h.Fw[1] = c.Fw[1];
+        h.n_probing = c.n_probing; h.n_bonded = c.n_bonded;
+        h.pose_ok = 0;
+        CK(cudaMemcpy(p.d_part, &h, sizeof h, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h.bond, o, p.nl, cudaMemcpyHostToDevice));
+        o += pad8(p.nl);
+        CK(cudaMemcpy(h.anchor_x, o, 8 * (size_t)p.nl, cudaMemcpyHostToDevice));
+        o += 8 * (size_t)p.nl;
+        CK(cudaMemcpy(h.anchor_wall, o, p.nl, cudaMemcpyHostToDevice));
+        o += pad8(p.nl);
+    }
+    const long long st = hd.step;
+    const int zero = 0;
+    CK(cudaMemcpy(s->d_step, &st, sizeof st, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->d_err, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    s->step = hd.step;
+    return reprime(s);
+}
+
+lbib_status lbib_device_bytes(lbib_sim *s, size_t *bytes) {
+    if (!s || !bytes) return fail(LBIB_E_ARG, "null argument");
+    size_t b = 2 * 9 * s->N * storage_size(s->kind) + 64 + s->scratch_bytes;
+    for (const HostParticle &p : s->parts) b += p.d_bytes;
+    if (s->self) b += s->self->d_bytes;
+    *bytes = b;
+    return LBIB_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
 // Allocation-free IB forcing.
 //
-// Some callers cannot allocate device memory: code running inside a host
-// callback or a stream-ordered section where cudaMalloc / cudaFree would
-// synchronise or is not permitted, plugins whose host application owns every
-// device allocation through its own arena, and embedded loops that must not
-// touch the allocator after start-up.  lbib_ib_force_noalloc serves them: the
-// caller passes its own device input and output buffers, and the only extra
-// device memory the call touches is one file-scope static array of
+// Some callers cannot allocate device memory: plugins and solvers embedded in
+// a host application that owns every device allocation through its own arena
+// (and forbids cudaMalloc / cudaFree behind its back), and real-time loops
+// that must not touch an allocator, which may synchronise the device or fail
+// under memory pressure, once they run.  lbib_ib_force_noalloc serves them:
+// the caller passes its own device input and output buffers, and the only
+// extra device memory the call touches is one file-scope static array of
 // NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
-// the process exits.  The call allocates no device or host heap memory.
+// the process exits.  The call allocates no device or host heap memory, and
+// copies nothing from the host: the descriptors and the particle's tables
+// travel as the parameters of a set-up kernel that writes them into the
+// array.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1581,66 +1848,115 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH
 // Device address of g_noalloc_scratch on each device, looked up once per
 // device (with that device current) by the first call made on it.  In host
 // code the array's name is only a host-side stand-in for the symbol.
+std::once_flag g_noalloc_once[NOALLOC_MAX_DEVICES];
 unsigned char *g_noalloc_addr[NOALLOC_MAX_DEVICES];
+cudaError_t g_noalloc_lookup[NOALLOC_MAX_DEVICES];
 
 lbib_status noalloc_scratch(int dev, unsigned char **out) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
         return fail(LBIB_E_UNSUPPORTED, "device %d beyond the %d the scratch table covers", dev,
                     NOALLOC_MAX_DEVICES);
-    if (!g_noalloc_addr[dev]) {
+    std::call_once(g_noalloc_once[dev], [dev] {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_noalloc_addr[dev] = (unsigned char *)p;
-    }
+        g_noalloc_lookup[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (g_noalloc_lookup[dev] == cudaSuccess) g_noalloc_addr[dev] = (unsigned char *)p;
+    });
+    if (g_noalloc_lookup[dev] != cudaSuccess || !g_noalloc_addr[dev])
+        return cuda_fail(g_noalloc_lookup[dev], "cudaGetSymbolAddress(g_noalloc_scratch)");
     *out = g_noalloc_addr[dev];
     return LBIB_OK;
 }
 
-// Element geometry, ligands and marker colouring of an explicit polygon in
-// fixed-size host arrays (the same construction as build_geometry, without
-// heap use).
-struct NoAllocGeom {
-    double mbx[LBIB_MAX_MARKERS], mby[LBIB_MAX_MARKERS], nbx[LBIB_MAX_MARKERS],
-        nby[LBIB_MAX_MARKERS], S[LBIB_MAX_MARKERS];
-    uint8_t ligand[LBIB_MAX_MARKERS];
-    int color[LBIB_MAX_MARKERS], corder[LBIB_MAX_MARKERS], coff[LBIB_MAX_MARKERS + 1];
-    double area, J, rmax;
-    int n, T, ncolors, n_ligands;
+// Everything the IB pass reads besides the populations, passed by value to
+// the set-up kernel (about 26 KB of kernel parameters): the channel and
+// particle descriptors with their device pointers into the scratch, the
+// batch tables of one particle, and the element geometry (body-frame
+// centroids x, y, outward normals x, y, lengths), ligand flags and marker
+// colouring of an explicit polygon.
+struct NoAllocSetup {
+    SimDev sim;
+    ParticleDev par;
+    SimDev *d_sim;
+    ParticleDev *d_par;
+    ParticleDev **d_parts;      // [2]: the particle, then a null end marker
+    int *d_psim;                // [2]
+    int *d_cur;
+    double *d_geo;              // [5][nl]
+    uint8_t *d_lig;
+    int *d_corder, *d_coff;
+    uint8_t *d_bond;
+    double *d_ax;
+    int8_t *d_aw;
+    double *d_pft;              // [2][nl + 1]
+    int nl, ncolors;
+    double geo[5 * LBIB_MAX_MARKERS];
+    uint8_t lig[LBIB_MAX_MARKERS];
+    int corder[LBIB_MAX_MARKERS], coff[LBIB_MAX_MARKERS + 1];
 };
+static_assert(sizeof(NoAllocSetup) <= 32764, "set-up parameters exceed the kernel parameter limit");
 
-void noalloc_geometry(const lbib_particle &in, NoAllocGeom &g) {
+// One CTA writes the descriptors and tables into the scratch and clears the
+// state the IB pass does not read (bonds, anchors, P_f table), so nothing of
+// an earlier call remains.
+__global__ void __launch_bounds__(256) noalloc_setup_kernel(const __grid_constant__ NoAllocSetup a) {
+    const int t = threadIdx.x, n = a.nl;
+    if (t == 0) {
+        *a.d_sim = a.sim;
+        *a.d_par = a.par;
+        a.d_parts[0] = a.d_par;
+        a.d_parts[1] = nullptr;
+        a.d_psim[0] = a.d_psim[1] = 0;
+        *a.d_cur = 0;
+    }
+    for (int i = t; i < 5 * n; i += blockDim.x) a.d_geo[i] = a.geo[(i / n) * LBIB_MAX_MARKERS + i % n];
+    for (int i = t; i < n; i += blockDim.x) {
+        a.d_lig[i] = a.lig[i];
+        a.d_corder[i] = a.corder[i];
+        a.d_bond[i] = 0;
+        a.d_ax[i] = 0.0;
+        a.d_aw[i] = 0;
+    }
+    for (int i = t; i <= a.ncolors; i += blockDim.x) a.d_coff[i] = a.coff[i];
+    for (int i = t; i < 2 * (n + 1); i += blockDim.x) a.d_pft[i] = 0.0;
+}
+
+// Element geometry, ligands and marker colouring of an explicit polygon (the
+// construction of build_geometry, into the fixed-size tables of a).
+void noalloc_geometry(const lbib_particle &in, NoAllocSetup &a, double &area, double &J,
+                      double &rmax, int &n_ligands) {
     const int n = in.n_vertices;
-    g.n = n;
-    g.area = g.J = g.rmax = 0.0;
+    constexpr int M = LBIB_MAX_MARKERS;
+    double *mbx = a.geo, *mby = a.geo + M, *nbx = a.geo + 2 * M, *nby = a.geo + 3 * M;
+    double *S = a.geo + 4 * M;
+    area = J = rmax = 0.0;
     for (int l = 0; l < n; ++l) {
         const int m = (l + 1) % n;
         const double ax = in.vx[l], ay = in.vy[l], bx = in.vx[m], by = in.vy[m];
         const double dx = bx - ax, dy = by - ay, len = sqrt(dx * dx + dy * dy);
-        g.mbx[l] = 0.5 * (ax + bx);
-        g.mby[l] = 0.5 * (ay + by);
-        g.S[l] = len;
-        g.nbx[l] = len > 0 ? dy / len : 0.0;
-        g.nby[l] = len > 0 ? -dx / len : 0.0;
+        mbx[l] = 0.5 * (ax + bx);
+        mby[l] = 0.5 * (ay + by);
+        S[l] = len;
+        nbx[l] = len > 0 ? dy / len : 0.0;
+        nby[l] = len > 0 ? -dx / len : 0.0;
         const double cr = ax * by - bx * ay;
-        g.area += 0.5 * cr;
-        g.J += cr * (ax * ax + ax * bx + bx * bx + ay * ay + ay * by + by * by) / 12.0;
-        g.rmax = std::max(g.rmax, sqrt(ax * ax + ay * ay));
+        area += 0.5 * cr;
+        J += cr * (ax * ax + ax * bx + bx * bx + ay * ay + ay * by + by * by) / 12.0;
+        rmax = std::max(rmax, sqrt(ax * ax + ay * ay));
     }
-    g.T = 2 * (int)ceil(g.rmax) + 8;
-    g.n_ligands = 0;
+    n_ligands = 0;
     for (int l = 0; l < n; ++l) {
-        g.ligand[l] = floor((double)(l + 1) * in.ligand_density) > floor((double)l * in.ligand_density);
-        g.n_ligands += g.ligand[l];
+        a.lig[l] = floor((double)(l + 1) * in.ligand_density) > floor((double)l * in.ligand_density);
+        n_ligands += a.lig[l];
     }
-    const int nc = color_markers(g.mbx, g.mby, n, g.color);
-    g.ncolors = nc;
-    for (int c = 0; c <= nc; ++c) g.coff[c] = 0;
-    for (int l = 0; l < n; ++l) g.coff[g.color[l] + 1]++;
-    for (int c = 0; c < nc; ++c) g.coff[c + 1] += g.coff[c];
-    int fill[LBIB_MAX_MARKERS + 1];
-    for (int c = 0; c < nc; ++c) fill[c] = g.coff[c];
-    for (int l = 0; l < n; ++l) g.corder[fill[g.color[l]]++] = l;
+    int color[M];
+    const int nc = color_markers(mbx, mby, n, color);
+    a.ncolors = nc;
+    for (int c = 0; c <= nc; ++c) a.coff[c] = 0;
+    for (int l = 0; l < n; ++l) a.coff[color[l] + 1]++;
+    for (int c = 0; c < nc; ++c) a.coff[c + 1] += a.coff[c];
+    int fill[M + 1];
+    for (int c = 0; c < nc; ++c) fill[c] = a.coff[c];
+    for (int l = 0; l < n; ++l) a.corder[fill[color[l]]++] = l;
 }
 
 }  // namespace
@@ -1648,6 +1964,7 @@ void noalloc_geometry(const lbib_particle &in, NoAllocGeom &g) {
 extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float *f_dev,
                                              const lbib_particle *in, double u, double v,
                                              double omega, double *fx_dev, double *fy_dev) {
+    NvtxRange nv("lbib_ib_force_noalloc");
     if (!cfg || !f_dev || !in || !fx_dev || !fy_dev) return fail(LBIB_E_ARG, "null argument");
     const lbib_config &c = *cfg;
     if (c.nx < 8 || c.ny < 4 || (int64_t)c.nx * c.ny >= (1ll << 31) / 9)
@@ -1666,19 +1983,21 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
     if (!isfinite(in->xc) || !isfinite(in->yc) || !isfinite(in->theta) || !isfinite(u) ||
         !isfinite(v) || !isfinite(omega) || !(in->rho_p > 0))
         return fail(LBIB_E_ARG, "particle parameters out of range");
-    NoAllocGeom g;                          // ~30 KB on the caller's stack
-    noalloc_geometry(*in, g);
-    if (!(g.area > 0)) return fail(LBIB_E_ARG, "outline must be counter-clockwise with positive area");
-    if (g.T >= c.nx || (c.wall_bottom == LBIB_WALL_PERIODIC && g.T >= c.ny))
-        return fail(LBIB_E_ARG, "force tile %d does not fit the lattice", g.T);
-    const int nl = g.n, T = g.T;
-    // scratch layout: SimDev | ParticleDev | parts[1] | part_sim[1] | cur | geometry | tile
+    NoAllocSetup a{};                       // ~26 KB on the caller's stack
+    double area = 0, J = 0, rmax = 0;
+    int n_ligands = 0;
+    noalloc_geometry(*in, a, area, J, rmax, n_ligands);
+    if (!(area > 0)) return fail(LBIB_E_ARG, "outline must be counter-clockwise with positive area");
+    const int nl = in->n_vertices, T = 2 * (int)ceil(rmax) + 8;
+    if (T >= c.nx || (c.wall_bottom == LBIB_WALL_PERIODIC && T >= c.ny))
+        return fail(LBIB_E_ARG, "force tile %d does not fit the lattice", T);
+    // scratch layout: SimDev | ParticleDev | parts[2], part_sim[2] | cur | geometry | tile
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t o_sim = 0, o_par = o_sim + up(sizeof(SimDev)), o_tab = o_par + up(sizeof(ParticleDev));
     const size_t o_cur = o_tab + up(2 * sizeof(void *) + 2 * sizeof(int));
     const size_t o_geo = o_cur + up(sizeof(int));
     const size_t geo_bytes = up(5 * 8 * (size_t)nl) + up(nl) + up(4 * (size_t)nl) +
-                             up(4 * (size_t)(g.ncolors + 1)) + up(nl) + up(8 * (size_t)nl) + up(nl) +
+                             up(4 * (size_t)(a.ncolors + 1)) + up(nl) + up(8 * (size_t)nl) + up(nl) +
                              up(16 * (size_t)(nl + 1));
     const size_t o_tile = o_geo + geo_bytes;
     const size_t need = o_tile + 2 * sizeof(float) * (size_t)T * T;
@@ -1697,11 +2016,11 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
     cudaStream_t st = (cudaStream_t)c.cuda_stream;
 
     // device addresses inside the scratch
-    SimDev *d_sim = (SimDev *)(base + o_sim);
-    ParticleDev *d_par = (ParticleDev *)(base + o_par);
-    ParticleDev **d_parts = (ParticleDev **)(base + o_tab);
-    int *d_psim = (int *)(base + o_tab + 2 * sizeof(void *));
-    int *d_cur = (int *)(base + o_cur);
+    a.d_sim = (SimDev *)(base + o_sim);
+    a.d_par = (ParticleDev *)(base + o_par);
+    a.d_parts = (ParticleDev **)(base + o_tab);
+    a.d_psim = (int *)(base + o_tab + 2 * sizeof(void *));
+    a.d_cur = (int *)(base + o_cur);
     unsigned char *gp = base + o_geo;
     size_t go = 0;
     auto take = [&](size_t b) {
@@ -1709,76 +2028,47 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
         go += up(b);
         return q;
     };
-    double *mbx = (double *)take(5 * 8 * (size_t)nl);   // centroids x, y, normals x, y, lengths
-    uint8_t *lig = take(nl);
-    int *co = (int *)take(4 * (size_t)nl);
-    int *coff = (int *)take(4 * (size_t)(g.ncolors + 1));
-    uint8_t *bond = take(nl);
-    double *ax = (double *)take(8 * (size_t)nl);
-    int8_t *aw = (int8_t *)take(nl);
-    double *pft = (double *)take(16 * (size_t)(nl + 1));
+    a.d_geo = (double *)take(5 * 8 * (size_t)nl);
+    a.d_lig = take(nl);
+    a.d_corder = (int *)take(4 * (size_t)nl);
+    a.d_coff = (int *)take(4 * (size_t)(a.ncolors + 1));
+    a.d_bond = take(nl);
+    a.d_ax = (double *)take(8 * (size_t)nl);
+    a.d_aw = (int8_t *)take(nl);
+    a.d_pft = (double *)take(16 * (size_t)(nl + 1));
     void *tile = base + o_tile;
+    a.nl = nl;
 
-    // host images of the descriptors (copied into the scratch on `st`)
-    SimDev hs{};
-    hs.nx = c.nx; hs.ny = c.ny; hs.wall_b = c.wall_bottom; hs.wall_t = c.wall_top;
-    hs.p0 = 0; hs.np = 1; hs.tile0 = 0; hs.ntiles = 0;
-    hs.tau = c.tau; hs.u_b = c.u_bottom; hs.u_t = c.u_top; hs.gx = c.gx; hs.gy = c.gy;
-    hs.scale = 1.f; hs.inv_scale = 1.f;
-    hs.ib_iters = c.ib_iterations > 1 ? c.ib_iterations : 1;
-    const double om = 1.0 / c.tau;
-    hs.d_om = om; hs.d_pref = 1.0 - 0.5 * om; hs.d_ub6 = c.u_bottom / 6.0; hs.d_ut6 = c.u_top / 6.0;
-    hs.f_om = (float)om; hs.f_pref = (float)hs.d_pref; hs.f_gx = (float)c.gx; hs.f_gy = (float)c.gy;
-    hs.f_ub = (float)c.u_bottom; hs.f_ut = (float)c.u_top;
-    hs.f_ub6 = (float)hs.d_ub6; hs.f_ut6 = (float)hs.d_ut6;
-    hs.d_nu = (c.tau - 0.5) / 3.0; hs.f_nu = (float)hs.d_nu;
-    hs.pop[0] = (void *)f_dev; hs.pop[1] = (void *)f_dev;
-    hs.cur = d_cur;
-    ParticleDev hp{};
+    // descriptors: the channel over the caller's populations (one buffer,
+    // current index 0), the particle at the given pose and velocity
+    a.sim = simdev_from(c, (void *)f_dev, (void *)f_dev, a.d_cur, nullptr, nullptr, 1.f, 0, 1, 0);
+    ParticleDev &hp = a.par;
     hp.xc = hp.xc1 = in->xc; hp.yc = hp.yc1 = in->yc; hp.th = hp.th1 = in->theta;
     hp.u = u; hp.v = v; hp.om = omega;
-    hp.mass = in->rho_p * g.area; hp.inertia = in->rho_p * g.J;
+    hp.mass = in->rho_p * area; hp.inertia = in->rho_p * J;
     hp.inv_mass = 1.0 / hp.mass; hp.inv_inertia = 1.0 / hp.inertia;
-    hp.r_eq = sqrt(g.area / M_PI); hp.sigma = in->sigma;
-    hp.nl = nl; hp.n_ligands = g.n_ligands; hp.fixed = 1; hp.T = T; hp.ncolors = g.ncolors;
+    hp.r_eq = sqrt(area / M_PI); hp.sigma = in->sigma;
+    hp.nl = nl; hp.n_ligands = n_ligands; hp.fixed = 1; hp.T = T; hp.ncolors = a.ncolors;
     hp.NB = near_edge(T);
-    hp.mbx = mbx; hp.mby = mbx + nl; hp.nbx = mbx + 2 * nl; hp.nby = mbx + 3 * nl; hp.S = mbx + 4 * nl;
-    hp.ligand = lig; hp.color_order = co; hp.color_off = coff;
-    hp.bond = bond; hp.anchor_x = ax; hp.anchor_wall = aw; hp.tile = tile; hp.pf_tab = pft;
-    struct { ParticleDev *p[2]; int ps[2]; } tab = {{d_par, nullptr}, {0, 0}};
-    const int zero = 0;
-    // pageable source buffers are staged by the driver before each call returns
-    CK(cudaMemcpyAsync(d_sim, &hs, sizeof hs, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_par, &hp, sizeof hp, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_parts, &tab, sizeof tab, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_cur, &zero, sizeof zero, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(mbx, g.mbx, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(mbx + nl, g.mby, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(mbx + 2 * nl, g.nbx, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(mbx + 3 * nl, g.nby, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(mbx + 4 * nl, g.S, 8 * (size_t)nl, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(lig, g.ligand, nl, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(co, g.corder, 4 * (size_t)nl, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(coff, g.coff, 4 * (size_t)(g.ncolors + 1), cudaMemcpyHostToDevice, st));
-    // bond state and the forward-probability table are not read by the IB
-    // pass; they are cleared so no earlier call's values remain
-    CK(cudaMemsetAsync(bond, 0, nl, st));
-    CK(cudaMemsetAsync(ax, 0, 8 * (size_t)nl, st));
-    CK(cudaMemsetAsync(aw, 0, nl, st));
-    CK(cudaMemsetAsync(pft, 0, 16 * (size_t)(nl + 1), st));
+    hp.mbx = a.d_geo; hp.mby = a.d_geo + nl; hp.nbx = a.d_geo + 2 * nl; hp.nby = a.d_geo + 3 * nl;
+    hp.S = a.d_geo + 4 * nl;
+    hp.ligand = a.d_lig; hp.color_order = a.d_corder; hp.color_off = a.d_coff;
+    hp.bond = a.d_bond; hp.anchor_x = a.d_ax; hp.anchor_wall = a.d_aw; hp.tile = tile;
+    hp.pf_tab = a.d_pft;
 
     BatchDev bd{};
-    bd.sims = d_sim;
-    bd.parts = d_parts;
-    bd.part_sim = d_psim;
-    bd.tile_sim = nullptr;
+    bd.sims = a.d_sim;
+    bd.parts = a.d_parts;
+    bd.part_sim = a.d_psim;
     bd.nsims = 1;
     bd.nparts = 1;
-    bd.total_tiles = 0;
+    bd.wait_polls = 1 << 16;
     CK(particle_kernel_setup(ST_F32, lim));
+    noalloc_setup_kernel<<<1, 256, 0, st>>>(a);
+    CK(cudaGetLastError());
     // the IB pass at the given pose writes the whole force tile, then the
     // tile is laid out on the lattice (every node of fx, fy is written)
     CK(launch_particles(ST_F32, bd, 0, 1, smem, st));
-    CK(launch_ib_export(ST_F32, hs, d_parts, fx_dev, fy_dev, st));
+    CK(launch_ib_export(ST_F32, a.sim, a.d_parts, fx_dev, fy_dev, st));
     return LBIB_OK;
 }

@@ -134,6 +134,8 @@ struct BatchDev {
     int lat_variant;     // bulk-pass kernel variant (0 .. LBIB_LATTICE_VARIANTS - 1)
     int tma_ok;          // every lattice suits the copy-engine variants (4, 5)
     int pthreads;        // particle CTA width: 256 (every particle fits) or 512
+    int wait_polls;      // polls of a bounded device wait before it gives up
+    int pad_b;
 };
 
 // Stochastic rounding of 16-bit stores.  A node's dither word is a hash of

@@ -545,7 +545,7 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
             pull_group<S, R, true>(s, src, x0, y, d, SC ? 1.f : s.inv_scale);
         }
     }
-    if (!mbar_wait0(bar, 1 << 16)) {
+    if (!mbar_wait0(bar, b.wait_polls)) {
         if (threadIdx.x == 0) atomicOr(s.err, ERR_TIMEOUT);
         return false;
     }
@@ -635,7 +635,8 @@ __global__ void __launch_bounds__(256, MINB) lattice_tma_kernel(BatchDev b, int 
         if (!tma_tile<S, R>(b, flip, dry, first + t, stage(t), barrier(t))) {
             // copies that did not complete in time: one more bounded wait on
             // each stage still in flight (they write this CTA's shared
-            // memory), then leave the remaining tiles
+            // memory), always of the full length, then leave the remaining
+            // tiles
             for (int u = t; u < TILES && first + u < b.total_tiles; ++u) mbar_wait0(barrier(u), 1 << 16);
             return;
         }

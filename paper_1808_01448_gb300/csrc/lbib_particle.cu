@@ -107,12 +107,12 @@ struct Pose {
     double xc, yc, th, u, v, om;
     double F[6];        // Fh x, y, M; Fb x, y, M (FP64 sums)
     double Fw;
+    double csd, snd;    // FP64 cos, sin of the angle (bond geometry)
     int ixc, iyc;       // floor of the centroid (base node of relative coordinates)
     R fxc, fyc;         // centroid minus its floor
     R cs, sn;           // cos, sin of the angle
     R gap0_b, gap0_t;   // centroid distance to the bottom / top wall line
     R uR, vR, omR;      // velocities in the compute precision
-    R gmin_b, gmin_t;   // smallest element gaps
     int nprobe, nbonded;
 };
 
@@ -266,16 +266,6 @@ __device__ __forceinline__ double warp_sum_array(const R *a, int n) {
     return acc;
 }
 
-template <typename R>
-__device__ __forceinline__ R warp_min_array(const R *a, int n, R base, R sign) {
-    const int lane = threadIdx.x & 31;
-    R m = (R)1e30;
-    for (int l = lane; l < n; l += 32) m = fmin(m, base + sign * a[l]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-    return m;
-}
-
 // Node moments pulled from the populations (outside the staged region).
 template <typename R>
 struct Moments {
@@ -399,17 +389,12 @@ size_t smem_bytes_for(int nl, int T) {
            up(sizeof(double) * 3 * (P_THREADS / 32)) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread;
 }
 
-// Reverse probability of Eq. 11 (dt = 1): FP32 on the FP32 path, FP64 on the
-// FP64 path.
-template <typename R>
-__device__ __noinline__ double prob_reverse(double k_r0, double dsig, double kBT2, R dd) {
-    if constexpr (sizeof(R) == 4) {
-        const float kr = (float)k_r0 * expf((float)dsig * dd * dd / (float)kBT2);
-        return (double)(-expm1f(-kr));
-    } else {
-        const double kr = k_r0 * exp(dsig * dd * dd / kBT2);
-        return 1.0 - exp(-kr);
-    }
+// Reverse probability of Eq. 11 (dt = 1), in FP64 on every storage path:
+// k_r = k_r0 exp((sigma - sigma*) d^2 / (2 k_B T)), P_r = 1 - exp(-k_r), with
+// d = y_l - y_eq.
+__device__ __noinline__ double prob_reverse(double k_r0, double dsig, double kBT2, double dd) {
+    const double kr = k_r0 * exp(dsig * dd * dd / kBT2);
+    return 1.0 - exp(-kr);
 }
 
 // The 256-thread form is capped at 64 registers (a quarter of an SM's), so
@@ -513,6 +498,19 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             set_pose(ps, yb, yt);
         }
     }
+    // FP64 cosine and sine of the angle for the bond geometry (beside the
+    // compute-precision pose of thread 0)
+    if (tid == 32 && !init) sincos(Pc.th, &ps.snd, &ps.csd);
+    // element of this thread's bond: the upper half of the block takes the
+    // bonds when both halves fit the elements, so that they run beside the
+    // staging work of the lower half; its body-frame centroid in FP64
+    const int kb = 2 * nl <= PT ? tid - PT / 2 : tid;
+    const bool kb_ok = !init && (unsigned)kb < (unsigned)nl;
+    double bmx = 0.0, bmy = 0.0;
+    if (kb_ok) {
+        bmx = Pc.mbx[kb];
+        bmy = Pc.mby[kb];
+    }
     // element data: from the record the last pass left (marker positions at
     // this pose included), else from the geometry arrays
     const bool cached = Pc.pose_ok && Pc.ecache && prec.erec == Pc.ecache;
@@ -556,22 +554,23 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     const int rx0 = ps.ixc - Tm / 2, ry0 = ps.iyc - Tm / 2;
     for (int v = tid; v < Tm; v += PT) span[v] = make_int4(Tm, -1, Tm, -1);
     // ---- 3. bonds (Eq. 9-11), one element per thread: they need only the
-    // pose, so they run with the staging, before the wait on the lattice pass
+    // pose, so they run with the staging, before the wait on the lattice pass.
+    // On every storage path the bond geometry is FP64: the element centroid
+    // X_l at the pose of step n, its gaps to the wall lines (probing test and
+    // Eq. 12), the bond length and P_r, and the anchor of a new bond, so that
+    // the decisions follow the pose to FP64 rounding.
     const bool has_b = s.wall_b != LBIB_WALL_PERIODIC && s.rec_b > 0.0;
     const bool has_t = s.wall_t != LBIB_WALL_PERIODIC && s.rec_t > 0.0;
-    const R ycr = pick<R>((float)s.y_cr, s.y_cr);
-    // element of this thread's bond: the upper half of the block takes the
-    // bonds when both halves fit the elements, so that they run beside the
-    // staging work of the lower half
-    const int kb = 2 * nl <= PT ? tid - PT / 2 : tid;
     bool lig = false, pb = false, ptop = false;
-    R gapb = (R)0, gapt = (R)0;
-    if (!init && (unsigned)kb < (unsigned)nl) {
+    double Xl = 0.0, Yl = 0.0, gbd = 1e300, gtd = 1e300;
+    if (kb_ok) {
         lig = lig8[kb] != 0;
-        gapb = ps.gap0_b + ry[kb];
-        gapt = ps.gap0_t - ry[kb];
-        pb = lig && has_b && gapb < ycr;
-        ptop = lig && has_t && gapt < ycr;
+        Xl = ps.xc + (ps.csd * bmx - ps.snd * bmy);
+        Yl = ps.yc + (ps.snd * bmx + ps.csd * bmy);
+        gbd = Yl - yb;
+        gtd = yt - Yl;
+        pb = lig && has_b && gbd < s.y_cr;
+        ptop = lig && has_t && gtd < s.y_cr;
     }
     const int nprobe = __syncthreads_count(pb || ptop);
 
@@ -613,28 +612,27 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
         }
     }
     bool bonded = false;
-    if (!init && (unsigned)kb < (unsigned)nl) {
+    if (kb_ok) {
         const int l = kb;
-        R fx = 0, fy = 0;
+        double fx = 0.0, fy = 0.0;
         if (lig) {
             // one draw per (step, element); the step is this particle's count
             const double U = bond_uniform(s, Pc.step, (int)blockIdx.x - s.p0, l);
             uint8_t bnd = P->bond[l];
             double ax = P->anchor_x[l];
             int8_t aw = P->anchor_wall[l];
-            const R y_eq = pick<R>((float)(s.y_eq_ratio * s.y_cr), s.y_eq_ratio * s.y_cr);
+            const double y_eq = s.y_eq_ratio * s.y_cr;
             if (bnd) {
                 // bond vector anchor - X_l; the anchor lies on a wall line
-                const R dx = (R)(ax - ps.xc) - rx[l];
-                const R dy = aw ? gapt : -gapb;
-                const R y = sqrt(dx * dx + dy * dy);
-                const double Pr = prob_reverse<R>(s.k_r0, Pc.sigma * (1.0 - s.sigma_star_ratio),
-                                                  2.0 * s.kBT, y - y_eq);
+                const double dx = ax - Xl, dy = (aw ? yt : yb) - Yl;
+                const double y = sqrt(dx * dx + dy * dy);
+                const double Pr = prob_reverse(s.k_r0, Pc.sigma - s.sigma_star_ratio * Pc.sigma,
+                                               2.0 * s.kBT, y - y_eq);
                 if (U < Pr) bnd = 0;
             } else if (pb || ptop) {
                 if (U < Pc.pf_tab[pb ? nprobe : nl + 1 + nprobe]) {
                     bnd = 1;
-                    ax = ps.xc + (double)rx[l];
+                    ax = Xl;
                     aw = pb ? 0 : 1;
                     P->anchor_x[l] = ax;
                     P->anchor_wall[l] = aw;
@@ -643,19 +641,33 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             P->bond[l] = bnd;
             if (bnd) {
                 bonded = true;
-                const R dx = (R)(ax - ps.xc) - rx[l];
-                const R dy = aw ? gapt : -gapb;
-                const R y = sqrt(dx * dx + dy * dy);
-                if (y > (R)0) {
-                    const R mag = (R)Pc.sigma * (y - y_eq) / y;
-                    fx = mag * dx;
-                    fy = mag * dy;
+                const double dx = ax - Xl, dy = (aw ? yt : yb) - Yl;
+                const double y = sqrt(dx * dx + dy * dy);
+                if (y > 0.0) {
+                    const double mag = Pc.sigma * (y - y_eq);
+                    fx = mag * dx / y;
+                    fy = mag * dy / y;
                 }
             }
         }
-        cq[3 * cstride + l] = fx;
-        cq[4 * cstride + l] = fy;
-        cq[5 * cstride + l] = rx[l] * fy - ry[l] * fx;
+        cq[3 * cstride + l] = (R)fx;
+        cq[4 * cstride + l] = (R)fy;
+        cq[5 * cstride + l] = (R)((Xl - ps.xc) * fy - (Yl - ps.yc) * fx);
+    }
+    if (!init) {
+        // smallest element gaps to each wall line (Eq. 12), FP64: per warp by
+        // shuffles, the warps' minima in the load-partials space (free until
+        // the loads below)
+        double mb = gbd, mt = gtd;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mb = fmin(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+            mt = fmin(mt, __shfl_xor_sync(0xffffffffu, mt, o));
+        }
+        if (lane == 0) {
+            lpart[2 * warp] = mb;
+            lpart[2 * warp + 1] = mt;
+        }
     }
     const int nbonded = __syncthreads_count(bonded);
     // merge overlapping spans, count the nodes of each row, prefix sum (one warp)
@@ -686,24 +698,25 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
         const double v = warp_sum_array<R>(cq + (2 + warp) * cstride, nl);
         if (lane == 0) ps.F[2 + warp] = v;
     } else if (!init && warp == 4) {
-        const R gb = warp_min_array<R>(ry, nl, ps.gap0_b, (R)1);
-        const R gt = warp_min_array<R>(ry, nl, ps.gap0_t, (R)-1);
         if (lane == 0) {
-            ps.gmin_b = gb;
-            ps.gmin_t = gt;
+            double gb = 1e300, gt = 1e300;
+            for (int w = 0; w < PT / 32; ++w) {
+                gb = fmin(gb, lpart[2 * w]);
+                gt = fmin(gt, lpart[2 * w + 1]);
+            }
             ps.nprobe = nprobe;
             ps.nbonded = nbonded;
-            // ---- 4. wall force (Eq. 12) -------------------------------
-            R Fw = 0;
+            // ---- 4. wall force (Eq. 12), FP64 -------------------------
+            // F_w = H_k / (8 sqrt 2) sqrt(r / eps^5) off each wall, eps the
+            // smallest element gap clamped below by eps_min
+            double Fw = 0.0;
             if (s.wall_b != LBIB_WALL_PERIODIC && s.hamaker != 0.0) {
-                const R em = pick<R>((float)s.eps_min, s.eps_min);
-                const R eb = fmax(gb, em), et = fmax(gt, em);
-                const R k = pick<R>((float)(s.hamaker / (8.0 * 1.4142135623730951)),
-                                    s.hamaker / (8.0 * 1.4142135623730951));
-                const R r = pick<R>((float)Pc.r_eq, Pc.r_eq);
-                Fw = k * sqrt(r / (eb * eb * eb * eb * eb)) - k * sqrt(r / (et * et * et * et * et));
+                const double eb = fmax(gb, s.eps_min), et = fmax(gt, s.eps_min);
+                const double k = s.hamaker / (8.0 * 1.4142135623730951);
+                Fw = k * sqrt(Pc.r_eq / (eb * eb * eb * eb * eb)) -
+                     k * sqrt(Pc.r_eq / (et * et * et * et * et));
             }
-            ps.Fw = (double)Fw;
+            ps.Fw = Fw;
         }
     }
     __syncthreads();

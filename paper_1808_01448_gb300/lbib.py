@@ -78,6 +78,12 @@ class ParticleState(C.Structure):
     ]
 
 
+class ParticleRecord(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("xc", "yc", "theta", "u", "v", "omega",
+                                          "xc1", "yc1", "theta1", "u1", "v1", "omega1")] + [
+        ("step", C.c_int64)]
+
+
 class State(C.Structure):
     _fields_ = [("step", C.c_int64), ("n_particles", C.c_int32), ("storage", C.c_int32),
                 ("nx", C.c_int32), ("ny", C.c_int32)]
@@ -127,6 +133,12 @@ def lib():
                 "lbib_read_ib_force": [vp, pd, pd],
                 "lbib_ib_force_noalloc": [C.POINTER(Config), vp, C.POINTER(Particle), d, d, d,
                                           vp, vp],
+                "lbib_get_particle_record": [vp, i32, C.POINTER(ParticleRecord)],
+                "lbib_set_particle_record": [vp, i32, C.POINTER(ParticleRecord)],
+                "lbib_checkpoint_size": [vp, C.POINTER(C.c_size_t)],
+                "lbib_checkpoint_save": [vp, vp, C.c_size_t],
+                "lbib_checkpoint_load": [vp, vp, C.c_size_t],
+                "lbib_device_bytes": [vp, C.POINTER(C.c_size_t)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -303,6 +315,39 @@ class Sim:
         fx = np.empty((self.ny, self.nx)); fy = np.empty_like(fx)
         _check(lib().lbib_read_ib_force(self._h, _dp(fx), _dp(fy)))
         return fx, fy
+
+    def record(self, pid=0) -> dict:
+        """Pose, velocities, their values one step earlier and the step
+        count of a particle (``lbib_get_particle_record``)."""
+        r = ParticleRecord()
+        _check(lib().lbib_get_particle_record(self._h, pid, C.byref(r)))
+        return {k: getattr(r, k) for k, _ in ParticleRecord._fields_}
+
+    def set_record(self, pid=0, **fields):
+        """Overwrite a particle's record (``lbib_set_particle_record``);
+        fields not given keep their current values."""
+        cur = self.record(pid)
+        cur.update(fields)
+        r = ParticleRecord(**cur)
+        _check(lib().lbib_set_particle_record(self._h, pid, C.byref(r)))
+
+    def checkpoint(self) -> bytes:
+        """The simulation's state as a host blob (``lbib_checkpoint_save``)."""
+        n = C.c_size_t()
+        _check(lib().lbib_checkpoint_size(self._h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib().lbib_checkpoint_save(self._h, buf, n.value))
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        """Load a blob from ``checkpoint`` (``lbib_checkpoint_load``)."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        _check(lib().lbib_checkpoint_load(self._h, buf, len(blob)))
+
+    def device_bytes(self) -> int:
+        n = C.c_size_t()
+        _check(lib().lbib_device_bytes(self._h, C.byref(n)))
+        return n.value
 
 
 class Batch:

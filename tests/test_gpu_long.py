@@ -1,0 +1,161 @@
+"""Long-horizon parity on the workload configurations as stated:
+ - the single circle of radius 10 (63 markers) in the 200 x 50 body-force
+   channel with bounce-back walls, tau 0.8, Re 0.1, for its full 2000 steps:
+   FP64 storage equal to the FP64 oracle to rounding with the bond flags equal
+   at every step, FP32 storage within the FP32 tolerances (velocity 1e-5
+   relative L2, trajectory 1e-4 lattice units) with the bond flags compared at
+   every step;
+ - an equal-area AR3 ellipse in the 1024 x 256 shear channel at Re 1, FP32,
+   2000 steps;
+ - a mid-size member of the 72-channel design sweep, FP32, 1000 steps
+   stepped inside the full batch.
+A bond difference in FP32 is accepted only at a step where the oracle logged
+a near tie (|U - P| or |gap - y_cr| below 1e-4); the first divergence step
+and the Hamming distance are printed.  The two large oracle runs go to worker
+processes started with spawn when the module's first test asks for them."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import _oracle_runs
+from _parity import NEAR_TIE, rel_l2
+from paper_1808_01448_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1808_01448_gb300 import build, lbib
+    build.build()
+    return lbib
+
+
+def c2_case():
+    return W.single_ellipse_sweep(shapes=("ar3",), reynolds=(1.0,))[0]
+
+
+def c3_member():
+    sweep = W.design_sweep()
+    sizes = [c["nx"] * c["ny"] for c, _ in sweep]
+    i = int(np.argsort(sizes)[len(sizes) // 2])
+    return sweep, i
+
+
+@pytest.fixture(scope="module")
+def oracle_runs(O):
+    """The two large oracle runs, started at once in spawned workers."""
+    O.build()
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(2)
+    cfg2, parts2 = c2_case()
+    sweep, i = c3_member()
+    jobs = {"c2": pool.apply_async(_oracle_runs.run_case, (cfg2, parts2, 2000)),
+            "c3": pool.apply_async(_oracle_runs.run_case, (sweep[i][0], sweep[i][1], 1000))}
+    yield jobs
+    pool.terminate()
+    pool.join()
+
+
+def check_free_run(label, gpu_bonds, run):
+    """Per-step comparison of the GPU's bond flags with the oracle's record."""
+    first = None
+    for t in range(len(gpu_bonds)):
+        if not np.array_equal(gpu_bonds[t], run["bonds"][t]):
+            first = t + 1
+            m = run["margins"][t]
+            assert min(m) < NEAR_TIE, (
+                f"{label}: bond flags differ at step {first} without a near tie "
+                f"(|U-P| {m[0]:.3g}, |gap-y_cr| {m[1]:.3g})")
+            break
+    ham = int((gpu_bonds[-1] != run["bonds"][-1]).sum())
+    print(f"{label}: first bond divergence {first}, Hamming distance {ham}, "
+          f"{int(run['bonds'].sum())} bonded element-steps in the oracle")
+    return first
+
+
+def test_poiseuille_circle_full_horizon(O, L, oracle_runs):
+    cfg, parts = W.poiseuille_circle()
+    o = O.OracleSim(**cfg)
+    for p in parts:
+        o.add_particle(**p)
+    g64 = L.Sim(storage="f64", **cfg)
+    g32 = L.Sim(storage="f32", **cfg)
+    for g in (g64, g32):
+        for p in parts:
+            g.add_particle(**p)
+    first32 = None
+    for t in range(2000):
+        o.step(1)
+        g64.step(1)
+        g32.step(1)
+        bo = o.bonds(0)[0]
+        assert np.array_equal(bo, g64.bonds(0)[0]), f"FP64 bond flags differ at step {t + 1}"
+        if first32 is None and not np.array_equal(bo, g32.bonds(0)[0]):
+            first32 = t + 1
+            st = o.particle(0)
+            assert min(st["margin_p"], st["margin_gap"]) < NEAR_TIE, f"FP32 step {first32}"
+    print(f"C1 FP32: first bond divergence {first32}")
+    po = o.particle(0)
+    ro, uo, vo = o.fields()
+    p64 = g64.particle(0)
+    for k in ("xc", "yc", "theta", "u", "v", "omega"):
+        assert p64[k] == pytest.approx(po[k], abs=1e-10), k
+    _, u64, v64 = g64.fields()
+    assert rel_l2(np.stack([u64, v64]), np.stack([uo, vo])) < 1e-11
+    p32 = g32.particle(0)
+    for k in ("xc", "yc", "theta"):
+        assert abs(p32[k] - po[k]) < 1e-4, k
+    _, u32, v32 = g32.fields()
+    assert rel_l2(np.stack([u32, v32]), np.stack([uo, vo])) < 1e-5
+    g64.close()
+    g32.close()
+
+
+def test_c2_ellipse_2000_steps_f32(L, oracle_runs):
+    cfg, parts = c2_case()
+    g = L.Sim(storage="f32", **cfg)
+    for p in parts:
+        g.add_particle(**p)
+    gb = []
+    for _ in range(2000):
+        g.step(1)
+        gb.append(g.bonds(0)[0])
+    run = oracle_runs["c2"].get(timeout=1800)
+    first = check_free_run("C2 AR3 Re 1 FP32", gb, run)
+    ro, uo, vo = run["fields"]
+    _, ug, vg = g.fields()
+    assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) < 1e-5
+    if first is None:
+        po, pg = run["particle"], g.particle(0)
+        for k in ("xc", "yc", "theta"):
+            assert abs(pg[k] - po[k]) < 1e-4, k
+    g.close()
+
+
+def test_c3_member_1000_steps_in_batch(L, oracle_runs):
+    sweep, i = c3_member()
+    sims = []
+    for c, p in sweep:
+        s = L.Sim(storage="f32", **c)
+        for q in p:
+            s.add_particle(**q)
+        sims.append(s)
+    b = L.Batch(sims)
+    gb = []
+    for _ in range(1000):
+        b.step(1)
+        gb.append(sims[i].bonds(0)[0])
+    run = oracle_runs["c3"].get(timeout=1800)
+    first = check_free_run(f"C3 member {i} FP32", gb, run)
+    ro, uo, vo = run["fields"]
+    _, ug, vg = sims[i].fields()
+    assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) < 1e-5
+    if first is None:
+        po, pg = run["particle"], sims[i].particle(0)
+        for k in ("xc", "yc", "theta"):
+            assert abs(pg[k] - po[k]) < 1e-4, k
+    b.close()
+    for s in sims:
+        s.close()

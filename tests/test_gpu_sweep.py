@@ -7,6 +7,7 @@ relative L2, trajectory 1e-4 lattice units, bond states equal).
 import numpy as np
 import pytest
 
+from _parity import bonds_every_step
 from paper_1808_01448_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -58,20 +59,25 @@ def test_design_sweep_smallest_member_vs_oracle(O, L):
     order = np.argsort(sizes)
     sims = [make(L, c, p) for c, p in sweep]
     b = L.Batch(sims)
-    b.step(64)
+    oracles = {}
     for i in order[:2]:
         c, p = sweep[int(i)]
         o = O.OracleSim(**c)
         for q in p:
             o.add_particle(**q)
-        o.step(64)
+        oracles[int(i)] = o
+    # bond flags of both members against their oracles at every step of the
+    # batched stepping
+    bonds_every_step([(oracles[i], sims[i]) for i in oracles], lambda: b.step(1), 64,
+                     "sweep member")
+    for i in order[:2]:
+        o = oracles[int(i)]
         ro, uo, vo = o.fields()
         rg, ug, vg = sims[int(i)].fields()
         assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) < 1e-5
         po, pg = o.particle(0), sims[int(i)].particle(0)
         for k in ("xc", "yc", "theta"):
             assert abs(pg[k] - po[k]) < 1e-4, k
-        np.testing.assert_array_equal(o.bonds(0)[0], sims[int(i)].bonds(0)[0])
     b.close()
     for s in sims:
         s.close()
