@@ -466,6 +466,74 @@ void or_spread(const or_config *c, int n, const double *X, const double *Y,
     }
 }
 
+/* Solved spreading scales (Vanella & Balaras, ref. [39], cited with the MLS
+ * transfer in Sec. "The combined LB-IB method").  Reading: eps is chosen so
+ * that the MLS interpolation at the markers of the field spread from a
+ * uniform marker force returns that force, i.e. sum_m A_lm eps_m = 1 with
+ * A_lm = sum_k phi_k(X_l) phi_k(X_m) over the lattice nodes k.  The dense
+ * system is solved by Gaussian elimination with partial pivoting; a marker
+ * without a fit (no support) is left out (eps = 0, identity row). */
+int or_vb_eps(const or_config *c, int n, const double *X, const double *Y, double *eps) {
+    int32_t *ix = (int32_t *)malloc((size_t)n * 16 * 2 * sizeof(int32_t));
+    int32_t *iy = ix + (size_t)n * 16;
+    double *phi = (double *)malloc((size_t)n * 16 * sizeof(double));
+    int *cnt = (int *)malloc((size_t)n * sizeof(int));
+    double *M = (double *)calloc((size_t)n * (n + 1), sizeof(double));
+    for (int l = 0; l < n; ++l)
+        cnt[l] = or_mls_shape(c, X[l], Y[l], ix + 16 * l, iy + 16 * l, phi + 16 * l);
+    /* augmented matrix [A | 1] */
+    for (int l = 0; l < n; ++l) {
+        double *row = M + (size_t)l * (n + 1);
+        if (cnt[l] == 0) {
+            row[l] = 1.0;
+            continue;
+        }
+        for (int m = 0; m < n; ++m) {
+            double a = 0.0;
+            for (int i = 0; i < cnt[l]; ++i)
+                for (int j = 0; j < cnt[m]; ++j)
+                    if (ix[16 * l + i] == ix[16 * m + j] && iy[16 * l + i] == iy[16 * m + j])
+                        a += phi[16 * l + i] * phi[16 * m + j];
+            row[m] = a;
+        }
+        row[n] = 1.0;
+    }
+    int ok = 0;
+    for (int k = 0; k < n && ok == 0; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(M[(size_t)r * (n + 1) + k]) > fabs(M[(size_t)piv * (n + 1) + k])) piv = r;
+        if (M[(size_t)piv * (n + 1) + k] == 0.0) {
+            ok = -1;
+            break;
+        }
+        if (piv != k)
+            for (int q = 0; q <= n; ++q) {
+                double t = M[(size_t)k * (n + 1) + q];
+                M[(size_t)k * (n + 1) + q] = M[(size_t)piv * (n + 1) + q];
+                M[(size_t)piv * (n + 1) + q] = t;
+            }
+        for (int r = k + 1; r < n; ++r) {
+            double f = M[(size_t)r * (n + 1) + k] / M[(size_t)k * (n + 1) + k];
+            if (f == 0.0) continue;
+            for (int q = k; q <= n; ++q) M[(size_t)r * (n + 1) + q] -= f * M[(size_t)k * (n + 1) + q];
+        }
+    }
+    if (ok == 0)
+        for (int k = n - 1; k >= 0; --k) {
+            double acc = M[(size_t)k * (n + 1) + n];
+            for (int q = k + 1; q < n; ++q) acc -= M[(size_t)k * (n + 1) + q] * eps[q];
+            eps[k] = acc / M[(size_t)k * (n + 1) + k];
+        }
+    for (int l = 0; l < n; ++l)
+        if (cnt[l] == 0) eps[l] = 0.0;
+    free(M);
+    free(cnt);
+    free(phi);
+    free(ix);
+    return ok;
+}
+
 /* ---- hydrodynamic loads (Eq. 7-8) --------------------------------------- */
 /* Probe Q_l = X_l + 1.2 n_l; p and the velocity gradient come from the MLS
  * fit there and are taken as the centroid's.  Reading: pressure relative to
@@ -711,7 +779,8 @@ static void moments(const or_sim *s, double *rho, double *ux, double *uy, double
 /* IB direct forcing (Favier et al. [38] with MLS [13], [39]).  Reading: the
  * desired marker velocity is the rigid motion U_c + omega x (X_l - X_c); the
  * force density that makes the Guo half-step velocity u* + F/(2 rho) match it
- * is F_l = 2 rho_l (U^d_l - u*_l) / dt; spread with eps_l = S_l dx.
+ * is F_l = 2 rho_l (U^d_l - u*_l) / dt; spread with eps_l = S_l dx, or with
+ * the solved scales of or_vb_eps when ib_spread = 1.
  * Multi-direct forcing (ib_iterations = M > 1): the velocity a marker sees
  * after its own particle's force is spread, u^m_l = u*_l + I_l[f^(m-1)] /
  * (2 rho_l) (I_l: the MLS interpolation at X_l, rho_l the marker's
@@ -734,6 +803,13 @@ static void ib_force(or_sim *s) {
         double *mx = buf, *my = mx + nv, *nxo = my + nv, *nyo = nxo + nv, *S = nyo + nv;
         double *rl = S + nv, *ul = rl + nv, *vl = ul + nv, *Fx = vl + nv, *Fy = Fx + nv;
         or_elements(nv, p->vx, p->vy, p->xc, p->yc, p->theta, mx, my, nxo, nyo, S);
+        if (s->c.ib_spread == 1) {
+            /* the spreading scales replace the element lengths (S is not
+             * used for anything else here) */
+            double *eps = (double *)malloc(nv * sizeof(double));
+            if (or_vb_eps(&s->c, nv, mx, my, eps) == 0) memcpy(S, eps, nv * sizeof(double));
+            free(eps);
+        }
         or_interp(&s->c, rho, nv, mx, my, rl);
         or_interp(&s->c, ux, nv, mx, my, ul);
         or_interp(&s->c, uy, nv, mx, my, vl);

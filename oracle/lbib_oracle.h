@@ -39,7 +39,8 @@ typedef struct or_config {
     double receptor_bottom, receptor_top; /* receptor density on each wall */
     uint64_t seed, sim_id;           /* Philox key */
     int32_t ib_iterations;           /* direct-forcing passes per step (<= 1: one) */
-    int32_t reserved;
+    int32_t ib_spread;               /* spreading scale eps_l: 0 element length S_l,
+                                        1 solved (Vanella & Balaras, ref. [39]) */
 } or_config;
 
 typedef struct or_particle_in {
@@ -106,6 +107,12 @@ int or_mls_fit(const or_config *c, const double *field, double X, double Y,
 void or_spread(const or_config *c, int n, const double *X, const double *Y,
                const double *Fx, const double *Fy, const double *eps, double *fx,
                double *fy);
+/* Spreading scales eps_l of n markers solved so that interpolating the
+ * spread of a uniform marker force gives it back at every marker
+ * (Vanella & Balaras, ref. [39]): sum_m A_lm eps_m = 1 with
+ * A_lm = sum_k phi_k(X_l) phi_k(X_m).  Markers without a fit get eps = 0.
+ * Returns 0, or -1 if the system is singular. */
+int or_vb_eps(const or_config *c, int n, const double *X, const double *Y, double *eps);
 /* Interpolate a nodal field at n points. */
 void or_interp(const or_config *c, const double *field, int n, const double *X,
                const double *Y, double *out);

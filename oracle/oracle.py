@@ -52,7 +52,7 @@ class OrConfig(C.Structure):
         ("hamaker", C.c_double), ("eps_min", C.c_double),
         ("receptor_bottom", C.c_double), ("receptor_top", C.c_double),
         ("seed", C.c_uint64), ("sim_id", C.c_uint64),
-        ("ib_iterations", C.c_int32), ("reserved", C.c_int32),
+        ("ib_iterations", C.c_int32), ("ib_spread", C.c_int32),
     ]
 
 
@@ -115,6 +115,7 @@ def lib():
                 "or_mls_fit": (C.c_int, [C.POINTER(OrConfig), pd, d, d, pd, pd, pd]),
                 "or_spread": (None, [C.POINTER(OrConfig), C.c_int, pd, pd, pd, pd, pd, pd, pd]),
                 "or_interp": (None, [C.POINTER(OrConfig), pd, C.c_int, pd, pd, pd]),
+                "or_vb_eps": (C.c_int, [C.POINTER(OrConfig), C.c_int, pd, pd, pd]),
                 "or_loads": (None, [C.POINTER(OrConfig), pd, pd, pd, C.c_int, pd, pd,
                                     d, d, d, pd]),
                 "or_elements": (None, [C.c_int, pd, pd, d, d, d, pd, pd, pd, pd, pd]),
@@ -141,7 +142,7 @@ def make_config(**kw) -> OrConfig:
                     tau=0.8, u_bottom=0.0, u_top=0.0, gx=0.0, gy=0.0, k_f=0.85,
                     k_r0=1e-4, kBT=0.1, sigma_star_ratio=0.5, y_cr=1.36,
                     y_eq_ratio=0.5, hamaker=0.0, eps_min=0.1, receptor_bottom=1.0,
-                    receptor_top=0.0, seed=1, sim_id=0, ib_iterations=1)
+                    receptor_top=0.0, seed=1, sim_id=0, ib_iterations=1, ib_spread=0)
     defaults.update(kw)
     for k, v in defaults.items():
         if k in ("wall_bottom", "wall_top") and isinstance(v, str):
@@ -294,6 +295,15 @@ def interp(cfg: OrConfig, field, X, Y):
     X = np.ascontiguousarray(X, dtype=np.float64); Y = np.ascontiguousarray(Y, dtype=np.float64)
     out = np.zeros(len(X))
     lib().or_interp(C.byref(cfg), _dp(field), len(X), _dp(X), _dp(Y), _dp(out))
+    return out
+
+
+def vb_eps(cfg: OrConfig, X, Y):
+    """Solved spreading scales of markers at (X, Y) (or_vb_eps)."""
+    X = np.ascontiguousarray(X, dtype=np.float64); Y = np.ascontiguousarray(Y, dtype=np.float64)
+    out = np.zeros(len(X))
+    if lib().or_vb_eps(C.byref(cfg), len(X), _dp(X), _dp(Y), _dp(out)) != 0:
+        raise RuntimeError("singular spreading-scale system")
     return out
 
 
