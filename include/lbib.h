@@ -19,8 +19,10 @@
  *    lbib_create / lbib_add_particle / first step, freed in lbib_destroy),
  *    through the caller's allocator hook when one is given.
  *  - Stepping is asynchronous on the configured CUDA stream; read calls
- *    synchronise that stream.  A device-side error (a non-finite state, a
- *    bounded wait that ran out) is reported by the next call.
+ *    synchronise that stream and the streams of the batches that hold the
+ *    simulation, so they see every step enqueued before them.  A
+ *    device-side error (a non-finite state, a bounded wait that ran out) is
+ *    reported by the next call.
  *  - A handle is not thread-safe; different handles are independent.
  *  - Device waits are bounded: a wait of the lattice pass on its staged
  *    copies gives up after LBIB_WAIT_POLLS polls (environment variable read
@@ -222,10 +224,11 @@ lbib_status lbib_batch_create(lbib_sim *const *sims, int32_t n, lbib_batch **out
 lbib_status lbib_batch_step(lbib_batch *b, int64_t nsteps);
 lbib_status lbib_batch_destroy(lbib_batch *b);
 /* Kernel timing with CUDA events: when nsamples > 0, later batch steps
- * record the duration of the kernels of one sampled step (event records
- * inside the replayed graphs, around the middle step of each graph of up to
- * nsamples graphs in turn, and around the middle step of the steps a call
- * runs outside a graph), so every stepping call takes at least one sample.
+ * record kernel durations (event records inside the replayed graphs, taken
+ * in up to nsamples graphs in turn, and in the steps a call runs outside a
+ * graph): the lattice pass of the middle step of a graph (or of a call's
+ * steps) and the particle and near-box passes of the step after it, so every
+ * stepping call takes at least one sample.
  * lbib_batch_kernel_times fills mean_ms[3] and count[3] with the
  * mean duration (ms) and number of samples taken since the last call:
  * [0] the lattice pass (the bulk pass when particle work is overlapped),

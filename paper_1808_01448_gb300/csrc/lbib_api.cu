@@ -718,6 +718,17 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     return LBIB_OK;
 }
 
+// Waits for all work on a simulation's state: its own stream and the streams
+// of the user batches that hold it (a batch steps its members on the first
+// member's stream, which joins the batch's other streams at the end of every
+// call).
+lbib_status sync_sim(lbib_sim *s) {
+    CK(cudaStreamSynchronize(s->stream));
+    for (lbib_batch *b : s->batches)
+        if (!b->orphan && b->stream != s->stream) CK(cudaStreamSynchronize(b->stream));
+    return LBIB_OK;
+}
+
 lbib_status ensure_self(lbib_sim *s) {
     if (s->self) return LBIB_OK;
     lbib_sim *one[1] = {s};
@@ -802,14 +813,17 @@ lbib_status prime_members(lbib_batch *b) {
 }
 
 // Enqueue nsteps steps.  ev (or null) receives event records around the
-// kernels of the middle step ks = nsteps / 2 (a step in the steady state of
-// the two-stream schedule): lattice / bulk [0, 1], particle [2, 3], near
-// boxes [4, 5].  capturing: the enqueue is being captured into a graph (the
-// records become event-record nodes).
+// lattice / bulk pass [0, 1] of the middle step ks = nsteps / 2 (a step in
+// the steady state of the two-stream schedule) and around the particle
+// [2, 3] and near-box [4, 5] passes of the step after it (a record between
+// two passes of the high-priority chain stops the later one from launching
+// early, which would otherwise slow the sampled bulk pass).  capturing: the
+// enqueue is being captured into a graph (the records become event-record
+// nodes).
 cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev, bool capturing = true) {
     cudaError_t e = cudaSuccess;
     const unsigned fl = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    const int ks = nsteps / 2;
+    const int ks = nsteps / 2, kp = ks + 1 < nsteps ? ks + 1 : ks;
     auto mark = [&](int i, cudaStream_t st) {
         return (ev) ? cudaEventRecordWithFlags(ev[i], st, fl) : cudaSuccess;
     };
@@ -819,10 +833,10 @@ cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev, bool captu
             if (k == ks && (e = mark(0, b->stream))) return e;
             if ((e = launch_lattice(b->kind, b->bd, f, 0, b->stream))) return e;
             if (k == ks && (e = mark(1, b->stream))) return e;
-            if (k == ks && (e = mark(2, b->stream))) return e;
+            if (k == kp && (e = mark(2, b->stream))) return e;
             if ((e = launch_particles(b->kind, b->bd, f ^ 1, 2, b->smem, b->stream))) return e;
-            if (k == ks && (e = mark(3, b->stream))) return e;
-            if (ev && k == ks && ((e = mark(4, b->stream)) || (e = mark(5, b->stream)))) return e;
+            if (k == kp && (e = mark(3, b->stream))) return e;
+            if (ev && k == kp && ((e = mark(4, b->stream)) || (e = mark(5, b->stream)))) return e;
         }
         return e;
     }
@@ -843,20 +857,20 @@ cudaError_t enqueue_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev, bool captu
         if (k == ks && (e = mark(1, b->s2))) return e;
         if ((e = cudaEventRecord(b->evb[k & 1], b->s2))) return e;
         if (k > 0 && (e = cudaStreamWaitEvent(b->s1, b->evb[(k - 1) & 1], 0))) return e;
-        if (k == ks && (e = mark(4, b->s1))) return e;
+        if (k == kp && (e = mark(4, b->s1))) return e;
         // programmatic dependent of the particle pass of the step before
         // (its CTAs are resident when that pass ends), unless an event record
         // sits between them
         if ((e = launch_lattice(b->kind, b->bd, f, 2, b->s1,
-                                k > 0 && !(ev && (k == ks || k == ks + 1)))))
+                                k > 0 && !(ev && (k == kp || k == kp + 1)))))
             return e;
-        if (k == ks && (e = mark(5, b->s1))) return e;
+        if (k == kp && (e = mark(5, b->s1))) return e;
         if ((e = cudaEventRecord(b->evn[k & 1], b->s1))) return e;
-        if (k == ks && (e = mark(2, b->s1))) return e;
+        if (k == kp && (e = mark(2, b->s1))) return e;
         // programmatic dependent of the near pass (its prologue overlaps it),
         // unless an event record sits between them
-        if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->s1, !(ev && k == ks)))) return e;
-        if (k == ks && (e = mark(3, b->s1))) return e;
+        if ((e = launch_particles(b->kind, b->bd, f ^ 1, 0, b->smem, b->s1, !(ev && k == kp)))) return e;
+        if (k == kp && (e = mark(3, b->s1))) return e;
     }
     if ((e = cudaEventRecord(b->evjoin, b->s2)) || (e = cudaEventRecord(b->evjoin1, b->s1)) ||
         (e = cudaStreamWaitEvent(b->stream, b->evjoin, 0)) ||
@@ -1531,7 +1545,10 @@ lbib_status lbib_batch_pass_nodes(lbib_batch *b, int64_t *nodes) {
 
 lbib_status lbib_synchronize(lbib_sim *s) {
     if (!s) return fail(LBIB_E_ARG, "null simulation");
-    CK(cudaStreamSynchronize(s->stream));
+    {
+        lbib_status r_ = sync_sim(s);
+        if (r_ != LBIB_OK) return r_;
+    }
     return check_err_word(s);
 }
 
@@ -1547,7 +1564,10 @@ lbib_status lbib_read_state(lbib_sim *s, lbib_state *st, lbib_particle_state *pa
         if (r == LBIB_OK) r = ensure_self(s);
         if (r != LBIB_OK) return r;
     }
-    CK(cudaStreamSynchronize(s->stream));
+    {
+        lbib_status r_ = sync_sim(s);
+        if (r_ != LBIB_OK) return r_;
+    }
     r = check_err_word(s);
     if (r != LBIB_OK) return r;
     if (st) {
@@ -1581,7 +1601,10 @@ lbib_status lbib_read_state(lbib_sim *s, lbib_state *st, lbib_particle_state *pa
 
 lbib_status lbib_read_populations(lbib_sim *s, double *f) {
     if (!s || !f) return fail(LBIB_E_ARG, "null argument");
-    CK(cudaStreamSynchronize(s->stream));
+    {
+        lbib_status r_ = sync_sim(s);
+        if (r_ != LBIB_OK) return r_;
+    }
     lbib_status r = ensure_scratch(s, 9 * s->N * sizeof(double));
     if (r != LBIB_OK) return r;
     SimDev d = make_simdev(s, 0, 0);
@@ -1595,7 +1618,10 @@ lbib_status lbib_read_bonds(lbib_sim *s, int32_t pid, uint8_t *bond, double *ax,
     if (!s) return fail(LBIB_E_ARG, "null simulation");
     if (pid < 0 || pid >= (int)s->parts.size()) return fail(LBIB_E_ARG, "no particle %d", pid);
     if (n != s->parts[pid].nl) return fail(LBIB_E_ARG, "particle %d has %d elements", pid, s->parts[pid].nl);
-    CK(cudaStreamSynchronize(s->stream));
+    {
+        lbib_status r_ = sync_sim(s);
+        if (r_ != LBIB_OK) return r_;
+    }
     ParticleDev h;
     CK(cudaMemcpy(&h, s->parts[pid].d_part, sizeof h, cudaMemcpyDeviceToHost));
     if (bond) CK(cudaMemcpy(bond, h.bond, n, cudaMemcpyDeviceToHost));
@@ -1605,7 +1631,9 @@ lbib_status lbib_read_bonds(lbib_sim *s, int32_t pid, uint8_t *bond, double *ax,
 
 lbib_status lbib_read_ib_force(lbib_sim *s, double *fx, double *fy) {
     if (!s || !fx || !fy) return fail(LBIB_E_ARG, "null argument");
-    lbib_status r = prime(s, s->stream);
+    lbib_status r = sync_sim(s);
+    if (r != LBIB_OK) return r;
+    r = prime(s, s->stream);
     if (r == LBIB_OK) r = ensure_self(s);
     if (r != LBIB_OK) return r;
     r = ensure_scratch(s, 2 * s->N * sizeof(double));
@@ -1621,7 +1649,10 @@ lbib_status lbib_read_ib_force(lbib_sim *s, double *fx, double *fy) {
 lbib_status lbib_get_particle_record(lbib_sim *s, int32_t pid, lbib_particle_record *out) {
     if (!s || !out) return fail(LBIB_E_ARG, "null argument");
     if (pid < 0 || pid >= (int)s->parts.size()) return fail(LBIB_E_ARG, "no particle %d", pid);
-    CK(cudaStreamSynchronize(s->stream));
+    {
+        lbib_status r_ = sync_sim(s);
+        if (r_ != LBIB_OK) return r_;
+    }
     ParticleDev h;
     CK(cudaMemcpy(&h, s->parts[pid].d_part, sizeof h, cudaMemcpyDeviceToHost));
     out->xc = h.xc; out->yc = h.yc; out->theta = h.th;
@@ -1641,7 +1672,10 @@ lbib_status lbib_set_particle_record(lbib_sim *s, int32_t pid, const lbib_partic
     for (double x : v)
         if (!isfinite(x)) return fail(LBIB_E_ARG, "non-finite particle record");
     if (in->step < 0) return fail(LBIB_E_ARG, "negative particle step count");
-    CK(cudaStreamSynchronize(s->stream));
+    {
+        lbib_status r_ = sync_sim(s);
+        if (r_ != LBIB_OK) return r_;
+    }
     ParticleDev h;
     CK(cudaMemcpy(&h, s->parts[pid].d_part, sizeof h, cudaMemcpyDeviceToHost));
     h.xc = in->xc; h.yc = in->yc; h.th = in->theta;
@@ -1710,7 +1744,10 @@ lbib_status lbib_checkpoint_save(lbib_sim *s, void *host, size_t bytes) {
     if (!s || !host) return fail(LBIB_E_ARG, "null argument");
     if (bytes < ckpt_bytes(s))
         return fail(LBIB_E_ARG, "checkpoint needs %zu bytes, buffer holds %zu", ckpt_bytes(s), bytes);
-    CK(cudaStreamSynchronize(s->stream));
+    {
+        lbib_status r_ = sync_sim(s);
+        if (r_ != LBIB_OK) return r_;
+    }
     lbib_status r = check_err_word(s);
     if (r != LBIB_OK) return r;
     unsigned char *o = (unsigned char *)host;
@@ -1777,7 +1814,10 @@ lbib_status lbib_checkpoint_load(lbib_sim *s, const void *host, size_t bytes) {
             q += sizeof c + pad8(p.nl) + 8 * (size_t)p.nl + pad8(p.nl);
         }
     }
-    CK(cudaStreamSynchronize(s->stream));
+    {
+        lbib_status r_ = sync_sim(s);
+        if (r_ != LBIB_OK) return r_;
+    }
     o += sizeof hd;
     CK(cudaMemcpy(s->pop[s->cur], o, hd.pop_bytes, cudaMemcpyHostToDevice));
     o += pad8(hd.pop_bytes);

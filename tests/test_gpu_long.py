@@ -39,7 +39,7 @@ def c2_case():
 def c3_member():
     sweep = W.design_sweep()
     sizes = [c["nx"] * c["ny"] for c, _ in sweep]
-    i = int(np.argsort(sizes)[len(sizes) // 2])
+    i = int(np.argsort(sizes, kind="stable")[len(sizes) // 2])
     return sweep, i
 
 

@@ -56,7 +56,7 @@ def test_design_sweep_batch_equals_solo(L):
 def test_design_sweep_smallest_member_vs_oracle(O, L):
     sweep = W.design_sweep()
     sizes = [c["nx"] * c["ny"] for c, _ in sweep]
-    order = np.argsort(sizes)
+    order = np.argsort(sizes, kind="stable")
     sims = [make(L, c, p) for c, p in sweep]
     b = L.Batch(sims)
     oracles = {}
@@ -231,4 +231,23 @@ def test_batch_synchronize_reports_a_member_error(L):
     assert e.value.status == "E_UNSTABLE"
     mixed.close()
     for s in good + [bad]:
+        s.close()
+
+
+def test_member_reads_wait_for_the_batch(L):
+    """A member's own read calls see every step its batch enqueued, although
+    the batch steps on another stream (the first member's): populations and
+    bonds read right after stepping equal those read after synchronising
+    the batch."""
+    sweep = W.design_sweep()[:4]
+    sims = [make(L, c, p) for c, p in sweep]
+    b = L.Batch(sims)
+    for _ in range(3):
+        b.step(5)
+        early = [sims[k].populations() for k in (1, 3)]
+        b.synchronize()
+        for f, k in zip(early, (1, 3)):
+            np.testing.assert_array_equal(f, sims[k].populations())
+    b.close()
+    for s in sims:
         s.close()
