@@ -128,7 +128,15 @@ typedef struct lbib_config {
      * interpolation at the marker and F0 the first pass's force; the last F
      * is spread.  0 .. 16, else E_ARG. */
     int32_t ib_iterations;
-    int32_t reserved1;
+    /* Spreading scale eps_l of the IB force (Sec. "The combined LB-IB
+     * method", MLS transfer of ref. [39]): 0 the element length S_l; 1 the
+     * scales solved so that interpolating the spread of a uniform marker
+     * force returns it at every marker, sum_m A_lm eps_m = 1 with
+     * A_lm = sum_k phi_k(X_l) phi_k(X_m), solved every step at the new
+     * pose.  With 1, a particle whose markers closer than 4 sqrt 2 lattice
+     * units lie more than LBIB_VB_MAX_BAND apart along its outline (a very
+     * thin or small particle) is refused by lbib_add_particle (E_ARG). */
+    int32_t ib_spread;
 } lbib_config;
 
 /* A rigid particle (Sec. "Pressure and viscous stresses"): a closed polygon
@@ -143,6 +151,7 @@ typedef struct lbib_config {
  * on-chip force tile: max radius <= LBIB_MAX_PARTICLE_RADIUS and
  * 3 <= nl <= LBIB_MAX_MARKERS. */
 #define LBIB_MAX_MARKERS 512
+#define LBIB_VB_MAX_BAND 8
 #define LBIB_MAX_PARTICLE_RADIUS 44.0
 #define LBIB_MAX_PARTICLES_PER_SIM 16
 

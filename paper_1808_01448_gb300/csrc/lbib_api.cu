@@ -125,6 +125,7 @@ struct HostParticle {
     int fixed = 0;
     double xc = 0, yc = 0, th = 0, rho_p = 1, lig = 0, sigma = 0;
     int nl = 0, n_ligands = 0, T = 0, ncolors = 0;
+    int vb_p = 0;                    // half bandwidth of the spreading-scale system
     double area = 0, mass = 0, inertia = 0, r_eq = 0, rmax = 0;
     std::vector<double> mbx, mby, nbx, nby, S;
     std::vector<uint8_t> ligand;
@@ -262,12 +263,31 @@ SimDev simdev_from(const lbib_config &c, void *pop0, void *pop1, int *cur, long 
     d.vec4 = c.nx % 4 == 0 && ((uintptr_t)pop0 % 32) == 0 && ((uintptr_t)pop1 % 32) == 0;
     d.sround = c.rounding == LBIB_ROUND_STOCHASTIC;
     d.ib_iters = c.ib_iterations > 1 ? c.ib_iterations : 1;
+    d.ib_spread = c.ib_spread != 0;
     return d;
 }
 
 SimDev make_simdev(const lbib_sim *s, int p0, int tile0) {
     return simdev_from(s->cfg, s->pop[0], s->pop[1], s->d_cur, s->d_step, s->d_err, s->scale, p0,
                        (int)s->parts.size(), tile0);
+}
+
+// Half bandwidth of a particle's spreading-scale system: the largest offset
+// along the outline (cyclic) between two element centroids closer than
+// 4 sqrt 2 (only such markers' 4 x 4 supports can share a node, at any pose),
+// or -1 when it exceeds LBIB_VB_MAX_BAND or the outline is too short for a
+// band of that width (n < 2 p + 2).
+int vb_band(const double *mx, const double *my, int n) {
+    const double r2 = 32.0;      // (4 sqrt 2)^2
+    int p = 0;
+    for (int l = 0; l < n; ++l)
+        for (int d = 1; d <= n / 2; ++d) {
+            const int m = (l + d) % n;
+            const double dx = mx[m] - mx[l], dy = my[m] - my[l];
+            if (dx * dx + dy * dy < r2) p = std::max(p, d);
+        }
+    if (p > LBIB_VB_MAX_BAND || n < 2 * p + 2) return -1;
+    return std::max(p, 1);
 }
 
 // Marker colouring for the spreading: two markers of one colour are at least
@@ -477,6 +497,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     h.nl = n; h.n_ligands = p.n_ligands; h.fixed = p.fixed; h.T = p.T; h.ncolors = p.ncolors;
     h.tile_ox = 0; h.tile_oy = -(1 << 28);   // no tile until the first IB pass
     h.NB = near_edge(p.T); h.step = 0;
+    h.vb_p = p.vb_p;
     h.mbx = mbx; h.mby = mby; h.nbx = nbx; h.nby = nby; h.S = S;
     h.ligand = lig; h.color_order = co; h.color_off = coff;
     h.bond = bond; h.anchor_x = ax; h.anchor_wall = aw; h.tile = tile; h.pf_tab = pft;
@@ -569,7 +590,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         nparts += (int)s->parts.size();
         tiles += (int)((s->N + LB_TILE_NODES - 1) / LB_TILE_NODES);
         for (auto &p : s->parts) {
-            smem = std::max(smem, particle_smem_bytes(b->kind, p.T, p.nl));
+            smem = std::max(smem, particle_smem_bytes(b->kind, p.T, p.nl, s->cfg.ib_spread != 0));
             const int NB = near_edge(p.T);
             near_tiles += (NB * NB + NEAR_TILE_NODES - 1) / NEAR_TILE_NODES;
             if (NB > s->cfg.nx || (s->cfg.wall_bottom == LBIB_WALL_PERIODIC && NB > s->cfg.ny))
@@ -1039,6 +1060,8 @@ lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out) {
     if (c.storage < 0 || c.storage > 3) return fail(LBIB_E_ARG, "unknown storage %d", c.storage);
     if (c.rounding != LBIB_ROUND_NEAREST && c.rounding != LBIB_ROUND_STOCHASTIC)
         return fail(LBIB_E_ARG, "unknown rounding %d", c.rounding);
+    if (c.ib_spread != 0 && c.ib_spread != 1)
+        return fail(LBIB_E_ARG, "ib_spread must be 0 or 1");
     if (!(c.kBT > 0) || c.k_f < 0 || c.k_r0 < 0 || c.y_cr < 0 || c.eps_min <= 0 ||
         c.receptor_bottom < 0 || c.receptor_top < 0)
         return fail(LBIB_E_ARG, "bond / wall-force parameters out of range");
@@ -1155,13 +1178,21 @@ lbib_status lbib_add_particle(lbib_sim *s, const lbib_particle *in, int32_t *pid
         return fail(LBIB_E_ARG, "force tile %d not lower than the periodic lattice", p.T);
     for (size_t l = 0; l < p.S.size(); ++l)
         if (!(p.S[l] > 0)) return fail(LBIB_E_ARG, "degenerate element %zu", l);
-    if (particle_smem_bytes(s->kind, p.T, p.nl) > SMEM_LIMIT)
+    const bool vb = s->cfg.ib_spread != 0;
+    if (vb) {
+        p.vb_p = vb_band(p.mbx.data(), p.mby.data(), p.nl);
+        if (p.vb_p < 0)
+            return fail(LBIB_E_ARG, "markers closer than 4 sqrt 2 lie more than %d elements apart "
+                        "along the outline: too thin for the solved spreading scales",
+                        LBIB_VB_MAX_BAND);
+    }
+    if (particle_smem_bytes(s->kind, p.T, p.nl, vb) > SMEM_LIMIT)
         return fail(LBIB_E_ARG, "particle needs more on-chip memory than one SM has");
     {
         const int lim = particle_smem_limit(s->kind);
-        if (lim > 0 && particle_smem_bytes(s->kind, p.T, p.nl) > lim)
+        if (lim > 0 && particle_smem_bytes(s->kind, p.T, p.nl, vb) > lim)
             return fail(LBIB_E_ARG, "particle needs %d bytes of shared memory (limit %d)",
-                        particle_smem_bytes(s->kind, p.T, p.nl), lim);
+                        particle_smem_bytes(s->kind, p.T, p.nl, vb), lim);
     }
     lbib_status r = upload_particle(s, p);
     if (r != LBIB_OK) return r;
@@ -2011,6 +2042,7 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
         return fail(LBIB_E_ARG, "lattice %d x %d outside 8 x 4 .. 2^31/9 nodes", c.nx, c.ny);
     if (c.ib_iterations < 0 || c.ib_iterations > 16)
         return fail(LBIB_E_ARG, "ib_iterations %d outside 0 .. 16", c.ib_iterations);
+    if (c.ib_spread != 0 && c.ib_spread != 1) return fail(LBIB_E_ARG, "ib_spread must be 0 or 1");
     if (!(c.tau > 0.5) || c.wall_bottom < 0 || c.wall_bottom > 2 || c.wall_top < 0 || c.wall_top > 2 ||
         (c.wall_bottom == LBIB_WALL_PERIODIC) != (c.wall_top == LBIB_WALL_PERIODIC))
         return fail(LBIB_E_ARG, "invalid channel configuration");
@@ -2044,7 +2076,13 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(LBIB_E_ARG, "particle needs %zu bytes of scratch; the static scratch holds %zu",
                     need, NOALLOC_SCRATCH_BYTES);
-    const int smem = particle_smem_bytes(ST_F32, T, nl);
+    const bool vb = c.ib_spread != 0;
+    int vbp = 0;
+    if (vb) {
+        vbp = vb_band(a.geo, a.geo + LBIB_MAX_MARKERS, nl);
+        if (vbp < 0) return fail(LBIB_E_ARG, "particle too thin for the solved spreading scales");
+    }
+    const int smem = particle_smem_bytes(ST_F32, T, nl, vb);
     const int lim = particle_smem_limit(ST_F32);
     if (lim <= 0 || smem > lim)
         return fail(LBIB_E_ARG, "particle needs %d bytes of shared memory (limit %d)", smem, lim);
@@ -2090,6 +2128,7 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
     hp.r_eq = sqrt(area / M_PI); hp.sigma = in->sigma;
     hp.nl = nl; hp.n_ligands = n_ligands; hp.fixed = 1; hp.T = T; hp.ncolors = a.ncolors;
     hp.NB = near_edge(T);
+    hp.vb_p = vbp;
     hp.mbx = a.d_geo; hp.mby = a.d_geo + nl; hp.nbx = a.d_geo + 2 * nl; hp.nby = a.d_geo + 3 * nl;
     hp.S = a.d_geo + 4 * nl;
     hp.ligand = a.d_lig; hp.color_order = a.d_corder; hp.color_off = a.d_coff;

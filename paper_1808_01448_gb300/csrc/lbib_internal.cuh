@@ -41,7 +41,7 @@ struct SimDev {
     int vec4;            // rows in whole groups of four aligned nodes
     int sround;          // 16-bit storage: stochastic rounding of the stores
     int ib_iters;        // direct-forcing passes per step (>= 1)
-    int pad_ib;
+    int ib_spread;       // spreading scale: 0 element lengths, 1 solved (A eps = 1)
     // k / nx = umulhi(k, nx_m) >> nx_s for 0 <= k < 2^31 (div_nx below)
     unsigned nx_m;
     int nx_s;
@@ -79,7 +79,8 @@ struct ParticleDev {
     double Fh[2], Mh, Fb[2], Mb, Fw[2];
     int nl, n_ligands, n_probing, n_bonded;
     int fixed, T, ncolors, tile_ox;     // T: force-tile edge; tile origin x in [0, nx)
-    int tile_oy, NB, pad1, pad2;        // NB: edge of the near box
+    int tile_oy, NB, vb_p, pad2;        // NB: edge of the near box; vb_p: half
+                                        // bandwidth of the spreading-scale system
     long long step;                     // completed steps of this particle (bond draws)
     // Near box of the lattice step that reads buffer parity p: nodes
     // [box_ox[p], +NB) x [box_oy[p], +NB), x wrapped to [0, nx).  The particle
@@ -459,7 +460,8 @@ cudaError_t launch_set_populations(int kind, const SimDev &s, const double *in, 
 cudaError_t launch_flip(int *const *curs, int n, cudaStream_t st);
 cudaError_t launch_ib_export(int kind, const SimDev &s, ParticleDev *const *parts, double *fx,
                              double *fy, cudaStream_t st);
-int particle_smem_bytes(int kind, int T, int nl);
+// vb: the particle's simulation solves its spreading scales (ib_spread = 1)
+int particle_smem_bytes(int kind, int T, int nl, bool vb);
 cudaError_t particle_kernel_setup(int kind, int smem);
 int particle_smem_limit(int kind);
 

@@ -28,7 +28,18 @@ __device__ __forceinline__ R recip(R x) {
 // of nine multiplications on load and nine on store.  The scale is a power
 // of two (unless the caller set another), so every rounding is the same as
 // in the unscaled form.
-template <typename R, bool SC = false>
+// FAST (16-bit storage, whose rounding dominates its error): the compact
+// pairwise form below.  Otherwise (FP32 / FP64 storage) the form that keeps
+// the rounding of slow transients unbiased:
+//  - the first-order (momentum) terms take weights W1 (axes) and W5
+//    (diagonals) with 2 W1 + 4 W5 = 1 exactly in the compute precision, so
+//    the equilibrium momentum is rho u to rounding; with 3 w_i rounded
+//    separately it is (1 + 3e-8) rho u, the same excess at every node and
+//    step, which in a flow driven by a body force of ~1e-7 per step grows
+//    into a velocity error of ~5e-5 after 2000 steps;
+//  - the Guo source is added as a term of its own, not rounded inside the
+//    ~10^4 times larger equilibrium term, where it loses ~1e-4 of itself.
+template <typename R, bool SC = false, bool FAST = false>
 __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy, bool &bad) {
     R drho, jx, jy;
     node_moments(d, drho, jx, jy);
@@ -53,28 +64,50 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
     // and an odd part 3 w (om rho (e.u) + pref (e.F)).
     const R A = drho - (R)1.5 * rho * (ux * ux + uy * uy);
     const R uF = ux * Fx + uy * Fy;
-    const R c = (R)1 - om, orho = oms * rho, p2 = (R)2 * pref;
-    const R base = oms * A - (R)3 * pref * uF;
-    d[0] = c * d[0] + (R)(4.0 / 9.0) * base;
-    auto pair = [&](int i, int j, R w, R eu, R eF) {
-        const R even = w * (base + (R)4.5 * eu * (orho * eu + p2 * eF));
-        const R odd = (R)3 * w * (orho * eu + pref * eF);
-        d[i] = c * d[i] + even + odd;
-        d[j] = c * d[j] + even - odd;
-    };
-    pair(1, 3, (R)(1.0 / 9.0), ux, Fx);
-    pair(2, 4, (R)(1.0 / 9.0), uy, Fy);
-    pair(5, 7, (R)(1.0 / 36.0), ux + uy, Fx + Fy);
-    pair(6, 8, (R)(1.0 / 36.0), uy - ux, Fy - Fx);
+    const R c = (R)1 - om;
+    if constexpr (FAST) {
+        const R orho = oms * rho, p2 = (R)2 * pref;
+        const R base = oms * A - (R)3 * pref * uF;
+        d[0] = c * d[0] + (R)(4.0 / 9.0) * base;
+        auto pair = [&](int i, int j, R w, R eu, R eF) {
+            const R even = w * (base + (R)4.5 * eu * (orho * eu + p2 * eF));
+            const R odd = (R)3 * w * (orho * eu + pref * eF);
+            d[i] = c * d[i] + even + odd;
+            d[j] = c * d[j] + even - odd;
+        };
+        pair(1, 3, (R)(1.0 / 9.0), ux, Fx);
+        pair(2, 4, (R)(1.0 / 9.0), uy, Fy);
+        pair(5, 7, (R)(1.0 / 36.0), ux + uy, Fx + Fy);
+        pair(6, 8, (R)(1.0 / 36.0), uy - ux, Fy - Fx);
+    } else {
+        const R W1 = (R)(1.0 / 3.0), W5 = ((R)1 - (R)2 * W1) * (R)0.25;
+        const R r45 = (R)4.5 * rho, m3uF = (R)-3 * uF;
+        const R w0 = (R)(4.0 / 9.0);
+        d[0] = c * d[0] + (oms * (w0 * A) + pref * (w0 * m3uF));
+        // pair (i, j = opposite of i): even part w (om A' + pref S_even),
+        // odd part W (om rho (e.u) + pref (e.F))
+        auto pair = [&](int i, int j, R w, R W, R eu, R eF) {
+            const R ee = oms * (w * (A + r45 * eu * eu));
+            const R oo = oms * (W * (rho * eu));
+            const R se = pref * (w * ((R)9 * eu * eF + m3uF));
+            const R so = pref * (W * eF);
+            d[i] = c * d[i] + (ee + oo) + (se + so);
+            d[j] = c * d[j] + (ee - oo) + (se - so);
+        };
+        pair(1, 3, (R)(1.0 / 9.0), W1, ux, Fx);
+        pair(2, 4, (R)(1.0 / 9.0), W1, uy, Fy);
+        pair(5, 7, (R)(1.0 / 36.0), W5, ux + uy, Fx + Fy);
+        pair(6, 8, (R)(1.0 / 36.0), W5, uy - ux, Fy - Fx);
+    }
     // non-finite state or a density outside (0, 2): the run has broken down
     // (the caller raises the error bit once for all its nodes)
     bad |= !(fabs(drho) < (R)1) | !(fabs(ux) + fabs(uy) < (R)10);
 }
 
-template <typename R, bool SC = false>
+template <typename R, bool SC = false, bool FAST = false>
 __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy) {
     bool bad = false;
-    collide_node<R, SC>(s, d, Fx, Fy, bad);
+    collide_node<R, SC, FAST>(s, d, Fx, Fy, bad);
     if (bad) atomicOr(s.err, ERR_UNSTABLE);
 }
 
@@ -251,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             for (int j = 0; j < 4; ++j) {
                 R Fx = gx, Fy = gy;
                 if (!BULK && s.np) tile_force<R>(s, b.parts, xg[g] + j, yg[g], Fx, Fy);
-                collide_node<R, SC>(s, d[4 * g + j], Fx, Fy, bad);
+                collide_node<R, SC, sizeof(S) == 2>(s, d[4 * g + j], Fx, Fy, bad);
             }
             const float sc = SC ? 1.f : s.scale;
             if (keep[g] == 0xFu && sizeof(S) == 2 && s.sround) {
@@ -314,7 +347,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
         if (!skip[j]) {
             R Fx = gx, Fy = gy;
             if (!BULK && s.np) tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
-            collide_node<R>(s, d[j], Fx, Fy, bad);
+            collide_node<R, false, sizeof(S) == 2>(s, d[j], Fx, Fy, bad);
             store_node<S, R, BULK>(s, dst, N, k0 + j * THREADS, d[j]);
         }
     }
@@ -379,7 +412,7 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
         if (!skip[j]) {
             R Fx = gx, Fy = gy;
             tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
-            collide_node<R>(s, d[j], Fx, Fy, bad);
+            collide_node<R, false, sizeof(S) == 2>(s, d[j], Fx, Fy, bad);
             store_node<S, R>(s, dst, N, ys[j] * nx + xs[j], d[j]);
         }
     }
@@ -575,7 +608,7 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
     bool bad = false;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) collide_node<R, SC>(s, d[j], gx, gy, bad);
+    for (int j = 0; j < 4; ++j) collide_node<R, SC, sizeof(S) == 2>(s, d[j], gx, gy, bad);
     if (bad) atomicOr(s.err, ERR_UNSTABLE);
     const float sc = SC ? 1.f : s.scale;
     if (keep == 0xFu && sizeof(S) == 2 && s.sround) {

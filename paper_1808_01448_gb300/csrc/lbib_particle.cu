@@ -375,18 +375,216 @@ __host__ __device__ __forceinline__ bool spread_in_moments(int nl, int cap) {
     return 32 * sizeof(R) * (size_t)nl <= m;
 }
 
+// Solved spreading scales: the band of A (half bandwidth up to VB_PMAX,
+// VB_W entries per marker), the p + 1 interior solutions, the scales, and
+// the p x p Schur complement with its right-hand side.
+constexpr int VB_PMAX = LBIB_VB_MAX_BAND;
+constexpr int VB_W = VB_PMAX + 1;
+
 template <typename R>
-size_t smem_bytes_for(int nl, int T) {
+size_t vb_bytes(int nl) {
+    auto up = [](size_t b) { return (b + 15) & ~size_t(15); };
+    return 2 * up(sizeof(R) * VB_W * (size_t)nl) + up(sizeof(R) * nl) +
+           up(sizeof(R) * VB_PMAX * VB_W);
+}
+
+template <typename R>
+size_t smem_bytes_for(int nl, int T, bool vb) {
     auto up = [](size_t b) { return (b + 15) & ~size_t(15); };
     const size_t Tm = (size_t)region_edge(T);
     const size_t cap = (size_t)stage_cap(nl, (int)Tm);
     // the staged moments (and, where they do not fit there, the spreading
-    // contributions) are laid out last
+    // contributions) are laid out last, then the spreading-scale system
     const size_t moments = 3 * up(sizeof(R) * cap);
-    const size_t spread = spread_in_moments<R>(nl, (int)cap) ? 0 : 32 * sizeof(R) * (size_t)nl;
+    const size_t spread = spread_in_moments<R>(nl, (int)cap) ? 0 : up(32 * sizeof(R) * (size_t)nl);
     return up(sizeof(Pose<R>)) + 21 * up(sizeof(R) * nl) + 3 * up(sizeof(int) * nl) + up(nl) +
            up(sizeof(int) * nl) + up(sizeof(int) * (nl + 1)) + up(sizeof(R) * 2 * T * T) +
-           up(sizeof(double) * 3 * (P_THREADS / 32)) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread;
+           up(sizeof(double) * 3 * (P_THREADS / 32)) + up(sizeof(int4) * Tm) + up(sizeof(int) * (Tm + 1)) + moments + spread +
+           (vb ? vb_bytes<R>(nl) : 0);
+}
+
+// MLS shape functions of point l (after setup_point) as separable factors:
+// phi_(a,b) = wx[a] py[b] on the support node (ix0 + a, iy0 + b) (zero
+// without a fit or for a row outside the lattice).
+template <typename R>
+__device__ __forceinline__ void point_phi(const Points<R> &pt, int l, R wx[4], R py[4]) {
+    const int rows = pt.rows[l];
+    const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l];
+    const R mu_v = pt.mu_v[l];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) wx[a] = (rows & 16) ? bspline((R)(a - 1) - fx) : (R)0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        py[b] = (R)0;
+        if ((rows & 16) && (rows & (1 << b))) {
+            const R dy = (R)(b - 1) - fy;
+            const R wy = bspline(dy) * invW;
+            const R dyc = dy - mu;
+            py[b] = wy * ((R)1 - dyc * mu_v);
+        }
+    }
+}
+
+// Row l of the spreading-scale system (Vanella & Balaras, ref. [39]):
+// A[l][d] = A_(l, l + d mod n) = sum_k phi_k(X_l) phi_k(X_(l+d)) for
+// d = 0 .. p over the nodes the two supports share; a marker without a fit
+// has the identity row (its scale is not used).
+template <typename R>
+__device__ void vb_row(const Points<R> &pt, int l, int n, int p, R *A) {
+    R wl[4], pl[4];
+    point_phi(pt, l, wl, pl);
+    const bool fl = (pt.rows[l] & 16) != 0;
+    R *row = A + (size_t)l * VB_W;
+    R diag = (R)0;
+    if (fl) {
+        R sx = 0, sy = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            sx += wl[a] * wl[a];
+            sy += pl[a] * pl[a];
+        }
+        diag = sx * sy;
+    }
+    row[0] = fl ? diag : (R)1;
+#pragma unroll 1
+    for (int d = 1; d < VB_W; ++d) {
+        R acc = (R)0;
+        const int m = l + d < n ? l + d : l + d - n;
+        if (d <= p && fl && (pt.rows[m] & 16)) {
+            const int dx = pt.ix0[m] - pt.ix0[l], dy = pt.iy0[m] - pt.iy0[l];
+            if (dx > -4 && dx < 4 && dy > -4 && dy < 4) {
+                R wm[4], pm[4];
+                point_phi(pt, m, wm, pm);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int bb = b - dy;
+                    if (bb < 0 || bb > 3) continue;
+                    R sxm = 0;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int aa = a - dx;
+                        if (aa >= 0 && aa <= 3) sxm += wl[a] * wm[aa];
+                    }
+                    acc += pl[b] * pm[bb] * sxm;
+                }
+            }
+        }
+        row[d] = acc;
+    }
+}
+
+// Entry (i, j) of the original A from the band (rows of the border and the
+// band entries that reach into it are never overwritten by the
+// factorisation, which is all the solve reads here).
+template <typename R>
+__device__ __forceinline__ R vb_at(const R *A, int n, int p, int i, int j) {
+    int d = j - i;
+    if (d < 0) d += n;
+    if (d <= p) return A[(size_t)i * VB_W + d];
+    d = n - d;
+    return d <= p ? A[(size_t)j * VB_W + d] : (R)0;
+}
+
+// A eps = 1 for the cyclic band A (half bandwidth p, n >= 2 p + 2) by one
+// warp, bordered: the interior B (the first m = n - p markers, banded
+// without wrap) is factored B = L D L^T in place by lane 0; lanes 0 .. p
+// solve B Y_t = C_t (the coupling columns of the p border markers) and
+// B z = 1; lanes build the p x p Schur complement S = E - C^T Y and
+// 1 - C^T z; lane 0 solves S x = 1 - C^T z; the lanes form the interior
+// scales z - Y x.  In the compute precision.
+template <typename R>
+__device__ void vb_solve(R *A, R *Y, R *eps, R *S, int n, int p) {
+    const int lane = threadIdx.x & 31;
+    const int m = n - p;
+    if (lane == 0) {
+#pragma unroll 1
+        for (int k = 0; k < m; ++k) {
+            R *ak = A + (size_t)k * VB_W;
+            const R r = (R)1 / ak[0];
+            R la[VB_W];
+#pragma unroll
+            for (int a = 1; a < VB_W; ++a) la[a] = (a <= p && k + a < m) ? ak[a] * r : (R)0;
+#pragma unroll
+            for (int a = 1; a < VB_W; ++a) {
+                if (a > p || k + a >= m) continue;
+                R *row = A + (size_t)(k + a) * VB_W;
+#pragma unroll
+                for (int b = a; b < VB_W; ++b)
+                    if (b <= p && k + b < m) row[b - a] -= la[a] * ak[b];
+            }
+#pragma unroll
+            for (int a = 1; a < VB_W; ++a)
+                if (a <= p && k + a < m) ak[a] = la[a];
+        }
+    }
+    __syncwarp();
+    if (lane <= p) {
+        R *y = Y + (size_t)lane * n;
+        // forward L y = rhs, then D and L^T
+        R win[VB_PMAX];
+#pragma unroll
+        for (int a = 0; a < VB_PMAX; ++a) win[a] = (R)0;
+#pragma unroll 1
+        for (int i = 0; i < m; ++i) {
+            R v = lane < p ? vb_at(A, n, p, i, m + lane) : (R)1;
+#pragma unroll
+            for (int a = 1; a <= VB_PMAX; ++a)
+                if (a <= p && i - a >= 0) v -= A[(size_t)(i - a) * VB_W + a] * win[a - 1];
+#pragma unroll
+            for (int a = VB_PMAX - 1; a > 0; --a) win[a] = win[a - 1];
+            win[0] = v;
+            y[i] = v;
+        }
+#pragma unroll
+        for (int a = 0; a < VB_PMAX; ++a) win[a] = (R)0;
+#pragma unroll 1
+        for (int i = m - 1; i >= 0; --i) {
+            R v = y[i] / A[(size_t)i * VB_W];
+#pragma unroll
+            for (int a = 1; a <= VB_PMAX; ++a)
+                if (a <= p && i + a < m) v -= A[(size_t)i * VB_W + a] * win[a - 1];
+#pragma unroll
+            for (int a = VB_PMAX - 1; a > 0; --a) win[a] = win[a - 1];
+            win[0] = v;
+            y[i] = v;
+        }
+    }
+    __syncwarp();
+    // Schur complement S[q][r] (q, r < p) and its right-hand side S[q][p]:
+    // the coupling C_(i,q) = A_(i, m+q) is non-zero only for i <= q (through
+    // the wrap) and i >= m + q - p
+    for (int e = lane; e < p * (p + 1); e += 32) {
+        const int q = e / (p + 1), r = e - q * (p + 1);
+        R acc = r < p ? vb_at(A, n, p, m + q, m + r) : (R)1;
+        const R *yr = Y + (size_t)r * n;
+        for (int i = 0; i <= q; ++i) acc -= vb_at(A, n, p, i, m + q) * yr[i];
+        for (int i = max(m + q - p, q + 1); i < m; ++i) acc -= vb_at(A, n, p, i, m + q) * yr[i];
+        S[q * VB_W + r] = acc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // Gaussian elimination on the small symmetric positive-definite S
+#pragma unroll 1
+        for (int k = 0; k < p; ++k) {
+            const R r = (R)1 / S[k * VB_W + k];
+            for (int i = k + 1; i < p; ++i) {
+                const R f = S[i * VB_W + k] * r;
+                for (int j = k; j <= p; ++j) S[i * VB_W + j] -= f * S[k * VB_W + j];
+            }
+        }
+        for (int k = p - 1; k >= 0; --k) {
+            R v = S[k * VB_W + p];
+            for (int j = k + 1; j < p; ++j) v -= S[k * VB_W + j] * eps[m + j];
+            eps[m + k] = v / S[k * VB_W + k];
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) {
+        R v = Y[(size_t)p * n + i];
+        for (int q = 0; q < p; ++q) v -= Y[(size_t)q * n + i] * eps[m + q];
+        eps[i] = v;
+    }
+    __syncwarp();
 }
 
 // Reverse probability of Eq. 11 (dt = 1), in FP64 on every storage path:
@@ -473,10 +671,20 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     // them, last (the spreading contributions follow them when they do not
     // fit in their space)
     const int cap = stage_cap(nl, Tm);
-    const size_t mstride = (sizeof(R) * (size_t)cap + 15) / 16 * 16 / sizeof(R);
     R *mr = (R *)take(sizeof(R) * (size_t)cap);
     R *mjx = (R *)take(sizeof(R) * (size_t)cap);
     R *mjy = (R *)take(sizeof(R) * (size_t)cap);
+    R *spread_own = spread_in_moments<R>(nl, cap) ? nullptr : (R *)take(32 * sizeof(R) * (size_t)nl);
+    // solved spreading scales (ib_spread): band of A, interior solutions,
+    // scales, Schur complement
+    const bool vb = s.ib_spread != 0 && Pc.vb_p > 0;
+    R *vbA = nullptr, *vbY = nullptr, *vbE = nullptr, *vbS = nullptr;
+    if (vb) {
+        vbA = (R *)take(sizeof(R) * VB_W * (size_t)nl);
+        vbY = (R *)take(sizeof(R) * VB_W * (size_t)nl);
+        vbE = (R *)take(sizeof(R) * (size_t)nl);
+        vbS = (R *)take(sizeof(R) * VB_PMAX * VB_W);
+    }
 
     const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -861,9 +1069,21 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     // ---- 6. IB direct forcing at the (new) pose ---------------------------
     const R ghx = (R)0.5 * pick<R>(s.f_gx, s.gx), ghy = (R)0.5 * pick<R>(s.f_gy, s.gy);
     R Fx = 0, Fy = 0;
+    if (tid < nl)
+        setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[tid], ps.fyc + ry[tid], pt, tid);
+    // solved spreading scales: every marker's row of A once all supports are
+    // set up, then one warp solves A eps = 1 -- the last warp, beside the
+    // interpolation below, when it holds no marker
+    const int vb_warp = nl + 32 <= PT ? PT / 32 - 1 : 0;
+    const bool vb_beside = nl + 32 <= PT;
+    if (vb) {
+        __syncthreads();
+        if (tid < nl) vb_row<R>(pt, tid, nl, Pc.vb_p, vbA);
+        __syncthreads();
+        if (vb_beside && warp == vb_warp) vb_solve<R>(vbA, vbY, vbE, vbS, nl, Pc.vb_p);
+    }
     if (tid < nl) {
         const int l = tid;
-        setup_point<R>(s, ps.ixc, ps.iyc, ps.fxc + rx[l], ps.fyc + ry[l], pt, l);
         R s_rho = 0, s_u = 0, s_v = 0;
         support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
                           [&](R, R, R, R phi, R drho, R jx, R jy) {
@@ -876,36 +1096,26 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             const R rl = (R)1 + s_rho;
             const R udx = ps.uR - ps.omR * ry[l];
             const R udy = ps.vR + ps.omR * rx[l];
-            Fx = (R)2 * rl * (udx - s_u) * sS[l];
-            Fy = (R)2 * rl * (udy - s_v) * sS[l];
+            Fx = (R)2 * rl * (udx - s_u);
+            Fy = (R)2 * rl * (udy - s_v);
         }
     }
+    if (vb) {
+        if (!vb_beside && warp == vb_warp) vb_solve<R>(vbA, vbY, vbE, vbS, nl, Pc.vb_p);
+        __syncthreads();
+    }
+    // the spreading scale eps_l: the element length, or the solved scale
+    const R el = tid < nl ? (vb ? vbE[tid] : sS[tid]) : (R)0;
+    Fx *= el;
+    Fy *= el;
     // the near-box pass of the next step may be scheduled from here on (it
     // waits for this pass to end before it reads the tiles)
     asm volatile("griddepcontrol.launch_dependents;");
     using R2 = typename Pair<R>::type;
-    R2 *ctb = spread_in_moments<R>(nl, cap) ? (R2 *)mr : (R2 *)(mr + 3 * mstride);
+    R2 *ctb = spread_in_moments<R>(nl, cap) ? (R2 *)mr : (R2 *)spread_own;
     const int ox = ps.ixc - T / 2;
     const int oy = ps.iyc - T / 2;
-    // phi_(a,b) = wx[a] py[b] of marker l, as in support_sum (zero without a
-    // fit or for a row outside the lattice)
-    auto marker_phi = [&](int l, R wx[4], R py[4]) {
-        const int rows = pt.rows[l];
-        const R fx = pt.fx[l], fy = pt.fy[l], invW = pt.invW[l], mu = pt.mu[l];
-        const R mu_v = pt.mu_v[l];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) wx[a] = (rows & 16) ? bspline((R)(a - 1) - fx) : (R)0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            py[b] = (R)0;
-            if ((rows & 16) && (rows & (1 << b))) {
-                const R dy = (R)(b - 1) - fy;
-                const R wy = bspline(dy) * invW;
-                const R dyc = dy - mu;
-                py[b] = wy * ((R)1 - dyc * mu_v);
-            }
-        }
-    };
+    auto marker_phi = [&](int l, R wx[4], R py[4]) { point_phi(pt, l, wx, py); };
     // one spreading pass of the markers' forces (Fx, Fy) into a zeroed tile
     auto spread_pass = [&]() {
         // a zero tile for the spreading (T is even: whole 16-byte words)
@@ -975,8 +1185,8 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
                     }
                 }
             }
-            Fx += F0x - sS[tid] * ix;
-            Fy += F0y - sS[tid] * iy;
+            Fx += F0x - el * ix;
+            Fy += F0y - el * iy;
         }
         __syncthreads();    // every read of the tile before it is zeroed
         spread_pass();
@@ -1047,8 +1257,9 @@ cudaError_t by_kind(int kind, F &&f) {
 
 }  // namespace
 
-int particle_smem_bytes(int kind, int T, int nl) {
-    return (int)(kind == ST_F64 ? smem_bytes_for<double>(nl, T) : smem_bytes_for<float>(nl, T));
+int particle_smem_bytes(int kind, int T, int nl, bool vb) {
+    return (int)(kind == ST_F64 ? smem_bytes_for<double>(nl, T, vb)
+                                : smem_bytes_for<float>(nl, T, vb));
 }
 
 // Largest dynamic shared memory the particle kernel can use: the device's
