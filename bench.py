@@ -150,6 +150,7 @@ def build_workload(L, W, storage, stream, allocator, rounding="stochastic", name
 
 def _oracle_worker(args):
     name, idx, steps = args
+    os.environ["OMP_NUM_THREADS"] = "1"     # one thread per simulation process
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
     cfg, parts = workload_cases(name)[idx]

@@ -16,6 +16,11 @@
  *   6. rigid-body update to X^{n+1}                              (Eq. 13-16)
  *   7. IB direct forcing at X^{n+1}, MLS interpolation/spreading (Sec. "LB-IB")
  * The stored state is the post-collision population f* of the last step.
+ *
+ * The node loops (streaming, collision, moments) may run in parallel over
+ * nodes (an OpenMP parallel for, when built with -fopenmp): every node is
+ * computed by the same statements from the same inputs, so the results do
+ * not depend on the thread count.
  */
 #include "lbib_oracle.h"
 
@@ -249,6 +254,7 @@ static void stream(or_sim *s) {
     const or_config *c = &s->c;
     int nx = c->nx, ny = c->ny;
     size_t n = NN(s);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double f[9];
@@ -279,6 +285,7 @@ static void stream(or_sim *s) {
 
 static void collide(or_sim *s) {
     size_t n = NN(s);
+#pragma omp parallel for schedule(static)
     for (size_t k = 0; k < n; ++k) {
         double f[9], fp[9];
         for (int i = 0; i < 9; ++i) f[i] = s->fpre[i * n + k];
@@ -762,6 +769,7 @@ static void rigid_update(or_particle *p) {
 static void moments(const or_sim *s, double *rho, double *ux, double *uy, double addx,
                     double addy) {
     size_t n = NN(s);
+#pragma omp parallel for schedule(static)
     for (size_t k = 0; k < n; ++k) {
         double r = 0.0, jx = 0.0, jy = 0.0;
         for (int i = 0; i < 9; ++i) {
@@ -896,6 +904,7 @@ int or_fields(or_sim *s, double *rho, double *ux, double *uy) {
     prime(s);
     size_t n = NN(s);
     moments(s, rho, ux, uy, 0.0, 0.0);
+#pragma omp parallel for schedule(static)
     for (size_t k = 0; k < n; ++k) {
         double jx = ux[k] * rho[k], jy = uy[k] * rho[k];
         ux[k] = (jx + 0.5 * (s->c.gx + s->fibx[k])) / rho[k];

@@ -27,3 +27,21 @@ def run_case(cfg, parts, steps):
     r, u, v = o.fields()
     return {"bonds": bonds, "margins": margins, "fields": (r, u, v),
             "particle": o.particle(0)}
+
+
+def run_crop(cfg, parts, steps, crop):
+    """The oracle for `steps` steps; returns the fields on the crop window
+    (x0, y0, width, height; x periodic) and every particle's state."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    o = O.OracleSim(**cfg)
+    for p in parts:
+        o.add_particle(**p)
+    o.step(steps)
+    x0, y0, w, h = crop
+    xs = (np.arange(x0, x0 + w)) % cfg["nx"]
+    r, u, v = o.fields()
+    cut = tuple(f[y0:y0 + h][:, xs] for f in (r, u, v))
+    return {"fields": cut, "particles": [o.particle(k) for k in range(len(parts))],
+            "bonds": [o.bonds(k)[0] for k in range(len(parts))]}

@@ -11,8 +11,16 @@
    stepped inside the full batch.
 A bond difference in FP32 is accepted only at a step where the oracle logged
 a near tie (|U - P| or |gap - y_cr| below 1e-4); the first divergence step
-and the Hamming distance are printed.  The two large oracle runs go to worker
-processes started with spawn when the module's first test asks for them."""
+and the Hamming distance are printed.  The large oracle runs go to worker
+processes started with spawn when the module's first test asks for them.
+
+Precision study (the 4096 x 1024 shear channel at Re 1 with 8 particles of
+equal-area radius 12-24 near the bottom wall): FP32, FP16 and BF16 storage
+(stochastic rounding) against the FP64 oracle after 1000 steps on the
+512 x 128 window of the bottom wall that holds the most particles, within
+the stated bounds (velocity relative L2 / largest centroid error: FP32 1e-5 /
+1e-4, FP16 1e-3 / 1e-5, BF16 1e-2 / 1e-4); then 100,000 steps of each, the
+16-bit runs' drift from the FP32 run printed."""
 import multiprocessing as mp
 
 import numpy as np
@@ -30,6 +38,26 @@ def L():
     from paper_1808_01448_gb300 import build, lbib
     build.build()
     return lbib
+
+
+C4_STEPS = 1000
+C4_DRIFT_STEPS = 100_000
+C4_BOUND = {"f32": (1e-5, 1e-4), "f16": (1e-3, 1e-5), "bf16": (1e-2, 1e-4)}
+
+
+def c4_crop(cfg, parts, w=512, h=128):
+    """The 512 x 128 window on the bottom wall that holds the most particle
+    centroids (x periodic): (x0, y0, width, height)."""
+    xs = np.array([p["xc"] for p in parts])
+    best = max(range(0, cfg["nx"], 16),
+               key=lambda x0: int((((xs - x0) % cfg["nx"]) < w).sum()))
+    return best, 0, w, h
+
+
+def cut(fields, crop, nx):
+    x0, y0, w, h = crop
+    xs = np.arange(x0, x0 + w) % nx
+    return tuple(f[y0:y0 + h][:, xs] for f in fields)
 
 
 def c2_case():
@@ -51,8 +79,11 @@ def oracle_runs(O):
     pool = ctx.Pool(2)
     cfg2, parts2 = c2_case()
     sweep, i = c3_member()
+    cfg4, parts4 = W.particle_cluster()
     jobs = {"c2": pool.apply_async(_oracle_runs.run_case, (cfg2, parts2, 2000)),
-            "c3": pool.apply_async(_oracle_runs.run_case, (sweep[i][0], sweep[i][1], 1000))}
+            "c3": pool.apply_async(_oracle_runs.run_case, (sweep[i][0], sweep[i][1], 1000)),
+            "c4": pool.apply_async(_oracle_runs.run_crop,
+                                   (cfg4, parts4, C4_STEPS, c4_crop(cfg4, parts4)))}
     yield jobs
     pool.terminate()
     pool.join()
@@ -159,3 +190,45 @@ def test_c3_member_1000_steps_in_batch(L, oracle_runs):
     b.close()
     for s in sims:
         s.close()
+
+
+def test_c4_precision_study(L, oracle_runs):
+    cfg, parts = W.particle_cluster()
+    crop = c4_crop(cfg, parts)
+    sims = {}
+    for st in ("f32", "f16", "bf16"):
+        g = L.Sim(storage=st, **cfg)
+        for p in parts:
+            g.add_particle(**p)
+        g.step(C4_STEPS)
+        sims[st] = g
+    run = oracle_runs["c4"].get(timeout=3600)
+    _, uo, vo = run["fields"]
+    rows = []
+    for st, g in sims.items():
+        _, ug, vg = cut(g.fields(), crop, cfg["nx"])
+        e_u = rel_l2(np.stack([ug, vg]), np.stack([uo, vo]))
+        e_x = max(max(abs(g.particle(k)[q] - run["particles"][k][q]) for q in ("xc", "yc"))
+                  for k in range(len(parts)))
+        same = all(np.array_equal(g.bonds(k)[0], run["bonds"][k]) for k in range(len(parts)))
+        rows.append((st, e_u, e_x, same))
+        bu, bx = C4_BOUND[st]
+        assert e_u < bu and e_x < bx, (st, e_u, e_x)
+    for st, e_u, e_x, same in rows:
+        print(f"C4 {st} after {C4_STEPS} steps on crop {crop}: velocity rel L2 {e_u:.2e}, "
+              f"largest centroid error {e_x:.2e}, bond flags equal {same}")
+    # long-run drift of the 16-bit formats from FP32
+    for g in sims.values():
+        g.step(C4_DRIFT_STEPS - C4_STEPS)
+    _, u32, v32 = sims["f32"].fields()
+    p32 = [sims["f32"].particle(k) for k in range(len(parts))]
+    for st in ("f16", "bf16"):
+        _, u, v = sims[st].fields()
+        d_u = rel_l2(np.stack([u, v]), np.stack([u32, v32]))
+        d_x = max(max(abs(sims[st].particle(k)[q] - p32[k][q]) for q in ("xc", "yc"))
+                  for k in range(len(parts)))
+        print(f"C4 {st} vs FP32 after {C4_DRIFT_STEPS} steps: velocity rel L2 {d_u:.2e}, "
+              f"largest centroid difference {d_x:.2e}")
+        assert np.isfinite(d_u) and d_u < 0.1
+    for g in sims.values():
+        g.close()
