@@ -51,7 +51,8 @@ typedef enum lbib_status {
     LBIB_E_STATE = 4,        /* call not allowed in the handle's state */
     LBIB_E_UNSTABLE = 5,     /* the state became non-finite */
     LBIB_E_TIMEOUT = 6,      /* a bounded device wait ran out */
-    LBIB_E_UNSUPPORTED = 7   /* feature not built / not supported by device */
+    LBIB_E_UNSUPPORTED = 7,  /* feature not built / not supported by device */
+    LBIB_E_BOUNDS = 8        /* a bounds check of the debug build failed */
 } lbib_status;
 
 /* Wall kinds for the bottom (y = 0) and top (y = ny - 1) rows.
@@ -173,7 +174,11 @@ typedef struct lbib_particle {
  * properties, and counts of elements, ligands, probing and bonded ligands.
  * p_adhesion is the probability of adhesion of the paper's Fig. 6 at this
  * step: bonded ligands over the ligands close enough to a receptor wall to
- * bond (n_bonded / n_probing; 0 when none is). */
+ * bond (n_bonded / n_probing; 0 when none is).  gap_bottom / gap_top: the
+ * smallest distance from an element centroid to the bottom / top wall line
+ * at the pose of that step's bonds (the paper's separation distance y_min;
+ * negative when a centroid lies beyond the wall line; +inf before the first
+ * step or with periodic walls), as Eq. 12 takes it before its clamp. */
 typedef struct lbib_particle_state {
     double xc, yc, theta, u, v, omega;
     double Fh[2], Mh;
@@ -182,6 +187,7 @@ typedef struct lbib_particle_state {
     double area, mass, inertia, r_eq;
     int32_t nl, n_ligands, n_probing, n_bonded;
     double p_adhesion;
+    double gap_bottom, gap_top;
 } lbib_particle_state;
 
 typedef struct lbib_state {

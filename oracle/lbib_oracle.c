@@ -96,6 +96,7 @@ typedef struct or_particle {
      * the smallest |U - P| over the draws compared with a probability, and
      * the smallest |gap - y_cr| over the ligands' probing tests */
     double margin_p, margin_gap;
+    double gap[2];                  /* smallest element gaps to the wall lines */
 } or_particle;
 
 struct or_sim {
@@ -224,6 +225,7 @@ int or_add_particle(or_sim *s, const or_particle_in *in) {
     p->r_eq = sqrt(A / M_PI);
     p->sigma = in->sigma;
     p->margin_p = p->margin_gap = INFINITY;
+    p->gap[0] = p->gap[1] = INFINITY;
     p->xc = p->xc1 = in->xc;
     p->yc = p->yc1 = in->yc;
     p->theta = p->theta1 = in->theta;
@@ -723,7 +725,8 @@ static void wall_force(or_sim *s, int pid, const double *my) {
     const or_config *c = &s->c;
     or_particle *p = &s->p[pid];
     p->Fw[0] = p->Fw[1] = 0.0;
-    if (c->wall_bottom == OR_WALL_PERIODIC || c->hamaker == 0.0) return;
+    p->gap[0] = p->gap[1] = INFINITY;
+    if (c->wall_bottom == OR_WALL_PERIODIC) return;
     double yb, yt;
     wall_lines(c, &yb, &yt);
     double eb = 1e300, et = 1e300;
@@ -731,6 +734,9 @@ static void wall_force(or_sim *s, int pid, const double *my) {
         if (my[l] - yb < eb) eb = my[l] - yb;
         if (yt - my[l] < et) et = yt - my[l];
     }
+    p->gap[0] = eb;
+    p->gap[1] = et;
+    if (c->hamaker == 0.0) return;
     if (eb < c->eps_min) eb = c->eps_min;
     if (et < c->eps_min) et = c->eps_min;
     double k = c->hamaker / (8.0 * sqrt(2.0));
@@ -932,6 +938,7 @@ int or_particle_get(const or_sim *s, int pid, or_particle_state *o) {
     o->nl = p->nv; o->n_ligands = p->n_ligands;
     o->n_probing = p->n_probing; o->n_bonded = p->n_bonded;
     o->margin_p = p->margin_p; o->margin_gap = p->margin_gap;
+    o->gap_bottom = p->gap[0]; o->gap_top = p->gap[1];
     return 0;
 }
 

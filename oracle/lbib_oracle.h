@@ -64,6 +64,10 @@ typedef struct or_particle_state {
      * smallest |U - P| over the draws compared with P_f or P_r, and smallest
      * |gap - y_cr| over the ligands' probing tests (inf when there was none) */
     double margin_p, margin_gap;
+    /* smallest element-centroid gap to the bottom / top wall line at the
+     * pose of the last bond step (inf before the first step or with
+     * periodic walls) */
+    double gap_bottom, gap_top;
 } or_particle_state;
 
 typedef struct or_sim or_sim;

@@ -81,6 +81,7 @@ class OrParticleState(C.Structure):
         ("nl", C.c_int32), ("n_ligands", C.c_int32), ("n_probing", C.c_int32),
         ("n_bonded", C.c_int32),
         ("margin_p", C.c_double), ("margin_gap", C.c_double),
+        ("gap_bottom", C.c_double), ("gap_top", C.c_double),
     ]
 
 

@@ -434,6 +434,9 @@ void ellipse_outline(double ax, double by, int n, std::vector<double> &vx,
 }
 
 lbib_status err_status(lbib_sim *s, int err) {
+    if (err & ERR_BOUNDS)
+        return fail(LBIB_E_BOUNDS, "simulation %llu: a population index failed the debug build's "
+                    "bounds check", (unsigned long long)s->cfg.sim_id);
     if (err & ERR_TIMEOUT)
         return fail(LBIB_E_TIMEOUT, "simulation %llu: a bounded device wait of the lattice pass ran out",
                     (unsigned long long)s->cfg.sim_id);
@@ -461,6 +464,8 @@ void fill_state(lbib_particle_state &o, const ParticleDev &h, const HostParticle
     o.nl = p.nl; o.n_ligands = p.n_ligands; o.n_probing = h.n_probing;
     o.n_bonded = h.n_bonded;
     o.p_adhesion = h.n_probing > 0 ? (double)h.n_bonded / h.n_probing : 0.0;
+    o.gap_bottom = h.gap[0];
+    o.gap_top = h.gap[1];
 }
 
 lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
@@ -496,6 +501,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     h.inv_mass = 1.0 / p.mass; h.inv_inertia = 1.0 / p.inertia;
     h.nl = n; h.n_ligands = p.n_ligands; h.fixed = p.fixed; h.T = p.T; h.ncolors = p.ncolors;
     h.tile_ox = 0; h.tile_oy = -(1 << 28);   // no tile until the first IB pass
+    h.gap[0] = h.gap[1] = INFINITY;          // no bond step yet
     h.NB = near_edge(p.T); h.step = 0;
     h.vb_p = p.vb_p;
     h.mbx = mbx; h.mby = mby; h.nbx = nbx; h.nby = nby; h.S = S;
@@ -1042,7 +1048,13 @@ extern "C" {
 
 const char *lbib_last_error(void) { return g_err.c_str(); }
 
-const char *lbib_version(void) { return "lbib 0.1 sm_103a (D2Q9 LB-IB-MLS, Philox4x64-10)"; }
+const char *lbib_version(void) {
+#ifdef LBIB_DEBUG
+    return "lbib 0.2 sm_103a (D2Q9 LB-IB-MLS, Philox4x64-10) debug: bounds-checked";
+#else
+    return "lbib 0.2 sm_103a (D2Q9 LB-IB-MLS, Philox4x64-10)";
+#endif
+}
 
 lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out) {
     if (!cfg || !out) return fail(LBIB_E_ARG, "null argument");

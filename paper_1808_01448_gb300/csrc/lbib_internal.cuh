@@ -31,7 +31,7 @@ constexpr int NEAR_NPT = 1;
 constexpr int NEAR_TILE_NODES = LB_THREADS * NEAR_NPT;
 
 // Error bits of the per-simulation device error word.
-enum { ERR_UNSTABLE = 1, ERR_TIMEOUT = 2 };
+enum { ERR_UNSTABLE = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 4 };
 
 // Per-simulation descriptor as seen by the kernels of one batch.
 struct SimDev {
@@ -62,6 +62,25 @@ struct SimDev {
     int *err;                 // device: error bits
 };
 
+// Bounds checks of the debug build (-DLBIB_DEBUG): an element index i of a
+// population buffer ([9][ny][nx]) with `span` consecutive elements must lie
+// in [0, 9 nx ny - span].  Out of range, the simulation's error word gets
+// ERR_BOUNDS (reported as LBIB_E_BOUNDS), loads read element 0 instead and
+// stores are dropped.  Release builds compile the checks away.
+__device__ __forceinline__ bool pop_index_ok(const SimDev &s, int i, int span = 1) {
+#ifdef LBIB_DEBUG
+    const int total = 9 * s.nx * s.ny;
+    if (i < 0 || i > total - span) {
+        if (s.err) atomicOr(s.err, ERR_BOUNDS);
+        return false;
+    }
+#endif
+    return true;
+}
+__device__ __forceinline__ int pop_load_index(const SimDev &s, int i, int span = 1) {
+    return pop_index_ok(s, i, span) ? i : 0;
+}
+
 // Row of node index k: with t = ceil(log2 nx), m = ceil(2^(31+t) / nx) < 2^32
 // and k = q nx + r, k m / 2^(31+t) = q + r / nx + k e / (nx 2^(31+t)) with
 // e = m nx - 2^(31+t) < nx, and the last two terms stay below 1 for k < 2^31,
@@ -77,6 +96,7 @@ struct ParticleDev {
     double mass, inertia, r_eq, sigma;
     double inv_mass, inv_inertia;
     double Fh[2], Mh, Fb[2], Mb, Fw[2];
+    double gap[2];                      // smallest element gap to the bottom / top wall line
     int nl, n_ligands, n_probing, n_bonded;
     int fixed, T, ncolors, tile_ox;     // T: force-tile edge; tile origin x in [0, nx)
     int tile_oy, NB, vb_p, pad2;        // NB: edge of the near box; vb_p: half
@@ -347,6 +367,7 @@ template <typename S, typename R, bool STREAM = false>
 __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__ src, int x,
                                           int y, R d[9]) {
     auto ld = [&](int i, float inv) -> R {
+        i = pop_load_index(s, i);
         if constexpr (STREAM) return Store<S>::ld_cs(src, i, inv); else return Store<S>::ld(src, i, inv);
     };
     const int nx = s.nx, ny = s.ny;

@@ -117,6 +117,7 @@ template <typename S, typename R, bool STREAM = false, bool SC = false>
 __device__ __forceinline__ void store_node(const SimDev &s, S *__restrict__ dst, int N, int k,
                                            const R d[9]) {
     const float sc = SC ? 1.f : s.scale;
+    if (!pop_index_ok(s, k) || !pop_index_ok(s, 8 * N + k)) return;
     if (sizeof(S) == 2 && s.sround) {
         const unsigned h = dither_word(k, SC ? (float)d[0] * s.inv_scale : (float)d[0]);
 #pragma unroll
@@ -145,12 +146,13 @@ __device__ __forceinline__ void pull_group(const SimDev &s, const S *__restrict_
     const int xl = x0 == 0 ? nx - 1 : x0 - 1;       // left of the group
     const int xr = x0 + 4 == nx ? 0 : x0 + 4;        // right of the group
     auto ld1 = [&](int i) -> R {
+        i = pop_load_index(s, i);
         if constexpr (STREAM) return Store<S>::ld_cs(src, i, inv); else return Store<S>::ld(src, i, inv);
     };
     R v[4];
     // (plane, row of the source, x shift of the pull: +1 pulls from x - 1)
     auto plane = [&](int i, int row, int sh) {
-        Vec4<S, STREAM>::ld(src + i * N + row + x0, inv, v);
+        Vec4<S, STREAM>::ld(src + pop_load_index(s, i * N + row + x0, 4), inv, v);
         if (sh == 0) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) d[j][i] = v[j];
@@ -298,13 +300,13 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
                     const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
                     const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
                                            dither_plane(h[2], i), dither_plane(h[3], i)};
-                    Vec4<S, BULK>::st_r(dst + i * N + k, o, sc, r);
+                    if (pop_index_ok(s, i * N + k, 4)) Vec4<S, BULK>::st_r(dst + i * N + k, o, sc, r);
                 }
             } else if (keep[g] == 0xFu) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
-                    Vec4<S, BULK>::st(dst + i * N + k, o, sc);
+                    if (pop_index_ok(s, i * N + k, 4)) Vec4<S, BULK>::st(dst + i * N + k, o, sc);
                 }
             } else {
 #pragma unroll
@@ -621,13 +623,13 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
             const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
             const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
                                    dither_plane(h[2], i), dither_plane(h[3], i)};
-            Vec4<S, true>::st_r(dst + (size_t)i * N + kt, o, sc, r);
+            if (pop_index_ok(s, i * N + kt, 4)) Vec4<S, true>::st_r(dst + (size_t)i * N + kt, o, sc, r);
         }
     } else if (keep == 0xFu) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const R o[4] = {d[0][i], d[1][i], d[2][i], d[3][i]};
-            Vec4<S, true>::st(dst + (size_t)i * N + kt, o, sc);
+            if (pop_index_ok(s, i * N + kt, 4)) Vec4<S, true>::st(dst + (size_t)i * N + kt, o, sc);
         }
     } else {
 #pragma unroll

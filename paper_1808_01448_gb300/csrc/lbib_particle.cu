@@ -107,6 +107,7 @@ struct Pose {
     double xc, yc, th, u, v, om;
     double F[6];        // Fh x, y, M; Fb x, y, M (FP64 sums)
     double Fw;
+    double gapb, gapt;  // smallest element gaps to the wall lines (FP64)
     double csd, snd;    // FP64 cos, sin of the angle (bond geometry)
     int ixc, iyc;       // floor of the centroid (base node of relative coordinates)
     R fxc, fyc;         // centroid minus its floor
@@ -914,6 +915,8 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             }
             ps.nprobe = nprobe;
             ps.nbonded = nbonded;
+            ps.gapb = gb;
+            ps.gapt = gt;
             // ---- 4. wall force (Eq. 12), FP64 -------------------------
             // F_w = H_k / (8 sqrt 2) sqrt(r / eps^5) off each wall, eps the
             // smallest element gap clamped below by eps_min
@@ -960,15 +963,16 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             const int ym = yy == 0 ? s.ny - 1 : yy - 1, yp = yy == s.ny - 1 ? 0 : yy + 1;
             const int r0 = yy * nx, rm = ym * nx, rp = yp * nx;
             R d[9];
-            d[0] = Store<S>::ld(pop, r0 + xx, inv);
-            d[1] = Store<S>::ld(pop, N + r0 + xm, inv);
-            d[3] = Store<S>::ld(pop, 3 * N + r0 + xp, inv);
-            d[2] = Store<S>::ld(pop, 2 * N + rm + xx, inv);
-            d[5] = Store<S>::ld(pop, 5 * N + rm + xm, inv);
-            d[6] = Store<S>::ld(pop, 6 * N + rm + xp, inv);
-            d[4] = Store<S>::ld(pop, 4 * N + rp + xx, inv);
-            d[7] = Store<S>::ld(pop, 7 * N + rp + xp, inv);
-            d[8] = Store<S>::ld(pop, 8 * N + rp + xm, inv);
+            auto ldp = [&](int i) { return Store<S>::ld(pop, pop_load_index(s, i), inv); };
+            d[0] = ldp(r0 + xx);
+            d[1] = ldp(N + r0 + xm);
+            d[3] = ldp(3 * N + r0 + xp);
+            d[2] = ldp(2 * N + rm + xx);
+            d[5] = ldp(5 * N + rm + xm);
+            d[6] = ldp(6 * N + rm + xp);
+            d[4] = ldp(4 * N + rp + xx);
+            d[7] = ldp(7 * N + rp + xp);
+            d[8] = ldp(8 * N + rp + xm);
             node_moments(d, mr[i], mjx[i], mjy[i]);
         } else {
             const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy);
@@ -1059,6 +1063,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
         if (tid == 96) {
             P->Fb[0] = ps.F[3]; P->Fb[1] = ps.F[4]; P->Mb = ps.F[5];
             P->Fw[0] = 0.0; P->Fw[1] = ps.Fw;
+            P->gap[0] = ps.gapb; P->gap[1] = ps.gapt;
             P->n_probing = ps.nprobe;
             P->n_bonded = ps.nbonded;
         }

@@ -15,13 +15,15 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "liblbib.so")
+# LBIB_DEBUG=1 in the environment loads the bounds-checked debug build
+LIB_PATH = os.path.join(HERE, "_build", "liblbib_debug.so" if os.environ.get("LBIB_DEBUG") == "1"
+                        else "liblbib.so")
 LATTICE_VARIANTS = 6        # LBIB_LATTICE_VARIANTS of include/lbib.h
 
 WALL = {"zou_he": 0, "bounce_back": 1, "periodic": 2}
 STORAGE = {"f32": 0, "f64": 1, "f16": 2, "bf16": 3}
 STATUS = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_CUDA", 4: "E_STATE", 5: "E_UNSTABLE",
-          6: "E_TIMEOUT", 7: "E_UNSUPPORTED"}
+          6: "E_TIMEOUT", 7: "E_UNSUPPORTED", 8: "E_BOUNDS"}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -75,6 +77,7 @@ class ParticleState(C.Structure):
         ("r_eq", C.c_double),
         ("nl", C.c_int32), ("n_ligands", C.c_int32), ("n_probing", C.c_int32),
         ("n_bonded", C.c_int32), ("p_adhesion", C.c_double),
+        ("gap_bottom", C.c_double), ("gap_top", C.c_double),
     ]
 
 

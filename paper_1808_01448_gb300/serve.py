@@ -2,7 +2,9 @@
 
 Requests (a channel, its particles, a step count and a storage format)
 arrive over time.  The loop admits them while their device memory fits a
-budget, keeps every admitted simulation resident, and steps all of them
+budget (a request is admitted when an upper bound of its memory fits what
+is left, and then counts with the bytes the library actually allocated for
+it, lbib_device_bytes), keeps every admitted simulation resident, and steps all of them
 together: one batch per storage format (members of a batch share one
 lattice launch and one particle launch per step, see lbib_batch_*), each on
 its own stream so that the two batches overlap on the device.  Batches are
@@ -54,9 +56,12 @@ class Server:
 
     engine: object with create(req) -> handle, step(handles_by_storage,
       nsteps) (enqueue nsteps on every handle, grouped by storage, and wait),
-      result(handle) -> list of particle states, destroy(handle).
-    budget_bytes: admission limit on the summed request_bytes of the active
-      requests.
+      result(handle) -> list of particle states, destroy(handle), and
+      optionally device_bytes(handle) -> the bytes the handle holds.
+    budget_bytes: admission limit on the device memory of the active
+      requests: a request is admitted when request_bytes (an upper bound)
+      fits what is left, and is then counted with device_bytes of its
+      handle (request_bytes when the engine has no device_bytes).
     quantum: largest number of steps between two scheduling decisions.
     max_active: optional cap on the number of resident simulations.
     clock: callable returning seconds (wall clock by default); tests pass a
@@ -90,8 +95,13 @@ class Server:
                 break
             heapq.heappop(waiting)
             h = self.engine.create(req)
-            self.active[rid] = [req, h, int(req["steps"]), now]
-            self.used += need
+            held = need
+            if hasattr(self.engine, "device_bytes"):
+                held = int(self.engine.device_bytes(h))
+                if held > need:
+                    raise RuntimeError(f"request {rid} holds {held} bytes, above its bound {need}")
+            self.active[rid] = [req, h, int(req["steps"]), now, held]
+            self.used += held
             admitted = True
         return admitted
 
@@ -126,10 +136,10 @@ class Server:
                 c = v[0]["config"]
                 self.updates += q * c["nx"] * c["ny"]
             for rid in finished:
-                req, h, _, adm = self.active.pop(rid)
+                req, h, _, adm, held = self.active.pop(rid)
                 parts = self.engine.result(h)
                 self.engine.destroy(h)
-                self.used -= request_bytes(req)
+                self.used -= held
                 c = req["config"]
                 self.results.append(Result(rid, req["arrival_s"], adm, now, int(req["steps"]),
                                            c["nx"] * c["ny"], parts))
@@ -202,6 +212,9 @@ class LbibEngine:
 
     def result(self, s):
         return s.particles()
+
+    def device_bytes(self, s):
+        return s.device_bytes()
 
     def destroy(self, s):
         # the batch holding s is rebuilt before the next step

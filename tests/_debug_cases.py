@@ -1,0 +1,55 @@
+"""Cases run under both library builds by test_gpu_debug.py: writes the
+populations and particle states they end with to an .npz (argv[1])."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_1808_01448_gb300 import lbib as L  # noqa: E402
+from paper_1808_01448_gb300 import workloads as W  # noqa: E402
+
+
+def adhesion(nx, ny, shape, sim_id):
+    cfg = W.shear_channel(nx, ny, 1.0, tau=0.9, k_f=0.85, k_r0=0.03, kBT=0.02, seed=5,
+                          sim_id=sim_id, hamaker=1e-6)
+    cfg["y_cr"] = 1.0
+    return cfg, W.adhesion_particle(cfg, shape, 6.0, x=nx / 3, ligand_density=0.7, sigma=0.02,
+                                    gap_over_h=0.3 / (ny - 1))
+
+
+def main(out):
+    res = {}
+    # FP32 and FP16 batches (bulk, near-box and particle passes, vector path)
+    for st in ("f32", "f16", "f64"):
+        sims = []
+        for k, (nx, ny, shape) in enumerate(((96, 40, "ar2"), (128, 48, "circle"))):
+            cfg, p = adhesion(nx, ny, shape, k)
+            s = L.Sim(storage=st, **cfg)
+            s.add_particle(**p)
+            sims.append(s)
+        b = L.Batch(sims)
+        b.step(45)
+        b.synchronize()
+        for k, s in enumerate(sims):
+            res[f"{st}_{k}_pop"] = s.populations()
+            res[f"{st}_{k}_x"] = np.array([s.particle(0)[q] for q in ("xc", "yc", "theta")])
+        b.close()
+    # copy-engine staging variant of the bulk pass
+    cfg, p = adhesion(160, 48, "ar3", 7)
+    s = L.Sim(storage="f32", **cfg)
+    s.add_particle(**p)
+    b = L.Batch([s])
+    b.set_variant(4)
+    b.step(20)
+    b.synchronize()
+    res["tma_pop"] = s.populations()
+    b.close()
+    print(L.version())
+    np.savez(out, **res)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1])

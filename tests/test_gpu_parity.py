@@ -140,6 +140,8 @@ def test_full_step_parity_f64_with_bonds(O, L):
         assert pg["Mb"] == pytest.approx(po["Mb"], rel=1e-9, abs=1e-15), f"Mb at step {t + 1}"
         np.testing.assert_allclose(pg["Fb"], po["Fb"], rtol=1e-9, atol=1e-15)
         assert pg["Mh"] == pytest.approx(po["Mh"], rel=1e-6, abs=1e-12), f"Mh at step {t + 1}"
+        for k in ("gap_bottom", "gap_top"):
+            assert pg[k] == pytest.approx(po[k], abs=1e-12), f"{k} at step {t + 1}"
     assert total_bonded > 0          # the case exercises bond formation
     po, pg = o.particle(0), g.particle(0)
     for k in ("xc", "yc", "theta", "u", "v", "omega"):

@@ -112,6 +112,41 @@ def test_admission_respects_the_memory_budget():
     assert all(a.admitted_s <= b.admitted_s for a, b in zip(adm, adm[1:]))
 
 
+class HoldingEngine(FakeEngine):
+    """A fake engine whose handles hold a known number of bytes (less than
+    the admission bound), as the library reports them."""
+
+    def __init__(self, held, **kw):
+        super().__init__(**kw)
+        self.held = held
+
+    def device_bytes(self, h):
+        return self.held[h]
+
+
+def test_admission_counts_the_bytes_actually_held():
+    """Admission checks a request's upper bound against what is left and
+    then counts the bytes its handle holds: with handles holding half their
+    bound, more requests run together than the bound alone allows, and the
+    held bytes of the resident requests never exceed the budget."""
+    trace = small_trace(24)
+    bound = {r["rid"]: serve.request_bytes(r) for r in trace}
+    held = {rid: b // 2 for rid, b in bound.items()}
+    budget = 3 * max(bound.values())
+    eng = HoldingEngine(held, rate=1e6)
+    eng.nodes = {r["rid"]: r["config"]["nx"] * r["config"]["ny"] for r in trace}
+    srv = serve.Server(eng, budget_bytes=budget, quantum=32, clock=eng.clock)
+    res = srv.run(trace, t0=0.0)
+    assert len(res) == len(trace) and srv.used == 0
+    for n, members in eng.calls:
+        assert sum(held[m] for m in members) <= budget
+    plain = FakeEngine(rate=1e6)
+    plain.nodes = eng.nodes
+    srv2 = serve.Server(plain, budget_bytes=budget, quantum=32, clock=plain.clock)
+    srv2.run(trace, t0=0.0)
+    assert eng.max_active > plain.max_active
+
+
 def test_oversized_request_is_rejected():
     trace = small_trace(2)
     eng = FakeEngine()
