@@ -708,7 +708,11 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         int max_nl = 0;
         for (int i = 0; i < n; ++i)
             for (auto &p : sims[i]->parts) max_nl = std::max(max_nl, p.nl);
-        b->bd.pthreads = (b->kind != ST_F64 && max_nl <= 256 && nparts >= 32) ? 256 : 512;
+        // (the solved spreading scales keep their factorisation window in
+        // registers: 512-thread CTAs, which have twice the registers)
+        bool vb = false;
+        for (int i = 0; i < n; ++i) vb |= sims[i]->cfg.ib_spread != 0;
+        b->bd.pthreads = (b->kind != ST_F64 && max_nl <= 256 && nparts >= 32 && !vb) ? 256 : 512;
     }
     // copy-engine staging (variants 4, 5): rows of whole 16-byte words,
     // walls that are not periodic, 4- or 2-byte storage
@@ -1471,9 +1475,12 @@ lbib_status lbib_batch_set_particle_threads(lbib_batch *b, int32_t threads) {
     if (threads != 256 && threads != 512) return fail(LBIB_E_ARG, "threads must be 256 or 512");
     if (threads == 256) {
         if (b->kind == ST_F64) return fail(LBIB_E_ARG, "FP64 storage runs 512-thread particle CTAs");
-        for (lbib_sim *s : b->sims)
+        for (lbib_sim *s : b->sims) {
+            if (s->cfg.ib_spread)
+                return fail(LBIB_E_ARG, "solved spreading scales run 512-thread particle CTAs");
             for (auto &p : s->parts)
                 if (p.nl > 256) return fail(LBIB_E_ARG, "a particle has %d elements (> 256)", p.nl);
+        }
     }
     if (b->bd.pthreads == threads) return LBIB_OK;
     CK(cudaStreamSynchronize(b->stream));

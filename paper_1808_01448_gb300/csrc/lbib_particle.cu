@@ -486,64 +486,95 @@ __device__ __forceinline__ R vb_at(const R *A, int n, int p, int i, int j) {
     return d <= p ? A[(size_t)j * VB_W + d] : (R)0;
 }
 
-// A eps = 1 for the cyclic band A (half bandwidth p, n >= 2 p + 2) by one
-// warp, bordered: the interior B (the first m = n - p markers, banded
-// without wrap) is factored B = L D L^T in place by lane 0; lanes 0 .. p
-// solve B Y_t = C_t (the coupling columns of the p border markers) and
-// B z = 1; lanes build the p x p Schur complement S = E - C^T Y and
-// 1 - C^T z; lane 0 solves S x = 1 - C^T z; the lanes form the interior
-// scales z - Y x.  In the compute precision.
+// A eps = 1 for the cyclic band A (half bandwidth p <= VB_PMAX, n >= 2 p + 2)
+// by one warp, bordered: the interior B (the first m = n - p markers,
+// banded without wrap) is factored B = L D L^T by lane 0, right-looking, with
+// the active window W[a][b] = B_(k+a, k+b) (b >= a) in registers (entries
+// past the band are zero and stay zero: a band factor has no fill outside
+// the band); L is written over the interior band and 1 / D over its
+// diagonal, the border rows and the band entries that reach into the border
+// are left as they were.  Lanes 0 .. p then solve B Y_t = C_t (the coupling
+// columns of the p border markers) and B z = 1; lanes build the p x p Schur
+// complement S = E - C^T Y and 1 - C^T z; lane 0 solves S x = 1 - C^T z; the
+// lanes form the interior scales z - Y x.  In the compute precision.
 template <typename R>
-__device__ void vb_solve(R *A, R *Y, R *eps, R *S, int n, int p) {
+__device__ __forceinline__ R vb_recip(R x) {
+    if constexpr (sizeof(R) == 4) return __frcp_rn(x); else return (R)1 / x;
+}
+
+template <typename R>
+__device__ __noinline__ void vb_solve(R *A, R *Y, R *eps, R *S, int n, int p) {
     const int lane = threadIdx.x & 31;
     const int m = n - p;
     if (lane == 0) {
+        R W[VB_W][VB_W];
+#pragma unroll
+        for (int a = 0; a < VB_W; ++a)
+#pragma unroll
+            for (int b = a; b < VB_W; ++b)
+                W[a][b] = (b < m) ? A[(size_t)a * VB_W + (b - a)] : (R)0;
 #pragma unroll 1
         for (int k = 0; k < m; ++k) {
-            R *ak = A + (size_t)k * VB_W;
-            const R r = (R)1 / ak[0];
+            const R r = vb_recip(W[0][0]);
             R la[VB_W];
 #pragma unroll
-            for (int a = 1; a < VB_W; ++a) la[a] = (a <= p && k + a < m) ? ak[a] * r : (R)0;
+            for (int b = 1; b < VB_W; ++b) la[b] = W[0][b] * r;
+            R *ak = A + (size_t)k * VB_W;
+            ak[0] = r;
 #pragma unroll
-            for (int a = 1; a < VB_W; ++a) {
-                if (a > p || k + a >= m) continue;
-                R *row = A + (size_t)(k + a) * VB_W;
+            for (int b = 1; b < VB_W; ++b)
+                if (b <= p && k + b < m) ak[b] = la[b];
+            // trailing update, shifted to the window of step k + 1
 #pragma unroll
-                for (int b = a; b < VB_W; ++b)
-                    if (b <= p && k + b < m) row[b - a] -= la[a] * ak[b];
-            }
+            for (int a = 0; a < VB_PMAX; ++a)
 #pragma unroll
-            for (int a = 1; a < VB_W; ++a)
-                if (a <= p && k + a < m) ak[a] = la[a];
+                for (int b = a; b < VB_PMAX; ++b)
+                    W[a][b] = W[a + 1][b + 1] - la[a + 1] * W[0][b + 1];
+            // the window's new last column: column k + 1 + VB_PMAX of B as given
+            const int col = k + 1 + VB_PMAX;
+#pragma unroll
+            for (int a = 0; a < VB_W; ++a)
+                W[a][VB_PMAX] = (col < m && k + 1 + a < m)
+                                    ? A[(size_t)(k + 1 + a) * VB_W + (VB_PMAX - a)] : (R)0;
         }
     }
     __syncwarp();
     if (lane <= p) {
         R *y = Y + (size_t)lane * n;
-        // forward L y = rhs, then D and L^T
+        // forward L y = rhs (rhs: coupling column `lane`, or ones), two
+        // partial sums per row
         R win[VB_PMAX];
 #pragma unroll
         for (int a = 0; a < VB_PMAX; ++a) win[a] = (R)0;
 #pragma unroll 1
         for (int i = 0; i < m; ++i) {
-            R v = lane < p ? vb_at(A, n, p, i, m + lane) : (R)1;
+            R v = lane == p ? (R)1
+                            : ((i <= lane || i >= m + lane - p) ? vb_at(A, n, p, i, m + lane) : (R)0);
+            R v2 = (R)0;
 #pragma unroll
-            for (int a = 1; a <= VB_PMAX; ++a)
-                if (a <= p && i - a >= 0) v -= A[(size_t)(i - a) * VB_W + a] * win[a - 1];
+            for (int a = 1; a <= VB_PMAX; ++a) {
+                const R l = i - a >= 0 ? A[(size_t)(i - a) * VB_W + a] : (R)0;
+                if (a & 1) v -= l * win[a - 1]; else v2 -= l * win[a - 1];
+            }
+            v += v2;
 #pragma unroll
             for (int a = VB_PMAX - 1; a > 0; --a) win[a] = win[a - 1];
             win[0] = v;
             y[i] = v;
         }
+        // D z = y, L^T x = z
 #pragma unroll
         for (int a = 0; a < VB_PMAX; ++a) win[a] = (R)0;
 #pragma unroll 1
         for (int i = m - 1; i >= 0; --i) {
-            R v = y[i] / A[(size_t)i * VB_W];
+            const R *ai = A + (size_t)i * VB_W;
+            R v = y[i] * ai[0], v2 = (R)0;
 #pragma unroll
-            for (int a = 1; a <= VB_PMAX; ++a)
-                if (a <= p && i + a < m) v -= A[(size_t)i * VB_W + a] * win[a - 1];
+            for (int a = 1; a <= VB_PMAX; ++a) {
+                const R l = i + a < m ? ai[a] : (R)0;
+                if (a & 1) v -= l * win[a - 1]; else v2 -= l * win[a - 1];
+            }
+            v += v2;
 #pragma unroll
             for (int a = VB_PMAX - 1; a > 0; --a) win[a] = win[a - 1];
             win[0] = v;

@@ -29,15 +29,26 @@ def run_case(cfg, parts, steps):
             "particle": o.particle(0)}
 
 
+def shear_populations(O, cfg):
+    """Populations of the developed shear flow between the walls: at each
+    row the equilibrium (the oracle's Eq. 2) at rho = 1 and the linear
+    profile u = u_top y / (ny - 1) of Zou-He walls, [9][ny][nx]."""
+    ny, nx = cfg["ny"], cfg["nx"]
+    rows = np.stack([O.equilibrium(1.0, cfg["u_top"] * y / (ny - 1), 0.0) for y in range(ny)])
+    return np.ascontiguousarray(np.broadcast_to(rows.T[:, :, None], (9, ny, nx)))
+
+
 def run_crop(cfg, parts, steps, crop):
-    """The oracle for `steps` steps; returns the fields on the crop window
-    (x0, y0, width, height; x periodic) and every particle's state."""
+    """The oracle for `steps` steps from the developed shear flow; returns
+    the fields on the crop window (x0, y0, width, height; x periodic) and
+    every particle's state."""
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
     from oracle import oracle as O
     o = O.OracleSim(**cfg)
     for p in parts:
         o.add_particle(**p)
+    o.set_populations(shear_populations(O, cfg))
     o.step(steps)
     x0, y0, w, h = crop
     xs = (np.arange(x0, x0 + w)) % cfg["nx"]

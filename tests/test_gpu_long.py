@@ -15,7 +15,9 @@ and the Hamming distance are printed.  The large oracle runs go to worker
 processes started with spawn when the module's first test asks for them.
 
 Precision study (the 4096 x 1024 shear channel at Re 1 with 8 particles of
-equal-area radius 12-24 near the bottom wall): FP32, FP16 and BF16 storage
+equal-area radius 12-24 near the bottom wall, started from the developed
+linear shear flow, so that the flow on the crop near the bottom wall is not
+at rest): FP32, FP16 and BF16 storage
 (stochastic rounding) against the FP64 oracle after 1000 steps on the
 512 x 128 window of the bottom wall that holds the most particles, within
 the stated bounds (velocity relative L2 / largest centroid error: FP32 1e-5 /
@@ -192,14 +194,16 @@ def test_c3_member_1000_steps_in_batch(L, oracle_runs):
         s.close()
 
 
-def test_c4_precision_study(L, oracle_runs):
+def test_c4_precision_study(O, L, oracle_runs):
     cfg, parts = W.particle_cluster()
     crop = c4_crop(cfg, parts)
+    f0 = _oracle_runs.shear_populations(O, cfg)
     sims = {}
     for st in ("f32", "f16", "bf16"):
         g = L.Sim(storage=st, **cfg)
         for p in parts:
             g.add_particle(**p)
+        g.set_populations(f0)
         g.step(C4_STEPS)
         sims[st] = g
     run = oracle_runs["c4"].get(timeout=3600)
