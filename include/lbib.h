@@ -138,6 +138,15 @@ typedef struct lbib_config {
      * units lie more than LBIB_VB_MAX_BAND apart along its outline (a very
      * thin or small particle) is refused by lbib_add_particle (E_ARG). */
     int32_t ib_spread;
+    /* Streaming of the populations: 0 A/B (two buffers, the next step's
+     * populations pulled from the last step's), 1 in place (AA pattern: one
+     * buffer, so half the population memory; the steps alternate between
+     * reading a node's own slots and writing its neighbours' and the
+     * reverse).  The same results bit for bit; in place, the lattice pass
+     * takes its per-node form (no vector or copy-engine variants) and
+     * lbib_batch_autotune has nothing to time. */
+    int32_t stream_mode;
+    int32_t reserved2;
 } lbib_config;
 
 /* A rigid particle (Sec. "Pressure and viscous stresses"): a closed polygon

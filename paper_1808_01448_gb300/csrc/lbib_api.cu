@@ -259,8 +259,10 @@ SimDev simdev_from(const lbib_config &c, void *pop0, void *pop1, int *cur, long 
     d.d_nu = (c.tau - 0.5) / 3.0; d.f_nu = (float)d.d_nu;
     d.pop[0] = pop0; d.pop[1] = pop1;
     d.cur = cur; d.step = step; d.err = err;
-    // vector path: whole groups of four nodes per row, buffers 32-byte aligned
-    d.vec4 = c.nx % 4 == 0 && ((uintptr_t)pop0 % 32) == 0 && ((uintptr_t)pop1 % 32) == 0;
+    d.aa = c.stream_mode == 1;
+    // vector path (A/B streaming): whole groups of four nodes per row,
+    // buffers 32-byte aligned
+    d.vec4 = !d.aa && c.nx % 4 == 0 && ((uintptr_t)pop0 % 32) == 0 && ((uintptr_t)pop1 % 32) == 0;
     d.sround = c.rounding == LBIB_ROUND_STOCHASTIC;
     d.ib_iters = c.ib_iterations > 1 ? c.ib_iterations : 1;
     d.ib_spread = c.ib_spread != 0;
@@ -719,7 +721,8 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     int tma_ok = b->kind != ST_F64;
     for (int i = 0; i < n; ++i) {
         const int per16 = 16 / (int)storage_size(b->kind);
-        if (!hs[i].vec4 || hs[i].nx % per16 != 0 || hs[i].wall_b == LBIB_WALL_PERIODIC) tma_ok = 0;
+        if (!hs[i].vec4 || hs[i].nx % per16 != 0 || hs[i].wall_b == LBIB_WALL_PERIODIC || hs[i].aa)
+            tma_ok = 0;
     }
     b->bd.tma_ok = tma_ok;
     b->bd.wait_polls = wait_polls_setting();
@@ -1078,6 +1081,8 @@ lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out) {
         return fail(LBIB_E_ARG, "unknown rounding %d", c.rounding);
     if (c.ib_spread != 0 && c.ib_spread != 1)
         return fail(LBIB_E_ARG, "ib_spread must be 0 or 1");
+    if (c.stream_mode != 0 && c.stream_mode != 1)
+        return fail(LBIB_E_ARG, "stream_mode must be 0 (A/B) or 1 (in place)");
     if (!(c.kBT > 0) || c.k_f < 0 || c.k_r0 < 0 || c.y_cr < 0 || c.eps_min <= 0 ||
         c.receptor_bottom < 0 || c.receptor_top < 0)
         return fail(LBIB_E_ARG, "bond / wall-force parameters out of range");
@@ -1110,7 +1115,8 @@ lbib_status lbib_create(const lbib_config *cfg, lbib_sim **out) {
     }
     const size_t pb = 9 * s->N * storage_size(s->kind);
     s->pop[0] = dalloc(c, s->stream, pb);
-    s->pop[1] = dalloc(c, s->stream, pb);
+    // in-place streaming: one buffer for both parities
+    s->pop[1] = c.stream_mode == 1 ? s->pop[0] : dalloc(c, s->stream, pb);
     s->d_small = dalloc(c, s->stream, 64);
     if (!s->pop[0] || !s->pop[1] || !s->d_small) {
         lbib_destroy(s);
@@ -1145,7 +1151,7 @@ lbib_status lbib_destroy(lbib_sim *s) {
     free_batch(s->self);
     for (auto &p : s->parts) dfree(s->cfg, s->stream, p.d_block);
     dfree(s->cfg, s->stream, s->pop[0]);
-    dfree(s->cfg, s->stream, s->pop[1]);
+    if (s->pop[1] != s->pop[0]) dfree(s->cfg, s->stream, s->pop[1]);
     dfree(s->cfg, s->stream, s->d_small);
     dfree(s->cfg, s->stream, s->d_scratch);
     if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -1524,6 +1530,15 @@ lbib_status lbib_batch_autotune(lbib_batch *b, int32_t reps, int32_t *variant, d
         if (r != LBIB_OK) return r;
     }
     const int mode = b->overlap ? 1 : 0;
+    // in-place streaming has one buffer: a timing run would overwrite the
+    // state, so there is nothing to time (the per-node form runs anyway)
+    for (lbib_sim *s : b->sims)
+        if (s->cfg.stream_mode == 1) {
+            if (variant) *variant = b->bd.lat_variant;
+            if (ms)
+                for (int v = 0; v < LBIB_LATTICE_VARIANTS; ++v) ms[v] = 0.0;
+            return LBIB_OK;
+        }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     cudaError_t e = cudaEventCreate(&e1);
@@ -1758,6 +1773,7 @@ struct CkptHeader {
     int64_t step;
     double scale;
     uint64_t pop_bytes;
+    int32_t stream_mode, parity;     // in-place streaming: the state parity
 };
 
 struct CkptParticle {
@@ -1768,7 +1784,7 @@ struct CkptParticle {
 };
 
 const char CKPT_MAGIC[8] = {'L', 'B', 'I', 'B', 'C', 'K', 'P', 'T'};
-constexpr uint32_t CKPT_VERSION = 1;
+constexpr uint32_t CKPT_VERSION = 2;
 
 size_t pad8(size_t b) { return (b + 7) & ~size_t(7); }
 
@@ -1810,6 +1826,8 @@ lbib_status lbib_checkpoint_save(lbib_sim *s, void *host, size_t bytes) {
     hd.step = s->step;
     hd.scale = s->scale;
     hd.pop_bytes = 9 * s->N * storage_size(s->kind);
+    hd.stream_mode = s->cfg.stream_mode;
+    hd.parity = s->cur;
     memcpy(o, &hd, sizeof hd);
     o += sizeof hd;
     CK(cudaMemcpy(o, s->pop[s->cur], hd.pop_bytes, cudaMemcpyDeviceToHost));
@@ -1849,7 +1867,8 @@ lbib_status lbib_checkpoint_load(lbib_sim *s, const void *host, size_t bytes) {
         return fail(LBIB_E_ARG, "not an lbib checkpoint of version %u", CKPT_VERSION);
     if (hd.nx != s->cfg.nx || hd.ny != s->cfg.ny || hd.storage != s->kind ||
         hd.n_particles != (int32_t)s->parts.size() || hd.scale != (double)s->scale ||
-        hd.pop_bytes != 9 * s->N * storage_size(s->kind) || hd.step < 0)
+        hd.pop_bytes != 9 * s->N * storage_size(s->kind) || hd.step < 0 ||
+        hd.stream_mode != s->cfg.stream_mode || hd.parity < 0 || hd.parity > 1)
         return fail(LBIB_E_ARG, "checkpoint of a %d x %d lattice (storage %d, %d particles) does "
                     "not match this simulation", hd.nx, hd.ny, hd.storage, hd.n_particles);
     if (bytes < ckpt_bytes(s)) return fail(LBIB_E_ARG, "checkpoint truncated");
@@ -1869,6 +1888,11 @@ lbib_status lbib_checkpoint_load(lbib_sim *s, const void *host, size_t bytes) {
         if (r_ != LBIB_OK) return r_;
     }
     o += sizeof hd;
+    if (s->cfg.stream_mode == 1) {
+        // in place: the layout of the buffer depends on the state parity
+        s->cur = hd.parity;
+        CK(cudaMemcpy(s->d_cur, &hd.parity, sizeof(int), cudaMemcpyHostToDevice));
+    }
     CK(cudaMemcpy(s->pop[s->cur], o, hd.pop_bytes, cudaMemcpyHostToDevice));
     o += pad8(hd.pop_bytes);
     for (HostParticle &p : s->parts) {
@@ -1903,7 +1927,8 @@ lbib_status lbib_checkpoint_load(lbib_sim *s, const void *host, size_t bytes) {
 
 lbib_status lbib_device_bytes(lbib_sim *s, size_t *bytes) {
     if (!s || !bytes) return fail(LBIB_E_ARG, "null argument");
-    size_t b = 2 * 9 * s->N * storage_size(s->kind) + 64 + s->scratch_bytes;
+    size_t b = (s->pop[1] == s->pop[0] ? 1 : 2) * 9 * s->N * storage_size(s->kind) + 64 +
+               s->scratch_bytes;
     for (const HostParticle &p : s->parts) b += p.d_bytes;
     if (s->self) b += s->self->d_bytes;
     *bytes = b;

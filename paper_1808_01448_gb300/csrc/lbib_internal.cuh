@@ -42,6 +42,8 @@ struct SimDev {
     int sround;          // 16-bit storage: stochastic rounding of the stores
     int ib_iters;        // direct-forcing passes per step (>= 1)
     int ib_spread;       // spreading scale: 0 element lengths, 1 solved (A eps = 1)
+    int aa;              // in-place (AA) streaming: pop[0] == pop[1], *cur the state parity
+    int pad_aa;
     // k / nx = umulhi(k, nx_m) >> nx_s for 0 <= k < 2^31 (div_nx below)
     unsigned nx_m;
     int nx_s;
@@ -352,9 +354,24 @@ __device__ __forceinline__ R pick(float f, double d) {
     if constexpr (sizeof(R) == 4) return f; else return d;
 }
 
+// In-place (AA) streaming keeps one buffer F, its state alternating in
+// parity (the device word `cur`):
+//  - parity 0, after a swap step: F[opp(i)][x] = g_i(x), the post-collision
+//    population i of node x kept at the node in the opposite slot;
+//  - parity 1, after a push step: F[i][x + e_i] = g_i(x), already streamed.
+// A step from parity 1 reads f_i(x) = F[i][x] and stores g_i(x) in
+// F[opp(i)][x]; a step from parity 0 reads f_i(x) = F[opp(i)][x - e_i] and
+// stores g_i(x) in F[i][x + e_i].  Each node reads and writes the same nine
+// slots, so the update is race-free in place.  A population leaving through
+// a non-periodic wall is kept, as it is, in F[opp(i)][x] (both parities);
+// the moving-wall term of bounce-back is added where it is read, as in the
+// A/B pull, so the two schemes give the same bits.  The step of A/B stepping
+// from the buffer `cur` is the step of AA stepping from parity `cur`.
+//
 // Pre-collision deviations of node (x, y) for the coming step, pulled from
 // the post-collision buffer `src` (Eq. 1 LHS): population i comes from
-// (x - e_i).  x is periodic; rows beyond the walls follow the wall kind:
+// (x - e_i) (AA: from state parity `par` of the single buffer, as above).
+// x is periodic; rows beyond the walls follow the wall kind:
 //  - periodic: wrap in y;
 //  - half-way bounce-back: the node's own opposite population plus the
 //    moving-wall term 6 w_i (e_i . u_w) (rho_w = 1);
@@ -365,7 +382,7 @@ __device__ __forceinline__ R pick(float f, double d) {
 
 template <typename S, typename R, bool STREAM = false>
 __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__ src, int x,
-                                          int y, R d[9]) {
+                                          int y, R d[9], int par = 0) {
     auto ld = [&](int i, float inv) -> R {
         i = pop_load_index(s, i);
         if constexpr (STREAM) return Store<S>::ld_cs(src, i, inv); else return Store<S>::ld(src, i, inv);
@@ -382,31 +399,40 @@ __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__
         if (top) yp = 0;
         bot = top = false;
     }
-    const int r0 = y * nx;
-    d[0] = ld(r0 + x, inv);
-    d[1] = ld(N + r0 + xm, inv);
-    d[3] = ld(3 * N + r0 + xp, inv);
+    const int r0 = y * nx, own = r0 + x;
+    const bool aa = s.aa != 0;
+    // population i (opposite o) pulled from neighbour node nb: A/B plane i
+    // at nb; AA parity 0 plane o at nb; AA parity 1 plane i at the node
+    auto pin = [&](int i, int o, int nb) -> R {
+        return ld(!aa ? i * N + nb : (par ? i * N + own : o * N + nb), inv);
+    };
+    // population i from beyond a bounce-back wall: the node's own population
+    // o after its last collision (A/B plane o; AA plane i)
+    auto pwall = [&](int i, int o) -> R { return ld((aa ? i : o) * N + own, inv); };
+    d[0] = ld(own, inv);
+    d[1] = pin(1, 3, r0 + xm);
+    d[3] = pin(3, 1, r0 + xp);
     if (!bot) {
         const int rm = ym * nx;
-        d[2] = ld(2 * N + rm + x, inv);
-        d[5] = ld(5 * N + rm + xm, inv);
-        d[6] = ld(6 * N + rm + xp, inv);
+        d[2] = pin(2, 4, rm + x);
+        d[5] = pin(5, 7, rm + xm);
+        d[6] = pin(6, 8, rm + xp);
     } else if (s.wall_b == LBIB_WALL_BOUNCE_BACK) {
         const R uw6 = pick<R>(s.f_ub6, s.d_ub6);
-        d[2] = ld(4 * N + r0 + x, inv);
-        d[5] = ld(7 * N + r0 + x, inv) + uw6;
-        d[6] = ld(8 * N + r0 + x, inv) - uw6;
+        d[2] = pwall(2, 4);
+        d[5] = pwall(5, 7) + uw6;
+        d[6] = pwall(6, 8) - uw6;
     }
     if (!top) {
         const int rp = yp * nx;
-        d[4] = ld(4 * N + rp + x, inv);
-        d[7] = ld(7 * N + rp + xp, inv);
-        d[8] = ld(8 * N + rp + xm, inv);
+        d[4] = pin(4, 2, rp + x);
+        d[7] = pin(7, 5, rp + xp);
+        d[8] = pin(8, 6, rp + xm);
     } else if (s.wall_t == LBIB_WALL_BOUNCE_BACK) {
         const R uw6 = pick<R>(s.f_ut6, s.d_ut6);
-        d[4] = ld(2 * N + r0 + x, inv);
-        d[7] = ld(5 * N + r0 + x, inv) - uw6;
-        d[8] = ld(6 * N + r0 + x, inv) + uw6;
+        d[4] = pwall(4, 2);
+        d[7] = pwall(7, 5) - uw6;
+        d[8] = pwall(8, 6) + uw6;
     }
     if (bot && s.wall_b == LBIB_WALL_ZOU_HE) {
         const R uw = pick<R>(s.f_ub, s.u_b);
@@ -424,6 +450,27 @@ __device__ __forceinline__ void pull_node(const SimDev &s, const S *__restrict__
         d[7] = d[5] + h - (R)0.5 * rho * uw;
         d[8] = d[6] - h + (R)0.5 * rho * uw;
     }
+}
+
+// Buffer index of post-collision population i of node k (at (x, y)) as the
+// step from state `par` stores it: A/B plane i at k; AA (see above) parity 1
+// plane opp(i) at k, parity 0 plane i at x + e_i, or plane opp(i) at k when
+// x + e_i lies beyond a non-periodic wall.
+__device__ __forceinline__ int post_index(const SimDev &s, int i, int k, int x, int y, int par) {
+    constexpr int EXo[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int EYo[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    constexpr int OPo[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    const int N = s.nx * s.ny;
+    if (!s.aa) return i * N + k;
+    if (par) return OPo[i] * N + k;
+    int xx = x + EXo[i], yy = y + EYo[i];
+    if (xx < 0) xx += s.nx;
+    if (xx >= s.nx) xx -= s.nx;
+    if (yy < 0 || yy >= s.ny) {
+        if (s.wall_b != LBIB_WALL_PERIODIC) return OPo[i] * N + k;
+        yy = yy < 0 ? yy + s.ny : yy - s.ny;
+    }
+    return i * N + yy * s.nx + xx;
 }
 
 // Density deviation and momentum of a set of deviations (sum_i w_i e_i = 0).

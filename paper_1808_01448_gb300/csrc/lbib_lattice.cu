@@ -113,11 +113,28 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
 
 // SC: d is scaled (see collide_node); the dither hash takes the unscaled
 // first deviation either way.
+// AA streaming (s.aa): the slots of post_index for the step from state par.
 template <typename S, typename R, bool STREAM = false, bool SC = false>
 __device__ __forceinline__ void store_node(const SimDev &s, S *__restrict__ dst, int N, int k,
-                                           const R d[9]) {
+                                           const R d[9], int par = 0) {
     const float sc = SC ? 1.f : s.scale;
     if (!pop_index_ok(s, k) || !pop_index_ok(s, 8 * N + k)) return;
+    if (s.aa) {
+        const int y = div_nx(s, k), x = k - y * s.nx;
+        const unsigned h = (sizeof(S) == 2 && s.sround)
+                               ? dither_word(k, SC ? (float)d[0] * s.inv_scale : (float)d[0]) : 0u;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int j = post_index(s, i, k, x, y, par);
+            if (sizeof(S) == 2 && s.sround)
+                Store<S>::template st_r<STREAM>(dst, j, d[i], sc, dither_plane(h, i));
+            else if constexpr (STREAM)
+                Store<S>::st_cs(dst, j, d[i], sc);
+            else
+                Store<S>::st(dst, j, d[i], sc);
+        }
+        return;
+    }
     if (sizeof(S) == 2 && s.sround) {
         const unsigned h = dither_word(k, SC ? (float)d[0] * s.inv_scale : (float)d[0]);
 #pragma unroll
@@ -342,7 +359,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
     }
 #pragma unroll
     for (int j = 0; j < NPT; ++j)
-        if (!skip[j]) pull_node<S, R, BULK>(s, src, xs[j], ys[j], d[j]);
+        if (!skip[j]) pull_node<S, R, BULK>(s, src, xs[j], ys[j], d[j], cur);
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
@@ -350,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             R Fx = gx, Fy = gy;
             if (!BULK && s.np) tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
             collide_node<R, false, sizeof(S) == 2>(s, d[j], Fx, Fy, bad);
-            store_node<S, R, BULK>(s, dst, N, k0 + j * THREADS, d[j]);
+            store_node<S, R, BULK>(s, dst, N, k0 + j * THREADS, d[j], cur);
         }
     }
     if (bad) atomicOr(s.err, ERR_UNSTABLE);
@@ -407,7 +424,7 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
     R d[NEAR_NPT][9];
 #pragma unroll
     for (int j = 0; j < NEAR_NPT; ++j)
-        if (!skip[j]) pull_node<S, R>(s, src, xs[j], ys[j], d[j]);
+        if (!skip[j]) pull_node<S, R>(s, src, xs[j], ys[j], d[j], cur);
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < NEAR_NPT; ++j) {
@@ -415,7 +432,7 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
             R Fx = gx, Fy = gy;
             tile_force<R>(s, b.parts, xs[j], ys[j], Fx, Fy);
             collide_node<R, false, sizeof(S) == 2>(s, d[j], Fx, Fy, bad);
-            store_node<S, R>(s, dst, N, ys[j] * nx + xs[j], d[j]);
+            store_node<S, R>(s, dst, N, ys[j] * nx + xs[j], d[j], cur);
         }
     }
     if (bad) atomicOr(s.err, ERR_UNSTABLE);
@@ -686,7 +703,7 @@ __global__ void fields_kernel(SimDev s, ParticleDev *const *parts, double *rho_o
     const int y = k / s.nx, x = k - y * s.nx;
     const S *src = (const S *)s.pop[*s.cur];
     R d[9];
-    pull_node<S, R>(s, src, x, y, d);
+    pull_node<S, R>(s, src, x, y, d, *s.cur);
     R drho, jx, jy;
     node_moments(d, drho, jx, jy);
     R Fx = (R)s.gx, Fy = (R)s.gy;
@@ -697,15 +714,18 @@ __global__ void fields_kernel(SimDev s, ParticleDev *const *parts, double *rho_o
     if (uy_o) uy_o[k] = ((double)jy + 0.5 * (double)Fy) / rho;
 }
 
+// Post-collision populations of the last step ([9][ny][nx], full f): with
+// AA streaming they sit where the step from the other parity stored them.
 template <typename S>
 __global__ void export_pops_kernel(SimDev s, double *out) {
     const size_t N = (size_t)s.nx * s.ny;
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 9 * N) return;
-    const int i = (int)(k / N);
+    const int i = (int)(k / N), n = (int)(k - (size_t)i * N);
+    const int y = n / s.nx, x = n - y * s.nx;
     const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
     const S *src = (const S *)s.pop[*s.cur];
-    out[k] = w + (double)Store<S>::ld(src, (int)k, s.inv_scale);
+    out[k] = w + (double)Store<S>::ld(src, post_index(s, i, n, x, y, *s.cur ^ 1), s.inv_scale);
 }
 
 template <typename S, typename R>
@@ -713,10 +733,11 @@ __global__ void import_pops_kernel(SimDev s, const double *in) {
     const size_t N = (size_t)s.nx * s.ny;
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 9 * N) return;
-    const int i = (int)(k / N);
+    const int i = (int)(k / N), n = (int)(k - (size_t)i * N);
+    const int y = n / s.nx, x = n - y * s.nx;
     const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
     S *dst = (S *)s.pop[*s.cur];
-    Store<S>::st(dst, (int)k, (R)(in[k] - w), s.scale);
+    Store<S>::st(dst, post_index(s, i, n, x, y, *s.cur ^ 1), (R)(in[k] - w), s.scale);
 }
 
 template <typename R>

@@ -274,9 +274,10 @@ struct Moments {
 };
 
 template <typename S, typename R>
-__device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, int x, int y) {
+__device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, int x, int y,
+                                                int par) {
     R d[9];
-    pull_node<S, R>(s, pop, x, y, d);
+    pull_node<S, R>(s, pop, x, y, d, par);
     Moments<R> m;
     node_moments(d, m.drho, m.jx, m.jy);
     return m;
@@ -289,7 +290,8 @@ __device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, i
 // (staged region, else pulled).  One thread per point: the staged region is
 // in shared memory, so the sixteen nodes are a short loop, not a reduction.
 template <typename S, typename R, typename F>
-__device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const Points<R> &pt,
+__device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, int par,
+                                            const Points<R> &pt,
                                             int l, const R *mr, const R *mjx, const R *mjy,
                                             const int4 *span, const int *pre, int cap, int Tm,
                                             int rx0, int ry0, F &&f) {
@@ -339,7 +341,7 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, const
                     yy %= s.ny;
                     if (yy < 0) yy += s.ny;
                 }
-                const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy);
+                const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy, par);
                 drho = m.drho;
                 jx = m.jx;
                 jy = m.jy;
@@ -516,9 +518,12 @@ __device__ __noinline__ void vb_solve(R *A, R *Y, R *eps, R *S, int n, int p) {
 #pragma unroll 1
         for (int k = 0; k < m; ++k) {
             const R r = vb_recip(W[0][0]);
-            R la[VB_W];
+            R la[VB_W], w0[VB_W];        // row k as it was before the update
 #pragma unroll
-            for (int b = 1; b < VB_W; ++b) la[b] = W[0][b] * r;
+            for (int b = 1; b < VB_W; ++b) {
+                w0[b] = W[0][b];
+                la[b] = w0[b] * r;
+            }
             R *ak = A + (size_t)k * VB_W;
             ak[0] = r;
 #pragma unroll
@@ -529,7 +534,7 @@ __device__ __noinline__ void vb_solve(R *A, R *Y, R *eps, R *S, int n, int p) {
             for (int a = 0; a < VB_PMAX; ++a)
 #pragma unroll
                 for (int b = a; b < VB_PMAX; ++b)
-                    W[a][b] = W[a + 1][b + 1] - la[a + 1] * W[0][b + 1];
+                    W[a][b] = W[a + 1][b + 1] - la[a + 1] * w0[b + 1];
             // the window's new last column: column k + 1 + VB_PMAX of B as given
             const int col = k + 1 + VB_PMAX;
 #pragma unroll
@@ -719,6 +724,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     }
 
     const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
+    const int par = *s.cur ^ flip;       // state parity (in-place AA streaming)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double yb = s.wall_b == LBIB_WALL_BOUNCE_BACK ? -0.5 : 0.0;
     const double yt = s.wall_t == LBIB_WALL_BOUNCE_BACK ? (double)s.ny - 0.5 : (double)(s.ny - 1);
@@ -986,7 +992,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             yy %= s.ny;
             if (yy < 0) yy += s.ny;
         }
-        if (s.wall_b == LBIB_WALL_PERIODIC || (yy >= 1 && yy <= s.ny - 2)) {
+        if (!s.aa && (s.wall_b == LBIB_WALL_PERIODIC || (yy >= 1 && yy <= s.ny - 2))) {
             // interior node: nine plain pulls from rows yy - 1, yy, yy + 1
             const int nx = s.nx, N = nx * s.ny;
             const float inv = s.inv_scale;
@@ -1006,7 +1012,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             d[8] = ldp(8 * N + rp + xm);
             node_moments(d, mr[i], mjx[i], mjy[i]);
         } else {
-            const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy);
+            const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy, par);
             mr[i] = m.drho;
             mjx[i] = m.jx;
             mjy[i] = m.jy;
@@ -1022,7 +1028,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             const int l = tid;
             // (its support was set up with the staging)
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-            support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
+            support_sum<S, R>(s, pop, par, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
                               [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
                                   const R irho = recip_rho((R)1 + drho);
                                   const R ux = jx * irho, uy = jy * irho;
@@ -1121,7 +1127,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     if (tid < nl) {
         const int l = tid;
         R s_rho = 0, s_u = 0, s_v = 0;
-        support_sum<S, R>(s, pop, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
+        support_sum<S, R>(s, pop, par, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
                           [&](R, R, R, R phi, R drho, R jx, R jy) {
                               const R irho = recip_rho((R)1 + drho);
                               s_rho += phi * drho;

@@ -52,6 +52,7 @@ class Config(C.Structure):
         ("cuda_stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
         ("ib_iterations", C.c_int32), ("ib_spread", C.c_int32),
+        ("stream_mode", C.c_int32), ("reserved2", C.c_int32),
     ]
 
 
@@ -171,13 +172,15 @@ def make_config(storage="f32", stream=None, allocator=None, **kw) -> Config:
                     k_r0=1e-4, kBT=0.1, sigma_star_ratio=0.5, y_cr=1.36,
                     y_eq_ratio=0.5, hamaker=0.0, eps_min=0.1, receptor_bottom=1.0,
                     receptor_top=0.0, seed=1, sim_id=0, f16_scale=0.0, rounding="stochastic",
-                    ib_iterations=1, ib_spread=0)
+                    ib_iterations=1, ib_spread=0, stream_mode="ab")
     defaults.update(kw)
     for k, v in defaults.items():
         if k in ("wall_bottom", "wall_top") and isinstance(v, str):
             v = WALL[v]
         if k == "rounding" and isinstance(v, str):
             v = {"stochastic": 0, "nearest": 1}[v]
+        if k == "stream_mode" and isinstance(v, str):
+            v = {"ab": 0, "aa": 1}[v]
         setattr(c, k, v)
     c.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     c.cuda_stream = stream
