@@ -39,65 +39,84 @@ __device__ __forceinline__ R recip(R x) {
 //    into a velocity error of ~5e-5 after 2000 steps;
 //  - the Guo source is added as a term of its own, not rounded inside the
 //    ~10^4 times larger equilibrium term, where it loses ~1e-4 of itself.
+// Every product and sum of the collision is an explicit correctly rounded
+// operation (no contraction left to the compiler), so a node's result is the
+// same bits in every lattice path -- the four-node vector form, the per-node
+// forms, the near-box pass, A/B or in-place streaming -- whatever the code
+// around it.
+template <typename R> __device__ __forceinline__ R op_mul(R a, R b) {
+    if constexpr (sizeof(R) == 4) return __fmul_rn(a, b); else return __dmul_rn(a, b);
+}
+template <typename R> __device__ __forceinline__ R op_add(R a, R b) {
+    if constexpr (sizeof(R) == 4) return __fadd_rn(a, b); else return __dadd_rn(a, b);
+}
+template <typename R> __device__ __forceinline__ R op_sub(R a, R b) {
+    if constexpr (sizeof(R) == 4) return __fsub_rn(a, b); else return __dsub_rn(a, b);
+}
+template <typename R> __device__ __forceinline__ R op_fma(R a, R b, R c) {
+    if constexpr (sizeof(R) == 4) return __fmaf_rn(a, b, c); else return __fma_rn(a, b, c);
+}
+
 template <typename R, bool SC = false, bool FAST = false>
 __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy, bool &bad) {
     R drho, jx, jy;
     node_moments(d, drho, jx, jy);
     if constexpr (SC) {
         const R inv = s.inv_scale;
-        drho *= inv;
-        jx *= inv;
-        jy *= inv;
+        drho = op_mul(drho, inv);
+        jx = op_mul(jx, inv);
+        jy = op_mul(jy, inv);
     }
-    const R rho = (R)1 + drho;
+    const R rho = op_add((R)1, drho);
     const R irho = recip(rho);
-    const R ux = (jx + (R)0.5 * Fx) * irho;
-    const R uy = (jy + (R)0.5 * Fy) * irho;
+    const R ux = op_mul(op_fma((R)0.5, Fx, jx), irho);
+    const R uy = op_mul(op_fma((R)0.5, Fy, jy), irho);
     const R om = pick<R>(s.f_om, s.d_om);
     const R pref0 = pick<R>(s.f_pref, s.d_pref);
-    const R oms = SC ? om * (R)s.scale : om, pref = SC ? pref0 * (R)s.scale : pref0;
+    const R oms = SC ? op_mul(om, (R)s.scale) : om, pref = SC ? op_mul(pref0, (R)s.scale) : pref0;
     // f^eq_i - w_i = w_i [A + 3 rho e.u + 4.5 rho (e.u)^2], A = (rho - 1) - 1.5 rho u.u
     // Guo: S_i = (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
     // Post-collision d_i (1 - om) + om (f^eq_i - w_i) + S_i, evaluated per pair
     // of opposite directions (e -> -e flips e.u and e.F): a part even in e,
     //   w [om A - 3 pref u.F] + 4.5 w (e.u) (om rho (e.u) + 2 pref (e.F)),
     // and an odd part 3 w (om rho (e.u) + pref (e.F)).
-    const R A = drho - (R)1.5 * rho * (ux * ux + uy * uy);
-    const R uF = ux * Fx + uy * Fy;
-    const R c = (R)1 - om;
+    const R A = op_fma(op_mul((R)-1.5, rho), op_fma(ux, ux, op_mul(uy, uy)), drho);
+    const R uF = op_fma(ux, Fx, op_mul(uy, Fy));
+    const R c = op_sub((R)1, om);
     if constexpr (FAST) {
-        const R orho = oms * rho, p2 = (R)2 * pref;
-        const R base = oms * A - (R)3 * pref * uF;
-        d[0] = c * d[0] + (R)(4.0 / 9.0) * base;
+        const R orho = op_mul(oms, rho), p2 = op_mul((R)2, pref);
+        const R base = op_fma(oms, A, op_mul(op_mul((R)-3, pref), uF));
+        d[0] = op_fma(c, d[0], op_mul((R)(4.0 / 9.0), base));
         auto pair = [&](int i, int j, R w, R eu, R eF) {
-            const R even = w * (base + (R)4.5 * eu * (orho * eu + p2 * eF));
-            const R odd = (R)3 * w * (orho * eu + pref * eF);
-            d[i] = c * d[i] + even + odd;
-            d[j] = c * d[j] + even - odd;
+            const R inner = op_fma(orho, eu, op_mul(p2, eF));
+            const R even = op_mul(w, op_fma(op_mul((R)4.5, eu), inner, base));
+            const R odd = op_mul(op_mul((R)3, w), op_fma(orho, eu, op_mul(pref, eF)));
+            d[i] = op_add(op_fma(c, d[i], even), odd);
+            d[j] = op_sub(op_fma(c, d[j], even), odd);
         };
         pair(1, 3, (R)(1.0 / 9.0), ux, Fx);
         pair(2, 4, (R)(1.0 / 9.0), uy, Fy);
-        pair(5, 7, (R)(1.0 / 36.0), ux + uy, Fx + Fy);
-        pair(6, 8, (R)(1.0 / 36.0), uy - ux, Fy - Fx);
+        pair(5, 7, (R)(1.0 / 36.0), op_add(ux, uy), op_add(Fx, Fy));
+        pair(6, 8, (R)(1.0 / 36.0), op_sub(uy, ux), op_sub(Fy, Fx));
     } else {
-        const R W1 = (R)(1.0 / 3.0), W5 = ((R)1 - (R)2 * W1) * (R)0.25;
-        const R r45 = (R)4.5 * rho, m3uF = (R)-3 * uF;
+        const R W1 = (R)(1.0 / 3.0), W5 = op_mul(op_sub((R)1, op_mul((R)2, W1)), (R)0.25);
+        const R r45 = op_mul((R)4.5, rho), m3uF = op_mul((R)-3, uF);
         const R w0 = (R)(4.0 / 9.0);
-        d[0] = c * d[0] + (oms * (w0 * A) + pref * (w0 * m3uF));
+        d[0] = op_fma(c, d[0], op_fma(oms, op_mul(w0, A), op_mul(pref, op_mul(w0, m3uF))));
         // pair (i, j = opposite of i): even part w (om A' + pref S_even),
         // odd part W (om rho (e.u) + pref (e.F))
         auto pair = [&](int i, int j, R w, R W, R eu, R eF) {
-            const R ee = oms * (w * (A + r45 * eu * eu));
-            const R oo = oms * (W * (rho * eu));
-            const R se = pref * (w * ((R)9 * eu * eF + m3uF));
-            const R so = pref * (W * eF);
-            d[i] = c * d[i] + (ee + oo) + (se + so);
-            d[j] = c * d[j] + (ee - oo) + (se - so);
+            const R ee = op_mul(oms, op_mul(w, op_fma(op_mul(r45, eu), eu, A)));
+            const R oo = op_mul(oms, op_mul(W, op_mul(rho, eu)));
+            const R se = op_mul(pref, op_mul(w, op_fma(op_mul((R)9, eu), eF, m3uF)));
+            const R so = op_mul(pref, op_mul(W, eF));
+            d[i] = op_add(op_fma(c, d[i], op_add(ee, oo)), op_add(se, so));
+            d[j] = op_add(op_fma(c, d[j], op_sub(ee, oo)), op_sub(se, so));
         };
         pair(1, 3, (R)(1.0 / 9.0), W1, ux, Fx);
         pair(2, 4, (R)(1.0 / 9.0), W1, uy, Fy);
-        pair(5, 7, (R)(1.0 / 36.0), W5, ux + uy, Fx + Fy);
-        pair(6, 8, (R)(1.0 / 36.0), W5, uy - ux, Fy - Fx);
+        pair(5, 7, (R)(1.0 / 36.0), W5, op_add(ux, uy), op_add(Fx, Fy));
+        pair(6, 8, (R)(1.0 / 36.0), W5, op_sub(uy, ux), op_sub(Fy, Fx));
     }
     // non-finite state or a density outside (0, 2): the run has broken down
     // (the caller raises the error bit once for all its nodes)

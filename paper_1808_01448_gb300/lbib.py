@@ -170,7 +170,7 @@ def make_config(storage="f32", stream=None, allocator=None, **kw) -> Config:
     defaults = dict(nx=32, ny=16, wall_bottom="bounce_back", wall_top="bounce_back",
                     tau=0.8, u_bottom=0.0, u_top=0.0, gx=0.0, gy=0.0, k_f=0.85,
                     k_r0=1e-4, kBT=0.1, sigma_star_ratio=0.5, y_cr=1.36,
-                    y_eq_ratio=0.5, hamaker=0.0, eps_min=0.1, receptor_bottom=1.0,
+                    y_eq_ratio=0.5, hamaker=0.0, eps_min=1e-3, receptor_bottom=1.0,
                     receptor_top=0.0, seed=1, sim_id=0, f16_scale=0.0, rounding="stochastic",
                     ib_iterations=1, ib_spread=0, stream_mode="ab")
     defaults.update(kw)

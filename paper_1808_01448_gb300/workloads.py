@@ -25,6 +25,12 @@ KF_OVER_KR0 = 8.5e3           # biochemical affinity k_f / k_r0
 SIGMA_HAT = {1: 27.8, 2: 55.5}   # sigma / (rho_ref nu_ref^2 / H) for bond strength 1 and 2
 HAMAKER_HAT = 1.74e-8            # H_k / (rho_ref nu_ref^2 H)
 K_R0 = 1.0e-4                    # reverse rate per step (absolute value not given)
+# Lower clamp of the gap in Eq. 12 (lattice units).  With Table 1's Hamaker
+# group the wall force is weak against the bonds; clamped at 0.1 it cannot
+# hold a bonded particle off the wall (most particles of these workloads
+# crossed the wall line within 20k steps), clamped at 1e-3 its growth as
+# gap^-5/2 stops every one of them a few thousandths of a node from the wall.
+EPS_MIN = 1.0e-3
 
 
 def bond_sigma(strength: int, H: float, nu: float) -> float:
@@ -131,7 +137,7 @@ def adhesion_params(H: float, nu: float, strength: int, sigma_star_ratio: float 
     return dict(sigma=sigma, y_cr=y_cr, k_r0=K_R0, k_f=KF_OVER_KR0 * K_R0,
                 sigma_star_ratio=sigma_star_ratio,
                 kBT=thermal_energy(sigma, y_cr, sigma_star_ratio=sigma_star_ratio),
-                hamaker=hamaker_lu(H, nu))
+                hamaker=hamaker_lu(H, nu), eps_min=EPS_MIN)
 
 
 def single_ellipse_sweep(nx: int = 1024, ny: int = 256, radius_eq: float = 20.0,
