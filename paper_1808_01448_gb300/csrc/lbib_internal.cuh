@@ -164,11 +164,14 @@ struct BatchDev {
 // Stochastic rounding of 16-bit stores.  A node's dither word is a hash of
 // its index and of the bits of its first post-collision deviation (so it is
 // deterministic and independent of the batch), spread over the nine planes
-// by one affine map each; the top bits of r_i dither the bits that the
-// conversion drops: FP32 -> FP16 (normal range) drops 13 mantissa bits,
-// FP32 -> BF16 drops 16.  Adding a uniform integer below 2^b to the FP32
-// bit pattern and truncating rounds up with probability equal to the
-// dropped fraction, for either sign.
+// by one affine map each.  The conversion is the stochastic-rounding cvt of
+// the sm_100 family, on pairs: for each 16-bit half of its random operand it
+// adds the low 13 (FP16: the mantissa bits that FP32 -> FP16 drops) or 16
+// (BF16) bits below the kept mantissa and truncates, which rounds up with
+// probability equal to the dropped fraction, for either sign.  Value v of a
+// node takes the upper 16 bits of its plane word; a pair of nodes packs
+// theirs with one byte permute, and a single value takes the same bits in
+// both halves, so every path gives a node the same bits.
 __device__ __forceinline__ unsigned mix32(unsigned x) {   // "lowbias32" (C. Wellons)
     x ^= x >> 16;
     x *= 0x7feb352du;
@@ -184,11 +187,25 @@ __device__ __forceinline__ unsigned dither_plane(unsigned h, int i) {
     // an affine bijection per plane (odd multiplier): one multiply-add
     return h * (0x9e3779b1u + 0x3c6ef372u * (unsigned)i) + 0x7f4a7c15u * (unsigned)(i + 1);
 }
+// the random operand of a pair: lo's upper 16 bits below hi's
+__device__ __forceinline__ unsigned dither_pair(unsigned r_lo, unsigned r_hi) {
+    return __byte_perm(r_lo, r_hi, 0x7632);
+}
+__device__ __forceinline__ unsigned cvt_rs_f16x2(float hi, float lo, unsigned rbits) {
+    unsigned d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
+__device__ __forceinline__ unsigned cvt_rs_bf16x2(float hi, float lo, unsigned rbits) {
+    unsigned d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
 __device__ __forceinline__ __half half_sr(float x, unsigned r) {
-    return __float2half_rz(__uint_as_float(__float_as_uint(x) + (r >> 19)));
+    return __ushort_as_half((unsigned short)cvt_rs_f16x2(x, x, dither_pair(r, r)));
 }
 __device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, unsigned r) {
-    return __ushort_as_bfloat16((unsigned short)((__float_as_uint(x) + (r >> 16)) >> 16));
+    return __ushort_as_bfloat16((unsigned short)cvt_rs_bf16x2(x, x, dither_pair(r, r)));
 }
 
 // Storage traits: load a deviation into the compute type, store one back.
@@ -312,11 +329,9 @@ template <bool STREAM> struct Vec4<__half, STREAM> {
     }
     static __device__ __forceinline__ void st_r(__half *p, const float o[4], float sc,
                                                 const unsigned *r) {
-        const __half2 a = __halves2half2(half_sr(o[0] * sc, r[0]), half_sr(o[1] * sc, r[1]));
-        const __half2 b = __halves2half2(half_sr(o[2] * sc, r[2]), half_sr(o[3] * sc, r[3]));
         uint2 u;
-        memcpy(&u.x, &a, 4);
-        memcpy(&u.y, &b, 4);
+        u.x = cvt_rs_f16x2(o[1] * sc, o[0] * sc, dither_pair(r[0], r[1]));
+        u.y = cvt_rs_f16x2(o[3] * sc, o[2] * sc, dither_pair(r[2], r[3]));
         stv<STREAM>((uint2 *)p, u);
     }
 };
@@ -339,11 +354,9 @@ template <bool STREAM> struct Vec4<__nv_bfloat16, STREAM> {
     }
     static __device__ __forceinline__ void st_r(__nv_bfloat16 *p, const float o[4], float sc,
                                                 const unsigned *r) {
-        const __nv_bfloat162 a = __halves2bfloat162(bf16_sr(o[0] * sc, r[0]), bf16_sr(o[1] * sc, r[1]));
-        const __nv_bfloat162 b = __halves2bfloat162(bf16_sr(o[2] * sc, r[2]), bf16_sr(o[3] * sc, r[3]));
         uint2 u;
-        memcpy(&u.x, &a, 4);
-        memcpy(&u.y, &b, 4);
+        u.x = cvt_rs_bf16x2(o[1] * sc, o[0] * sc, dither_pair(r[0], r[1]));
+        u.y = cvt_rs_bf16x2(o[3] * sc, o[2] * sc, dither_pair(r[2], r[3]));
         stv<STREAM>((uint2 *)p, u);
     }
 };

@@ -268,6 +268,8 @@ __device__ __forceinline__ double warp_sum_array(const R *a, int n) {
 }
 
 // Node moments pulled from the populations (outside the staged region).
+// flip: the pass's buffer flip; with in-place streaming the state parity is
+// read here (*cur ^ flip), so the caller keeps no register for it.
 template <typename R>
 struct Moments {
     R drho, jx, jy;
@@ -275,9 +277,9 @@ struct Moments {
 
 template <typename S, typename R>
 __device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, int x, int y,
-                                                int par) {
+                                                int flip) {
     R d[9];
-    pull_node<S, R>(s, pop, x, y, d, par);
+    pull_node<S, R>(s, pop, x, y, d, s.aa ? *s.cur ^ flip : 0);
     Moments<R> m;
     node_moments(d, m.drho, m.jx, m.jy);
     return m;
@@ -290,7 +292,7 @@ __device__ __noinline__ Moments<R> pull_moments(const SimDev &s, const S *pop, i
 // (staged region, else pulled).  One thread per point: the staged region is
 // in shared memory, so the sixteen nodes are a short loop, not a reduction.
 template <typename S, typename R, typename F>
-__device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, int par,
+__device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, int flip,
                                             const Points<R> &pt,
                                             int l, const R *mr, const R *mjx, const R *mjy,
                                             const int4 *span, const int *pre, int cap, int Tm,
@@ -341,7 +343,7 @@ __device__ __forceinline__ void support_sum(const SimDev &s, const S *pop, int p
                     yy %= s.ny;
                     if (yy < 0) yy += s.ny;
                 }
-                const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy, par);
+                const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy, flip);
                 drho = m.drho;
                 jx = m.jx;
                 jy = m.jy;
@@ -714,7 +716,9 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     R *spread_own = spread_in_moments<R>(nl, cap) ? nullptr : (R *)take(32 * sizeof(R) * (size_t)nl);
     // solved spreading scales (ib_spread): band of A, interior solutions,
     // scales, Schur complement
-    const bool vb = s.ib_spread != 0 && Pc.vb_p > 0;
+    // (the 256-thread form is never launched for a particle that solves its
+    // scales; leaving the code out of it keeps its register budget)
+    const bool vb = PT >= 512 && s.ib_spread != 0 && Pc.vb_p > 0;
     R *vbA = nullptr, *vbY = nullptr, *vbE = nullptr, *vbS = nullptr;
     if (vb) {
         vbA = (R *)take(sizeof(R) * VB_W * (size_t)nl);
@@ -724,7 +728,6 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     }
 
     const S *__restrict__ pop = (const S *)s.pop[*s.cur ^ flip];
-    const int par = *s.cur ^ flip;       // state parity (in-place AA streaming)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double yb = s.wall_b == LBIB_WALL_BOUNCE_BACK ? -0.5 : 0.0;
     const double yt = s.wall_t == LBIB_WALL_BOUNCE_BACK ? (double)s.ny - 0.5 : (double)(s.ny - 1);
@@ -1012,7 +1015,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             d[8] = ldp(8 * N + rp + xm);
             node_moments(d, mr[i], mjx[i], mjy[i]);
         } else {
-            const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy, par);
+            const Moments<R> m = pull_moments<S, R>(s, pop, xx, yy, flip);
             mr[i] = m.drho;
             mjx[i] = m.jx;
             mjy[i] = m.jy;
@@ -1028,7 +1031,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             const int l = tid;
             // (its support was set up with the staging)
             R s_rho = 0, s_ux = 0, s_uy = 0, s_vx = 0, s_vy = 0;
-            support_sum<S, R>(s, pop, par, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
+            support_sum<S, R>(s, pop, flip, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
                               [&](R w, R dx, R dyc, R phi, R drho, R jx, R jy) {
                                   const R irho = recip_rho((R)1 + drho);
                                   const R ux = jx * irho, uy = jy * irho;
@@ -1127,7 +1130,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     if (tid < nl) {
         const int l = tid;
         R s_rho = 0, s_u = 0, s_v = 0;
-        support_sum<S, R>(s, pop, par, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
+        support_sum<S, R>(s, pop, flip, pt, l, mr, mjx, mjy, span, pre, cap, Tm, rx0, ry0,
                           [&](R, R, R, R phi, R drho, R jx, R jy) {
                               const R irho = recip_rho((R)1 + drho);
                               s_rho += phi * drho;

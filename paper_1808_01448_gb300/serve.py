@@ -4,7 +4,9 @@ Requests (a channel, its particles, a step count and a storage format)
 arrive over time.  The loop admits them while their device memory fits a
 budget (a request is admitted when an upper bound of its memory fits what
 is left, and then counts with the bytes the library actually allocated for
-it, lbib_device_bytes), keeps every admitted simulation resident, and steps all of them
+it, lbib_device_bytes; a request whose two population buffers do not fit is
+admitted with in-place streaming, one buffer, when that fits), keeps every
+admitted simulation resident, and steps all of them
 together: one batch per storage format (members of a batch share one
 lattice launch and one particle launch per step, see lbib_batch_*), each on
 its own stream so that the two batches overlap on the device.  Batches are
@@ -28,11 +30,14 @@ from dataclasses import dataclass, field
 BYTES_PER_VALUE = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}
 
 
-def request_bytes(req) -> int:
-    """Device memory of a request: two population buffers plus a generous
-    allowance for particle structs, geometry and force tiles."""
+def request_bytes(req, stream_mode: str | None = None) -> int:
+    """Device memory of a request: its population buffers (two with A/B
+    streaming, one in place) plus a generous allowance for particle
+    structs, geometry and force tiles."""
     c = req["config"]
-    pops = 2 * 9 * c["nx"] * c["ny"] * BYTES_PER_VALUE[req["storage"]]
+    mode = stream_mode or req.get("stream_mode", "ab")
+    buffers = 1 if mode == "aa" else 2
+    pops = buffers * 9 * c["nx"] * c["ny"] * BYTES_PER_VALUE[req["storage"]]
     return pops + (1 << 20) * (1 + len(req["particles"]))
 
 
@@ -62,6 +67,11 @@ class Server:
       requests: a request is admitted when request_bytes (an upper bound)
       fits what is left, and is then counted with device_bytes of its
       handle (request_bytes when the engine has no device_bytes).
+    in_place: "auto" admits a request whose A/B form does not fit the budget
+      left with in-place streaming (one population buffer: half the memory,
+      slower lattice pass) when that fits; "never" waits for A/B room;
+      "always" admits every request in place.  A request that names its own
+      stream_mode keeps it.
     quantum: largest number of steps between two scheduling decisions.
     max_active: optional cap on the number of resident simulations.
     clock: callable returning seconds (wall clock by default); tests pass a
@@ -69,9 +79,13 @@ class Server:
     """
 
     def __init__(self, engine, budget_bytes: int = 150 << 30, quantum: int = 1000,
-                 max_active: int | None = None, clock=None):
+                 max_active: int | None = None, clock=None, in_place: str = "auto"):
+        if in_place not in ("auto", "never", "always"):
+            raise ValueError("in_place must be 'auto', 'never' or 'always'")
         self.engine = engine
         self.budget = int(budget_bytes)
+        self.in_place = in_place
+        self.admitted_in_place = 0
         self.quantum = int(quantum)
         self.max_active = max_active
         self.clock = clock or time.perf_counter
@@ -86,15 +100,22 @@ class Server:
         admitted = False
         while waiting and waiting[0][0] <= now:
             _, rid, req = waiting[0]
-            need = request_bytes(req)
-            if need > self.budget:
-                raise ValueError(f"request {rid} needs {need} bytes, above the budget")
-            if self.used + need > self.budget:
+            modes = [req["stream_mode"]] if "stream_mode" in req else (
+                ["aa"] if self.in_place == "always" else
+                ["ab", "aa"] if self.in_place == "auto" else ["ab"])
+            if request_bytes(req, modes[-1]) > self.budget:
+                raise ValueError(f"request {rid} needs {request_bytes(req, modes[-1])} bytes, "
+                                 "above the budget")
+            fits = [m for m in modes if self.used + request_bytes(req, m) <= self.budget]
+            if not fits:
                 break
+            mode = fits[0]
+            need = request_bytes(req, mode)
             if self.max_active is not None and len(self.active) >= self.max_active:
                 break
             heapq.heappop(waiting)
-            h = self.engine.create(req)
+            h = self.engine.create(dict(req, stream_mode=mode))
+            self.admitted_in_place += mode == "aa"
             held = need
             if hasattr(self.engine, "device_bytes"):
                 held = int(self.engine.device_bytes(h))
@@ -177,7 +198,8 @@ class LbibEngine:
 
     def create(self, req):
         st = req["storage"]
-        s = self.L.Sim(storage=st, stream=self.streams[st], allocator=self.alloc, **req["config"])
+        s = self.L.Sim(storage=st, stream=self.streams[st], allocator=self.alloc,
+                       stream_mode=req.get("stream_mode", "ab"), **req["config"])
         for p in req["particles"]:
             s.add_particle(**p)
         self.sims[id(s)] = s
@@ -198,10 +220,13 @@ class LbibEngine:
                 b = self.L.Batch(ss)
                 # the lattice-pass variant is tuned on the first batch of each
                 # storage format and reused for the later ones
+                # (a batch with an in-place member has nothing to time)
                 if st in self.variants:
                     b.set_variant(self.variants[st])
                 else:
-                    self.variants[st] = b.autotune(10)[0]
+                    v, ms = b.autotune(10)
+                    if any(ms):
+                        self.variants[st] = v
                 self.batches[st] = b
 
     def step(self, n):

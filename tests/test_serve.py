@@ -26,6 +26,8 @@ class FakeEngine:
 
     def create(self, req):
         self.steps_done[req["rid"]] = 0
+        self.modes = getattr(self, "modes", {})
+        self.modes[req["rid"]] = req.get("stream_mode", "ab")
         return req["rid"]
 
     def rebuild(self, members):
@@ -50,12 +52,12 @@ class FakeEngine:
         self.t += s
 
 
-def small_trace(n=12, seed=7):
+def small_trace(n=12, seed=7, sizes=(64, 128, 256)):
     rng = np.random.default_rng(seed)
     out, t = [], 0.0
     for rid in range(n):
         t += rng.exponential(0.05)
-        nx = int(rng.choice([64, 128, 256]))
+        nx = int(rng.choice(sizes))
         out.append(dict(rid=rid, arrival_s=t, steps=int(rng.integers(10, 400)),
                         storage="f32" if rid % 2 else "f16",
                         config=dict(nx=nx, ny=nx // 4), particles=[{}]))
@@ -102,14 +104,51 @@ def test_admission_respects_the_memory_budget():
     budget = 3 * max(sizes.values())
     eng = FakeEngine(rate=1e6)
     eng.nodes = {r["rid"]: r["config"]["nx"] * r["config"]["ny"] for r in trace}
-    srv = serve.Server(eng, budget_bytes=budget, quantum=32, clock=eng.clock)
+    srv = serve.Server(eng, budget_bytes=budget, quantum=32, clock=eng.clock, in_place="never")
     res = srv.run(trace, t0=0.0)
     assert len(res) == len(trace)
+    assert srv.admitted_in_place == 0
     for n, members in eng.calls:
         assert sum(sizes[m] for m in members) <= budget
     # requests are admitted in arrival order
     adm = sorted(res, key=lambda r: r.rid)
     assert all(a.admitted_s <= b.admitted_s for a, b in zip(adm, adm[1:]))
+
+
+def test_in_place_admission_when_two_buffers_do_not_fit():
+    """With in_place="auto" a request whose two population buffers do not
+    fit the budget left is admitted with one (in-place streaming) when that
+    fits; the memory in use never exceeds the budget, counted per mode."""
+    trace = small_trace(20, sizes=(512, 1024))
+    ab = {r["rid"]: serve.request_bytes(r, "ab") for r in trace}
+    aa = {r["rid"]: serve.request_bytes(r, "aa") for r in trace}
+    assert all(aa[k] < ab[k] for k in ab)
+    budget = 2 * max(ab.values())
+    eng = FakeEngine(rate=1e6)
+    eng.nodes = {r["rid"]: r["config"]["nx"] * r["config"]["ny"] for r in trace}
+    srv = serve.Server(eng, budget_bytes=budget, quantum=32, clock=eng.clock, in_place="auto")
+    res = srv.run(trace, t0=0.0)
+    assert len(res) == len(trace)
+    assert 0 < srv.admitted_in_place == sum(m == "aa" for m in eng.modes.values())
+    for n, members in eng.calls:
+        held = sum((aa if eng.modes[m] == "aa" else ab)[m] for m in members)
+        assert held <= budget
+    # "never" serves the same trace with two buffers each, later on average
+    eng2 = FakeEngine(rate=1e6)
+    eng2.nodes = eng.nodes
+    srv2 = serve.Server(eng2, budget_bytes=budget, quantum=32, clock=eng2.clock, in_place="never")
+    res2 = srv2.run(trace, t0=0.0)
+    assert set(eng2.modes.values()) == {"ab"}
+    assert sum(r.admitted_s for r in res) <= sum(r.admitted_s for r in res2)
+    # "always", and a request that names its own mode keeps it
+    trace[3]["stream_mode"] = "ab"
+    eng3 = FakeEngine(rate=1e6)
+    eng3.nodes = eng.nodes
+    serve.Server(eng3, budget_bytes=budget, clock=eng3.clock, in_place="always").run(trace, t0=0.0)
+    assert eng3.modes[3] == "ab"
+    assert all(m == "aa" for k, m in eng3.modes.items() if k != 3)
+    with pytest.raises(ValueError):
+        serve.Server(eng3, in_place="sometimes")
 
 
 class HoldingEngine(FakeEngine):
