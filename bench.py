@@ -50,6 +50,22 @@ def workload_cases(name):
     return W.design_sweep() if name == "sweep72" else W.single_ellipse_sweep()
 
 
+def wall_report(batch, name, steps):
+    """The particles' smallest element-centroid gap to the bottom wall line
+    (the paper's y_min, Eq. 12), over the channel height, after the run;
+    a particle past the wall line has a negative gap."""
+    H = [c["ny"] - 1 if c.get("wall_bottom", "zou_he") == "zou_he" else c["ny"]
+         for c, _ in workload_cases(name)]
+    gaps, bonded = [], 0
+    for h, row in zip(H, batch.particles()):
+        for p in row:
+            gaps.append(p["gap_bottom"] / h)
+            bonded += p["n_bonded"] > 0
+    return {"y_min_over_h": min(gaps), "y_min_over_h_median": sorted(gaps)[len(gaps) // 2],
+            "crossed": sum(g <= 0 for g in gaps), "bonded_particles": bonded,
+            "particles": len(gaps), "after_steps": steps}
+
+
 def env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -282,6 +298,8 @@ def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="
     kt, source = bulk_timing(b, b.kernel_times())
     pn = b.pass_nodes()
     b.synchronize()
+    walls = wall_report(b, name, 2 + warmup + steps +
+                        (32 * SAMPLE_GRAPHS if source.startswith("sampled run") else 0))
     bpu = BYTES_PER_UPDATE[storage]
     value = nodes * steps / (ms * 1e-3) / 1e6
     ach = pn["bulk"] * bpu / (kt["lattice_ms"] * 1e-3) / 1e9 if kt["lattice_ms"] > 0 else None
@@ -294,7 +312,8 @@ def storage_leg(lbib, W, storage, stream, alloc, steps, warmup, peak, rounding="
             "lattice_kernel_ms": kt["lattice_ms"], "particle_kernel_ms": kt["particle_ms"],
             "near_kernel_ms": kt["near_ms"], "lattice_variant": variant,
             "kernel_timing": source, "bulk_le_step": kt["lattice_ms"] <= ms / steps,
-            "roofline_achieved_gbs": ach, "roofline_frac": ach / peak if ach else None}
+            "roofline_achieved_gbs": ach, "roofline_frac": ach / peak if ach else None,
+            "walls": walls}
 
 
 def serving_leg(lbib, W, n_requests, alloc, quantum):
@@ -375,6 +394,9 @@ def run_gpu(args):
     pn = batch.pass_nodes()
     for s in sims:
         s.synchronize()             # raises on a device-side error
+    walls = wall_report(batch, args.workload,
+                        2 + args.warmup + args.steps +
+                        (32 * SAMPLE_GRAPHS if kt_source.startswith("sampled run") else 0))
     ms = max_over_ranks(ms, "cuda")
     value = aggregate_mlups(world, nodes, args.steps, ms)
 
@@ -470,7 +492,7 @@ def run_gpu(args):
                          "alone_ms": round(variant_ms[variant], 5),
                          "samples": kt["lattice_n"], "timing": kt_source,
                          "bulk_le_step": lat_ms <= ms / args.steps},
-            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "walls": walls, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": base,
         }
         line.update(legs)

@@ -308,11 +308,13 @@ lbib_status lbib_batch_step_flushed(lbib_batch *b, int64_t nsteps, void *flush,
  * group of four nodes; 1 = the same, at most 64 registers (four CTAs per
  * SM); 2 = 128 threads x two groups; 3 = the same, four CTAs per SM;
  * 4 = variant 1 with each plane's source range staged in shared memory by
- * bulk asynchronous copies (copy engine, mbarrier completion); 5 = the same
- * with two tiles per CTA in two stages (the second tile's copies in flight
- * while the first is computed).  Variants 4 and 5 need FP32/FP16/BF16 storage, rows of
- * whole 16-byte words and walls that are not periodic in every member (else
- * they run as variant 1).  FP64 storage and the plain (non-overlapped) pass
+ * bulk asynchronous copies (copy engine, mbarrier completion); 5 = a
+ * pipeline of such copies: eight tiles per CTA through a ring of shared-memory
+ * stages (four for 16-bit storage, two for FP32), one producer warp issuing
+ * the copies of the next tiles while eight warps compute the current one.
+ * Variants 4 and 5 need FP32/FP16/BF16 storage, rows of whole 16-byte words
+ * and walls that are not periodic in every member (else they run as
+ * variant 1).  FP64 storage and the plain (non-overlapped) pass
  * always use variant 0.  A new batch starts with variant 1.
  * lbib_batch_autotune runs the lattice pass of each variant `reps` times on
  * the batch's current state (timing runs: they write only the buffer the next

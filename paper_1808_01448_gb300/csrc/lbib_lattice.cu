@@ -69,54 +69,98 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
     }
     const R rho = op_add((R)1, drho);
     const R irho = recip(rho);
-    const R ux = op_mul(op_fma((R)0.5, Fx, jx), irho);
-    const R uy = op_mul(op_fma((R)0.5, Fy, jy), irho);
     const R om = pick<R>(s.f_om, s.d_om);
     const R pref0 = pick<R>(s.f_pref, s.d_pref);
     const R oms = SC ? op_mul(om, (R)s.scale) : om, pref = SC ? op_mul(pref0, (R)s.scale) : pref0;
+    const R c = op_sub((R)1, om);
     // f^eq_i - w_i = w_i [A + 3 rho e.u + 4.5 rho (e.u)^2], A = (rho - 1) - 1.5 rho u.u
     // Guo: S_i = (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
     // Post-collision d_i (1 - om) + om (f^eq_i - w_i) + S_i, evaluated per pair
     // of opposite directions (e -> -e flips e.u and e.F): a part even in e,
     //   w [om A - 3 pref u.F] + 4.5 w (e.u) (om rho (e.u) + 2 pref (e.F)),
     // and an odd part 3 w (om rho (e.u) + pref (e.F)).
-    const R A = op_fma(op_mul((R)-1.5, rho), op_fma(ux, ux, op_mul(uy, uy)), drho);
-    const R uF = op_fma(ux, Fx, op_mul(uy, Fy));
-    const R c = op_sub((R)1, om);
-    if constexpr (FAST) {
-        const R orho = op_mul(oms, rho), p2 = op_mul((R)2, pref);
-        const R base = op_fma(oms, A, op_mul(op_mul((R)-3, pref), uF));
-        d[0] = op_fma(c, d[0], op_mul((R)(4.0 / 9.0), base));
-        auto pair = [&](int i, int j, R w, R eu, R eF) {
-            const R inner = op_fma(orho, eu, op_mul(p2, eF));
-            const R even = op_mul(w, op_fma(op_mul((R)4.5, eu), inner, base));
-            const R odd = op_mul(op_mul((R)3, w), op_fma(orho, eu, op_mul(pref, eF)));
-            d[i] = op_add(op_fma(c, d[i], even), odd);
-            d[j] = op_sub(op_fma(c, d[j], even), odd);
-        };
-        pair(1, 3, (R)(1.0 / 9.0), ux, Fx);
-        pair(2, 4, (R)(1.0 / 9.0), uy, Fy);
-        pair(5, 7, (R)(1.0 / 36.0), op_add(ux, uy), op_add(Fx, Fy));
-        pair(6, 8, (R)(1.0 / 36.0), op_sub(uy, ux), op_sub(Fy, Fx));
+    // A node without force (F = 0 exactly: the bulk of a channel driven by
+    // its walls alone) takes the same expressions with the force terms left
+    // out, which are zero; the choice depends on F alone, so every path
+    // takes the same one for a node.
+    R ux, uy;
+    if (Fx != (R)0 || Fy != (R)0) {
+        ux = op_mul(op_fma((R)0.5, Fx, jx), irho);
+        uy = op_mul(op_fma((R)0.5, Fy, jy), irho);
     } else {
-        const R W1 = (R)(1.0 / 3.0), W5 = op_mul(op_sub((R)1, op_mul((R)2, W1)), (R)0.25);
-        const R r45 = op_mul((R)4.5, rho), m3uF = op_mul((R)-3, uF);
-        const R w0 = (R)(4.0 / 9.0);
-        d[0] = op_fma(c, d[0], op_fma(oms, op_mul(w0, A), op_mul(pref, op_mul(w0, m3uF))));
-        // pair (i, j = opposite of i): even part w (om A' + pref S_even),
-        // odd part W (om rho (e.u) + pref (e.F))
-        auto pair = [&](int i, int j, R w, R W, R eu, R eF) {
-            const R ee = op_mul(oms, op_mul(w, op_fma(op_mul(r45, eu), eu, A)));
-            const R oo = op_mul(oms, op_mul(W, op_mul(rho, eu)));
-            const R se = op_mul(pref, op_mul(w, op_fma(op_mul((R)9, eu), eF, m3uF)));
-            const R so = op_mul(pref, op_mul(W, eF));
-            d[i] = op_add(op_fma(c, d[i], op_add(ee, oo)), op_add(se, so));
-            d[j] = op_add(op_fma(c, d[j], op_sub(ee, oo)), op_sub(se, so));
-        };
-        pair(1, 3, (R)(1.0 / 9.0), W1, ux, Fx);
-        pair(2, 4, (R)(1.0 / 9.0), W1, uy, Fy);
-        pair(5, 7, (R)(1.0 / 36.0), W5, op_add(ux, uy), op_add(Fx, Fy));
-        pair(6, 8, (R)(1.0 / 36.0), W5, op_sub(uy, ux), op_sub(Fy, Fx));
+        ux = op_mul(jx, irho);
+        uy = op_mul(jy, irho);
+    }
+    const R A = op_fma(op_mul((R)-1.5, rho), op_fma(ux, ux, op_mul(uy, uy)), drho);
+    if (Fx != (R)0 || Fy != (R)0) {
+        const R uF = op_fma(ux, Fx, op_mul(uy, Fy));
+        if constexpr (FAST) {
+            const R orho = op_mul(oms, rho), p2 = op_mul((R)2, pref);
+            const R base = op_fma(oms, A, op_mul(op_mul((R)-3, pref), uF));
+            d[0] = op_fma(c, d[0], op_mul((R)(4.0 / 9.0), base));
+            auto pair = [&](int i, int j, R w, R eu, R eF) {
+                const R inner = op_fma(orho, eu, op_mul(p2, eF));
+                const R even = op_mul(w, op_fma(op_mul((R)4.5, eu), inner, base));
+                const R odd = op_mul(op_mul((R)3, w), op_fma(orho, eu, op_mul(pref, eF)));
+                d[i] = op_add(op_fma(c, d[i], even), odd);
+                d[j] = op_sub(op_fma(c, d[j], even), odd);
+            };
+            pair(1, 3, (R)(1.0 / 9.0), ux, Fx);
+            pair(2, 4, (R)(1.0 / 9.0), uy, Fy);
+            pair(5, 7, (R)(1.0 / 36.0), op_add(ux, uy), op_add(Fx, Fy));
+            pair(6, 8, (R)(1.0 / 36.0), op_sub(uy, ux), op_sub(Fy, Fx));
+        } else {
+            const R W1 = (R)(1.0 / 3.0), W5 = op_mul(op_sub((R)1, op_mul((R)2, W1)), (R)0.25);
+            const R r45 = op_mul((R)4.5, rho), m3uF = op_mul((R)-3, uF);
+            const R w0 = (R)(4.0 / 9.0);
+            d[0] = op_fma(c, d[0], op_fma(oms, op_mul(w0, A), op_mul(pref, op_mul(w0, m3uF))));
+            // pair (i, j = opposite of i): even part w (om A' + pref S_even),
+            // odd part W (om rho (e.u) + pref (e.F))
+            auto pair = [&](int i, int j, R w, R W, R eu, R eF) {
+                const R ee = op_mul(oms, op_mul(w, op_fma(op_mul(r45, eu), eu, A)));
+                const R oo = op_mul(oms, op_mul(W, op_mul(rho, eu)));
+                const R se = op_mul(pref, op_mul(w, op_fma(op_mul((R)9, eu), eF, m3uF)));
+                const R so = op_mul(pref, op_mul(W, eF));
+                d[i] = op_add(op_fma(c, d[i], op_add(ee, oo)), op_add(se, so));
+                d[j] = op_add(op_fma(c, d[j], op_sub(ee, oo)), op_sub(se, so));
+            };
+            pair(1, 3, (R)(1.0 / 9.0), W1, ux, Fx);
+            pair(2, 4, (R)(1.0 / 9.0), W1, uy, Fy);
+            pair(5, 7, (R)(1.0 / 36.0), W5, op_add(ux, uy), op_add(Fx, Fy));
+            pair(6, 8, (R)(1.0 / 36.0), W5, op_sub(uy, ux), op_sub(Fy, Fx));
+        }
+    } else {
+        if constexpr (FAST) {
+            const R orho = op_mul(oms, rho);
+            const R base = op_mul(oms, A);
+            d[0] = op_fma(c, d[0], op_mul((R)(4.0 / 9.0), base));
+            auto pair = [&](int i, int j, R w, R eu) {
+                const R inner = op_mul(orho, eu);
+                const R even = op_mul(w, op_fma(op_mul((R)4.5, eu), inner, base));
+                const R odd = op_mul(op_mul((R)3, w), inner);
+                d[i] = op_add(op_fma(c, d[i], even), odd);
+                d[j] = op_sub(op_fma(c, d[j], even), odd);
+            };
+            pair(1, 3, (R)(1.0 / 9.0), ux);
+            pair(2, 4, (R)(1.0 / 9.0), uy);
+            pair(5, 7, (R)(1.0 / 36.0), op_add(ux, uy));
+            pair(6, 8, (R)(1.0 / 36.0), op_sub(uy, ux));
+        } else {
+            const R W1 = (R)(1.0 / 3.0), W5 = op_mul(op_sub((R)1, op_mul((R)2, W1)), (R)0.25);
+            const R r45 = op_mul((R)4.5, rho);
+            const R w0 = (R)(4.0 / 9.0);
+            d[0] = op_fma(c, d[0], op_mul(oms, op_mul(w0, A)));
+            auto pair = [&](int i, int j, R w, R W, R eu) {
+                const R ee = op_mul(oms, op_mul(w, op_fma(op_mul(r45, eu), eu, A)));
+                const R oo = op_mul(oms, op_mul(W, op_mul(rho, eu)));
+                d[i] = op_fma(c, d[i], op_add(ee, oo));
+                d[j] = op_fma(c, d[j], op_sub(ee, oo));
+            };
+            pair(1, 3, (R)(1.0 / 9.0), W1, ux);
+            pair(2, 4, (R)(1.0 / 9.0), W1, uy);
+            pair(5, 7, (R)(1.0 / 36.0), W5, op_add(ux, uy));
+            pair(6, 8, (R)(1.0 / 36.0), W5, op_sub(uy, ux));
+        }
     }
     // non-finite state or a density outside (0, 2): the run has broken down
     // (the caller raises the error bit once for all its nodes)
@@ -318,11 +362,18 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
         for (int g = 0; g < GROUPS; ++g) {
             if (!keep[g]) continue;
             const int k = kg[g];
+            if (BULK && gx == (R)0 && gy == (R)0) {
+                // no body force and no particle tile: the force-free form
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                R Fx = gx, Fy = gy;
-                if (!BULK && s.np) tile_force<R>(s, b.parts, xg[g] + j, yg[g], Fx, Fy);
-                collide_node<R, SC, sizeof(S) == 2>(s, d[4 * g + j], Fx, Fy, bad);
+                for (int j = 0; j < 4; ++j)
+                    collide_node<R, SC, sizeof(S) == 2>(s, d[4 * g + j], (R)0, (R)0, bad);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    R Fx = gx, Fy = gy;
+                    if (!BULK && s.np) tile_force<R>(s, b.parts, xg[g] + j, yg[g], Fx, Fy);
+                    collide_node<R, SC, sizeof(S) == 2>(s, d[4 * g + j], Fx, Fy, bad);
+                }
             }
             const float sc = SC ? 1.f : s.scale;
             if (keep[g] == 0xFu && sizeof(S) == 2 && s.sround) {
@@ -474,20 +525,24 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
-// Waits for phase 0 of the mbarrier, at most `limit` polls; true if it completed.
-__device__ __forceinline__ bool mbar_wait0(const uint64_t *bar, int limit) {
+// Waits for the phase of the given parity of the mbarrier to complete, at
+// most `limit` polls; true if it completed.
+__device__ __forceinline__ bool mbar_wait(const uint64_t *bar, unsigned parity, int limit) {
     for (int it = 0; it < limit; ++it) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(smem_addr(bar))
+            : "r"(smem_addr(bar)), "r"(parity)
             : "memory");
         if (done) return true;
     }
     return false;
+}
+__device__ __forceinline__ bool mbar_wait0(const uint64_t *bar, int limit) {
+    return mbar_wait(bar, 0u, limit);
 }
 
 // Four consecutive staged values (p 16-byte aligned) and one staged value, in
@@ -582,7 +637,8 @@ __device__ __forceinline__ void tma_issue(const BatchDev &b, int flip, int tile,
 // false if the stage's copies did not complete within the bounded wait.
 template <typename S, typename R>
 __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, int tile,
-                                         const S *stg, const uint64_t *bar) {
+                                         const S *stg, const uint64_t *bar,
+                                         unsigned parity = 0) {
     constexpr int H = tma_margin<S>(), W = tma_width<S>();
     constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
@@ -616,8 +672,10 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
             pull_group<S, R, true>(s, src, x0, y, d, SC ? 1.f : s.inv_scale);
         }
     }
-    if (!mbar_wait0(bar, b.wait_polls)) {
-        if (threadIdx.x == 0) atomicOr(s.err, ERR_TIMEOUT);
+    // the warp gives up as a whole (its lanes may see the limit at different
+    // polls), and reports it
+    if (!__all_sync(0xffffffffu, mbar_wait(bar, parity, b.wait_polls))) {
+        if ((threadIdx.x & 31) == 0) atomicOr(s.err, ERR_TIMEOUT);
         return false;
     }
     if (!keep) return true;
@@ -645,8 +703,13 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     }
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
     bool bad = false;
+    if (gx == (R)0 && gy == (R)0) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) collide_node<R, SC, sizeof(S) == 2>(s, d[j], gx, gy, bad);
+        for (int j = 0; j < 4; ++j) collide_node<R, SC, sizeof(S) == 2>(s, d[j], (R)0, (R)0, bad);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) collide_node<R, SC, sizeof(S) == 2>(s, d[j], gx, gy, bad);
+    }
     if (bad) atomicOr(s.err, ERR_UNSTABLE);
     const float sc = SC ? 1.f : s.scale;
     if (keep == 0xFu && sizeof(S) == 2 && s.sround) {
@@ -711,6 +774,74 @@ __global__ void __launch_bounds__(256, MINB) lattice_tma_kernel(BatchDev b, int 
             for (int u = t; u < TILES && first + u < b.total_tiles; ++u) mbar_wait0(barrier(u), 1 << 16);
             return;
         }
+    }
+}
+
+// Copy-engine pipeline: TILES consecutive tiles per CTA through a ring of
+// STAGES shared-memory stages.  Warp 8 is the producer: its lane 0 issues
+// the bulk copies of tile j into stage j % STAGES (completing on full[s])
+// once the eight consumer warps have released the stage's previous tile
+// (empty[s], one arrival per warp); the consumer warps compute tile j from
+// its stage (tma_tile) and release it.  The copies of the next STAGES - 1
+// tiles are in flight while a tile is computed, so the load latency is off
+// the consumers' path.  Every wait is bounded: a consumer warp that gives up
+// reports ERR_TIMEOUT and leaves; the producer, when a release does not come,
+// waits (bounded, full length) for the copies it has in flight and leaves;
+// at the end it waits for its last copies, so no copy outlives the CTA.
+template <typename S>
+__host__ __device__ constexpr int pipe_stages() { return sizeof(S) == 2 ? 4 : 2; }
+constexpr int PIPE_TILES = 8;
+constexpr int PIPE_THREADS = 288;
+template <typename S>
+__host__ __device__ constexpr size_t pipe_smem_bytes() {
+    return pipe_stages<S>() * tma_stage_bytes<S>() + 2 * pipe_stages<S>() * sizeof(uint64_t);
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(PIPE_THREADS, 2) lattice_pipe_kernel(BatchDev b, int flip) {
+    constexpr int STAGES = pipe_stages<S>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const bool dry = (flip & 2) != 0;
+    flip &= 1;
+    auto stage = [&](int t) { return (S *)(smem_raw + t * tma_stage_bytes<S>()); };
+    uint64_t *bars = (uint64_t *)(smem_raw + STAGES * tma_stage_bytes<S>());
+    auto full = [&](int t) { return bars + t; };
+    auto empty = [&](int t) { return bars + STAGES + t; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int t = 0; t < STAGES; ++t) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(full(t))) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(empty(t))) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int first = blockIdx.x * PIPE_TILES;
+    const int n = min(PIPE_TILES, b.total_tiles - first);
+    if (warp == 8) {
+        if (lane != 0) return;
+        for (int j = 0; j < n; ++j) {
+            const int st = j % STAGES;
+            if (j >= STAGES && !mbar_wait(empty(st), (unsigned)((j / STAGES) - 1) & 1u, b.wait_polls)) {
+                for (int u = j - STAGES; u < j; ++u)
+                    mbar_wait(full(u % STAGES), (unsigned)(u / STAGES) & 1u, 1 << 16);
+                return;
+            }
+            // the consumers' reads of the stage come before the copy's writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_issue<S>(b, flip, first + j, stage(st), full(st));
+        }
+        for (int u = max(0, n - STAGES); u < n; ++u)
+            mbar_wait(full(u % STAGES), (unsigned)(u / STAGES) & 1u, 1 << 16);
+        return;
+    }
+    for (int j = 0; j < n; ++j) {
+        const int st = j % STAGES;
+        if (!tma_tile<S, R>(b, flip, dry, first + j, stage(st), full(st), (unsigned)(j / STAGES) & 1u))
+            return;
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(empty(st))) : "memory");
     }
 }
 
@@ -805,8 +936,9 @@ cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_
             [[fallthrough]];
         case 5:
             if constexpr (TUNED) {
-                lattice_tma_kernel<S, R, 3, 2>
-                    <<<(b.total_tiles + 1) / 2, 256, tma_smem_bytes<S, 2>(), st>>>(b, flip);
+                lattice_pipe_kernel<S, R>
+                    <<<(b.total_tiles + PIPE_TILES - 1) / PIPE_TILES, PIPE_THREADS,
+                       pipe_smem_bytes<S>(), st>>>(b, flip);
                 break;
             }
             [[fallthrough]];
@@ -839,9 +971,9 @@ cudaError_t lattice_kernel_setup(int kind) {
         using S = decltype(sv);
         using R = decltype(rv);
         if constexpr (sizeof(S) <= 4)
-            return cudaFuncSetAttribute(lattice_tma_kernel<S, R, 3, 2>,
+            return cudaFuncSetAttribute(lattice_pipe_kernel<S, R>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)tma_smem_bytes<S, 2>());
+                                        (int)pipe_smem_bytes<S>());
         return cudaSuccess;
     });
 }

@@ -37,16 +37,18 @@ def main(out):
             res[f"{st}_{k}_pop"] = s.populations()
             res[f"{st}_{k}_x"] = np.array([s.particle(0)[q] for q in ("xc", "yc", "theta")])
         b.close()
-    # copy-engine staging variant of the bulk pass
-    cfg, p = adhesion(160, 48, "ar3", 7)
-    s = L.Sim(storage="f32", **cfg)
-    s.add_particle(**p)
-    b = L.Batch([s])
-    b.set_variant(4)
-    b.step(20)
-    b.synchronize()
-    res["tma_pop"] = s.populations()
-    b.close()
+    # copy-engine staging variants of the bulk pass (single stage, pipeline)
+    for v in (4, 5):
+        for st in ("f32", "f16"):
+            cfg, p = adhesion(160, 48, "ar3", 7)
+            s = L.Sim(storage=st, **cfg)
+            s.add_particle(**p)
+            b = L.Batch([s])
+            b.set_variant(v)
+            b.step(20)
+            b.synchronize()
+            res[f"tma{v}_{st}_pop"] = s.populations()
+            b.close()
     print(L.version())
     np.savez(out, **res)
 

@@ -55,3 +55,25 @@ def test_reference_arm_runs_on_rank_zero_only():
                        capture_output=True, text=True, env=env, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_wall_report_takes_each_channels_height():
+    """y_min over H per particle with H = ny - 1 (Zou-He wall rows) or ny
+    (bounce-back), the crossing count and the bonded count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cases = bench.workload_cases("ellipse6")
+
+    class FakeBatch:
+        def particles(self):
+            rows = []
+            for k, (c, _) in enumerate(cases):
+                rows.append([{"gap_bottom": (k - 1) * 0.01 * (c["ny"] - 1), "n_bonded": k % 2}])
+            return rows
+
+    r = bench.wall_report(FakeBatch(), "ellipse6", 100)
+    assert r["particles"] == len(cases)
+    assert r["y_min_over_h"] == pytest.approx(-0.01)
+    assert r["crossed"] == 2              # gaps -0.01 H and 0
+    assert r["bonded_particles"] == len(cases) // 2
+    assert r["after_steps"] == 100

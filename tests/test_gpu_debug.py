@@ -2,7 +2,7 @@
 population index of the lattice and particle passes is checked against its
 buffer and a failed check is reported as LBIB_E_BOUNDS.  The same cases --
 FP32, FP16 and FP64 batches with particles and bonds (bulk, near-box and
-particle passes), and the copy-engine variant of the bulk pass -- run under
+particle passes), and the copy-engine variants of the bulk pass -- run under
 the debug and the release build in fresh processes: no check fails, and the
 results are the same bits."""
 import os

@@ -189,19 +189,21 @@ def test_allocator_failure_is_reported_and_handles_stay_destroyable(L):
     s.close()
 
 
-def test_bounded_wait_reports_timeout(L, monkeypatch):
-    """The copy-engine variant of the bulk lattice pass waits for its staged
-    copies at most LBIB_WAIT_POLLS polls; with 0 polls that wait gives up
-    at once (each CTA then drains its own copies with a full-length bounded
-    wait before it leaves) and the next call reports LBIB_E_TIMEOUT.  The
-    context stays usable."""
+@pytest.mark.parametrize("variant", [4, 5])
+def test_bounded_wait_reports_timeout(L, monkeypatch, variant):
+    """The copy-engine variants of the bulk lattice pass wait for their
+    staged copies (and the pipeline's producer for the release of a stage)
+    at most LBIB_WAIT_POLLS polls; with 0 polls those waits give up at once
+    (each CTA then drains its own copies with a full-length bounded wait
+    before it leaves) and the next call reports LBIB_E_TIMEOUT.  The context
+    stays usable."""
     cfg, parts = two_particle_case("f32")
     s = make(L, "f32", cfg, parts)
     s.step(2)
     monkeypatch.setenv("LBIB_WAIT_POLLS", "0")
     b = L.Batch([s])
     monkeypatch.delenv("LBIB_WAIT_POLLS")
-    b.set_variant(4)
+    b.set_variant(variant)
     b.step(1)
     with pytest.raises(L.LbibError) as e:
         b.synchronize()
@@ -213,7 +215,7 @@ def test_bounded_wait_reports_timeout(L, monkeypatch):
     t = make(L, "f32", cfg, parts)
     u = make(L, "f32", cfg, parts)
     bt = L.Batch([t])
-    bt.set_variant(4)
+    bt.set_variant(variant)
     bt.step(6)
     bt.synchronize()
     u.step(6)
