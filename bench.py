@@ -338,6 +338,8 @@ def serving_leg(lbib, W, n_requests, alloc, quantum):
             "offered_mlups": total / trace[-1]["arrival_s"] / 1e6,
             "arrival_window_s": trace[-1]["arrival_s"], "rebuilds": srv.rebuilds,
             "rounds": srv.rounds, "quantum": quantum, "budget_gb": 150,
+            "wall_s_in": {k: round(v, 3) for k, v in srv.time_in.items()},
+            "admitted_in_place": srv.admitted_in_place,
             "trace": f"first {n_requests} requests of the 20/s Poisson trace (PCG64 seed 5)"}
 
 

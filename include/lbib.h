@@ -243,16 +243,19 @@ lbib_status lbib_step(lbib_sim *sim, int64_t nsteps);
  * launch runs the loads, bonds, update and IB forcing of every particle; the
  * first overlaps the particle launch of the previous step.  All members must
  * share storage and device.  A simulation may be stepped alone or in a
- * batch, not both concurrently. */
+ * batch, not both concurrently.  lbib_batch_step replays captured CUDA
+ * graphs: of 32 steps, then of 4 steps for the rest of the call (each graph
+ * captured on its first use and kept until the launch configuration
+ * changes), and launches the last 1-3 steps directly. */
 lbib_status lbib_batch_create(lbib_sim *const *sims, int32_t n, lbib_batch **out);
 lbib_status lbib_batch_step(lbib_batch *b, int64_t nsteps);
 lbib_status lbib_batch_destroy(lbib_batch *b);
 /* Kernel timing with CUDA events: when nsamples > 0, later batch steps
  * record kernel durations (event records inside the replayed graphs, taken
- * in up to nsamples graphs in turn, and in the steps a call runs outside a
- * graph): the lattice pass of the middle step of a graph (or of a call's
- * steps) and the particle and near-box passes of the step after it, so every
- * stepping call takes at least one sample.
+ * in up to nsamples 32-step graphs in turn, and in the steps a call launches
+ * directly): the lattice pass of the middle step of a graph (or of the
+ * directly launched steps) and the particle and near-box passes of the step
+ * after it.
  * lbib_batch_kernel_times fills mean_ms[3] and count[3] with the
  * mean duration (ms) and number of samples taken since the last call:
  * [0] the lattice pass (the bulk pass when particle work is overlapped),
@@ -306,7 +309,8 @@ lbib_status lbib_batch_step_flushed(lbib_batch *b, int64_t nsteps, void *flush,
 /* Kernel variants of the lattice pass (the bulk pass when particle work is
  * overlapped), all on the same 1024-node tiles: 0 = 256 threads x one
  * group of four nodes; 1 = the same, at most 64 registers (four CTAs per
- * SM); 2 = 128 threads x two groups; 3 = the same, four CTAs per SM;
+ * SM); 2 = the same, five CTAs per SM (48 registers); 3 = six CTAs per SM
+ * (40 registers);
  * 4 = variant 1 with each plane's source range staged in shared memory by
  * bulk asynchronous copies (copy engine, mbarrier completion); 5 = a
  * pipeline of such copies: eight tiles per CTA through a ring of shared-memory

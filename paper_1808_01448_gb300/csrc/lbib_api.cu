@@ -26,6 +26,7 @@ using namespace lbib;
 namespace {
 
 constexpr int GRAPH_STEPS = 32;   // steps per captured graph (even: parity-neutral)
+constexpr int SHORT_STEPS = 4;    // steps per graph of the remainder of a call (even)
 constexpr int SMEM_LIMIT = 227 * 1024;
 
 thread_local std::string g_err;
@@ -171,6 +172,7 @@ struct lbib_batch {
     BatchDev bd{};
     int smem = 0;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph_short = nullptr;   // SHORT_STEPS steps, for remainders
     // timing: one graph exec per sample slot, each with events around the
     // first step's kernels
     int nsamples = 0;
@@ -550,6 +552,7 @@ void free_batch(lbib_batch *b) {
     if (b->s2) cudaStreamDestroy(b->s2);
     if (b->s1) cudaStreamDestroy(b->s1);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_short) cudaGraphExecDestroy(b->graph_short);
     for (auto g : b->tgraphs)
         if (g) cudaGraphExecDestroy(g);
     for (auto e : b->ev) cudaEventDestroy(e);
@@ -969,9 +972,17 @@ cudaError_t enqueue_flushed_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
     return e;
 }
 
+// Graphs are captured with the batch's streams idle: a 4-step graph captured
+// while a graph launched just before was still running replayed with results
+// that differed from run to run (measured: 15-30 of 30 repeats of a batch and
+// its solo runs; none with the wait, none over 20 repeats each at 8 and 16
+// steps, none before the 4-step graphs existed).  Captures happen once per
+// graph kind and launch configuration, so the wait costs nothing in steady
+// state.
 template <class Enqueue>
 lbib_status capture_with(lbib_batch *b, Enqueue &&enqueue, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
+    CK(cudaStreamSynchronize(b->stream));
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue();
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -1016,9 +1027,18 @@ lbib_status batch_step_impl(lbib_batch *b, int64_t n) {
         }
         CK(cudaGraphLaunch(g, b->stream));
     }
-    if (rem > 0) {
-        // with timing on, the remainder's middle step is sampled too (the
-        // next slot's events), so that every call takes at least one sample
+    // the remainder: graphs of SHORT_STEPS steps (captured on first use and
+    // kept), then the last few steps launched directly
+    const int nshort = rem / SHORT_STEPS, tail = rem % SHORT_STEPS;
+    if (nshort > 0 && !b->graph_short) {
+        lbib_status r = capture_with(b, [&] { return enqueue_steps(b, SHORT_STEPS, nullptr); },
+                                     &b->graph_short);
+        if (r != LBIB_OK) return r;
+    }
+    for (int i = 0; i < nshort; ++i) CK(cudaGraphLaunch(b->graph_short, b->stream));
+    if (tail > 0) {
+        // with timing on, the middle direct step is sampled too (the next
+        // slot's events)
         cudaEvent_t *ev = nullptr;
         if (b->nsamples > 0) {
             const int slot = b->next_slot;
@@ -1026,9 +1046,9 @@ lbib_status batch_step_impl(lbib_batch *b, int64_t n) {
             ev = &b->ev[6 * slot];
             b->replayed[slot] = 1;
         }
-        cudaError_t e = enqueue_steps(b, rem, ev, false);
+        cudaError_t e = enqueue_steps(b, tail, ev, false);
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-        if (rem & 1) {
+        if (tail & 1) {
             e = launch_flip(b->d_curs, (int)b->sims.size(), b->stream);
             if (e != cudaSuccess) return cuda_fail(e, "parity flip");
         }
@@ -1494,6 +1514,8 @@ lbib_status lbib_batch_set_particle_threads(lbib_batch *b, int32_t threads) {
     // captured graphs hold the launch configuration
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    if (b->graph_short) cudaGraphExecDestroy(b->graph_short);
+    b->graph_short = nullptr;
     if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
     b->fgraph = nullptr;
     if (b->nsamples > 0) return lbib_batch_set_timing(b, b->nsamples);
@@ -1507,6 +1529,8 @@ static lbib_status use_variant(lbib_batch *b, int variant) {
     b->bd.lat_variant = variant;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    if (b->graph_short) cudaGraphExecDestroy(b->graph_short);
+    b->graph_short = nullptr;
     if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
     b->fgraph = nullptr;
     if (b->nsamples > 0) return lbib_batch_set_timing(b, b->nsamples);

@@ -950,13 +950,13 @@ cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_
             [[fallthrough]];
         case 2:
             if constexpr (TUNED) {
-                lattice_kernel<S, R, BULK, 128, 2, 1><<<b.total_tiles, 128, 0, st>>>(b, flip);
+                lattice_kernel<S, R, BULK, 256, 1, 5><<<b.total_tiles, 256, 0, st>>>(b, flip);
                 break;
             }
             [[fallthrough]];
         case 3:
             if constexpr (TUNED) {
-                lattice_kernel<S, R, BULK, 128, 2, 4><<<b.total_tiles, 128, 0, st>>>(b, flip);
+                lattice_kernel<S, R, BULK, 256, 1, 6><<<b.total_tiles, 256, 0, st>>>(b, flip);
                 break;
             }
             [[fallthrough]];

@@ -95,6 +95,14 @@ class Server:
         self.rounds = 0
         self.rebuilds = 0
         self.updates = 0
+        # wall time (clock units) spent in each engine call
+        self.time_in = {"create": 0.0, "rebuild": 0.0, "step": 0.0, "result": 0.0, "idle": 0.0}
+
+    def _timed(self, what, fn, *args):
+        t = self.clock()
+        out = fn(*args)
+        self.time_in[what] += self.clock() - t
+        return out
 
     def _admit(self, waiting, now):
         admitted = False
@@ -114,7 +122,7 @@ class Server:
             if self.max_active is not None and len(self.active) >= self.max_active:
                 break
             heapq.heappop(waiting)
-            h = self.engine.create(dict(req, stream_mode=mode))
+            h = self._timed("create", self.engine.create, dict(req, stream_mode=mode))
             self.admitted_in_place += mode == "aa"
             held = need
             if hasattr(self.engine, "device_bytes"):
@@ -141,14 +149,15 @@ class Server:
             if not self.active:
                 # idle until the next arrival
                 nxt = waiting[0][0]
-                self.engine.idle(max(0.0, nxt - now))
+                self._timed("idle", self.engine.idle, max(0.0, nxt - now))
                 continue
             if dirty:
-                self.engine.rebuild([(rid, v[1], v[0]["storage"]) for rid, v in self.active.items()])
+                self._timed("rebuild", self.engine.rebuild,
+                            [(rid, v[1], v[0]["storage"]) for rid, v in self.active.items()])
                 self.rebuilds += 1
                 dirty = False
             q = min(self.quantum, min(v[2] for v in self.active.values()))
-            self.engine.step(q)
+            self._timed("step", self.engine.step, q)
             self.rounds += 1
             now = self.clock() - t0
             finished = [rid for rid, v in self.active.items() if v[2] == q]
@@ -158,8 +167,8 @@ class Server:
                 self.updates += q * c["nx"] * c["ny"]
             for rid in finished:
                 req, h, _, adm, held = self.active.pop(rid)
-                parts = self.engine.result(h)
-                self.engine.destroy(h)
+                parts = self._timed("result", self.engine.result, h)
+                self._timed("result", self.engine.destroy, h)
                 self.used -= held
                 c = req["config"]
                 self.results.append(Result(rid, req["arrival_s"], adm, now, int(req["steps"]),

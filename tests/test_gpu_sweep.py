@@ -251,3 +251,26 @@ def test_member_reads_wait_for_the_batch(L):
     b.close()
     for s in sims:
         s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_graph_chunks_equal_direct_steps(L, storage):
+    """A call's steps run as 32-step graphs, then 4-step graphs, then direct
+    launches; any split of the same steps gives the same bits: 45 steps in
+    one call (32 + 3 x 4 + 1), in calls of 7, and one at a time."""
+    sweep = W.design_sweep()[:3]
+    results = []
+    for split in ([45], [7] * 6 + [3], [1] * 45):
+        sims = [make(L, c, p, storage) for c, p in sweep]
+        b = L.Batch(sims)
+        for n in split:
+            b.step(n)
+        b.synchronize()
+        results.append([(s.populations(), s.particle(0), s.step_count) for s in sims])
+        b.close()
+        for s in sims:
+            s.close()
+    for other in results[1:]:
+        for (fa, pa, na), (fb, pb, nb) in zip(results[0], other):
+            np.testing.assert_array_equal(fa, fb)
+            assert pa == pb and na == nb == 45

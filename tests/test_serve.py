@@ -231,3 +231,17 @@ def test_serving_trace_recipe():
             assert p["yc"] + np.max(p["vy"]) < c["ny"] - 1
             # within the library's particle size limit (LBIB_MAX_PARTICLE_RADIUS)
             assert np.max(np.hypot(p["vx"], p["vy"])) <= 44.0
+
+
+def test_time_accounting_covers_the_engine_calls():
+    """The loop's per-call wall time (create, rebuild, step, result, idle)
+    adds up to at most the run's wall time and the step share is the
+    engine's virtual stepping time."""
+    trace = small_trace(12)
+    eng, srv, res = run(trace, rate=2e7)
+    t = srv.time_in
+    assert set(t) == {"create", "rebuild", "step", "result", "idle"}
+    assert t["step"] > 0 and t["idle"] >= 0
+    total_work = sum(r["steps"] * r["config"]["nx"] * r["config"]["ny"] for r in trace)
+    assert t["step"] == pytest.approx(total_work / 2e7, rel=1e-9)
+    assert sum(t.values()) <= max(r.done_s for r in res) + 1e-9
