@@ -264,7 +264,7 @@ SimDev simdev_from(const lbib_config &c, void *pop0, void *pop1, int *cur, long 
     d.aa = c.stream_mode == 1;
     // vector path (A/B streaming): whole groups of four nodes per row,
     // buffers 32-byte aligned
-    d.vec4 = !d.aa && c.nx % 4 == 0 && ((uintptr_t)pop0 % 32) == 0 && ((uintptr_t)pop1 % 32) == 0;
+    d.vec4 = c.nx % 4 == 0 && ((uintptr_t)pop0 % 32) == 0 && ((uintptr_t)pop1 % 32) == 0;
     d.sround = c.rounding == LBIB_ROUND_STOCHASTIC;
     d.ib_iters = c.ib_iterations > 1 ? c.ib_iterations : 1;
     d.ib_spread = c.ib_spread != 0;
@@ -728,6 +728,8 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
             tma_ok = 0;
     }
     b->bd.tma_ok = tma_ok;
+    b->bd.any_aa = 0;
+    for (int i = 0; i < n; ++i) b->bd.any_aa |= hs[i].aa;
     b->bd.wait_polls = wait_polls_setting();
     if (tma_ok && (e = lattice_kernel_setup(b->kind)) != cudaSuccess) {
         free_batch(b);

@@ -158,7 +158,7 @@ struct BatchDev {
     int tma_ok;          // every lattice suits the copy-engine variants (4, 5)
     int pthreads;        // particle CTA width: 256 (every particle fits) or 512
     int wait_polls;      // polls of a bounded device wait before it gives up
-    int pad_b;
+    int any_aa;          // a member streams in place
 };
 
 // Stochastic rounding of 16-bit stores.  A node's dither word is a hash of

@@ -216,9 +216,12 @@ __device__ __forceinline__ void store_node(const SimDev &s, S *__restrict__ dst,
 // from the walls (or of a lattice periodic in y): one vector load per
 // population plane, plus one scalar load for the node the x shift brings in
 // from the next group (x periodic).  Same values as pull_node per node.
-template <typename S, typename R, bool STREAM>
+// AA (in-place streaming, see post_index) from parity 0 pulls population i
+// from plane opp(i) of the same neighbour: OPP = true.
+template <typename S, typename R, bool STREAM, bool OPP = false>
 __device__ __forceinline__ void pull_group(const SimDev &s, const S *__restrict__ src, int x0,
                                            int y, R (*d)[9], float inv) {
+    constexpr int OPq[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     const int nx = s.nx, ny = s.ny, N = nx * ny;
     const int ym = y == 0 ? ny - 1 : y - 1;
     const int yp = y == ny - 1 ? 0 : y + 1;
@@ -232,18 +235,19 @@ __device__ __forceinline__ void pull_group(const SimDev &s, const S *__restrict_
     R v[4];
     // (plane, row of the source, x shift of the pull: +1 pulls from x - 1)
     auto plane = [&](int i, int row, int sh) {
-        Vec4<S, STREAM>::ld(src + pop_load_index(s, i * N + row + x0, 4), inv, v);
+        const int q = OPP ? OPq[i] : i;
+        Vec4<S, STREAM>::ld(src + pop_load_index(s, q * N + row + x0, 4), inv, v);
         if (sh == 0) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) d[j][i] = v[j];
         } else if (sh > 0) {
-            d[0][i] = ld1(i * N + row + xl);
+            d[0][i] = ld1(q * N + row + xl);
 #pragma unroll
             for (int j = 1; j < 4; ++j) d[j][i] = v[j - 1];
         } else {
 #pragma unroll
             for (int j = 0; j < 3; ++j) d[j][i] = v[j + 1];
-            d[3][i] = ld1(i * N + row + xr);
+            d[3][i] = ld1(q * N + row + xr);
         }
     };
     plane(0, r0, 0);
@@ -310,7 +314,7 @@ __device__ __forceinline__ unsigned outside_near_boxes4(const SimDev &s,
 // and are updated by lattice_near_kernel, after the particle pass).
 // flip bit 1 (DRY): a timing run that leaves the step counter alone; it
 // writes only the buffer the next step overwrites.
-template <typename S, typename R, bool BULK, int THREADS, int GROUPS, int MINB>
+template <typename S, typename R, bool BULK, int THREADS, int GROUPS, int MINB, bool AA = false>
 __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int flip) {
     static_assert(THREADS * 4 * GROUPS == LB_TILE_NODES, "tile size");
     constexpr int NPT = 4 * GROUPS;
@@ -347,14 +351,26 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             if (s.wall_b != LBIB_WALL_PERIODIC && (y == 0 || y == s.ny - 1)) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    pull_node<S, R, BULK>(s, src, xg[g] + j, y, d[4 * g + j]);
+                    pull_node<S, R, BULK>(s, src, xg[g] + j, y, d[4 * g + j], AA ? cur : 0);
                     if constexpr (SC) {
 #pragma unroll
                         for (int i = 0; i < 9; ++i) d[4 * g + j][i] *= s.scale;
                     }
                 }
-            } else {
+            } else if (!AA || !s.aa) {
                 pull_group<S, R, BULK>(s, src, xg[g], y, &d[4 * g], SC ? 1.f : s.inv_scale);
+            } else if (cur) {
+                // in place, parity 1: the node's own slots, plane i
+                R v[4];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    Vec4<S, BULK>::ld(src + pop_load_index(s, i * N + kg[g], 4), SC ? 1.f : s.inv_scale, v);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) d[4 * g + j][i] = v[j];
+                }
+            } else {
+                // in place, parity 0: the neighbours' opposite planes
+                pull_group<S, R, BULK, true>(s, src, xg[g], y, &d[4 * g], SC ? 1.f : s.inv_scale);
             }
         }
         bool bad = false;
@@ -375,31 +391,101 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
                     collide_node<R, SC, sizeof(S) == 2>(s, d[4 * g + j], Fx, Fy, bad);
                 }
             }
-            const float sc = SC ? 1.f : s.scale;
-            if (keep[g] == 0xFu && sizeof(S) == 2 && s.sround) {
-                unsigned h[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    h[j] = dither_word(k + j, SC ? (float)d[4 * g + j][0] * s.inv_scale
-                                                 : (float)d[4 * g + j][0]);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
-                    const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
-                                           dither_plane(h[2], i), dither_plane(h[3], i)};
-                    if (pop_index_ok(s, i * N + k, 4)) Vec4<S, BULK>::st_r(dst + i * N + k, o, sc, r);
+            if constexpr (AA) {
+                const float sc = SC ? 1.f : s.scale;
+                const bool sr = sizeof(S) == 2 && s.sround;
+                const int y = yg[g];
+                const bool wallrow = s.wall_b != LBIB_WALL_PERIODIC && (y == 0 || y == s.ny - 1);
+                unsigned h[4] = {0u, 0u, 0u, 0u};
+                if (keep[g] == 0xFu && sr) {
+    #pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        h[j] = dither_word(k + j, SC ? (float)d[4 * g + j][0] * s.inv_scale
+                                                     : (float)d[4 * g + j][0]);
                 }
-            } else if (keep[g] == 0xFu) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
-                    if (pop_index_ok(s, i * N + k, 4)) Vec4<S, BULK>::st(dst + i * N + k, o, sc);
+                if (AA && keep[g] == 0xFu && s.aa && !wallrow && cur == 0) {
+                    // in place, parity 0, away from the walls: population i to
+                    // x + e_i, whole groups for the planes without an x
+                    // component, one node at a time for the others (x periodic)
+                    constexpr int EXq[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+                    constexpr int EYq[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        int yy = y + EYq[i];
+                        if (yy < 0) yy += s.ny;
+                        if (yy >= s.ny) yy -= s.ny;
+                        const int row = i * N + yy * nx;
+                        const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
+                        unsigned r[4];
+    #pragma unroll
+                        for (int j = 0; j < 4; ++j) r[j] = dither_plane(h[j], i);
+                        if (EXq[i] == 0) {
+                            if (!pop_index_ok(s, row + xg[g], 4)) continue;
+                            if (sr) Vec4<S, BULK>::st_r(dst + row + xg[g], o, sc, r);
+                            else Vec4<S, BULK>::st(dst + row + xg[g], o, sc);
+                        } else {
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                int xx = xg[g] + j + EXq[i];
+                                if (xx < 0) xx += nx;
+                                if (xx >= nx) xx -= nx;
+                                if (!pop_index_ok(s, row + xx)) continue;
+                                if (sr) Store<S>::template st_r<BULK>(dst, row + xx, o[j], sc, r[j]);
+                                else if constexpr (BULK) Store<S>::st_cs(dst, row + xx, o[j], sc);
+                                else Store<S>::st(dst, row + xx, o[j], sc);
+                            }
+                        }
+                    }
+                } else if (keep[g] == 0xFu && (!AA || !s.aa || !wallrow)) {
+                    // A/B, or in place from parity 1 (population i to plane
+                    // opp(i) of the node itself)
+                    constexpr int OPq[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int q = (AA && s.aa) ? OPq[i] : i;
+                        const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
+                        if (!pop_index_ok(s, q * N + k, 4)) continue;
+                        if (sr) {
+                            const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
+                                                   dither_plane(h[2], i), dither_plane(h[3], i)};
+                            Vec4<S, BULK>::st_r(dst + q * N + k, o, sc, r);
+                        } else {
+                            Vec4<S, BULK>::st(dst + q * N + k, o, sc);
+                        }
+                    }
+                } else {
+    #pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (keep[g] & (1u << j))
+                            store_node<S, R, BULK, SC>(s, dst, N, k + j, d[4 * g + j], cur);
                 }
             } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (keep[g] & (1u << j))
-                        store_node<S, R, BULK, SC>(s, dst, N, k + j, d[4 * g + j]);
+                const float sc = SC ? 1.f : s.scale;
+                if (keep[g] == 0xFu && sizeof(S) == 2 && s.sround) {
+                    unsigned h[4];
+    #pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        h[j] = dither_word(k + j, SC ? (float)d[4 * g + j][0] * s.inv_scale
+                                                     : (float)d[4 * g + j][0]);
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
+                        const unsigned r[4] = {dither_plane(h[0], i), dither_plane(h[1], i),
+                                               dither_plane(h[2], i), dither_plane(h[3], i)};
+                        if (pop_index_ok(s, i * N + k, 4)) Vec4<S, BULK>::st_r(dst + i * N + k, o, sc, r);
+                    }
+                } else if (keep[g] == 0xFu) {
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const R o[4] = {d[4 * g][i], d[4 * g + 1][i], d[4 * g + 2][i], d[4 * g + 3][i]};
+                        if (pop_index_ok(s, i * N + k, 4)) Vec4<S, BULK>::st(dst + i * N + k, o, sc);
+                    }
+                } else {
+    #pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (keep[g] & (1u << j))
+                            store_node<S, R, BULK, SC>(s, dst, N, k + j, d[4 * g + j]);
+                }
             }
         }
         if (bad) atomicOr(s.err, ERR_UNSTABLE);
@@ -924,6 +1010,12 @@ cudaError_t by_kind(int kind, F &&f) {
 template <typename S, typename R, bool BULK>
 cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_t st) {
     constexpr bool TUNED = BULK && sizeof(S) <= 4;
+    if (b.any_aa) {
+        // a member streams in place: the form with the in-place vector path
+        // (its extra code costs the other forms registers, so it is apart)
+        lattice_kernel<S, R, BULK, 256, 1, sizeof(S) == 8 ? 1 : 4, true><<<b.total_tiles, 256, 0, st>>>(b, flip);
+        return cudaGetLastError();
+    }
     if (!TUNED) variant = 0;
     if (variant >= 4 && !b.tma_ok) variant = 1;     // lattices unsuited to staging
     switch (variant) {

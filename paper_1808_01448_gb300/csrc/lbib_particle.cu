@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     uint8_t *lig8 = (uint8_t *)take(nl);
     int *corder = (int *)take(sizeof(int) * nl);
     int *coff = (int *)take(sizeof(int) * (nl + 1));
-    double *lpart = (double *)take(sizeof(double) * 3 * (PT / 32));   // load partials
+    double *lpart = (double *)take(sizeof(double) * 3 * (PT / 32));   // per-warp gap minima
     int4 *span = (int4 *)take(sizeof(int4) * Tm);       // staged spans per region row
     int *pre = (int *)take(sizeof(int) * (Tm + 1));     // staged nodes before each row
     R *tile = (R *)take(sizeof(R) * 2 * T * T);
@@ -1052,52 +1052,42 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
                 ty = (-p * nyl + txy * nxl + nu * (R)2 * dvdy * nyl) * sS[l];
             }
             tq = rx[l] * ty - ry[l] * tx;
-        }
-        // FP64 sums of the loads: a tree over each warp's probes, the warps'
-        // partial sums added in warp order by the update lanes below (the
-        // bond loads and the wall force were summed during the staging)
-        if (warp < (nl + 31) / 32) {
-            double a0 = (double)tx, a1 = (double)ty, a2 = (double)tq;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-            }
-            if (lane == 0) {
-                lpart[3 * warp] = a0;
-                lpart[3 * warp + 1] = a1;
-                lpart[3 * warp + 2] = a2;
-            }
+            cq[l] = tx;
+            cq[cstride + l] = ty;
+            cq[2 * cstride + l] = tq;
         }
         __syncthreads();
         // ---- 5. rigid update (Eq. 13-16), one degree of freedom per warp ---
-        // (lane 0 of warps 0, 1, 2: the three chains of FP64 arithmetic run
-        // side by side instead of one after another in a divergent warp)
-        if ((tid & 31) == 0 && tid < 96) {
-            const int k = tid >> 5;
-            double h = 0.0;
-            for (int w = 0; w < (nl + 31) / 32; ++w) h += lpart[3 * w + k];
-            ps.F[k] = h;
-            if (k == 2) P->Mh = h; else P->Fh[k] = h;
-            if (!Pc.fixed) {
-                const double F = k == 0 ? h + ps.F[3] : (k == 1 ? h + ps.F[4] + ps.Fw : h + ps.F[5]);
-                const double im = k == 2 ? Pc.inv_inertia : Pc.inv_mass;
-                const double u0 = k == 0 ? ps.u : (k == 1 ? ps.v : ps.om);
-                const double u1 = k == 0 ? Pc.u1 : (k == 1 ? Pc.v1 : Pc.om1);
-                const double x0 = k == 0 ? ps.xc : (k == 1 ? ps.yc : ps.th);
-                const double x1 = k == 0 ? Pc.xc1 : (k == 1 ? Pc.yc1 : Pc.th1);
-                const double un = 2.0 / 3.0 * (2.0 * u0 - 0.5 * u1 + F * im);
-                const double xn = (4.0 * x0 - x1 + 2.0 * un) * (1.0 / 3.0);
-                double *Pu = k == 0 ? &P->u : (k == 1 ? &P->v : &P->om);
-                double *Pu1 = k == 0 ? &P->u1 : (k == 1 ? &P->v1 : &P->om1);
-                double *Px = k == 0 ? &P->xc : (k == 1 ? &P->yc : &P->th);
-                double *Px1 = k == 0 ? &P->xc1 : (k == 1 ? &P->yc1 : &P->th1);
-                *Pu1 = u0; *Pu = un; *Px1 = x0; *Px = xn;
-                if (k == 0) { ps.u = un; ps.xc = xn; }
-                if (k == 1) { ps.v = un; ps.yc = xn; }
-                if (k == 2) { ps.om = un; ps.th = xn; }
-                set_pose_dof(ps, k, yb, yt);     // this degree of freedom of the new pose
+        // Warp k sums load k over the probes in FP64 (the bond loads and the
+        // wall force were summed during the staging), then its lane 0 updates
+        // degree of freedom k: the three chains of FP64 arithmetic run side by
+        // side, and only three warps issue FP64 instructions (each occupies
+        // its sub-partition's FP64 pipe for ~64 cycles whatever its lanes).
+        if (warp < 3) {
+            const int k = warp;
+            const double h = warp_sum_array<R>(cq + k * cstride, nl);
+            if (lane == 0) {
+                ps.F[k] = h;
+                if (k == 2) P->Mh = h; else P->Fh[k] = h;
+                if (!Pc.fixed) {
+                    const double F = k == 0 ? h + ps.F[3] : (k == 1 ? h + ps.F[4] + ps.Fw : h + ps.F[5]);
+                    const double im = k == 2 ? Pc.inv_inertia : Pc.inv_mass;
+                    const double u0 = k == 0 ? ps.u : (k == 1 ? ps.v : ps.om);
+                    const double u1 = k == 0 ? Pc.u1 : (k == 1 ? Pc.v1 : Pc.om1);
+                    const double x0 = k == 0 ? ps.xc : (k == 1 ? ps.yc : ps.th);
+                    const double x1 = k == 0 ? Pc.xc1 : (k == 1 ? Pc.yc1 : Pc.th1);
+                    const double un = 2.0 / 3.0 * (2.0 * u0 - 0.5 * u1 + F * im);
+                    const double xn = (4.0 * x0 - x1 + 2.0 * un) * (1.0 / 3.0);
+                    double *Pu = k == 0 ? &P->u : (k == 1 ? &P->v : &P->om);
+                    double *Pu1 = k == 0 ? &P->u1 : (k == 1 ? &P->v1 : &P->om1);
+                    double *Px = k == 0 ? &P->xc : (k == 1 ? &P->yc : &P->th);
+                    double *Px1 = k == 0 ? &P->xc1 : (k == 1 ? &P->yc1 : &P->th1);
+                    *Pu1 = u0; *Pu = un; *Px1 = x0; *Px = xn;
+                    if (k == 0) { ps.u = un; ps.xc = xn; }
+                    if (k == 1) { ps.v = un; ps.yc = xn; }
+                    if (k == 2) { ps.om = un; ps.th = xn; }
+                    set_pose_dof(ps, k, yb, yt);     // this degree of freedom of the new pose
+                }
             }
         }
         if (tid == 96) {
