@@ -142,9 +142,10 @@ typedef struct lbib_config {
      * populations pulled from the last step's), 1 in place (AA pattern: one
      * buffer, so half the population memory; the steps alternate between
      * reading a node's own slots and writing its neighbours' and the
-     * reverse).  The same results bit for bit; in place, the lattice pass
-     * takes its per-node form (no vector or copy-engine variants) and
-     * lbib_batch_autotune has nothing to time. */
+     * reverse).  The same results bit for bit; a batch with an in-place
+     * member runs one lattice-pass form (vector loads and stores where the
+     * layout allows, no copy-engine variants), so lbib_batch_autotune has
+     * nothing to time. */
     int32_t stream_mode;
     int32_t reserved2;
 } lbib_config;

@@ -256,6 +256,17 @@ __device__ __forceinline__ void setup_point(const SimDev &s, int bx, int by, R X
     pt.inv_v[l] = inv_v;
 }
 
+// Order-preserving map of a (non-NaN) double to a 64-bit integer and back:
+// the bits of a non-negative double order as integers; a negative one has
+// its magnitude bits flipped.  min over keys = the FP64 minimum, exactly.
+__device__ __forceinline__ long long gap_key(double g) {
+    const long long b = __double_as_longlong(g);
+    return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ double key_gap(long long k) {
+    return __longlong_as_double(k >= 0 ? k : k ^ 0x7fffffffffffffffLL);
+}
+
 // FP64 sum of n values of an array by one warp.
 template <typename R>
 __device__ __forceinline__ double warp_sum_array(const R *a, int n) {
@@ -702,7 +713,7 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     uint8_t *lig8 = (uint8_t *)take(nl);
     int *corder = (int *)take(sizeof(int) * nl);
     int *coff = (int *)take(sizeof(int) * (nl + 1));
-    double *lpart = (double *)take(sizeof(double) * 3 * (PT / 32));   // per-warp gap minima
+    double *lpart = (double *)take(sizeof(double) * 3 * (PT / 32));   // per-warp gap minima (keys)
     int4 *span = (int4 *)take(sizeof(int4) * Tm);       // staged spans per region row
     int *pre = (int *)take(sizeof(int) * (Tm + 1));     // staged nodes before each row
     R *tile = (R *)take(sizeof(R) * 2 * T * T);
@@ -871,10 +882,14 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             double ax = P->anchor_x[l];
             int8_t aw = P->anchor_wall[l];
             const double y_eq = s.y_eq_ratio * s.y_cr;
+            // bond vector anchor - X_l (the anchor lies on a wall line) and
+            // length: of a bond that stays, as its reverse draw saw it; of a
+            // new one, straight to its wall line (the anchor is at x = X_l)
+            double dx = 0.0, dy = 0.0, y = 0.0;
             if (bnd) {
-                // bond vector anchor - X_l; the anchor lies on a wall line
-                const double dx = ax - Xl, dy = (aw ? yt : yb) - Yl;
-                const double y = sqrt(dx * dx + dy * dy);
+                dx = ax - Xl;
+                dy = (aw ? yt : yb) - Yl;
+                y = sqrt(dx * dx + dy * dy);
                 const double Pr = prob_reverse(s.k_r0, Pc.sigma - s.sigma_star_ratio * Pc.sigma,
                                                2.0 * s.kBT, y - y_eq);
                 if (U < Pr) bnd = 0;
@@ -885,17 +900,18 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
                     aw = pb ? 0 : 1;
                     P->anchor_x[l] = ax;
                     P->anchor_wall[l] = aw;
+                    dx = ax - Xl;
+                    dy = (aw ? yt : yb) - Yl;
+                    y = sqrt(dx * dx + dy * dy);
                 }
             }
             P->bond[l] = bnd;
             if (bnd) {
                 bonded = true;
-                const double dx = ax - Xl, dy = (aw ? yt : yb) - Yl;
-                const double y = sqrt(dx * dx + dy * dy);
                 if (y > 0.0) {
-                    const double mag = Pc.sigma * (y - y_eq);
-                    fx = mag * dx / y;
-                    fy = mag * dy / y;
+                    const double q = Pc.sigma * (y - y_eq) / y;     // one FP64 division
+                    fx = q * dx;
+                    fy = q * dy;
                 }
             }
         }
@@ -904,18 +920,20 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
         cq[5 * cstride + l] = (R)((Xl - ps.xc) * fy - (Yl - ps.yc) * fx);
     }
     if (!init) {
-        // smallest element gaps to each wall line (Eq. 12), FP64: per warp by
-        // shuffles, the warps' minima in the load-partials space (free until
-        // the loads below)
-        double mb = gbd, mt = gtd;
+        // smallest element gaps to each wall line (Eq. 12): exact minima of
+        // the FP64 gaps as order-preserving 64-bit integer keys (integer
+        // instructions: an FP64 minimum costs ~64 cycles of its
+        // sub-partition per warp), per warp by shuffles, the warps' minima in
+        // the per-warp space
+        long long mb = gap_key(gbd), mt = gap_key(gtd);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            mb = fmin(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-            mt = fmin(mt, __shfl_xor_sync(0xffffffffu, mt, o));
+            mb = min(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+            mt = min(mt, __shfl_xor_sync(0xffffffffu, mt, o));
         }
         if (lane == 0) {
-            lpart[2 * warp] = mb;
-            lpart[2 * warp + 1] = mt;
+            ((long long *)lpart)[2 * warp] = mb;
+            ((long long *)lpart)[2 * warp + 1] = mt;
         }
     }
     const int nbonded = __syncthreads_count(bonded);
@@ -948,11 +966,12 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
         if (lane == 0) ps.F[2 + warp] = v;
     } else if (!init && warp == 4) {
         if (lane == 0) {
-            double gb = 1e300, gt = 1e300;
+            long long kb_ = gap_key(1e300), kt_ = gap_key(1e300);
             for (int w = 0; w < PT / 32; ++w) {
-                gb = fmin(gb, lpart[2 * w]);
-                gt = fmin(gt, lpart[2 * w + 1]);
+                kb_ = min(kb_, ((const long long *)lpart)[2 * w]);
+                kt_ = min(kt_, ((const long long *)lpart)[2 * w + 1]);
             }
+            const double gb = key_gap(kb_), gt = key_gap(kt_);
             ps.nprobe = nprobe;
             ps.nbonded = nbonded;
             ps.gapb = gb;
