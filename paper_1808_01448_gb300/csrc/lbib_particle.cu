@@ -660,6 +660,10 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     __shared__ __align__(16) unsigned char s_sim_raw[sizeof(SimDev)];
     __shared__ __align__(16) unsigned char s_par_raw[sizeof(ParticleDev)];
     ParticleDev *P = b.parts[blockIdx.x];
+    // FP64 cosine and sine of the angle for the bond geometry: by the last
+    // thread, which has no share of the descriptor copy below, meanwhile
+    double th_sn = 0.0, th_cs = 1.0;
+    if (threadIdx.x == PT - 1 && !init) sincos(P->th, &th_sn, &th_cs);
     // this thread's element record, loaded beside the descriptor (used only
     // if the descriptor says it is valid)
     R ev[ECACHE];
@@ -758,9 +762,10 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             set_pose(ps, yb, yt);
         }
     }
-    // FP64 cosine and sine of the angle for the bond geometry (beside the
-    // compute-precision pose of thread 0)
-    if (tid == 32 && !init) sincos(Pc.th, &ps.snd, &ps.csd);
+    if (tid == PT - 1 && !init) {
+        ps.snd = th_sn;
+        ps.csd = th_cs;
+    }
     // element of this thread's bond: the upper half of the block takes the
     // bonds when both halves fit the elements, so that they run beside the
     // staging work of the lower half; its body-frame centroid in FP64
@@ -960,33 +965,17 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             carry += __shfl_sync(0xffffffffu, incl, 31);
         }
         if (lane == 0) pre[Tm] = carry;
-    } else if (!init && warp <= 3) {
-        // FP64 sums of the bond loads, one warp per quantity
-        const double v = warp_sum_array<R>(cq + (2 + warp) * cstride, nl);
-        if (lane == 0) ps.F[2 + warp] = v;
-    } else if (!init && warp == 4) {
+    } else if (!init && warp == 1) {
         if (lane == 0) {
             long long kb_ = gap_key(1e300), kt_ = gap_key(1e300);
             for (int w = 0; w < PT / 32; ++w) {
                 kb_ = min(kb_, ((const long long *)lpart)[2 * w]);
                 kt_ = min(kt_, ((const long long *)lpart)[2 * w + 1]);
             }
-            const double gb = key_gap(kb_), gt = key_gap(kt_);
             ps.nprobe = nprobe;
             ps.nbonded = nbonded;
-            ps.gapb = gb;
-            ps.gapt = gt;
-            // ---- 4. wall force (Eq. 12), FP64 -------------------------
-            // F_w = H_k / (8 sqrt 2) sqrt(r / eps^5) off each wall, eps the
-            // smallest element gap clamped below by eps_min
-            double Fw = 0.0;
-            if (s.wall_b != LBIB_WALL_PERIODIC && s.hamaker != 0.0) {
-                const double eb = fmax(gb, s.eps_min), et = fmax(gt, s.eps_min);
-                const double k = s.hamaker / (8.0 * 1.4142135623730951);
-                Fw = k * sqrt(Pc.r_eq / (eb * eb * eb * eb * eb)) -
-                     k * sqrt(Pc.r_eq / (et * et * et * et * et));
-            }
-            ps.Fw = Fw;
+            ps.gapb = key_gap(kb_);
+            ps.gapt = key_gap(kt_);
         }
     }
     __syncthreads();
@@ -994,8 +983,33 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     // for it here (everything above reads only particle and geometry data)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nlist = min(pre[Tm], cap);
+    // the last warp, meanwhile: the FP64 sums of the bond loads and the wall
+    // force (only the rigid update below needs them)
+    constexpr int SW = PT / 32 - 1;
+    if (warp == SW) {
+        if (!init) {
+#pragma unroll 1
+            for (int q = 3; q < 6; ++q) {
+                const double v = warp_sum_array<R>(cq + q * cstride, nl);
+                if (lane == 0) ps.F[q] = v;
+            }
+            if (lane == 0) {
+                // ---- 4. wall force (Eq. 12), FP64 ---------------------
+                // F_w = H_k / (8 sqrt 2) sqrt(r / eps^5) off each wall, eps
+                // the smallest element gap clamped below by eps_min
+                double Fw = 0.0;
+                if (s.wall_b != LBIB_WALL_PERIODIC && s.hamaker != 0.0) {
+                    const double eb = fmax(ps.gapb, s.eps_min), et = fmax(ps.gapt, s.eps_min);
+                    const double k = s.hamaker / (8.0 * 1.4142135623730951);
+                    Fw = k * sqrt(Pc.r_eq / (eb * eb * eb * eb * eb)) -
+                         k * sqrt(Pc.r_eq / (et * et * et * et * et));
+                }
+                ps.Fw = Fw;
+            }
+        }
+    } else
 #pragma unroll 2
-    for (int k = tid; k < nlist; k += PT) {
+    for (int k = tid; k < nlist; k += PT - 32) {
         // staged node k: row v is the last with pre[v] <= k, then its spans
         int lo = 0, hi = Tm;
         while (hi - lo > 1) {
