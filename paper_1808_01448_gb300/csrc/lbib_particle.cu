@@ -660,10 +660,6 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
     __shared__ __align__(16) unsigned char s_sim_raw[sizeof(SimDev)];
     __shared__ __align__(16) unsigned char s_par_raw[sizeof(ParticleDev)];
     ParticleDev *P = b.parts[blockIdx.x];
-    // FP64 cosine and sine of the angle for the bond geometry: by the last
-    // thread, which has no share of the descriptor copy below, meanwhile
-    double th_sn = 0.0, th_cs = 1.0;
-    if (threadIdx.x == PT - 1 && !init) sincos(P->th, &th_sn, &th_cs);
     // this thread's element record, loaded beside the descriptor (used only
     // if the descriptor says it is valid)
     R ev[ECACHE];
@@ -762,10 +758,9 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
             set_pose(ps, yb, yt);
         }
     }
-    if (tid == PT - 1 && !init) {
-        ps.snd = th_sn;
-        ps.csd = th_cs;
-    }
+    // FP64 cosine and sine of the angle for the bond geometry (beside the
+    // compute-precision pose of thread 0)
+    if (tid == 32 && !init) sincos(Pc.th, &ps.snd, &ps.csd);
     // element of this thread's bond: the upper half of the block takes the
     // bonds when both halves fit the elements, so that they run beside the
     // staging work of the lower half; its body-frame centroid in FP64

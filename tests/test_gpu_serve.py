@@ -94,3 +94,47 @@ def test_served_results_equal_solo_runs(L):
             np.testing.assert_array_equal(solo.bonds(i)[0], bonds_mix[i])
         solo.close()
     eng.close()
+
+
+def test_in_place_admission_results_equal_solo_runs(L):
+    """With a budget that fits the requests' two population buffers for only
+    part of the trace, the loop admits some of them with in-place streaming
+    (one buffer); their results are still bit for bit the A/B solo runs, and
+    the memory the library holds never exceeds the budget."""
+    import torch
+    reqs = small_requests()
+    ab = [serve.request_bytes(r, "ab") for r in reqs]
+    aa = [serve.request_bytes(r, "aa") for r in reqs]
+    # every request fits alone in place; those whose two buffers do not fit
+    # can only be admitted in place
+    budget = max(aa)
+    must = sum(x > budget for x in ab)
+    assert must > 0
+    streams = {"f32": torch.cuda.Stream(), "f16": torch.cuda.Stream()}
+    eng = RecordingEngine(L, {k: v.cuda_stream for k, v in streams.items()}, L.torch_allocator())
+    srv = serve.Server(eng, budget_bytes=budget, quantum=16, clock=eng.clock, in_place="auto")
+    peak = 0
+    orig_step = eng.step
+
+    def step(n):
+        nonlocal peak
+        peak = max(peak, srv.used)
+        orig_step(n)
+
+    eng.step = step
+    res = srv.run(reqs, t0=0.0)
+    assert sorted(r.rid for r in res) == list(range(len(reqs)))
+    assert srv.admitted_in_place >= must
+    assert peak <= budget
+    by_rid = {r["rid"]: r for r in reqs}
+    for r in res:
+        req = by_rid[r.rid]
+        solo = L.Sim(storage=req["storage"], **req["config"])
+        for p in req["particles"]:
+            solo.add_particle(**p)
+        solo.step(req["steps"])
+        f_mix, bonds_mix, parts_mix = eng.final[r.rid]
+        np.testing.assert_array_equal(solo.populations(), f_mix)
+        assert solo.particles() == parts_mix
+        solo.close()
+    eng.close()
