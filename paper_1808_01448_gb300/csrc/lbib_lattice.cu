@@ -57,22 +57,72 @@ template <typename R> __device__ __forceinline__ R op_fma(R a, R b, R c) {
     if constexpr (sizeof(R) == 4) return __fmaf_rn(a, b, c); else return __fma_rn(a, b, c);
 }
 
-template <typename R, bool SC = false, bool FAST = false>
-__device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy, bool &bad) {
-    R drho, jx, jy;
-    node_moments(d, drho, jx, jy);
+// Two FP32 nodes side by side (float2): the sm_100 family's paired FFMA2 /
+// FADD2 / FMUL2, per component the correctly rounded FP32 operation of the
+// scalar form (a - b as fma(b, -1, a), rounded once as the subtraction), so
+// each node of a pair gets the bits it gets alone, with half the
+// instructions.
+__device__ __forceinline__ float2 op_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 op_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 op_sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 op_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Scalar type of a lane and broadcast of a scalar.
+template <typename V> struct Lane;
+template <> struct Lane<float> {
+    using S = float;
+    static __device__ __forceinline__ float bc(float x) { return x; }
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    static __device__ __forceinline__ bool bad(float drho, float ux, float uy) {
+        return !(fabsf(drho) < 1.f) | !(fabsf(ux) + fabsf(uy) < 10.f);
+    }
+};
+template <> struct Lane<double> {
+    using S = double;
+    static __device__ __forceinline__ double bc(double x) { return x; }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ bool bad(double drho, double ux, double uy) {
+        return !(fabs(drho) < 1.0) | !(fabs(ux) + fabs(uy) < 10.0);
+    }
+};
+template <> struct Lane<float2> {
+    using S = float;
+    static __device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
+    static __device__ __forceinline__ float2 rcp(float2 x) {
+        return make_float2(__frcp_rn(x.x), __frcp_rn(x.y));
+    }
+    static __device__ __forceinline__ bool bad(float2 drho, float2 ux, float2 uy) {
+        return Lane<float>::bad(drho.x, ux.x, uy.x) | Lane<float>::bad(drho.y, ux.y, uy.y);
+    }
+};
+
+// The collision of one node (V = R) or of two FP32 nodes (V = float2);
+// forced: F != 0 (the same for both nodes of a pair).
+template <typename V, bool SC, bool FAST>
+__device__ __forceinline__ void collide_core(const SimDev &s, V d[9], V Fx, V Fy, bool forced,
+                                             bool &bad) {
+    using R = typename Lane<V>::S;
+    auto C = [](R x) { return Lane<V>::bc(x); };
+    // moments (Eq. 5-6) in the order of node_moments
+    V drho = op_add(op_add(op_add(d[0], d[1]), op_add(d[2], d[3])),
+                    op_add(op_add(d[4], d[5]), op_add(d[6], d[7])));
+    drho = op_add(drho, d[8]);
+    V jx = op_add(op_add(op_sub(d[1], d[3]), op_sub(d[5], d[6])), op_sub(d[8], d[7]));
+    V jy = op_sub(op_add(op_sub(d[2], d[4]), op_add(d[5], d[6])), op_add(d[7], d[8]));
     if constexpr (SC) {
-        const R inv = s.inv_scale;
+        const V inv = C((R)s.inv_scale);
         drho = op_mul(drho, inv);
         jx = op_mul(jx, inv);
         jy = op_mul(jy, inv);
     }
-    const R rho = op_add((R)1, drho);
-    const R irho = recip(rho);
+    const V rho = op_add(C((R)1), drho);
+    const V irho = Lane<V>::rcp(rho);
     const R om = pick<R>(s.f_om, s.d_om);
     const R pref0 = pick<R>(s.f_pref, s.d_pref);
-    const R oms = SC ? op_mul(om, (R)s.scale) : om, pref = SC ? op_mul(pref0, (R)s.scale) : pref0;
-    const R c = op_sub((R)1, om);
+    const R oms_s = SC ? op_mul(om, (R)s.scale) : om, pref_s = SC ? op_mul(pref0, (R)s.scale) : pref0;
+    const V oms = C(oms_s), pref = C(pref_s), c = C(op_sub((R)1, om));
     // f^eq_i - w_i = w_i [A + 3 rho e.u + 4.5 rho (e.u)^2], A = (rho - 1) - 1.5 rho u.u
     // Guo: S_i = (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
     // Post-collision d_i (1 - om) + om (f^eq_i - w_i) + S_i, evaluated per pair
@@ -83,25 +133,25 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
     // its walls alone) takes the same expressions with the force terms left
     // out, which are zero; the choice depends on F alone, so every path
     // takes the same one for a node.
-    R ux, uy;
-    if (Fx != (R)0 || Fy != (R)0) {
-        ux = op_mul(op_fma((R)0.5, Fx, jx), irho);
-        uy = op_mul(op_fma((R)0.5, Fy, jy), irho);
+    V ux, uy;
+    if (forced) {
+        ux = op_mul(op_fma(C((R)0.5), Fx, jx), irho);
+        uy = op_mul(op_fma(C((R)0.5), Fy, jy), irho);
     } else {
         ux = op_mul(jx, irho);
         uy = op_mul(jy, irho);
     }
-    const R A = op_fma(op_mul((R)-1.5, rho), op_fma(ux, ux, op_mul(uy, uy)), drho);
-    if (Fx != (R)0 || Fy != (R)0) {
-        const R uF = op_fma(ux, Fx, op_mul(uy, Fy));
+    const V A = op_fma(op_mul(C((R)-1.5), rho), op_fma(ux, ux, op_mul(uy, uy)), drho);
+    if (forced) {
+        const V uF = op_fma(ux, Fx, op_mul(uy, Fy));
         if constexpr (FAST) {
-            const R orho = op_mul(oms, rho), p2 = op_mul((R)2, pref);
-            const R base = op_fma(oms, A, op_mul(op_mul((R)-3, pref), uF));
-            d[0] = op_fma(c, d[0], op_mul((R)(4.0 / 9.0), base));
-            auto pair = [&](int i, int j, R w, R eu, R eF) {
-                const R inner = op_fma(orho, eu, op_mul(p2, eF));
-                const R even = op_mul(w, op_fma(op_mul((R)4.5, eu), inner, base));
-                const R odd = op_mul(op_mul((R)3, w), op_fma(orho, eu, op_mul(pref, eF)));
+            const V orho = op_mul(oms, rho), p2 = C(op_mul((R)2, pref_s));
+            const V base = op_fma(oms, A, op_mul(C(op_mul((R)-3, pref_s)), uF));
+            d[0] = op_fma(c, d[0], op_mul(C((R)(4.0 / 9.0)), base));
+            auto pair = [&](int i, int j, R w, V eu, V eF) {
+                const V inner = op_fma(orho, eu, op_mul(p2, eF));
+                const V even = op_mul(C(w), op_fma(op_mul(C((R)4.5), eu), inner, base));
+                const V odd = op_mul(C(op_mul((R)3, w)), op_fma(orho, eu, op_mul(pref, eF)));
                 d[i] = op_add(op_fma(c, d[i], even), odd);
                 d[j] = op_sub(op_fma(c, d[j], even), odd);
             };
@@ -110,34 +160,34 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
             pair(5, 7, (R)(1.0 / 36.0), op_add(ux, uy), op_add(Fx, Fy));
             pair(6, 8, (R)(1.0 / 36.0), op_sub(uy, ux), op_sub(Fy, Fx));
         } else {
-            const R W1 = (R)(1.0 / 3.0), W5 = op_mul(op_sub((R)1, op_mul((R)2, W1)), (R)0.25);
-            const R r45 = op_mul((R)4.5, rho), m3uF = op_mul((R)-3, uF);
+            const R W1s = (R)(1.0 / 3.0), W5s = op_mul(op_sub((R)1, op_mul((R)2, W1s)), (R)0.25);
+            const V r45 = op_mul(C((R)4.5), rho), m3uF = op_mul(C((R)-3), uF);
             const R w0 = (R)(4.0 / 9.0);
-            d[0] = op_fma(c, d[0], op_fma(oms, op_mul(w0, A), op_mul(pref, op_mul(w0, m3uF))));
+            d[0] = op_fma(c, d[0], op_fma(oms, op_mul(C(w0), A), op_mul(pref, op_mul(C(w0), m3uF))));
             // pair (i, j = opposite of i): even part w (om A' + pref S_even),
             // odd part W (om rho (e.u) + pref (e.F))
-            auto pair = [&](int i, int j, R w, R W, R eu, R eF) {
-                const R ee = op_mul(oms, op_mul(w, op_fma(op_mul(r45, eu), eu, A)));
-                const R oo = op_mul(oms, op_mul(W, op_mul(rho, eu)));
-                const R se = op_mul(pref, op_mul(w, op_fma(op_mul((R)9, eu), eF, m3uF)));
-                const R so = op_mul(pref, op_mul(W, eF));
+            auto pair = [&](int i, int j, R w, R W, V eu, V eF) {
+                const V ee = op_mul(oms, op_mul(C(w), op_fma(op_mul(r45, eu), eu, A)));
+                const V oo = op_mul(oms, op_mul(C(W), op_mul(rho, eu)));
+                const V se = op_mul(pref, op_mul(C(w), op_fma(op_mul(C((R)9), eu), eF, m3uF)));
+                const V so = op_mul(pref, op_mul(C(W), eF));
                 d[i] = op_add(op_fma(c, d[i], op_add(ee, oo)), op_add(se, so));
                 d[j] = op_add(op_fma(c, d[j], op_sub(ee, oo)), op_sub(se, so));
             };
-            pair(1, 3, (R)(1.0 / 9.0), W1, ux, Fx);
-            pair(2, 4, (R)(1.0 / 9.0), W1, uy, Fy);
-            pair(5, 7, (R)(1.0 / 36.0), W5, op_add(ux, uy), op_add(Fx, Fy));
-            pair(6, 8, (R)(1.0 / 36.0), W5, op_sub(uy, ux), op_sub(Fy, Fx));
+            pair(1, 3, (R)(1.0 / 9.0), W1s, ux, Fx);
+            pair(2, 4, (R)(1.0 / 9.0), W1s, uy, Fy);
+            pair(5, 7, (R)(1.0 / 36.0), W5s, op_add(ux, uy), op_add(Fx, Fy));
+            pair(6, 8, (R)(1.0 / 36.0), W5s, op_sub(uy, ux), op_sub(Fy, Fx));
         }
     } else {
         if constexpr (FAST) {
-            const R orho = op_mul(oms, rho);
-            const R base = op_mul(oms, A);
-            d[0] = op_fma(c, d[0], op_mul((R)(4.0 / 9.0), base));
-            auto pair = [&](int i, int j, R w, R eu) {
-                const R inner = op_mul(orho, eu);
-                const R even = op_mul(w, op_fma(op_mul((R)4.5, eu), inner, base));
-                const R odd = op_mul(op_mul((R)3, w), inner);
+            const V orho = op_mul(oms, rho);
+            const V base = op_mul(oms, A);
+            d[0] = op_fma(c, d[0], op_mul(C((R)(4.0 / 9.0)), base));
+            auto pair = [&](int i, int j, R w, V eu) {
+                const V inner = op_mul(orho, eu);
+                const V even = op_mul(C(w), op_fma(op_mul(C((R)4.5), eu), inner, base));
+                const V odd = op_mul(C(op_mul((R)3, w)), inner);
                 d[i] = op_add(op_fma(c, d[i], even), odd);
                 d[j] = op_sub(op_fma(c, d[j], even), odd);
             };
@@ -146,25 +196,87 @@ __device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy
             pair(5, 7, (R)(1.0 / 36.0), op_add(ux, uy));
             pair(6, 8, (R)(1.0 / 36.0), op_sub(uy, ux));
         } else {
-            const R W1 = (R)(1.0 / 3.0), W5 = op_mul(op_sub((R)1, op_mul((R)2, W1)), (R)0.25);
-            const R r45 = op_mul((R)4.5, rho);
+            const R W1s = (R)(1.0 / 3.0), W5s = op_mul(op_sub((R)1, op_mul((R)2, W1s)), (R)0.25);
+            const V r45 = op_mul(C((R)4.5), rho);
             const R w0 = (R)(4.0 / 9.0);
-            d[0] = op_fma(c, d[0], op_mul(oms, op_mul(w0, A)));
-            auto pair = [&](int i, int j, R w, R W, R eu) {
-                const R ee = op_mul(oms, op_mul(w, op_fma(op_mul(r45, eu), eu, A)));
-                const R oo = op_mul(oms, op_mul(W, op_mul(rho, eu)));
+            d[0] = op_fma(c, d[0], op_mul(oms, op_mul(C(w0), A)));
+            auto pair = [&](int i, int j, R w, R W, V eu) {
+                const V ee = op_mul(oms, op_mul(C(w), op_fma(op_mul(r45, eu), eu, A)));
+                const V oo = op_mul(oms, op_mul(C(W), op_mul(rho, eu)));
                 d[i] = op_fma(c, d[i], op_add(ee, oo));
                 d[j] = op_fma(c, d[j], op_sub(ee, oo));
             };
-            pair(1, 3, (R)(1.0 / 9.0), W1, ux);
-            pair(2, 4, (R)(1.0 / 9.0), W1, uy);
-            pair(5, 7, (R)(1.0 / 36.0), W5, op_add(ux, uy));
-            pair(6, 8, (R)(1.0 / 36.0), W5, op_sub(uy, ux));
+            pair(1, 3, (R)(1.0 / 9.0), W1s, ux);
+            pair(2, 4, (R)(1.0 / 9.0), W1s, uy);
+            pair(5, 7, (R)(1.0 / 36.0), W5s, op_add(ux, uy));
+            pair(6, 8, (R)(1.0 / 36.0), W5s, op_sub(uy, ux));
         }
     }
     // non-finite state or a density outside (0, 2): the run has broken down
     // (the caller raises the error bit once for all its nodes)
-    bad |= !(fabs(drho) < (R)1) | !(fabs(ux) + fabs(uy) < (R)10);
+    bad |= Lane<V>::bad(drho, ux, uy);
+}
+
+template <typename R, bool SC = false, bool FAST = false>
+__device__ __forceinline__ void collide_node(const SimDev &s, R d[9], R Fx, R Fy, bool &bad) {
+    collide_core<R, SC, FAST>(s, d, Fx, Fy, Fx != (R)0 || Fy != (R)0, bad);
+}
+
+// Two FP32 nodes at once (paired arithmetic, the same bits as two
+// collide_node calls); nodes of which only one has a force go one by one.
+template <bool SC, bool FAST>
+__device__ __forceinline__ void collide_pair(const SimDev &s, float da[9], float db[9], float Fxa,
+                                             float Fya, float Fxb, float Fyb, bool &bad) {
+    const bool fa = Fxa != 0.f || Fya != 0.f, fb = Fxb != 0.f || Fyb != 0.f;
+    if (fa != fb) {
+        collide_core<float, SC, FAST>(s, da, Fxa, Fya, fa, bad);
+        collide_core<float, SC, FAST>(s, db, Fxb, Fyb, fb, bad);
+        return;
+    }
+    float2 d2[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d2[i] = make_float2(da[i], db[i]);
+    collide_core<float2, SC, FAST>(s, d2, make_float2(Fxa, Fxb), make_float2(Fya, Fyb), fa, bad);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        da[i] = d2[i].x;
+        db[i] = d2[i].y;
+    }
+}
+
+// Four nodes under one force (F, the same for all four: no particle tile);
+// the same bits as four collide_node calls.  From 16-bit storage (SC) the
+// FP32 arithmetic runs in two pairs of paired instructions, which halves the
+// collision's issue count there (where issue, not DRAM, limits the pass);
+// from FP32 storage the pairs cost more in register pressure than they save,
+// and from FP64 there is no paired form.  The debug build collides node by
+// node, so comparing its bits with the release build's checks the pairs.
+#ifdef LBIB_DEBUG
+constexpr bool kPairedCollision = false;
+#else
+constexpr bool kPairedCollision = true;
+#endif
+
+template <typename R, bool SC, bool FAST>
+__device__ __forceinline__ void collide_group4(const SimDev &s, R (*d)[9], R Fx, R Fy, bool &bad) {
+    const bool forced = Fx != (R)0 || Fy != (R)0;
+    if constexpr (sizeof(R) == 4 && SC && kPairedCollision) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float2 d2[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d2[i] = make_float2(d[2 * h][i], d[2 * h + 1][i]);
+            collide_core<float2, SC, FAST>(s, d2, make_float2(Fx, Fx), make_float2(Fy, Fy), forced, bad);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                d[2 * h][i] = d2[i].x;
+                d[2 * h + 1][i] = d2[i].y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) collide_core<R, SC, FAST>(s, d[j], Fx, Fy, forced, bad);
+    }
 }
 
 template <typename R, bool SC = false, bool FAST = false>
@@ -380,9 +492,9 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             const int k = kg[g];
             if (BULK && gx == (R)0 && gy == (R)0) {
                 // no body force and no particle tile: the force-free form
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    collide_node<R, SC, sizeof(S) == 2>(s, d[4 * g + j], (R)0, (R)0, bad);
+                collide_group4<R, SC, sizeof(S) == 2>(s, &d[4 * g], (R)0, (R)0, bad);
+            } else if (BULK) {
+                collide_group4<R, SC, sizeof(S) == 2>(s, &d[4 * g], gx, gy, bad);
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -789,13 +901,8 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     }
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
     bool bad = false;
-    if (gx == (R)0 && gy == (R)0) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) collide_node<R, SC, sizeof(S) == 2>(s, d[j], (R)0, (R)0, bad);
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) collide_node<R, SC, sizeof(S) == 2>(s, d[j], gx, gy, bad);
-    }
+    if (gx == (R)0 && gy == (R)0) collide_group4<R, SC, sizeof(S) == 2>(s, d, (R)0, (R)0, bad);
+    else collide_group4<R, SC, sizeof(S) == 2>(s, d, gx, gy, bad);
     if (bad) atomicOr(s.err, ERR_UNSTABLE);
     const float sc = SC ? 1.f : s.scale;
     if (keep == 0xFu && sizeof(S) == 2 && s.sround) {

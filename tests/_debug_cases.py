@@ -37,6 +37,17 @@ def main(out):
             res[f"{st}_{k}_pop"] = s.populations()
             res[f"{st}_{k}_x"] = np.array([s.particle(0)[q] for q in ("xc", "yc", "theta")])
         b.close()
+    # body-force channel in 16-bit storage (the forced collision of the
+    # bulk pass, paired in the release build, node by node in the debug one)
+    for st in ("f16", "bf16"):
+        cfg, parts = W.poiseuille_circle(Re=5.0)
+        s = L.Sim(storage=st, **cfg)
+        s.add_particle(**parts[0])
+        b = L.Batch([s])
+        b.step(30)
+        b.synchronize()
+        res[f"body_{st}_pop"] = s.populations()
+        b.close()
     # copy-engine staging variants of the bulk pass (single stage, pipeline)
     for v in (4, 5):
         for st in ("f32", "f16"):
