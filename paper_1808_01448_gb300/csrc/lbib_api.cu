@@ -611,8 +611,8 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     const size_t bytes = sizeof(SimDev) * n + sizeof(ParticleDev *) * (nparts + 1) +
                          sizeof(PartRec) * (nparts + 1) +
                          sizeof(int) * (nparts + 1) + sizeof(int *) * n +
-                         sizeof(int) * (size_t)tiles + sizeof(int) * (size_t)(near_tiles + nparts) +
-                         256;
+                         sizeof(TileDev) * (size_t)tiles + sizeof(int) * (size_t)(near_tiles + nparts) +
+                         sizeof(int) * n + sizeof(NearBox) * (nparts + 1) + 512;
     unsigned char *blk = (unsigned char *)dalloc(sims[0]->cfg, b->stream, bytes);
     if (!blk) { delete b; return fail(LBIB_E_OOM, "device allocation for the batch failed"); }
     b->d_block = blk;
@@ -628,9 +628,11 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     PartRec *dprec = (PartRec *)take(sizeof(PartRec) * (nparts + 1));
     int *dpsim = (int *)take(sizeof(int) * (nparts + 1));
     int **dcurs = (int **)take(sizeof(int *) * n);
-    int *dtsim = (int *)take(sizeof(int) * (size_t)tiles);
+    TileDev *dtiles = (TileDev *)take(sizeof(TileDev) * (size_t)tiles);
     int *dnpart = (int *)take(sizeof(int) * (size_t)(near_tiles + 1));
     int *dntile0 = (int *)take(sizeof(int) * (size_t)(nparts + 1));
+    int *dpar = (int *)take(sizeof(int) * n);
+    NearBox *dnbox = (NearBox *)take(sizeof(NearBox) * (nparts + 1));
     std::vector<SimDev> hs;
     std::vector<ParticleDev *> hp;
     std::vector<PartRec> hpr;
@@ -651,9 +653,10 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     hp.push_back(nullptr);
     hpr.push_back(PartRec{nullptr, 0, 0});
     hps.push_back(0);
-    std::vector<int> hts((size_t)tiles);
+    std::vector<TileDev> hts((size_t)tiles);
     for (int i = 0; i < n; ++i)
-        for (int t = 0; t < hs[i].ntiles; ++t) hts[(size_t)hs[i].tile0 + t] = i;
+        for (int t = 0; t < hs[i].ntiles; ++t)
+            hts[(size_t)hs[i].tile0 + t] = TileDev{i, t * LB_TILE_NODES, hs[i].p0, hs[i].np};
     std::vector<int> hnp, hnt0;
     for (int i = 0; i < n; ++i)
         for (auto &p : sims[i]->parts) {
@@ -671,7 +674,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         (e = cudaMemcpyAsync(dprec, hpr.data(), sizeof(PartRec) * hpr.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dpsim, hps.data(), sizeof(int) * hps.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dcurs, hc.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(dtsim, hts.data(), sizeof(int) * hts.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(dtiles, hts.data(), sizeof(TileDev) * hts.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dnpart, hnp.data(), sizeof(int) * hnp.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dntile0, hnt0.data(), sizeof(int) * hnt0.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaStreamSynchronize(st))) {
@@ -696,7 +699,9 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->bd.parts = dparts;
     b->bd.prec = dprec;
     b->bd.part_sim = dpsim;
-    b->bd.tile_sim = dtsim;
+    b->bd.tiles = dtiles;
+    b->bd.par = dpar;
+    b->bd.nbox = dnbox;
     b->bd.nsims = n;
     b->bd.nparts = nparts;
     b->bd.total_tiles = tile0;
@@ -821,7 +826,7 @@ lbib_status reprime(lbib_sim *s) {
 // takes one initial IB launch over all its particles instead of one launch
 // and one private batch per simulation; otherwise each member is primed on
 // its own.
-lbib_status prime_members(lbib_batch *b) {
+lbib_status prime_members_once(lbib_batch *b) {
     bool none = true, all = true;
     for (lbib_sim *s : b->sims) {
         if (s->primed) none = false;
@@ -848,6 +853,17 @@ lbib_status prime_members(lbib_batch *b) {
         if (e != cudaSuccess) return cuda_fail(e, "particle kernel (init)");
     }
     for (lbib_sim *s : b->sims) s->primed = true;
+    return LBIB_OK;
+}
+
+// Before every batched call: prime the members, then copy their parity words
+// and near boxes into the batch (what the members did on their own since the
+// last call, restores included, is picked up here).
+lbib_status prime_members(lbib_batch *b) {
+    lbib_status r = prime_members_once(b);
+    if (r != LBIB_OK) return r;
+    cudaError_t e = launch_batch_refresh(b->bd, b->d_curs, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch refresh");
     return LBIB_OK;
 }
 
@@ -970,7 +986,7 @@ cudaError_t enqueue_flushed_steps(lbib_batch *b, int nsteps, cudaEvent_t *ev) {
         }
         if ((e = cudaEventRecordWithFlags(E[4], b->stream, fl))) return e;
     }
-    if (nsteps & 1) e = launch_flip(b->d_curs, (int)b->sims.size(), b->stream);
+    if (nsteps & 1) e = launch_flip(b->d_curs, b->bd.par, (int)b->sims.size(), b->stream);
     return e;
 }
 
@@ -1051,7 +1067,7 @@ lbib_status batch_step_impl(lbib_batch *b, int64_t n) {
         cudaError_t e = enqueue_steps(b, tail, ev, false);
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         if (tail & 1) {
-            e = launch_flip(b->d_curs, (int)b->sims.size(), b->stream);
+            e = launch_flip(b->d_curs, b->bd.par, (int)b->sims.size(), b->stream);
             if (e != cudaSuccess) return cuda_fail(e, "parity flip");
         }
     }

@@ -144,12 +144,34 @@ struct PartRec {
     int nl, pad;
 };
 
+// Per lattice work tile: its simulation, its first node, and the range of the
+// batch's particles (and near boxes) of that simulation.
+struct TileDev {
+    int sim, k0, p0, np;
+};
+
+// A particle's near boxes (ParticleDev::box_ox / box_oy, both parities) and
+// edge, copied into one flat per-batch table so that the bulk pass finds
+// them in one load round, independent of the parity.
+struct NearBox {
+    int ox0, oy0, ox1, oy1;
+    int NB, pad[3];
+};
+
+// The bulk pass reads its tile, the simulation's descriptor, its parity and
+// its near boxes in two rounds of loads (tile; descriptor, parity and boxes),
+// not through a chain of dependent loads: the batch keeps its own copies of
+// the members' parity words (par) and near boxes (nbox).  They are refreshed
+// from the members before every batched call, the parity flip updates both
+// copies, and the near-box pass publishes each new box into both.
 struct BatchDev {
     SimDev *sims;
     ParticleDev **parts;
     const PartRec *prec;     // [nparts] or null
     int *part_sim;
-    int *tile_sim;       // lattice work tile -> simulation index
+    const TileDev *tiles;    // lattice work tile -> its simulation, first node, particles
+    int *par;                // [nsims] copy of each member's parity word (*SimDev::cur)
+    NearBox *nbox;           // [nparts] copy of each particle's near boxes
     int *near_part;      // near-box work tile -> batch particle index
     int *near_tile0;     // first near-box tile of each batch particle
     int total_near_tiles;
@@ -538,7 +560,10 @@ cudaError_t launch_fields(int kind, const SimDev &s, ParticleDev *const *parts, 
                           double *ux, double *uy, cudaStream_t st);
 cudaError_t launch_populations(int kind, const SimDev &s, double *out, cudaStream_t st);
 cudaError_t launch_set_populations(int kind, const SimDev &s, const double *in, cudaStream_t st);
-cudaError_t launch_flip(int *const *curs, int n, cudaStream_t st);
+// Flip each member's parity word and the batch's copy of it.
+cudaError_t launch_flip(int *const *curs, int *par, int n, cudaStream_t st);
+// Copy the members' parity words and near boxes into the batch (par, nbox).
+cudaError_t launch_batch_refresh(const BatchDev &b, int *const *curs, cudaStream_t st);
 cudaError_t launch_ib_export(int kind, const SimDev &s, ParticleDev *const *parts, double *fx,
                              double *fy, cudaStream_t st);
 // vb: the particle's simulation solves its spreading scales (ib_spread = 1)

@@ -373,40 +373,48 @@ __device__ __forceinline__ void pull_group(const SimDev &s, const S *__restrict_
     plane(8, rp, 1);
 }
 
-// Node (x, y) inside a near box of the simulation's particles (box slot =
-// the parity of the buffer this step reads).
-__device__ __forceinline__ bool in_near_box(const SimDev &s, ParticleDev *const *parts, int slot,
+// Near box of a batch particle for the step that reads buffer parity slot,
+// from the batch's flat copy (both slots in one load, so the load does not
+// wait for the parity).
+struct BoxView {
+    int ox, oy, NB;
+};
+__device__ __forceinline__ BoxView near_box(const NearBox *nb, int slot) {
+    const int4 o = *reinterpret_cast<const int4 *>(nb);
+    return BoxView{slot ? o.z : o.x, slot ? o.w : o.y, nb->NB};
+}
+
+// Node (x, y) inside a near box of the simulation's particles (the batch's
+// near boxes nb[0 .. np); box slot = the parity of the buffer this step reads).
+__device__ __forceinline__ bool in_near_box(const SimDev &s, const NearBox *nb, int np, int slot,
                                             int x, int y) {
-    for (int k = 0; k < s.np; ++k) {
-        const ParticleDev *p = parts[s.p0 + k];
-        const int NB = p->NB;
-        int dx = x - p->box_ox[slot];
+    for (int k = 0; k < np; ++k) {
+        const BoxView q = near_box(nb + k, slot);
+        int dx = x - q.ox;
         if (dx < 0) dx += s.nx;
-        int dy = y - p->box_oy[slot];
+        int dy = y - q.oy;
         if (dy < 0 && s.wall_b == LBIB_WALL_PERIODIC) dy += s.ny;
-        if (dx < NB && (unsigned)dy < (unsigned)NB) return true;
+        if (dx < q.NB && (unsigned)dy < (unsigned)q.NB) return true;
     }
     return false;
 }
 
 // Bit j set: node (x0 + j, y) lies outside every near box (x0 + 3 < nx).
-__device__ __forceinline__ unsigned outside_near_boxes4(const SimDev &s,
-                                                        ParticleDev *const *parts, int slot,
-                                                        int x0, int y) {
+__device__ __forceinline__ unsigned outside_near_boxes4(const SimDev &s, const NearBox *nb, int np,
+                                                        int slot, int x0, int y) {
     unsigned keep = 0xFu;
-    for (int k = 0; k < s.np; ++k) {
-        const ParticleDev *p = parts[s.p0 + k];
-        const int NB = p->NB;
-        int dy = y - p->box_oy[slot];
+    for (int k = 0; k < np; ++k) {
+        const BoxView q = near_box(nb + k, slot);
+        int dy = y - q.oy;
         if (dy < 0 && s.wall_b == LBIB_WALL_PERIODIC) dy += s.ny;
-        if ((unsigned)dy >= (unsigned)NB) continue;
-        int dx = x0 - p->box_ox[slot];
+        if ((unsigned)dy >= (unsigned)q.NB) continue;
+        int dx = x0 - q.ox;
         if (dx < 0) dx += s.nx;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int e = dx + j;
             if (e >= s.nx) e -= s.nx;
-            if (e < NB) keep &= ~(1u << j);
+            if (e < q.NB) keep &= ~(1u << j);
         }
     }
     return keep;
@@ -433,11 +441,12 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
     const bool dry = (flip & 2) != 0;
     flip &= 1;
     const int tile = blockIdx.x;
-    const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
+    const TileDev t = b.tiles[tile];
+    const SimDev &s = b.sims[t.sim];
     const int nx = s.nx;
     const int N = nx * s.ny;
-    if (!dry && tile == s.tile0 && threadIdx.x == 0) *s.step += 1;
-    const int cur = *s.cur ^ flip;
+    if (!dry && t.k0 == 0 && threadIdx.x == 0) *s.step += 1;
+    const int cur = b.par[t.sim] ^ flip;
     const S *__restrict__ src = (const S *)s.pop[cur];
     S *__restrict__ dst = (S *)s.pop[cur ^ 1];
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
@@ -445,7 +454,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
     if (s.vec4) {
         // 16-bit storage: groups collide in the scaled form (collide_node)
         constexpr bool SC = sizeof(S) == 2;
-        const int kt = (tile - s.tile0) * LB_TILE_NODES + 4 * (int)threadIdx.x;
+        const int kt = t.k0 + 4 * (int)threadIdx.x;
         int kg[GROUPS], yg[GROUPS], xg[GROUPS];
         unsigned keep[GROUPS];
 #pragma unroll
@@ -454,7 +463,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             yg[g] = div_nx(s, kg[g]);
             xg[g] = kg[g] - yg[g] * nx;
             keep[g] = kg[g] < N ? 0xFu : 0u;
-            if (BULK && s.np && keep[g]) keep[g] = outside_near_boxes4(s, b.parts, cur, xg[g], yg[g]);
+            if (BULK && t.np && keep[g]) keep[g] = outside_near_boxes4(s, b.nbox + t.p0, t.np, cur, xg[g], yg[g]);
         }
 #pragma unroll
         for (int g = 0; g < GROUPS; ++g) {
@@ -603,7 +612,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
         if (bad) atomicOr(s.err, ERR_UNSTABLE);
         return;
     }
-    const int k0 = (tile - s.tile0) * LB_TILE_NODES + (int)threadIdx.x;
+    const int k0 = t.k0 + (int)threadIdx.x;
     bool skip[NPT];
     // node coordinates: one division per thread, then step by THREADS
     int xs[NPT], ys[NPT];
@@ -623,7 +632,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         skip[j] = k0 + j * THREADS >= N;
-        if (BULK && !skip[j] && s.np) skip[j] = in_near_box(s, b.parts, cur, xs[j], ys[j]);
+        if (BULK && !skip[j] && t.np) skip[j] = in_near_box(s, b.nbox + t.p0, t.np, cur, xs[j], ys[j]);
     }
 #pragma unroll
     for (int j = 0; j < NPT; ++j)
@@ -664,8 +673,12 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
     const int NB = P->NB, ox = P->box_ox[cur], oy = P->box_oy[cur];
     const int t0 = __ldg(b.near_tile0 + pi);
     if (tile == t0 && threadIdx.x == 0) {
-        P->box_ox[cur ^ 1] = P->pend_ox;
-        P->box_oy[cur ^ 1] = P->pend_oy;
+        const int px = P->pend_ox, py = P->pend_oy;
+        P->box_ox[cur ^ 1] = px;
+        P->box_oy[cur ^ 1] = py;
+        // and into the batch's copy read by the bulk pass
+        NearBox &q = b.nbox[pi];
+        if (cur ^ 1) { q.ox1 = px; q.oy1 = py; } else { q.ox0 = px; q.oy0 = py; }
     }
     const int nx = s.nx, ny = s.ny, N = nx * ny;
     const S *__restrict__ src = (const S *)s.pop[cur];
@@ -800,10 +813,11 @@ __device__ __forceinline__ void tma_issue(const BatchDev &b, int flip, int tile,
                                           uint64_t *bar) {
     constexpr int H = tma_margin<S>(), W = tma_width<S>();
     constexpr int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
+    const TileDev t = b.tiles[tile];
+    const SimDev &s = b.sims[t.sim];
     const int nx = s.nx, N = nx * s.ny;
-    const S *src = (const S *)s.pop[*s.cur ^ flip];
-    const int k0 = (tile - s.tile0) * LB_TILE_NODES;
+    const S *src = (const S *)s.pop[b.par[t.sim] ^ flip];
+    const int k0 = t.k0;
     // plane i of node k comes from node k - EY[i] nx - EX[i]: stage nodes
     // [k0 - EY[i] nx - H, + W), clipped to the lattice (the clipped part is
     // only ever needed by wall-row groups, which pull from global memory)
@@ -839,18 +853,19 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
                                          unsigned parity = 0) {
     constexpr int H = tma_margin<S>(), W = tma_width<S>();
     constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const SimDev &s = b.sims[__ldg(b.tile_sim + tile)];
+    const TileDev t = b.tiles[tile];
+    const SimDev &s = b.sims[t.sim];
     const int nx = s.nx, ny = s.ny, N = nx * ny;
-    if (!dry && tile == s.tile0 && threadIdx.x == 0) *s.step += 1;
-    const int cur = *s.cur ^ flip;
+    if (!dry && t.k0 == 0 && threadIdx.x == 0) *s.step += 1;
+    const int cur = b.par[t.sim] ^ flip;
     const S *__restrict__ src = (const S *)s.pop[cur];
     S *__restrict__ dst = (S *)s.pop[cur ^ 1];
-    const int k0 = (tile - s.tile0) * LB_TILE_NODES;
+    const int k0 = t.k0;
     // this thread's group of four nodes (decided while the copies run)
     const int kt = k0 + 4 * (int)threadIdx.x;
     const int y = div_nx(s, kt), x0 = kt - y * nx;
     unsigned keep = kt < N ? 0xFu : 0u;
-    if (s.np && keep) keep = outside_near_boxes4(s, b.parts, cur, x0, y);
+    if (t.np && keep) keep = outside_near_boxes4(s, b.nbox + t.p0, t.np, cur, x0, y);
     const bool wall = y == 0 || y == ny - 1;
     const bool global_pull = wall || x0 == 0 || x0 + 4 == nx;
     // 16-bit storage: the group collides in the scaled form (collide_node)
@@ -1094,9 +1109,29 @@ __global__ void ib_export_kernel(SimDev s, ParticleDev *const *parts, double *fx
     fy[k] = (double)c;
 }
 
-__global__ void flip_kernel(int *const *curs, int n) {
+__global__ void flip_kernel(int *const *curs, int *par, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) *curs[i] ^= 1;
+    if (i < n) {
+        *curs[i] ^= 1;
+        par[i] ^= 1;
+    }
+}
+
+// The batch's copies of its members' parity words and near boxes.
+__global__ void batch_refresh_kernel(BatchDev b, int *const *curs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < b.nsims) b.par[i] = *curs[i];
+    if (i < b.nparts) {
+        const ParticleDev *P = b.parts[i];
+        NearBox q;
+        q.ox0 = P->box_ox[0];
+        q.oy0 = P->box_oy[0];
+        q.ox1 = P->box_ox[1];
+        q.oy1 = P->box_oy[1];
+        q.NB = P->NB;
+        q.pad[0] = q.pad[1] = q.pad[2] = 0;
+        b.nbox[i] = q;
+    }
 }
 
 template <typename F>
@@ -1238,8 +1273,15 @@ cudaError_t launch_ib_export(int kind, const SimDev &s, ParticleDev *const *part
     });
 }
 
-cudaError_t launch_flip(int *const *curs, int n, cudaStream_t st) {
-    flip_kernel<<<(n + 127) / 128, 128, 0, st>>>(curs, n);
+cudaError_t launch_flip(int *const *curs, int *par, int n, cudaStream_t st) {
+    flip_kernel<<<(n + 127) / 128, 128, 0, st>>>(curs, par, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_refresh(const BatchDev &b, int *const *curs, cudaStream_t st) {
+    const int n = b.nsims > b.nparts ? b.nsims : b.nparts;
+    if (n == 0) return cudaSuccess;
+    batch_refresh_kernel<<<(n + 127) / 128, 128, 0, st>>>(b, curs);
     return cudaGetLastError();
 }
 
