@@ -612,7 +612,8 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
                          sizeof(PartRec) * (nparts + 1) +
                          sizeof(int) * (nparts + 1) + sizeof(int *) * n +
                          sizeof(TileDev) * (size_t)tiles + sizeof(int) * (size_t)(near_tiles + nparts) +
-                         sizeof(int) * n + sizeof(NearBox) * (nparts + 1) + 512;
+                         sizeof(int) * n + sizeof(NearBox) * (nparts + 1) +
+                         sizeof(unsigned) * (size_t)tiles + 640;
     unsigned char *blk = (unsigned char *)dalloc(sims[0]->cfg, b->stream, bytes);
     if (!blk) { delete b; return fail(LBIB_E_OOM, "device allocation for the batch failed"); }
     b->d_block = blk;
@@ -633,6 +634,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     int *dntile0 = (int *)take(sizeof(int) * (size_t)(nparts + 1));
     int *dpar = (int *)take(sizeof(int) * n);
     NearBox *dnbox = (NearBox *)take(sizeof(NearBox) * (nparts + 1));
+    unsigned *dtboxes = (unsigned *)take(sizeof(unsigned) * (size_t)tiles);
     std::vector<SimDev> hs;
     std::vector<ParticleDev *> hp;
     std::vector<PartRec> hpr;
@@ -702,6 +704,7 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     b->bd.tiles = dtiles;
     b->bd.par = dpar;
     b->bd.nbox = dnbox;
+    b->bd.tile_boxes = dtboxes;
     b->bd.nsims = n;
     b->bd.nparts = nparts;
     b->bd.total_tiles = tile0;

@@ -68,7 +68,10 @@ struct SimDev {
 // population buffer ([9][ny][nx]) with `span` consecutive elements must lie
 // in [0, 9 nx ny - span].  Out of range, the simulation's error word gets
 // ERR_BOUNDS (reported as LBIB_E_BOUNDS), loads read element 0 instead and
-// stores are dropped.  Release builds compile the checks away.
+// stores are dropped.  The debug build also checks the bulk pass's per-tile
+// near-box counts (BatchDev::tile_boxes): a node of a near box in a tile
+// counted free of them raises ERR_BOUNDS too.  Release builds compile the
+// checks away.
 __device__ __forceinline__ bool pop_index_ok(const SimDev &s, int i, int span = 1) {
 #ifdef LBIB_DEBUG
     const int total = 9 * s.nx * s.ny;
@@ -163,7 +166,12 @@ struct NearBox {
 // not through a chain of dependent loads: the batch keeps its own copies of
 // the members' parity words (par) and near boxes (nbox).  They are refreshed
 // from the members before every batched call, the parity flip updates both
-// copies, and the near-box pass publishes each new box into both.
+// copies, and the near-box pass publishes each new box into both.  Most tiles
+// meet no near box: per tile and box slot, tile_boxes counts the near boxes
+// whose rows (whole rows, so a superset of the box) reach into the tile, and
+// a tile whose count is zero skips the near-box test altogether.  The counts
+// are rebuilt with the copies and kept by the near-box pass, which moves a
+// box's count from its old tiles to its new ones when it publishes it.
 struct BatchDev {
     SimDev *sims;
     ParticleDev **parts;
@@ -172,6 +180,8 @@ struct BatchDev {
     const TileDev *tiles;    // lattice work tile -> its simulation, first node, particles
     int *par;                // [nsims] copy of each member's parity word (*SimDev::cur)
     NearBox *nbox;           // [nparts] copy of each particle's near boxes
+    unsigned *tile_boxes;    // [total_tiles] near boxes reaching the tile: slot 0 in
+                             // the low 16 bits, slot 1 in the high 16 bits
     int *near_part;      // near-box work tile -> batch particle index
     int *near_tile0;     // first near-box tile of each batch particle
     int total_near_tiles;

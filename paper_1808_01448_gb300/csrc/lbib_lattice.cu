@@ -420,6 +420,32 @@ __device__ __forceinline__ unsigned outside_near_boxes4(const SimDev &s, const N
     return keep;
 }
 
+// Calls f(tile) for each batch lattice tile holding a node of the rows of a
+// near box with lower edge oy and edge NB (rows wrapped for a periodic y,
+// clipped to the lattice between walls); lanes lane, lane + nlanes, ... of
+// the caller share the tiles.  Whole rows: a superset of the box's tiles.
+template <class F>
+__device__ __forceinline__ void for_box_tiles(const SimDev &s, int oy, int NB, int lane,
+                                              int nlanes, F &&f) {
+    auto rows = [&](int r0, int r1) {
+        const int a = s.tile0 + (int)(((long long)r0 * s.nx) / LB_TILE_NODES);
+        const int e = s.tile0 + (int)(((long long)(r1 + 1) * s.nx - 1) / LB_TILE_NODES);
+        for (int t = a + lane; t <= e; t += nlanes) f(t);
+    };
+    const int last = oy + NB - 1;
+    if (s.wall_b == LBIB_WALL_PERIODIC) {
+        if (last < s.ny) {
+            rows(oy, last);
+        } else {
+            rows(oy, s.ny - 1);
+            rows(0, min(last - s.ny, s.ny - 1));
+        }
+    } else {
+        const int r0 = max(oy, 0), r1 = min(last, s.ny - 1);
+        if (r0 <= r1) rows(r0, r1);
+    }
+}
+
 // One launch advances every simulation of a batch by one step.  A CTA of
 // THREADS threads owns LB_TILE_NODES consecutive nodes (row-major) of one
 // simulation.  With rows in whole aligned groups of four, each thread takes
@@ -442,11 +468,14 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
     flip &= 1;
     const int tile = blockIdx.x;
     const TileDev t = b.tiles[tile];
+    const unsigned tboxes = BULK && t.np ? b.tile_boxes[tile] : 0u;
     const SimDev &s = b.sims[t.sim];
     const int nx = s.nx;
     const int N = nx * s.ny;
     if (!dry && t.k0 == 0 && threadIdx.x == 0) *s.step += 1;
     const int cur = b.par[t.sim] ^ flip;
+    // a near box reaches this tile in this step's slot
+    const bool boxes = ((tboxes >> (16 * cur)) & 0xFFFFu) != 0;
     const S *__restrict__ src = (const S *)s.pop[cur];
     S *__restrict__ dst = (S *)s.pop[cur ^ 1];
     const R gx = pick<R>(s.f_gx, s.gx), gy = pick<R>(s.f_gy, s.gy);
@@ -463,7 +492,14 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
             yg[g] = div_nx(s, kg[g]);
             xg[g] = kg[g] - yg[g] * nx;
             keep[g] = kg[g] < N ? 0xFu : 0u;
-            if (BULK && t.np && keep[g]) keep[g] = outside_near_boxes4(s, b.nbox + t.p0, t.np, cur, xg[g], yg[g]);
+            if (BULK && boxes && keep[g]) keep[g] = outside_near_boxes4(s, b.nbox + t.p0, t.np, cur, xg[g], yg[g]);
+#ifdef LBIB_DEBUG
+            // the debug build checks the tile counts: a node of a near box in
+            // a tile counted free of them is a bookkeeping error
+            if (BULK && !boxes && t.np && keep[g] &&
+                outside_near_boxes4(s, b.nbox + t.p0, t.np, cur, xg[g], yg[g]) != 0xFu)
+                atomicOr(s.err, ERR_BOUNDS);
+#endif
         }
 #pragma unroll
         for (int g = 0; g < GROUPS; ++g) {
@@ -632,7 +668,11 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         skip[j] = k0 + j * THREADS >= N;
-        if (BULK && !skip[j] && t.np) skip[j] = in_near_box(s, b.nbox + t.p0, t.np, cur, xs[j], ys[j]);
+        if (BULK && !skip[j] && boxes) skip[j] = in_near_box(s, b.nbox + t.p0, t.np, cur, xs[j], ys[j]);
+#ifdef LBIB_DEBUG
+        if (BULK && !skip[j] && !boxes && t.np && in_near_box(s, b.nbox + t.p0, t.np, cur, xs[j], ys[j]))
+            atomicOr(s.err, ERR_BOUNDS);
+#endif
     }
 #pragma unroll
     for (int j = 0; j < NPT; ++j)
@@ -672,13 +712,25 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
     const int cur = *s.cur ^ flip;
     const int NB = P->NB, ox = P->box_ox[cur], oy = P->box_oy[cur];
     const int t0 = __ldg(b.near_tile0 + pi);
-    if (tile == t0 && threadIdx.x == 0) {
+    if (tile == t0 && threadIdx.x < 32) {
+        // warp 0 of the particle's first CTA: move the box's count from the
+        // tiles of the box it replaces in slot cur ^ 1 to those of the new one
+        // (no bulk pass reads that slot before this grid ends), then publish
         const int px = P->pend_ox, py = P->pend_oy;
-        P->box_ox[cur ^ 1] = px;
-        P->box_oy[cur ^ 1] = py;
-        // and into the batch's copy read by the bulk pass
         NearBox &q = b.nbox[pi];
-        if (cur ^ 1) { q.ox1 = px; q.oy1 = py; } else { q.ox0 = px; q.oy0 = py; }
+        const int old_oy = (cur ^ 1) ? q.oy1 : q.oy0;
+        const unsigned one = 1u << (16 * (cur ^ 1));
+        for_box_tiles(s, old_oy, NB, (int)threadIdx.x, 32,
+                      [&](int t) { atomicSub(b.tile_boxes + t, one); });
+        for_box_tiles(s, py, NB, (int)threadIdx.x, 32,
+                      [&](int t) { atomicAdd(b.tile_boxes + t, one); });
+        __syncwarp();
+        if (threadIdx.x == 0) {
+            P->box_ox[cur ^ 1] = px;
+            P->box_oy[cur ^ 1] = py;
+            // and into the batch's copy read by the bulk pass
+            if (cur ^ 1) { q.ox1 = px; q.oy1 = py; } else { q.ox0 = px; q.oy0 = py; }
+        }
     }
     const int nx = s.nx, ny = s.ny, N = nx * ny;
     const S *__restrict__ src = (const S *)s.pop[cur];
@@ -854,10 +906,12 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     constexpr int H = tma_margin<S>(), W = tma_width<S>();
     constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const TileDev t = b.tiles[tile];
+    const unsigned tboxes = t.np ? b.tile_boxes[tile] : 0u;
     const SimDev &s = b.sims[t.sim];
     const int nx = s.nx, ny = s.ny, N = nx * ny;
     if (!dry && t.k0 == 0 && threadIdx.x == 0) *s.step += 1;
     const int cur = b.par[t.sim] ^ flip;
+    const bool boxes = ((tboxes >> (16 * cur)) & 0xFFFFu) != 0;
     const S *__restrict__ src = (const S *)s.pop[cur];
     S *__restrict__ dst = (S *)s.pop[cur ^ 1];
     const int k0 = t.k0;
@@ -865,7 +919,11 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
     const int kt = k0 + 4 * (int)threadIdx.x;
     const int y = div_nx(s, kt), x0 = kt - y * nx;
     unsigned keep = kt < N ? 0xFu : 0u;
-    if (t.np && keep) keep = outside_near_boxes4(s, b.nbox + t.p0, t.np, cur, x0, y);
+    if (boxes && keep) keep = outside_near_boxes4(s, b.nbox + t.p0, t.np, cur, x0, y);
+#ifdef LBIB_DEBUG
+    if (!boxes && t.np && keep && outside_near_boxes4(s, b.nbox + t.p0, t.np, cur, x0, y) != 0xFu)
+        atomicOr(s.err, ERR_BOUNDS);
+#endif
     const bool wall = y == 0 || y == ny - 1;
     const bool global_pull = wall || x0 == 0 || x0 + 4 == nx;
     // 16-bit storage: the group collides in the scaled form (collide_node)
@@ -1120,6 +1178,7 @@ __global__ void flip_kernel(int *const *curs, int *par, int n) {
 // The batch's copies of its members' parity words and near boxes.
 __global__ void batch_refresh_kernel(BatchDev b, int *const *curs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < b.total_tiles) b.tile_boxes[i] = 0u;
     if (i < b.nsims) b.par[i] = *curs[i];
     if (i < b.nparts) {
         const ParticleDev *P = b.parts[i];
@@ -1132,6 +1191,17 @@ __global__ void batch_refresh_kernel(BatchDev b, int *const *curs) {
         q.pad[0] = q.pad[1] = q.pad[2] = 0;
         b.nbox[i] = q;
     }
+}
+
+// The per-tile near-box counts of both slots (one warp per particle), after
+// batch_refresh_kernel.
+__global__ void tile_boxes_kernel(BatchDev b) {
+    const int p = blockIdx.x;
+    const SimDev &s = b.sims[b.part_sim[p]];
+    const NearBox q = b.nbox[p];
+    const int lane = (int)threadIdx.x;
+    for_box_tiles(s, q.oy0, q.NB, lane, 32, [&](int t) { atomicAdd(b.tile_boxes + t, 1u); });
+    for_box_tiles(s, q.oy1, q.NB, lane, 32, [&](int t) { atomicAdd(b.tile_boxes + t, 1u << 16); });
 }
 
 template <typename F>
@@ -1279,9 +1349,10 @@ cudaError_t launch_flip(int *const *curs, int *par, int n, cudaStream_t st) {
 }
 
 cudaError_t launch_batch_refresh(const BatchDev &b, int *const *curs, cudaStream_t st) {
-    const int n = b.nsims > b.nparts ? b.nsims : b.nparts;
+    const int n = max(b.total_tiles, max(b.nsims, b.nparts));
     if (n == 0) return cudaSuccess;
     batch_refresh_kernel<<<(n + 127) / 128, 128, 0, st>>>(b, curs);
+    if (b.nparts > 0) tile_boxes_kernel<<<b.nparts, 32, 0, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,21 @@ def main(out):
         b.synchronize()
         res[f"body_{st}_pop"] = s.populations()
         b.close()
+    # a particle carried across work tiles and around the periodic y
+    # boundary (the debug build checks the bulk pass's near-box counts)
+    for st in ("f32", "f16"):
+        cfg = dict(nx=96, ny=64, wall_bottom="periodic", wall_top="periodic", tau=0.8, gy=2e-4,
+                   hamaker=0.0, seed=3, sim_id=0)
+        vx, vy = W.circle_polygon(6.0, 40)
+        s = L.Sim(storage=st, **cfg)
+        s.add_particle(vx=vx, vy=vy, xc=40.0, yc=50.0, theta=0.0, rho_p=1.0,
+                       ligand_density=0.0, sigma=0.02)
+        b = L.Batch([s])
+        b.step(400)
+        b.synchronize()
+        res[f"rise_{st}_pop"] = s.populations()
+        res[f"rise_{st}_y"] = np.array([s.particle(0)["yc"]])
+        b.close()
     # copy-engine staging variants of the bulk pass (single stage, pipeline)
     for v in (4, 5):
         for st in ("f32", "f16"):

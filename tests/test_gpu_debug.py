@@ -2,9 +2,11 @@
 population index of the lattice and particle passes is checked against its
 buffer and a failed check is reported as LBIB_E_BOUNDS.  The same cases --
 FP32, FP16 and FP64 batches with particles and bonds (bulk, near-box and
-particle passes), a body-force channel in 16-bit storage, and the
-copy-engine variants of the bulk pass -- run under the debug and the release
-build in fresh processes: no check fails, and the results are the same bits.
+particle passes), a body-force channel in 16-bit storage, a particle carried
+across work tiles and around a periodic boundary (the debug build checks the
+bulk pass's per-tile near-box counts), and the copy-engine variants of the
+bulk pass -- run under the debug and the release build in fresh processes:
+no check fails, and the results are the same bits.
 The debug build collides every node on its own, the release build the bulk
 nodes of 16-bit storage two at a time in paired FP32 instructions, so the
 comparison also checks that the pairs give each node its own bits."""

@@ -154,6 +154,34 @@ def test_full_step_parity_f64_with_bonds(O, L):
     assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) < 1e-11
 
 
+def test_moving_near_box_parity_f64(O, L):
+    """A particle carried across the lattice's work tiles and around the
+    periodic y boundary (a fully periodic box whose fluid the body force
+    accelerates in y): the bulk pass skips the near box through per-tile
+    counts that the near-box pass moves with the box every step, so a count
+    left behind would let the bulk pass overwrite a near-box node.  FP64
+    storage against the oracle to rounding after 400 steps, the particle
+    having risen across more than one tile's rows."""
+    nx, ny = 96, 64
+    cfg = dict(nx=nx, ny=ny, wall_bottom="periodic", wall_top="periodic", tau=0.8, gy=2e-4,
+               hamaker=0.0, seed=3, sim_id=0)
+    vx, vy = W.circle_polygon(6.0, 40)
+    p = dict(vx=vx, vy=vy, xc=40.0, yc=ny - 14.0, theta=0.0, rho_p=1.0, ligand_density=0.0,
+             sigma=0.02)
+    o, g = pair(O, L, cfg, [p])
+    y0 = g.particle(0)["yc"]
+    o.step(400)
+    g.step(400)
+    po, pg = o.particle(0), g.particle(0)
+    rise = pg["yc"] - y0
+    assert rise > 1024 / nx + 1, f"the particle rose only {rise:.2f} rows"
+    for k in ("xc", "yc", "theta", "u", "v", "omega"):
+        assert pg[k] == pytest.approx(po[k], abs=1e-10), k
+    ro, uo, vo = o.fields()
+    rg, ug, vg = g.fields()
+    assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) < 1e-11
+
+
 def test_catch_bond_parity_f64(O, L):
     """Catch bonds (sigma* = 2 sigma in Eq. 11: a stretched bond breaks less
     often): bond states bit for bit with the oracle at every step, and the
