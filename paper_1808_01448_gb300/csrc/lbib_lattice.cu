@@ -700,16 +700,18 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
     const int tile = blockIdx.x;
     const int pi = __ldg(b.near_part + tile);
     ParticleDev *P = b.parts[pi];
-    const SimDev &s = b.sims[b.part_sim[pi]];
+    const int si = b.part_sim[pi];
+    const SimDev &s = b.sims[si];
+    // the batch's copy of the parity word changes only between batched calls
+    const int cur = b.par[si] ^ flip;
     // when launched as a programmatic dependent of the particle pass before
     // it, wait for that pass here: it wrote the force tiles and the next box
-    // (everything read above is fixed for the batch)
+    // (everything read above is fixed for the call)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     // then let the particle pass that follows start its prologue (which
     // reads what the particle pass before wrote); it waits for this grid to
     // complete before reading the populations
     asm volatile("griddepcontrol.launch_dependents;");
-    const int cur = *s.cur ^ flip;
     const int NB = P->NB, ox = P->box_ox[cur], oy = P->box_oy[cur];
     const int t0 = __ldg(b.near_tile0 + pi);
     if (tile == t0 && threadIdx.x < 32) {
