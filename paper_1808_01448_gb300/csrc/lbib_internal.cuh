@@ -554,8 +554,8 @@ __device__ __forceinline__ void tile_force(const SimDev &s, ParticleDev *const *
 // Launchers (defined in the .cu files), one instantiation per storage kind.
 // mode: 0 every node; 1 bulk (nodes outside the near boxes); 2 near boxes only.
 // flip bit 1 marks a timing run of modes 0 / 1 (step counters untouched).
-// pdl (mode 2): launched as a programmatic dependent of the particle pass
-// before it on st
+// pdl: launched as a programmatic dependent of the kernel before it on st
+// (mode 1: the bulk pass of the step before; mode 2: the particle pass)
 cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cudaStream_t st,
                            bool pdl = false);
 // mode: 0 overlapped step, 1 init (IB forcing at the current pose), 2 step

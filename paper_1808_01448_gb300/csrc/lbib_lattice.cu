@@ -467,13 +467,21 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
     const bool dry = (flip & 2) != 0;
     flip &= 1;
     const int tile = blockIdx.x;
+    // the next step's bulk pass, a programmatic dependent of this one, may
+    // start its CTAs once every CTA of this grid has started
+    asm volatile("griddepcontrol.launch_dependents;");
     const TileDev t = b.tiles[tile];
-    const unsigned tboxes = BULK && t.np ? b.tile_boxes[tile] : 0u;
     const SimDev &s = b.sims[t.sim];
     const int nx = s.nx;
     const int N = nx * s.ny;
-    if (!dry && t.k0 == 0 && threadIdx.x == 0) *s.step += 1;
     const int cur = b.par[t.sim] ^ flip;
+    // the above is fixed for the batched call; when launched as a
+    // programmatic dependent of the step before, wait for its grids here,
+    // before reading what they wrote (populations, box counts and boxes,
+    // the step counter)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const unsigned tboxes = BULK && t.np ? b.tile_boxes[tile] : 0u;
+    if (!dry && t.k0 == 0 && threadIdx.x == 0) *s.step += 1;
     // a near box reaches this tile in this step's slot
     const bool boxes = ((tboxes >> (16 * cur)) & 0xFFFFu) != 0;
     const S *__restrict__ src = (const S *)s.pop[cur];
@@ -1012,6 +1020,8 @@ __device__ __forceinline__ bool tma_tile(const BatchDev &b, int flip, bool dry, 
 template <typename S, typename R, int MINB, int TILES>
 __global__ void __launch_bounds__(256, MINB) lattice_tma_kernel(BatchDev b, int flip) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    // (as a programmatic dependent: wait for the step before)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const bool dry = (flip & 2) != 0;
     flip &= 1;
     auto stage = [&](int t) { return (S *)(smem_raw + t * (tma_stage_bytes<S>() + 16)); };
@@ -1069,6 +1079,8 @@ template <typename S, typename R>
 __global__ void __launch_bounds__(PIPE_THREADS, 2) lattice_pipe_kernel(BatchDev b, int flip) {
     constexpr int STAGES = pipe_stages<S>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    // (as a programmatic dependent: wait for the step before)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const bool dry = (flip & 2) != 0;
     flip &= 1;
     auto stage = [&](int t) { return (S *)(smem_raw + t * tma_stage_bytes<S>()); };
@@ -1221,53 +1233,70 @@ cudaError_t by_kind(int kind, F &&f) {
 
 // Bulk-pass variants (threads, groups of four nodes per thread, minimum
 // resident CTAs per SM); FP64 storage and the plain pass use variant 0.
+// A lattice-pass kernel launch; pdl: as a programmatic dependent of the
+// previous kernel on st.
+cudaError_t launch_pass(void (*k)(BatchDev, int), unsigned grid, unsigned block, size_t smem,
+                        cudaStream_t st, bool pdl, const BatchDev &b, int flip) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, b, flip);
+}
+
 template <typename S, typename R, bool BULK>
-cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_t st) {
+cudaError_t launch_variant(int variant, const BatchDev &b, int flip, cudaStream_t st,
+                           bool pdl = false) {
     constexpr bool TUNED = BULK && sizeof(S) <= 4;
     if (b.any_aa) {
         // a member streams in place: the form with the in-place vector path
         // (its extra code costs the other forms registers, so it is apart)
-        lattice_kernel<S, R, BULK, 256, 1, sizeof(S) == 8 ? 1 : 4, true><<<b.total_tiles, 256, 0, st>>>(b, flip);
-        return cudaGetLastError();
+        return launch_pass(lattice_kernel<S, R, BULK, 256, 1, sizeof(S) == 8 ? 1 : 4, true>,
+                           b.total_tiles, 256, 0, st, pdl, b, flip);
     }
     if (!TUNED) variant = 0;
     if (variant >= 4 && !b.tma_ok) variant = 1;     // lattices unsuited to staging
     switch (variant) {
         case 4:
             if constexpr (TUNED) {
-                lattice_tma_kernel<S, R, 4, 1>
-                    <<<b.total_tiles, 256, tma_smem_bytes<S, 1>(), st>>>(b, flip);
-                break;
+                return launch_pass(lattice_tma_kernel<S, R, 4, 1>, b.total_tiles, 256,
+                                   tma_smem_bytes<S, 1>(), st, pdl, b, flip);
             }
             [[fallthrough]];
         case 5:
             if constexpr (TUNED) {
-                lattice_pipe_kernel<S, R>
-                    <<<(b.total_tiles + PIPE_TILES - 1) / PIPE_TILES, PIPE_THREADS,
-                       pipe_smem_bytes<S>(), st>>>(b, flip);
-                break;
+                return launch_pass(lattice_pipe_kernel<S, R>,
+                                   (b.total_tiles + PIPE_TILES - 1) / PIPE_TILES, PIPE_THREADS,
+                                   pipe_smem_bytes<S>(), st, pdl, b, flip);
             }
             [[fallthrough]];
         case 1:
             if constexpr (TUNED) {
-                lattice_kernel<S, R, BULK, 256, 1, 4><<<b.total_tiles, 256, 0, st>>>(b, flip);
-                break;
+                return launch_pass(lattice_kernel<S, R, BULK, 256, 1, 4>, b.total_tiles, 256, 0, st,
+                                   pdl, b, flip);
             }
             [[fallthrough]];
         case 2:
             if constexpr (TUNED) {
-                lattice_kernel<S, R, BULK, 256, 1, 5><<<b.total_tiles, 256, 0, st>>>(b, flip);
-                break;
+                return launch_pass(lattice_kernel<S, R, BULK, 256, 1, 5>, b.total_tiles, 256, 0, st,
+                                   pdl, b, flip);
             }
             [[fallthrough]];
         case 3:
             if constexpr (TUNED) {
-                lattice_kernel<S, R, BULK, 256, 1, 6><<<b.total_tiles, 256, 0, st>>>(b, flip);
-                break;
+                return launch_pass(lattice_kernel<S, R, BULK, 256, 1, 6>, b.total_tiles, 256, 0, st,
+                                   pdl, b, flip);
             }
             [[fallthrough]];
         default:
-            lattice_kernel<S, R, BULK, 256, 1, 1><<<b.total_tiles, 256, 0, st>>>(b, flip);
+            return launch_pass(lattice_kernel<S, R, BULK, 256, 1, 1>, b.total_tiles, 256, 0, st, pdl,
+                               b, flip);
     }
     return cudaGetLastError();
 }
@@ -1290,7 +1319,7 @@ cudaError_t launch_lattice(int kind, const BatchDev &b, int flip, int mode, cuda
         using S = decltype(sv);
         using R = decltype(rv);
         if (mode == 0) return launch_variant<S, R, false>(b.lat_variant, b, flip, st);
-        if (mode == 1) return launch_variant<S, R, true>(b.lat_variant, b, flip, st);
+        if (mode == 1) return launch_variant<S, R, true>(b.lat_variant, b, flip, st, pdl);
         if (b.total_near_tiles == 0) return cudaSuccess;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(b.total_near_tiles);
