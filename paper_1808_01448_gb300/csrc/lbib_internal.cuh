@@ -168,10 +168,11 @@ struct NearBox {
 // from the members before every batched call, the parity flip updates both
 // copies, and the near-box pass publishes each new box into both.  Most tiles
 // meet no near box: per tile and box slot, tile_boxes counts the near boxes
-// whose rows (whole rows, so a superset of the box) reach into the tile, and
-// a tile whose count is zero skips the near-box test altogether.  The counts
-// are rebuilt with the copies and kept by the near-box pass, which moves a
-// box's count from its old tiles to its new ones when it publishes it.
+// that reach into the tile (through their whole rows where a row is at most
+// a tile, through their spans of each row on wider lattices), and a tile
+// whose count is zero skips the near-box test altogether.  The counts are
+// rebuilt with the copies and kept by the near-box pass, which moves a box's
+// counts from its old tiles to its new ones when it publishes it.
 struct BatchDev {
     SimDev *sims;
     ParticleDev **parts;

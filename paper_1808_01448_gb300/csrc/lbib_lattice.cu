@@ -420,29 +420,58 @@ __device__ __forceinline__ unsigned outside_near_boxes4(const SimDev &s, const N
     return keep;
 }
 
-// Calls f(tile) for each batch lattice tile holding a node of the rows of a
-// near box with lower edge oy and edge NB (rows wrapped for a periodic y,
-// clipped to the lattice between walls); lanes lane, lane + nlanes, ... of
-// the caller share the tiles.  Whole rows: a superset of the box's tiles.
+// Calls f(tile) for each batch lattice tile holding a node of the near box
+// [ox, ox + NB) x [oy, oy + NB) (x wrapped; rows wrapped for a periodic y,
+// clipped to the lattice between walls), possibly more than once; lanes
+// lane, lane + nlanes, ... of the caller share the calls.  Rows of at most a
+// tile: every tile holding a node of the box's rows (a superset); wider rows:
+// per row, the tiles of the box's span of it.
 template <class F>
-__device__ __forceinline__ void for_box_tiles(const SimDev &s, int oy, int NB, int lane,
+__device__ __forceinline__ void for_box_tiles(const SimDev &s, int ox, int oy, int NB, int lane,
                                               int nlanes, F &&f) {
     auto rows = [&](int r0, int r1) {
         const int a = s.tile0 + (int)(((long long)r0 * s.nx) / LB_TILE_NODES);
         const int e = s.tile0 + (int)(((long long)(r1 + 1) * s.nx - 1) / LB_TILE_NODES);
         for (int t = a + lane; t <= e; t += nlanes) f(t);
     };
+    const bool periodic = s.wall_b == LBIB_WALL_PERIODIC;
     const int last = oy + NB - 1;
-    if (s.wall_b == LBIB_WALL_PERIODIC) {
-        if (last < s.ny) {
-            rows(oy, last);
+    if (s.nx <= LB_TILE_NODES) {
+        if (periodic) {
+            if (last < s.ny) {
+                rows(oy, last);
+            } else {
+                rows(oy, s.ny - 1);
+                rows(0, min(last - s.ny, s.ny - 1));
+            }
         } else {
-            rows(oy, s.ny - 1);
-            rows(0, min(last - s.ny, s.ny - 1));
+            const int r0 = max(oy, 0), r1 = min(last, s.ny - 1);
+            if (r0 <= r1) rows(r0, r1);
         }
-    } else {
-        const int r0 = max(oy, 0), r1 = min(last, s.ny - 1);
-        if (r0 <= r1) rows(r0, r1);
+        return;
+    }
+    const int w = min(NB, s.nx);
+    ox %= s.nx;
+    if (ox < 0) ox += s.nx;
+    auto span = [&](long long a, long long e) {   // lattice nodes a .. e
+        for (int t = (int)(a / LB_TILE_NODES); t <= (int)(e / LB_TILE_NODES); ++t) f(s.tile0 + t);
+    };
+    const int nr = periodic ? min(NB, s.ny) : NB;
+    for (int r = lane; r < nr; r += nlanes) {
+        int y = oy + r;
+        if (periodic) {
+            y %= s.ny;
+            if (y < 0) y += s.ny;
+        } else if (y < 0 || y >= s.ny) {
+            continue;
+        }
+        const long long row = (long long)y * s.nx;
+        if (ox + w <= s.nx) {
+            span(row + ox, row + ox + w - 1);
+        } else {
+            span(row + ox, row + s.nx - 1);
+            span(row, row + ox + w - 1 - s.nx);
+        }
     }
 }
 
@@ -728,11 +757,11 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
         // (no bulk pass reads that slot before this grid ends), then publish
         const int px = P->pend_ox, py = P->pend_oy;
         NearBox &q = b.nbox[pi];
-        const int old_oy = (cur ^ 1) ? q.oy1 : q.oy0;
+        const int old_ox = (cur ^ 1) ? q.ox1 : q.ox0, old_oy = (cur ^ 1) ? q.oy1 : q.oy0;
         const unsigned one = 1u << (16 * (cur ^ 1));
-        for_box_tiles(s, old_oy, NB, (int)threadIdx.x, 32,
+        for_box_tiles(s, old_ox, old_oy, NB, (int)threadIdx.x, 32,
                       [&](int t) { atomicSub(b.tile_boxes + t, one); });
-        for_box_tiles(s, py, NB, (int)threadIdx.x, 32,
+        for_box_tiles(s, px, py, NB, (int)threadIdx.x, 32,
                       [&](int t) { atomicAdd(b.tile_boxes + t, one); });
         __syncwarp();
         if (threadIdx.x == 0) {
@@ -1214,8 +1243,9 @@ __global__ void tile_boxes_kernel(BatchDev b) {
     const SimDev &s = b.sims[b.part_sim[p]];
     const NearBox q = b.nbox[p];
     const int lane = (int)threadIdx.x;
-    for_box_tiles(s, q.oy0, q.NB, lane, 32, [&](int t) { atomicAdd(b.tile_boxes + t, 1u); });
-    for_box_tiles(s, q.oy1, q.NB, lane, 32, [&](int t) { atomicAdd(b.tile_boxes + t, 1u << 16); });
+    for_box_tiles(s, q.ox0, q.oy0, q.NB, lane, 32, [&](int t) { atomicAdd(b.tile_boxes + t, 1u); });
+    for_box_tiles(s, q.ox1, q.oy1, q.NB, lane, 32,
+                  [&](int t) { atomicAdd(b.tile_boxes + t, 1u << 16); });
 }
 
 template <typename F>

@@ -57,11 +57,18 @@ def main(out):
         s = L.Sim(storage=st, **cfg)
         s.add_particle(vx=vx, vy=vy, xc=40.0, yc=50.0, theta=0.0, rho_p=1.0,
                        ligand_density=0.0, sigma=0.02)
-        b = L.Batch([s])
+        # a lattice with rows wider than a tile, the box across the x edge
+        cfg2 = dict(cfg, nx=2048, ny=48, sim_id=1)
+        s2 = L.Sim(storage=st, **cfg2)
+        s2.add_particle(vx=vx, vy=vy, xc=2044.0, yc=30.0, theta=0.0, rho_p=1.0,
+                        ligand_density=0.0, sigma=0.02)
+        b = L.Batch([s, s2])
         b.step(400)
         b.synchronize()
         res[f"rise_{st}_pop"] = s.populations()
         res[f"rise_{st}_y"] = np.array([s.particle(0)["yc"]])
+        res[f"rise2_{st}_pop"] = s2.populations()
+        res[f"rise2_{st}_y"] = np.array([s2.particle(0)["yc"], s2.particle(0)["xc"]])
         b.close()
     # copy-engine staging variants of the bulk pass (single stage, pipeline)
     for v in (4, 5):
