@@ -527,10 +527,15 @@ __device__ __forceinline__ void node_moments(const R d[9], R &drho, R &jx, R &jy
     jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
 }
 
-// Edge of the near box: the force tile plus four nodes a side.  It contains
+// Core of the near box: the force tile plus four nodes a side.  It contains
 // the force tile and the staged region (plus its pull halo) of the next
 // particle pass for any motion below one node per step.
-__host__ __device__ __forceinline__ int near_edge(int T) { return T + 8; }
+__host__ __device__ __forceinline__ int near_core(int T) { return T + 8; }
+// Edge of the near box: the core widened by three nodes and rounded up to a
+// multiple of four, so that the box can start on a multiple of four in x
+// (the bulk pass's groups of four nodes then lie wholly inside a box or
+// wholly outside it) and still contain the core.
+__host__ __device__ __forceinline__ int near_edge(int T) { return (near_core(T) + 6) & ~3; }
 
 // Force-tile lookup: IB force density at (x, y) summed over the simulation's
 // particles whose tile covers the node.

@@ -1267,10 +1267,13 @@ __global__ void __launch_bounds__(PT, PT == 256 ? 4 : 1) particle_kernel(BatchDe
         }
         P->tile_ox = oxw;
         P->tile_oy = oyw;
-        // near box of the lattice step after next, around the new pose
-        int bx = (ps.ixc - Pc.NB / 2) % s.nx;
+        // near box of the lattice step after next: its core centred on the
+        // new pose, the box's x origin rounded down to a multiple of four
+        const int half = near_core(Pc.T) / 2;
+        int bx = (ps.ixc - half) % s.nx;
         if (bx < 0) bx += s.nx;
-        int by = ps.iyc - Pc.NB / 2;
+        bx &= ~3;
+        int by = ps.iyc - half;
         if (s.wall_b == LBIB_WALL_PERIODIC) {
             by %= s.ny;
             if (by < 0) by += s.ny;
