@@ -334,7 +334,7 @@ lbib_status lbib_batch_set_variant(lbib_batch *b, int32_t variant);
 
 /* Nodes each lattice pass of the next step updates, at the particles'
  * current near boxes: nodes[0] the lattice (bulk) pass, nodes[1] the
- * near-box pass (NB x NB per particle, rows outside the lattice left out; 0
+ * near-box pass (NBx x NBy per particle, rows outside the lattice left out; 0
  * when not overlapped), nodes[2] all nodes of the members.  For the
  * algorithmic bytes of the timed passes.  Synchronises the stream and reads
  * the particle structs back (a few hundred bytes per particle). */

@@ -509,7 +509,7 @@ lbib_status upload_particle(lbib_sim *s, HostParticle &p) {
     h.nl = n; h.n_ligands = p.n_ligands; h.fixed = p.fixed; h.T = p.T; h.ncolors = p.ncolors;
     h.tile_ox = 0; h.tile_oy = -(1 << 28);   // no tile until the first IB pass
     h.gap[0] = h.gap[1] = INFINITY;          // no bond step yet
-    h.NB = near_edge(p.T); h.step = 0;
+    h.NBx = near_edge_x(p.T); h.NBy = near_edge_y(p.T); h.step = 0;
     h.vb_p = p.vb_p;
     h.mbx = mbx; h.mby = mby; h.nbx = nbx; h.nby = nby; h.S = S;
     h.ligand = lig; h.color_order = co; h.color_off = coff;
@@ -605,9 +605,9 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
         tiles += (int)((s->N + LB_TILE_NODES - 1) / LB_TILE_NODES);
         for (auto &p : s->parts) {
             smem = std::max(smem, particle_smem_bytes(b->kind, p.T, p.nl, s->cfg.ib_spread != 0));
-            const int NB = near_edge(p.T);
-            near_tiles += (NB * NB + NEAR_TILE_NODES - 1) / NEAR_TILE_NODES;
-            if (NB > s->cfg.nx || (s->cfg.wall_bottom == LBIB_WALL_PERIODIC && NB > s->cfg.ny))
+            const int NBx = near_edge_x(p.T), NBy = near_edge_y(p.T);
+            near_tiles += (NBx * NBy + NEAR_TILE_NODES - 1) / NEAR_TILE_NODES;
+            if (NBx > s->cfg.nx || (s->cfg.wall_bottom == LBIB_WALL_PERIODIC && NBy > s->cfg.ny))
                 boxes_fit = false;
         }
     }
@@ -665,9 +665,9 @@ lbib_status make_batch(lbib_sim *const *sims, int n, lbib_batch **out) {
     std::vector<int> hnp, hnt0;
     for (int i = 0; i < n; ++i)
         for (auto &p : sims[i]->parts) {
-            const int NB = near_edge(p.T);
+            const int NBx = near_edge_x(p.T), NBy = near_edge_y(p.T);
             hnt0.push_back((int)hnp.size());
-            for (int t = 0; t < (NB * NB + NEAR_TILE_NODES - 1) / NEAR_TILE_NODES; ++t)
+            for (int t = 0; t < (NBx * NBy + NEAR_TILE_NODES - 1) / NEAR_TILE_NODES; ++t)
                 hnp.push_back((int)hnt0.size() - 1);
         }
     hnp.push_back(0);
@@ -1653,12 +1653,12 @@ lbib_status lbib_batch_pass_nodes(lbib_batch *b, int64_t *nodes) {
         for (const HostParticle &hp : s->parts) {
             ParticleDev P;
             CK(cudaMemcpy(&P, hp.d_part, sizeof(P), cudaMemcpyDeviceToHost));
-            for (int by = 0; by < P.NB; ++by) {
+            for (int by = 0; by < P.NBy; ++by) {
                 int y = P.box_oy[cur] + by;
                 if (periodic) y = ((y % ny) + ny) % ny;
                 if (y < 0 || y >= ny) continue;
-                near += P.NB;   // one row of the box, as the near pass does it
-                for (int bx = 0; bx < P.NB; ++bx) {
+                near += P.NBx;   // one row of the box, as the near pass does it
+                for (int bx = 0; bx < P.NBx; ++bx) {
                     const int x = ((P.box_ox[cur] + bx) % nx + nx) % nx;
                     in_box[(size_t)y * nx + x] = 1;
                 }
@@ -2235,7 +2235,8 @@ extern "C" lbib_status lbib_ib_force_noalloc(const lbib_config *cfg, const float
     hp.inv_mass = 1.0 / hp.mass; hp.inv_inertia = 1.0 / hp.inertia;
     hp.r_eq = sqrt(area / M_PI); hp.sigma = in->sigma;
     hp.nl = nl; hp.n_ligands = n_ligands; hp.fixed = 1; hp.T = T; hp.ncolors = a.ncolors;
-    hp.NB = near_edge(T);
+    hp.NBx = near_edge_x(T);
+    hp.NBy = near_edge_y(T);
     hp.vb_p = vbp;
     hp.mbx = a.d_geo; hp.mby = a.d_geo + nl; hp.nbx = a.d_geo + 2 * nl; hp.nby = a.d_geo + 3 * nl;
     hp.S = a.d_geo + 4 * nl;

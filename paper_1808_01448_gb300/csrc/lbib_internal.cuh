@@ -104,11 +104,11 @@ struct ParticleDev {
     double gap[2];                      // smallest element gap to the bottom / top wall line
     int nl, n_ligands, n_probing, n_bonded;
     int fixed, T, ncolors, tile_ox;     // T: force-tile edge; tile origin x in [0, nx)
-    int tile_oy, NB, vb_p, pad2;        // NB: edge of the near box; vb_p: half
+    int tile_oy, NBx, vb_p, NBy;        // NBx, NBy: edges of the near box; vb_p: half
                                         // bandwidth of the spreading-scale system
     long long step;                     // completed steps of this particle (bond draws)
     // Near box of the lattice step that reads buffer parity p: nodes
-    // [box_ox[p], +NB) x [box_oy[p], +NB), x wrapped to [0, nx).  The particle
+    // [box_ox[p], +NBx) x [box_oy[p], +NBy), x wrapped to [0, nx).  The particle
     // kernel of step k leaves the box for step k + 2 in pend_ox / pend_oy; the
     // near lattice kernel of step k + 1 publishes it into the slot of step k + 2.
     int box_ox[2], box_oy[2];
@@ -158,7 +158,7 @@ struct TileDev {
 // them in one load round, independent of the parity.
 struct NearBox {
     int ox0, oy0, ox1, oy1;
-    int NB, pad[3];
+    int NBx, NBy, pad[2];
 };
 
 // The bulk pass reads its tile, the simulation's descriptor, its parity and
@@ -531,11 +531,12 @@ __device__ __forceinline__ void node_moments(const R d[9], R &drho, R &jx, R &jy
 // the force tile and the staged region (plus its pull halo) of the next
 // particle pass for any motion below one node per step.
 __host__ __device__ __forceinline__ int near_core(int T) { return T + 8; }
-// Edge of the near box: the core widened by three nodes and rounded up to a
-// multiple of four, so that the box can start on a multiple of four in x
+// Edges of the near box: in x the core widened by three nodes and rounded up
+// to a multiple of four, so that the box can start on a multiple of four
 // (the bulk pass's groups of four nodes then lie wholly inside a box or
-// wholly outside it) and still contain the core.
-__host__ __device__ __forceinline__ int near_edge(int T) { return (near_core(T) + 6) & ~3; }
+// wholly outside it) and still contain the core; in y the core.
+__host__ __device__ __forceinline__ int near_edge_x(int T) { return (near_core(T) + 6) & ~3; }
+__host__ __device__ __forceinline__ int near_edge_y(int T) { return near_core(T); }
 
 // Force-tile lookup: IB force density at (x, y) summed over the simulation's
 // particles whose tile covers the node.

@@ -377,11 +377,12 @@ __device__ __forceinline__ void pull_group(const SimDev &s, const S *__restrict_
 // from the batch's flat copy (both slots in one load, so the load does not
 // wait for the parity).
 struct BoxView {
-    int ox, oy, NB;
+    int ox, oy, NBx, NBy;
 };
 __device__ __forceinline__ BoxView near_box(const NearBox *nb, int slot) {
     const int4 o = *reinterpret_cast<const int4 *>(nb);
-    return BoxView{slot ? o.z : o.x, slot ? o.w : o.y, nb->NB};
+    const int2 e = *reinterpret_cast<const int2 *>(&nb->NBx);
+    return BoxView{slot ? o.z : o.x, slot ? o.w : o.y, e.x, e.y};
 }
 
 // Node (x, y) inside a near box of the simulation's particles (the batch's
@@ -394,7 +395,7 @@ __device__ __forceinline__ bool in_near_box(const SimDev &s, const NearBox *nb, 
         if (dx < 0) dx += s.nx;
         int dy = y - q.oy;
         if (dy < 0 && s.wall_b == LBIB_WALL_PERIODIC) dy += s.ny;
-        if (dx < q.NB && (unsigned)dy < (unsigned)q.NB) return true;
+        if (dx < q.NBx && (unsigned)dy < (unsigned)q.NBy) return true;
     }
     return false;
 }
@@ -407,35 +408,35 @@ __device__ __forceinline__ unsigned outside_near_boxes4(const SimDev &s, const N
         const BoxView q = near_box(nb + k, slot);
         int dy = y - q.oy;
         if (dy < 0 && s.wall_b == LBIB_WALL_PERIODIC) dy += s.ny;
-        if ((unsigned)dy >= (unsigned)q.NB) continue;
+        if ((unsigned)dy >= (unsigned)q.NBy) continue;
         int dx = x0 - q.ox;
         if (dx < 0) dx += s.nx;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int e = dx + j;
             if (e >= s.nx) e -= s.nx;
-            if (e < q.NB) keep &= ~(1u << j);
+            if (e < q.NBx) keep &= ~(1u << j);
         }
     }
     return keep;
 }
 
 // Calls f(tile) for each batch lattice tile holding a node of the near box
-// [ox, ox + NB) x [oy, oy + NB) (x wrapped; rows wrapped for a periodic y,
+// [ox, ox + NBx) x [oy, oy + NBy) (x wrapped; rows wrapped for a periodic y,
 // clipped to the lattice between walls), possibly more than once; lanes
 // lane, lane + nlanes, ... of the caller share the calls.  Rows of at most a
 // tile: every tile holding a node of the box's rows (a superset); wider rows:
 // per row, the tiles of the box's span of it.
 template <class F>
-__device__ __forceinline__ void for_box_tiles(const SimDev &s, int ox, int oy, int NB, int lane,
-                                              int nlanes, F &&f) {
+__device__ __forceinline__ void for_box_tiles(const SimDev &s, int ox, int oy, int NBx, int NBy,
+                                              int lane, int nlanes, F &&f) {
     auto rows = [&](int r0, int r1) {
         const int a = s.tile0 + (int)(((long long)r0 * s.nx) / LB_TILE_NODES);
         const int e = s.tile0 + (int)(((long long)(r1 + 1) * s.nx - 1) / LB_TILE_NODES);
         for (int t = a + lane; t <= e; t += nlanes) f(t);
     };
     const bool periodic = s.wall_b == LBIB_WALL_PERIODIC;
-    const int last = oy + NB - 1;
+    const int last = oy + NBy - 1;
     if (s.nx <= LB_TILE_NODES) {
         if (periodic) {
             if (last < s.ny) {
@@ -450,13 +451,13 @@ __device__ __forceinline__ void for_box_tiles(const SimDev &s, int ox, int oy, i
         }
         return;
     }
-    const int w = min(NB, s.nx);
+    const int w = min(NBx, s.nx);
     ox %= s.nx;
     if (ox < 0) ox += s.nx;
     auto span = [&](long long a, long long e) {   // lattice nodes a .. e
         for (int t = (int)(a / LB_TILE_NODES); t <= (int)(e / LB_TILE_NODES); ++t) f(s.tile0 + t);
     };
-    const int nr = periodic ? min(NB, s.ny) : NB;
+    const int nr = periodic ? min(NBy, s.ny) : NBy;
     for (int r = lane; r < nr; r += nlanes) {
         int y = oy + r;
         if (periodic) {
@@ -727,7 +728,7 @@ __global__ void __launch_bounds__(THREADS, MINB) lattice_kernel(BatchDev b, int 
     if (bad) atomicOr(s.err, ERR_UNSTABLE);
 }
 
-// The nodes of the near boxes (one box per particle; NB x NB nodes, rows
+// The nodes of the near boxes (one box per particle; NBx x NBy nodes, rows
 // outside the lattice skipped), with the IB force of every force tile of the
 // simulation.  Runs after the particle pass that wrote the tiles.  The first
 // CTA of each particle also publishes the box the last particle pass left for
@@ -749,7 +750,7 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
     // reads what the particle pass before wrote); it waits for this grid to
     // complete before reading the populations
     asm volatile("griddepcontrol.launch_dependents;");
-    const int NB = P->NB, ox = P->box_ox[cur], oy = P->box_oy[cur];
+    const int NBx = P->NBx, NBy = P->NBy, ox = P->box_ox[cur], oy = P->box_oy[cur];
     const int t0 = __ldg(b.near_tile0 + pi);
     if (tile == t0 && threadIdx.x < 32) {
         // warp 0 of the particle's first CTA: move the box's count from the
@@ -759,9 +760,9 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
         NearBox &q = b.nbox[pi];
         const int old_ox = (cur ^ 1) ? q.ox1 : q.ox0, old_oy = (cur ^ 1) ? q.oy1 : q.oy0;
         const unsigned one = 1u << (16 * (cur ^ 1));
-        for_box_tiles(s, old_ox, old_oy, NB, (int)threadIdx.x, 32,
+        for_box_tiles(s, old_ox, old_oy, NBx, NBy, (int)threadIdx.x, 32,
                       [&](int t) { atomicSub(b.tile_boxes + t, one); });
-        for_box_tiles(s, px, py, NB, (int)threadIdx.x, 32,
+        for_box_tiles(s, px, py, NBx, NBy, (int)threadIdx.x, 32,
                       [&](int t) { atomicAdd(b.tile_boxes + t, one); });
         __syncwarp();
         if (threadIdx.x == 0) {
@@ -781,7 +782,7 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
 #pragma unroll
     for (int j = 0; j < NEAR_NPT; ++j) {
         const int k = k0 + j * LB_THREADS;
-        const int by = k / NB, bx = k - by * NB;
+        const int by = k / NBx, bx = k - by * NBx;
         int x = ox + bx;
         if (x >= nx) x -= nx;
         int y = oy + by;
@@ -791,7 +792,7 @@ __global__ void __launch_bounds__(LB_THREADS) lattice_near_kernel(BatchDev b, in
         }
         xs[j] = x;
         ys[j] = y;
-        skip[j] = k >= NB * NB || y < 0 || y >= ny;
+        skip[j] = k >= NBx * NBy || y < 0 || y >= ny;
     }
     R d[NEAR_NPT][9];
 #pragma unroll
@@ -1230,8 +1231,9 @@ __global__ void batch_refresh_kernel(BatchDev b, int *const *curs) {
         q.oy0 = P->box_oy[0];
         q.ox1 = P->box_ox[1];
         q.oy1 = P->box_oy[1];
-        q.NB = P->NB;
-        q.pad[0] = q.pad[1] = q.pad[2] = 0;
+        q.NBx = P->NBx;
+        q.NBy = P->NBy;
+        q.pad[0] = q.pad[1] = 0;
         b.nbox[i] = q;
     }
 }
@@ -1243,8 +1245,9 @@ __global__ void tile_boxes_kernel(BatchDev b) {
     const SimDev &s = b.sims[b.part_sim[p]];
     const NearBox q = b.nbox[p];
     const int lane = (int)threadIdx.x;
-    for_box_tiles(s, q.ox0, q.oy0, q.NB, lane, 32, [&](int t) { atomicAdd(b.tile_boxes + t, 1u); });
-    for_box_tiles(s, q.ox1, q.oy1, q.NB, lane, 32,
+    for_box_tiles(s, q.ox0, q.oy0, q.NBx, q.NBy, lane, 32,
+                  [&](int t) { atomicAdd(b.tile_boxes + t, 1u); });
+    for_box_tiles(s, q.ox1, q.oy1, q.NBx, q.NBy, lane, 32,
                   [&](int t) { atomicAdd(b.tile_boxes + t, 1u << 16); });
 }
 
