@@ -228,7 +228,11 @@ lbib_status lbib_add_particle(lbib_sim *sim, const lbib_particle *p, int32_t *pi
 lbib_status lbib_set_receptors(lbib_sim *sim, int32_t wall, double density);
 
 /* Set the post-collision populations f*_i of "step -1" ([9][ny][nx], host,
- * full f, not deviations) before the first step.  Errors: E_STATE, E_CUDA. */
+ * full f, not deviations) before the first step.  Page-locked host memory
+ * the device can address is read in place by the import kernel; other host
+ * memory is copied through a device scratch of 72 bytes per node (kept for
+ * later reads).  Returns after the import (the buffer may be reused).
+ * Errors: E_STATE, E_CUDA, E_OOM (scratch). */
 lbib_status lbib_set_populations(lbib_sim *sim, const double *f_post_host);
 
 /* Enqueue nsteps time steps (weak coupling, Sec. "Fluid-structure

@@ -1299,11 +1299,27 @@ lbib_status lbib_set_populations(lbib_sim *s, const double *f) {
     if (!s || !f) return fail(LBIB_E_ARG, "null argument");
     lbib_status r = reopen_setup(s, "lbib_set_populations");
     if (r != LBIB_OK) return r;
-    r = ensure_scratch(s, 9 * s->N * sizeof(double));
-    if (r != LBIB_OK) return r;
-    CK(cudaMemcpyAsync(s->d_scratch, f, 9 * s->N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    // Page-locked host memory the device can address (cudaHostAlloc, a
+    // registered range) is read by the import kernel in place; any other
+    // source is copied into a device scratch first.  Either way the call
+    // returns after the import, so the caller may reuse f at once.
+    const double *src = nullptr;
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, f) == cudaSuccess) {
+        if (pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr)
+            src = (const double *)pa.devicePointer;
+    } else {
+        (void)cudaGetLastError();   // an unknown pointer: not an error of this call
+    }
+    if (!src) {
+        r = ensure_scratch(s, 9 * s->N * sizeof(double));
+        if (r != LBIB_OK) return r;
+        CK(cudaMemcpyAsync(s->d_scratch, f, 9 * s->N * sizeof(double), cudaMemcpyHostToDevice,
+                           s->stream));
+        src = s->d_scratch;
+    }
     SimDev d = make_simdev(s, 0, 0);
-    CK(launch_set_populations(s->kind, d, s->d_scratch, s->stream));
+    CK(launch_set_populations(s->kind, d, src, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return LBIB_OK;
 }

@@ -182,6 +182,27 @@ def test_moving_near_box_parity_f64(O, L):
     assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) < 1e-11
 
 
+def test_set_populations_from_page_locked_memory(O, L):
+    """The import reads page-locked host memory in place and any other host
+    memory through a device copy: the same state either way, before and
+    after stepping."""
+    import torch
+    cfg = dict(nx=64, ny=32, wall_bottom="bounce_back", wall_top="bounce_back", tau=0.8,
+               u_top=0.01, seed=2, sim_id=0)
+    f = random_start(O, 64, 32, 7)
+    pinned = torch.from_numpy(f.copy()).pin_memory()
+    a = L.Sim(storage="f32", **cfg)
+    b = L.Sim(storage="f32", **cfg)
+    a.set_populations(f)
+    b.set_populations(pinned.numpy())
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    a.step(10)
+    b.step(10)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    a.close()
+    b.close()
+
+
 def test_catch_bond_parity_f64(O, L):
     """Catch bonds (sigma* = 2 sigma in Eq. 11: a stretched bond breaks less
     often): bond states bit for bit with the oracle at every step, and the
